@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 trans_ev_tridi_to_band (back-transformation of
+eigenvectors from tridiagonal to band form, Kus et al. Sec. 2 / Sec. 3.1).
+
+One step = one call of gb_trans_ev_tridi_to_band_d on the whole workload:
+n = 16384, nev = 4096 eigenvectors (25%), band width nbw = 64, FP64 real,
+reflectors in the bulge-chase layout (seeded synthetic, see
+paper_1811_01277_gb300/inputs.py) and a seeded Z.  Inputs (Z 0.54 GB,
+reflectors 1.07 GB) are larger than the 129 MB L2, so no flush is needed.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs its own
+independent problem (weak scaling) and the time is the max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "n16384": dict(n=16384, nev=4096, nbw=64),
+    "n1024": dict(n=1024, nev=1024, nbw=32),
+}
+# FP64 DFMA: 2 lanes per clock per SM on GB300 (1.25 TFLOP/s nominal at the
+# 2070 MHz maximum SM clock over 152 SMs: 152 * 2 * 2 flop * 2.07e9).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP64_DFMA_MEASURED_TFLOPS = 1.19  # DFMA microbenchmark on this machine's GB300 (profiles/)
+
+
+def algorithmic_flops(n, nev, cplx=False):
+    """4 flops per reflector element and column (16 for complex); the
+    reflectors of a sweep s cover n-s rows, so sum len = n(n-1)/2."""
+    return (16 if cplx else 4) * nev * n * (n - 1) // 2
+
+
+def kernel_sources_sha1():
+    h = hashlib.sha1()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1811_01277_gb300", "csrc", "*.cu*"))):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profile_traffic(kernel, workload, variant, sha):
+    """DRAM bytes per step from a committed ncu summary, if it was taken on
+    the current kernel sources; None otherwise."""
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")) + glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        with open(p) as f:
+            for line in f:
+                if line.startswith("traffic:") and f"kernel={kernel}" in line and \
+                        f"workload={workload}" in line and f"variant={variant}" in line:
+                    kv = dict(x.split("=", 1) for x in line.split()[1:] if "=" in x)
+                    if kv.get("sha1") == sha:
+                        return float(kv["bytes_per_step"])
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(n, nev, nbw, hv, ht, Z, target_s=12.0):
+    """The oracle as it stands, on a bounded sample of the workload's columns
+    (columns are independent, so time scales linearly with the count)."""
+    import numpy as np
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cols = cores
+    t0 = time.perf_counter()
+    oracle.trans_ev(n, nbw, hv, ht, np.asfortranarray(Z[:, :cols]))
+    t1 = time.perf_counter() - t0
+    reps = max(1, int(target_s / max(t1, 1e-3)))
+    cols2 = min(nev, cols * reps)
+    t0 = time.perf_counter()
+    oracle.trans_ev(n, nbw, hv, ht, np.asfortranarray(Z[:, :cols2]))
+    t2 = time.perf_counter() - t0
+    return {"value": (cols2 / nev) / t2, "unit": "back-transforms/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cols2} of {nev} columns (n={n}, nbw={nbw}), {t2:.1f} s; "
+                      f"value scaled to the full nev (columns are independent)"}
+
+
+def run_reference(args, wl):
+    """The oracle (plain C, OpenMP over columns) on this host's cores."""
+    import numpy as np
+    from paper_1811_01277_gb300 import inputs
+    import oracle
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    n, nev, nbw = wl["n"], wl["nev"], wl["nbw"]
+    hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024)
+    Z = inputs.z_gaussian(n, nev, seed=2025)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cols = min(nev, cores)
+    Zs = np.asfortranarray(Z[:, :cols])
+    for _ in range(args.warmup):
+        oracle.trans_ev(n, nbw, hv, ht, Zs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.trans_ev(n, nbw, hv, ht, Zs)
+    el = time.perf_counter() - t0
+    value = args.steps * (cols / nev) / el
+    sample = f"each step {cols} of {nev} columns (n={n}, nbw={nbw}); value scaled to the full nev"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "back-transforms/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl), "variant": "oracle",
+        "cpu_baseline": {"value": value, "unit": "back-transforms/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "back-transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+METRIC = "trans_ev_tridi_to_band throughput at n=16384, nev=4096 (25% vecs), nbw=64 (1/value = solve s)"
+
+
+def config_of(wl):
+    n, nev, nbw = wl["n"], wl["nev"], wl["nbw"]
+    count = sum((n - s + nbw - 1) // nbw for s in range(1, n))
+    return {"workload": f"trans_ev_tridi_to_band n={n} nev={nev} nbw={nbw} real FP64",
+            "n": n, "nev": nev, "nbw": nbw,
+            "l2": "inputs larger than L2 (Z %.2f GB, reflectors %.2f GB); no flush" % (
+                8 * n * nev / 1e9, 8 * nbw * count / 1e9)}
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    from paper_1811_01277_gb300 import inputs
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbuild.build()
+    gb.load()
+    n, nev, nbw = wl["n"], wl["nev"], wl["nbw"]
+    opts = {"variant": args.variant, "sweeps_per_tile": args.nb, "cols_per_block": args.threads}
+    variant_name = {0: "auto", 1: "wavefront", 2: "pipeline"}[args.variant]
+
+    hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024 + 1000 * rank)
+    Z = inputs.z_gaussian(n, nev, seed=2025 + 1000 * rank)
+    hv_d = torch.from_numpy(hv).to(dev)
+    ht_d = torch.from_numpy(ht).to(dev)
+    Z_d = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)  # (nev, n) row-major = column-major Z
+    wsb = gb.gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts)
+    ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        gb.gb_trans_ev_tridi_to_band_d(n, nbw, nev, hv_d, ht_d, Z_d, n, ws, wsb, stream, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_index = vis.split(",")[local] if vis else str(local)
+    sampler = ClockSampler(smi_index) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    el_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    clocks = sampler.stop() if sampler else None
+    ms_per_step = el_ms / args.steps
+    value = world * args.steps / (el_ms / 1e3)
+    F = algorithmic_flops(n, nev)
+    achieved = F / (ms_per_step / 1e3) / 1e12
+    launches = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
+    sha = kernel_sources_sha1()
+    kernel = "wavefront_tile_d" if args.variant in (0, 1) else "pipeline_d"
+    traffic = profile_traffic(kernel, args.workload, variant_name, sha)
+
+    # end to end through the host-buffer entry point: H2D of reflectors and Z,
+    # the kernels, D2H of Z, per step
+    e2e = None
+    if not args.no_e2e:
+        hv_h = torch.from_numpy(hv).pin_memory()
+        ht_h = torch.from_numpy(ht).pin_memory()
+        Z_h = torch.from_numpy(np.ascontiguousarray(Z.T)).pin_memory()
+        bufb = gb.gb_trans_ev_host_buffer_bytes(n, nbw, nev, n, 0, opts)
+        buf = torch.empty(bufb, dtype=torch.uint8, device=dev)
+
+        def hstep():
+            gb.gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, hv_h, ht_h, Z_h, n, buf, bufb, stream, opts)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            hstep()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
+        h2d = hv.nbytes + ht.nbytes + Z.nbytes
+        e2e = {"value": world * args.steps / el, "unit": "back-transforms/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(Z.nbytes),
+               "api": "gb_trans_ev_tridi_to_band_d_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, nev, nbw, hv, ht, Z)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "back-transforms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl), "variant": variant_name,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "peak_source": "FP64 DFMA: 152 SMs x 2 lanes/clk x 2 flop x 2070 MHz "
+                                        f"(DFMA microbenchmark {FP64_DFMA_MEASURED_TFLOPS} TFLOP/s)",
+                         "kernel": kernel, "per": "step",
+                         "algorithmic_tflop_per_step": F / 1e12},
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches) * args.steps,
+            "clocks": clocks, "kernel_sources_sha1": sha,
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n16384")
+    ap.add_argument("--variant", type=int, default=1)
+    ap.add_argument("--nb", type=int, default=16)
+    ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

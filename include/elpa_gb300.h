@@ -1,0 +1,124 @@
+/*
+ * elpa_gb300 -- C ABI of the GB300 (sm_103a) back-transformation of
+ * eigenvectors from tridiagonal to band form (trans_ev_tridi_to_band).
+ *
+ * Operation (Kus et al., "Optimizations of the Eigensolvers in the ELPA
+ * Library", Sec. 2, two-stage paragraph and Eq. 6; Sec. 3.1, the
+ * non-BLAS kernel of the two-stage back transformation):
+ *
+ *     Z <- Q2 Z,   Q2 = H(1,0) H(1,1) ... H(1,nk(1)-1) H(2,0) ... H(n-1,0),
+ *
+ * where H(s,k) = I - tau(s,k) v(s,k) v(s,k)^H are the Householder reflectors
+ * that the band -> tridiagonal bulge chase emits (T = Q2^H B Q2), and Z holds
+ * nev eigenvectors of T.  The result holds the corresponding eigenvectors of
+ * the band matrix B.  Columns of Z are independent.
+ *
+ * Reflector storage layout (n = matrix order, b = nbw = band width, i.e. the
+ * number of super-diagonals of B; 1-based sweep s, 0-based block k):
+ *   - sweep s = 1..n-1 has nk(s) = ceil((n-s)/b) reflectors, k = 0..nk(s)-1;
+ *   - H(s,k) acts on rows s+1+k*b .. min(s+(k+1)*b, n) (1-based), so its
+ *     length is len(s,k) = min(b, n-s-k*b) >= 1;
+ *   - idx(s,k) = sum_{s'<s} nk(s') + k  (see gb_hh_index);
+ *   - hh_v[idx*b + i], i = 0..b-1, holds v_i for 0 < i < len; v_0 = 1 is
+ *     implicit and hh_v[idx*b] is not read; entries len <= i < b are not read;
+ *   - hh_tau[idx] holds tau.
+ *   Complex data (the _z entry points) is interleaved (re, im) doubles, i.e.
+ *   C99 double complex / std::complex<double> / numpy complex128.
+ *
+ * All matrices are column-major.  Z is n x nev with leading dimension ldz.
+ *
+ * Ownership: the caller owns every buffer.  Z is updated in place.  The
+ * device entry points allocate nothing; the calls are asynchronous on the
+ * given CUDA stream (NULL = legacy default stream).  Input buffers must stay
+ * valid and unmodified until the stream reaches the end of the call.
+ *
+ * Errors: every entry point returns 0 on success; -i when argument i
+ * (1-based) is invalid (nothing is launched); a positive GB_ERR_* code when a
+ * CUDA call fails or a device-side wait gives up.  No entry point aborts or
+ * throws.
+ */
+#ifndef ELPA_GB300_H
+#define ELPA_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_OK 0
+#define GB_ERR_CUDA 1        /* a CUDA runtime call failed (launch, copy, ...) */
+#define GB_ERR_TIMEOUT 2     /* a device-side dependency wait exceeded its bound */
+#define GB_ERR_WORKSPACE 3   /* workspace pointer NULL/misaligned or too small */
+#define GB_ERR_UNSUPPORTED 4 /* valid arguments outside what this build supports */
+
+/* Kernel variants for gb_trans_ev_opts.variant. */
+#define GB_VARIANT_AUTO 0      /* library picks */
+#define GB_VARIANT_WAVEFRONT 1 /* one launch per anti-diagonal of the tile DAG */
+#define GB_VARIANT_PIPELINE 2  /* one persistent launch, tiles ordered by flags */
+
+/* Tuning knobs (the paper's MEDIUM autotuning level tunes the blocking of the
+ * back transformation, Sec. 4.3 and Sec. 5.3).  Zero fields mean "default". */
+typedef struct gb_trans_ev_opts {
+    int variant;         /* GB_VARIANT_* */
+    int sweeps_per_tile; /* nb: consecutive sweeps applied per tile, 1..32 */
+    int cols_per_block;  /* eigenvector columns per thread block: 32, 64 or 128 */
+    int spin_limit;      /* pipeline only: polls before a wait gives up (0 = default) */
+} gb_trans_ev_opts;
+
+/* Number of reflectors of the layout above (-1 if n < 1 or nbw < 1). */
+long long gb_hh_count(int n, int nbw);
+
+/* Storage index idx(s,k) (-1 if (s,k) is not a reflector of the layout). */
+long long gb_hh_index(int n, int nbw, int s, int k);
+
+/* Largest band width the kernels of this build accept. */
+int gb_max_nbw(void);
+
+/* Bytes of device workspace a call needs (0 is possible); the workspace must
+ * be 256-byte aligned.  Returns 0 for invalid arguments as well. */
+size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex,
+                                   const gb_trans_ev_opts *opts);
+
+/* Z <- Q2 Z, real symmetric case (FP64).  All pointers are device pointers.
+ * Arguments: 1 n >= 1; 2 nbw in 1..gb_max_nbw(); 3 nev >= 0; 4 hh_v
+ * (gb_hh_count * nbw doubles); 5 hh_tau (gb_hh_count doubles); 6 Z (8-byte
+ * aligned); 7 ldz >= n; 8 workspace; 9 ws_bytes >=
+ * gb_trans_ev_workspace_bytes(...); 10 stream (cudaStream_t); 11 opts (may be
+ * NULL for defaults). */
+int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v,
+                                const double *hh_tau, double *Z, int ldz,
+                                void *workspace, size_t ws_bytes, void *stream,
+                                const gb_trans_ev_opts *opts);
+
+/* Complex Hermitian case: same arguments, complex128 data interleaved as
+ * doubles (hh_v: 2 * count * nbw doubles, hh_tau: 2 * count, Z: 2 * ldz * nev). */
+int gb_trans_ev_tridi_to_band_z(int n, int nbw, int nev, const double *hh_v,
+                                const double *hh_tau, double *Z, int ldz,
+                                void *workspace, size_t ws_bytes, void *stream,
+                                const gb_trans_ev_opts *opts);
+
+/* Host-buffer form of the real case: hh_v, hh_tau and Z are HOST pointers
+ * (pinned memory gives the fastest copies).  dev_buf is a caller-owned device
+ * buffer of at least gb_trans_ev_host_buffer_bytes(...) bytes (256-byte
+ * aligned) that receives the copies and the workspace.  The call copies the
+ * inputs to the device, runs the back-transformation, copies Z back and
+ * synchronises the stream before it returns. */
+size_t gb_trans_ev_host_buffer_bytes(int n, int nbw, int nev, int ldz, int is_complex,
+                                     const gb_trans_ev_opts *opts);
+int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v,
+                                     const double *hh_tau, double *Z, int ldz,
+                                     void *dev_buf, size_t dev_bytes, void *stream,
+                                     const gb_trans_ev_opts *opts);
+
+/* Number of kernel launches one call with these arguments issues. */
+long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex,
+                                   const gb_trans_ev_opts *opts);
+
+/* Human-readable text for a status code (never NULL). */
+const char *gb_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

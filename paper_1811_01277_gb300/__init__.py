@@ -1,0 +1,36 @@
+"""GB300 (sm_103a) back-transformation of eigenvectors from tridiagonal to
+band form -- the hot path of the two-stage ELPA eigensolver (Kus et al.,
+"Optimizations of the Eigensolvers in the ELPA Library", Sec. 2 and 3.1).
+
+The computation runs in ``libelpa_gb300.so`` (CUDA C++, C ABI declared in
+``include/elpa_gb300.h``).  This package is its thin ctypes binding plus the
+seeded input generators; PyTorch only provides device memory and streams.
+"""
+from ._lib import (  # noqa: F401
+    EXPORTS, GB_ERR_CUDA, GB_ERR_TIMEOUT, GB_ERR_UNSUPPORTED, GB_ERR_WORKSPACE, GB_OK,
+    GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
+    gb_hh_count, gb_hh_index, gb_max_nbw, gb_status_string, gb_trans_ev_host_buffer_bytes,
+    gb_trans_ev_launch_count, gb_trans_ev_opts, gb_trans_ev_tridi_to_band_d,
+    gb_trans_ev_tridi_to_band_d_host, gb_trans_ev_tridi_to_band_z, gb_trans_ev_workspace_bytes,
+    load,
+)
+
+
+def trans_ev_tridi_to_band(n, nbw, hh_v, hh_tau, Z, stream=None, opts=None):
+    """Z <- Q2 Z in place for device tensors (float64 or complex128).
+
+    Allocates the workspace the call needs with torch and forwards to the
+    C entry point; ``Z`` is column-major (a transposed row-major tensor, i.e.
+    ``Z.T`` contiguous) with leading dimension ``Z.stride(1)``."""
+    import torch
+    cplx = Z.is_complex()
+    nev = Z.shape[1]
+    ldz = Z.stride(1) if nev > 1 else max(n, 1)
+    if Z.stride(0) != 1:
+        raise ValueError("Z must be column-major (stride(0) == 1)")
+    ws_bytes = gb_trans_ev_workspace_bytes(n, nbw, nev, cplx, opts)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=Z.device) if ws_bytes else None
+    f = gb_trans_ev_tridi_to_band_z if cplx else gb_trans_ev_tridi_to_band_d
+    f(n, nbw, nev, hh_v, hh_tau, Z, ldz, ws, ws_bytes,
+      stream if stream is not None else torch.cuda.current_stream(Z.device), opts)
+    return Z

@@ -1,0 +1,159 @@
+"""ctypes binding of libelpa_gb300.so (argument marshalling only).
+
+Every function here has the name of the C entry point it forwards to (see
+``include/elpa_gb300.h``).  Pointer arguments accept a ``torch.Tensor``
+(its ``data_ptr()``), a numpy array (host pointer), an ``int`` or ``None``.
+No step of the computation runs in Python: if the library is missing the
+calls raise instead of falling back to anything else.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libelpa_gb300.so")
+
+GB_OK = 0
+GB_ERR_CUDA = 1
+GB_ERR_TIMEOUT = 2
+GB_ERR_WORKSPACE = 3
+GB_ERR_UNSUPPORTED = 4
+GB_VARIANT_AUTO = 0
+GB_VARIANT_WAVEFRONT = 1
+GB_VARIANT_PIPELINE = 2
+
+EXPORTS = (
+    "gb_hh_count", "gb_hh_index", "gb_max_nbw", "gb_trans_ev_workspace_bytes",
+    "gb_trans_ev_tridi_to_band_d", "gb_trans_ev_tridi_to_band_z",
+    "gb_trans_ev_host_buffer_bytes", "gb_trans_ev_tridi_to_band_d_host",
+    "gb_trans_ev_launch_count", "gb_status_string",
+)
+
+
+class gb_trans_ev_opts(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("sweeps_per_tile", ctypes.c_int),
+                ("cols_per_block", ctypes.c_int), ("spin_limit", ctypes.c_int)]
+
+
+class GbError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what} returned {status}: {gb_status_string(status)}")
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library not found at {path}; build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    i, ll, sz, p = ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t, ctypes.c_void_p
+    po = ctypes.POINTER(gb_trans_ev_opts)
+    L.gb_hh_count.argtypes = [i, i]; L.gb_hh_count.restype = ll
+    L.gb_hh_index.argtypes = [i, i, i, i]; L.gb_hh_index.restype = ll
+    L.gb_max_nbw.argtypes = []; L.gb_max_nbw.restype = i
+    L.gb_trans_ev_workspace_bytes.argtypes = [i, i, i, i, po]; L.gb_trans_ev_workspace_bytes.restype = sz
+    for nm in ("gb_trans_ev_tridi_to_band_d", "gb_trans_ev_tridi_to_band_z"):
+        getattr(L, nm).argtypes = [i, i, i, p, p, p, i, p, sz, p, po]
+        getattr(L, nm).restype = i
+    L.gb_trans_ev_host_buffer_bytes.argtypes = [i, i, i, i, i, po]
+    L.gb_trans_ev_host_buffer_bytes.restype = sz
+    L.gb_trans_ev_tridi_to_band_d_host.argtypes = [i, i, i, p, p, p, i, p, sz, p, po]
+    L.gb_trans_ev_tridi_to_band_d_host.restype = i
+    L.gb_trans_ev_launch_count.argtypes = [i, i, i, i, po]; L.gb_trans_ev_launch_count.restype = ll
+    L.gb_status_string.argtypes = [i]; L.gb_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _opts(o):
+    if o is None:
+        return None
+    if isinstance(o, gb_trans_ev_opts):
+        return ctypes.byref(o)
+    return ctypes.byref(gb_trans_ev_opts(**o))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def gb_hh_count(n, nbw):
+    return load().gb_hh_count(n, nbw)
+
+
+def gb_hh_index(n, nbw, s, k):
+    return load().gb_hh_index(n, nbw, s, k)
+
+
+def gb_max_nbw():
+    return load().gb_max_nbw()
+
+
+def gb_trans_ev_workspace_bytes(n, nbw, nev, is_complex=0, opts=None):
+    return load().gb_trans_ev_workspace_bytes(n, nbw, nev, int(is_complex), _opts(opts))
+
+
+def gb_trans_ev_tridi_to_band_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, workspace=None, ws_bytes=0,
+                                stream=None, opts=None, check=True):
+    rc = load().gb_trans_ev_tridi_to_band_d(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
+                                            _p(workspace), ws_bytes, _stream(stream), _opts(opts))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_trans_ev_tridi_to_band_d")
+    return rc
+
+
+def gb_trans_ev_tridi_to_band_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, workspace=None, ws_bytes=0,
+                                stream=None, opts=None, check=True):
+    rc = load().gb_trans_ev_tridi_to_band_z(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
+                                            _p(workspace), ws_bytes, _stream(stream), _opts(opts))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_trans_ev_tridi_to_band_z")
+    return rc
+
+
+def gb_trans_ev_host_buffer_bytes(n, nbw, nev, ldz, is_complex=0, opts=None):
+    return load().gb_trans_ev_host_buffer_bytes(n, nbw, nev, ldz, int(is_complex), _opts(opts))
+
+
+def gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, hh_v, hh_tau, Z, ldz, dev_buf, dev_bytes,
+                                     stream=None, opts=None, check=True):
+    rc = load().gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
+                                                 _p(dev_buf), dev_bytes, _stream(stream), _opts(opts))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_trans_ev_tridi_to_band_d_host")
+    return rc
+
+
+def gb_trans_ev_launch_count(n, nbw, nev, is_complex=0, opts=None):
+    return load().gb_trans_ev_launch_count(n, nbw, nev, int(is_complex), _opts(opts))
+
+
+def gb_status_string(status):
+    try:
+        return load().gb_status_string(status).decode()
+    except RuntimeError:
+        return f"status {status}"

@@ -1,0 +1,173 @@
+// C ABI of the library (declarations and the operation's definition are in
+// include/elpa_gb300.h).  This file validates arguments, picks the kernel
+// variant and launches it; it never allocates device memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "elpa_gb300.h"
+#include "layout.cuh"
+#include "trans_ev_kernels.cuh"
+
+namespace {
+
+constexpr int kMaxNbw = 64;
+
+struct Opts {
+    int variant, nb, threads, spin;
+};
+
+// Returns 0 or -11 (opts is the 11th argument of the device entry points).
+int resolve(const gb_trans_ev_opts *o, int is_complex, Opts *r)
+{
+    (void)is_complex;
+    r->variant = GB_VARIANT_WAVEFRONT;
+    r->nb = 16;
+    r->threads = 128;
+    r->spin = 0;
+    if (!o) return 0;
+    if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE) return -11;
+    if (o->sweeps_per_tile < 0 || o->sweeps_per_tile > 32) return -11;
+    if (o->cols_per_block != 0 && o->cols_per_block != 32 && o->cols_per_block != 64 &&
+        o->cols_per_block != 128)
+        return -11;
+    if (o->spin_limit < 0) return -11;
+    if (o->variant == GB_VARIANT_PIPELINE) return -11;  // not in this build yet
+    if (o->sweeps_per_tile) r->nb = o->sweeps_per_tile;
+    if (o->cols_per_block) r->threads = o->cols_per_block;
+    r->spin = o->spin_limit;
+    return 0;
+}
+
+int check_common(int n, int nbw, int nev, const void *hh_v, const void *hh_tau, const void *Z,
+                 int ldz, size_t elem)
+{
+    if (n < 1) return -1;
+    if (nbw < 1 || nbw > kMaxNbw) return -2;
+    if (nev < 0) return -3;
+    bool has_hh = n > 1;
+    if (has_hh && (!hh_v || ((uintptr_t)hh_v % elem) != 0)) return -4;
+    if (has_hh && (!hh_tau || ((uintptr_t)hh_tau % elem) != 0)) return -5;
+    if (nev > 0 && (!Z || ((uintptr_t)Z % elem) != 0)) return -6;
+    if (ldz < n) return -7;
+    return 0;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+long long gb_hh_count(int n, int nbw)
+{
+    if (n < 1 || nbw < 1) return -1;
+    return gb::hh_total(n, nbw);
+}
+
+long long gb_hh_index(int n, int nbw, int s, int k)
+{
+    if (n < 1 || nbw < 1 || s < 1 || s > n - 1 || k < 0 || k >= gb::sweep_count(n, nbw, s)) return -1;
+    return gb::sweep_first(n, nbw, s) + k;
+}
+
+int gb_max_nbw(void) { return kMaxNbw; }
+
+size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
+{
+    Opts o;
+    if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, is_complex, &o) != 0) return 0;
+    return 0;  // the wavefront variant needs no workspace
+}
+
+int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, const double *hh_tau,
+                                double *Z, int ldz, void *workspace, size_t ws_bytes, void *stream,
+                                const gb_trans_ev_opts *opts)
+{
+    int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, sizeof(double));
+    if (rc) return rc;
+    Opts o;
+    if ((rc = resolve(opts, 0, &o)) != 0) return rc;
+    size_t need = gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts);
+    if (need > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0)) return -8;
+    if (ws_bytes < need) return -9;
+    if (n == 1 || nev == 0) return GB_OK;
+    cudaError_t e = gb::wavefront_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+int gb_trans_ev_tridi_to_band_z(int n, int nbw, int nev, const double *hh_v, const double *hh_tau,
+                                double *Z, int ldz, void *workspace, size_t ws_bytes, void *stream,
+                                const gb_trans_ev_opts *opts)
+{
+    int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, 2 * sizeof(double));
+    if (rc) return rc;
+    (void)workspace; (void)ws_bytes; (void)stream; (void)opts;
+    return GB_ERR_UNSUPPORTED;
+}
+
+size_t gb_trans_ev_host_buffer_bytes(int n, int nbw, int nev, int ldz, int is_complex,
+                                     const gb_trans_ev_opts *opts)
+{
+    if (n < 1 || nbw < 1 || nev < 0 || ldz < n) return 0;
+    size_t el = is_complex ? 16 : 8;
+    size_t cnt = (size_t)gb::hh_total(n, nbw);
+    return align256(cnt * (size_t)nbw * el) + align256(cnt * el) + align256((size_t)ldz * nev * el) +
+           align256(gb_trans_ev_workspace_bytes(n, nbw, nev, is_complex, opts));
+}
+
+int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v, const double *hh_tau,
+                                     double *Z, int ldz, void *dev_buf, size_t dev_bytes, void *stream,
+                                     const gb_trans_ev_opts *opts)
+{
+    int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, sizeof(double));
+    if (rc) return rc;
+    Opts o;
+    if ((rc = resolve(opts, 0, &o)) != 0) return rc;
+    size_t need = gb_trans_ev_host_buffer_bytes(n, nbw, nev, ldz, 0, opts);
+    if (!dev_buf || ((uintptr_t)dev_buf % 256) != 0) return -8;
+    if (dev_bytes < need) return -9;
+    if (n == 1 || nev == 0) return GB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t cnt = (size_t)gb::hh_total(n, nbw);
+    char *p = (char *)dev_buf;
+    double *d_v = (double *)p;   p += align256(cnt * nbw * sizeof(double));
+    double *d_t = (double *)p;   p += align256(cnt * sizeof(double));
+    double *d_z = (double *)p;   p += align256((size_t)ldz * nev * sizeof(double));
+    void *d_ws = p;
+    size_t zbytes = ((size_t)ldz * (nev - 1) + n) * sizeof(double);
+    if (cudaMemcpyAsync(d_v, hh_v, cnt * nbw * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_t, hh_tau, cnt * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_z, Z, zbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return GB_ERR_CUDA;
+    rc = gb_trans_ev_tridi_to_band_d(n, nbw, nev, d_v, d_t, d_z, ldz, d_ws,
+                                     gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts), stream, opts);
+    if (rc != GB_OK) return rc;
+    if (cudaMemcpyAsync(Z, d_z, zbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GB_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GB_ERR_CUDA;
+    return GB_OK;
+}
+
+long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
+{
+    Opts o;
+    if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, is_complex, &o) != 0) return -1;
+    if (n == 1 || nev == 0) return 0;
+    return gb::wavefront_launch_count(n, nbw, o.nb);
+}
+
+const char *gb_status_string(int status)
+{
+    switch (status) {
+    case GB_OK: return "success";
+    case GB_ERR_CUDA: return "a CUDA runtime call failed";
+    case GB_ERR_TIMEOUT: return "a device-side dependency wait exceeded its bound";
+    case GB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case GB_ERR_UNSUPPORTED: return "arguments valid but not supported by this build";
+    default: break;
+    }
+    if (status < 0) return "invalid argument (status -i names argument i)";
+    return "unknown status";
+}
+
+}  // extern "C"

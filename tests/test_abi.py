@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+function include/elpa_gb300.h declares; the layout helpers agree with the
+oracle; invalid arguments are rejected before anything touches a GPU."""
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_1811_01277_gb300 as gb
+from paper_1811_01277_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return gb.load()
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(gb_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "gb_trans_ev_tridi_to_band_d" in names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(names) == set(gb.EXPORTS)
+
+
+@pytest.mark.parametrize("n,b", [(1, 1), (2, 1), (3, 2), (100, 7), (1024, 32), (16384, 64), (1000, 64)])
+def test_layout_matches_oracle(lib, n, b):
+    assert gb.gb_hh_count(n, b) == oracle.hh_count(n, b)
+    for s in sorted({1, 2, n // 2, n - 2, n - 1}):
+        if 1 <= s <= n - 1:
+            nk = (n - s + b - 1) // b
+            for k in sorted({0, nk // 2, nk - 1}):
+                assert gb.gb_hh_index(n, b, s, k) == oracle.hh_index(n, b, s, k)
+            assert gb.gb_hh_index(n, b, s, nk) == -1
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    f = gb.gb_trans_ev_tridi_to_band_d
+    ok = dict(n=10, nbw=3, nev=2, hh_v=256, hh_tau=256, Z=256, ldz=10)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return f(a["n"], a["nbw"], a["nev"], a["hh_v"], a["hh_tau"], a["Z"], a["ldz"], check=False)
+
+    assert call(n=0) == -1
+    assert call(nbw=0) == -2
+    assert call(nbw=gb.gb_max_nbw() + 1) == -2
+    assert call(nev=-1) == -3
+    assert call(hh_v=None) == -4
+    assert call(hh_v=257) == -4          # misaligned
+    assert call(hh_tau=None) == -5
+    assert call(Z=None) == -6
+    assert call(Z=260) == -6
+    assert call(ldz=9) == -7
+    assert f(10, 3, 2, 256, 256, 256, 10, opts={"variant": 7}, check=False) == -11
+    assert f(10, 3, 2, 256, 256, 256, 10, opts={"variant": 1, "cols_per_block": 48}, check=False) == -11
+    # no-op cases return success without touching memory or a GPU
+    assert f(1, 3, 5, None, None, 256, 1, check=False) == 0
+    assert f(10, 3, 0, 256, 256, None, 10, check=False) == 0
+    assert gb.gb_trans_ev_tridi_to_band_z(0, 3, 2, 256, 256, 256, 10, check=False) == -1
+    assert gb.gb_status_string(-3).startswith("invalid argument")
+    assert gb.gb_status_string(gb.GB_ERR_TIMEOUT).startswith("a device-side")
+
+
+def test_launch_count_is_host_only(lib):
+    # one launch per anti-diagonal of the tile graph
+    assert gb.gb_trans_ev_launch_count(1, 4, 10) == 0
+    n, b = 1024, 32
+    c = gb.gb_trans_ev_launch_count(n, b, 1024, opts={"variant": 1, "sweeps_per_tile": 16})
+    G = (n - 1 + 15) // 16
+    assert G <= c <= G + (n + b - 1) // b
