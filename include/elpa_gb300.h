@@ -60,10 +60,17 @@ extern "C" {
 /* Tuning knobs (the paper's MEDIUM autotuning level tunes the blocking of the
  * back transformation, Sec. 4.3 and Sec. 5.3).  Zero fields mean "default". */
 typedef struct gb_trans_ev_opts {
-    int variant;         /* GB_VARIANT_* */
-    int sweeps_per_tile; /* nb: consecutive sweeps applied per tile, 1..32 */
-    int cols_per_block;  /* eigenvector columns per thread block: 32, 64 or 128 */
-    int spin_limit;      /* pipeline only: polls before a wait gives up (0 = default) */
+    int variant;         /* GB_VARIANT_*; PIPELINE needs nbw in {8,16,32,64} and
+                            otherwise runs as WAVEFRONT */
+    int sweeps_per_tile; /* nb: consecutive sweeps per tile, 1..32 (rounded up to
+                            4, 8 or 16 for WAVEFRONT and 8 or 16 for PIPELINE) */
+    int cols_per_block;  /* eigenvector columns per thread block: 32, 64 or 128
+                            (PIPELINE: 64 or 128) */
+    int spin_limit;      /* PIPELINE only: polls before a dependency wait gives up
+                            (0 = default; every wait also gives up after 10 s) */
+    int test_hold_group; /* fault-injection hook for tests: when g+1 > 0, sweep
+                            group g never publishes its progress so that the
+                            next group's wait must give up; 0 = off */
 } gb_trans_ev_opts;
 
 /* Number of reflectors of the layout above (-1 if n < 1 or nbw < 1). */
@@ -110,6 +117,13 @@ int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v
                                      const double *hh_tau, double *Z, int ldz,
                                      void *dev_buf, size_t dev_bytes, void *stream,
                                      const gb_trans_ev_opts *opts);
+
+/* Completion status of the device work of earlier calls that used this
+ * workspace: synchronises the stream, then returns GB_OK, GB_ERR_TIMEOUT (a
+ * PIPELINE dependency wait gave up; Z is then unspecified) or GB_ERR_CUDA.
+ * workspace may be NULL (WAVEFRONT calls need none): then only the stream is
+ * synchronised. */
+int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream);
 
 /* Number of kernel launches one call with these arguments issues. */
 long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex,

@@ -25,13 +25,14 @@ EXPORTS = (
     "gb_hh_count", "gb_hh_index", "gb_max_nbw", "gb_trans_ev_workspace_bytes",
     "gb_trans_ev_tridi_to_band_d", "gb_trans_ev_tridi_to_band_z",
     "gb_trans_ev_host_buffer_bytes", "gb_trans_ev_tridi_to_band_d_host",
-    "gb_trans_ev_launch_count", "gb_status_string",
+    "gb_trans_ev_launch_count", "gb_status_string", "gb_trans_ev_query",
 )
 
 
 class gb_trans_ev_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("sweeps_per_tile", ctypes.c_int),
-                ("cols_per_block", ctypes.c_int), ("spin_limit", ctypes.c_int)]
+                ("cols_per_block", ctypes.c_int), ("spin_limit", ctypes.c_int),
+                ("test_hold_group", ctypes.c_int)]
 
 
 class GbError(RuntimeError):
@@ -69,6 +70,7 @@ def load(path=None):
     L.gb_trans_ev_tridi_to_band_d_host.restype = i
     L.gb_trans_ev_launch_count.argtypes = [i, i, i, i, po]; L.gb_trans_ev_launch_count.restype = ll
     L.gb_status_string.argtypes = [i]; L.gb_status_string.restype = ctypes.c_char_p
+    L.gb_trans_ev_query.argtypes = [p, sz, p]; L.gb_trans_ev_query.restype = i
     _lib = L
     return L
 
@@ -150,6 +152,10 @@ def gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, hh_v, hh_tau, Z, ldz, dev_buf,
 
 def gb_trans_ev_launch_count(n, nbw, nev, is_complex=0, opts=None):
     return load().gb_trans_ev_launch_count(n, nbw, nev, int(is_complex), _opts(opts))
+
+
+def gb_trans_ev_query(workspace=None, ws_bytes=0, stream=None):
+    return load().gb_trans_ev_query(_p(workspace), ws_bytes, _stream(stream))
 
 
 def gb_status_string(status):

@@ -13,28 +13,39 @@ namespace {
 constexpr int kMaxNbw = 64;
 
 struct Opts {
-    int variant, nb, threads, spin;
+    int variant, nb, threads, hold;
+    long long spin;
 };
 
+constexpr long long kDefaultSpinPolls = 1LL << 40;  // effectively bounded by the timeout
+constexpr long long kTimeoutNs = 10LL * 1000 * 1000 * 1000;
+
 // Returns 0 or -11 (opts is the 11th argument of the device entry points).
-int resolve(const gb_trans_ev_opts *o, int is_complex, Opts *r)
+// The variant is resolved against nbw: PIPELINE needs nbw in {8,16,32,64}.
+int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
 {
     (void)is_complex;
-    r->variant = GB_VARIANT_WAVEFRONT;
+    int variant = GB_VARIANT_AUTO;
     r->nb = 16;
     r->threads = 128;
-    r->spin = 0;
-    if (!o) return 0;
-    if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE) return -11;
-    if (o->sweeps_per_tile < 0 || o->sweeps_per_tile > 32) return -11;
-    if (o->cols_per_block != 0 && o->cols_per_block != 32 && o->cols_per_block != 64 &&
-        o->cols_per_block != 128)
-        return -11;
-    if (o->spin_limit < 0) return -11;
-    if (o->variant == GB_VARIANT_PIPELINE) return -11;  // not in this build yet
-    if (o->sweeps_per_tile) r->nb = o->sweeps_per_tile;
-    if (o->cols_per_block) r->threads = o->cols_per_block;
-    r->spin = o->spin_limit;
+    r->spin = kDefaultSpinPolls;
+    r->hold = 0;
+    if (o) {
+        if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE) return -11;
+        if (o->sweeps_per_tile < 0 || o->sweeps_per_tile > 32) return -11;
+        if (o->cols_per_block != 0 && o->cols_per_block != 32 && o->cols_per_block != 64 &&
+            o->cols_per_block != 128)
+            return -11;
+        if (o->spin_limit < 0 || o->test_hold_group < 0) return -11;
+        variant = o->variant;
+        if (o->sweeps_per_tile) r->nb = o->sweeps_per_tile;
+        if (o->cols_per_block) r->threads = o->cols_per_block;
+        if (o->spin_limit) r->spin = o->spin_limit;
+        r->hold = o->test_hold_group;
+    }
+    if (variant == GB_VARIANT_AUTO) variant = GB_VARIANT_WAVEFRONT;
+    if (variant == GB_VARIANT_PIPELINE && !gb::pipeline_supported(nbw)) variant = GB_VARIANT_WAVEFRONT;
+    r->variant = variant;
     return 0;
 }
 
@@ -75,7 +86,9 @@ int gb_max_nbw(void) { return kMaxNbw; }
 size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
 {
     Opts o;
-    if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, is_complex, &o) != 0) return 0;
+    if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return 0;
+    if (o.variant == GB_VARIANT_PIPELINE && n > 1 && nev > 0)
+        return gb::pipeline_workspace_bytes(n, nev, o.nb, o.threads);
     return 0;  // the wavefront variant needs no workspace
 }
 
@@ -86,13 +99,17 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, sizeof(double));
     if (rc) return rc;
     Opts o;
-    if ((rc = resolve(opts, 0, &o)) != 0) return rc;
+    if ((rc = resolve(opts, nbw, 0, &o)) != 0) return rc;
     size_t need = gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts);
     if (need > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0)) return -8;
     if (ws_bytes < need) return -9;
     if (n == 1 || nev == 0) return GB_OK;
-    cudaError_t e = gb::wavefront_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads,
-                                    (cudaStream_t)stream);
+    cudaError_t e;
+    if (o.variant == GB_VARIANT_PIPELINE)
+        e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, workspace, need, o.spin,
+                           kTimeoutNs, o.hold, (cudaStream_t)stream);
+    else
+        e = gb::wavefront_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
     return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 
@@ -123,7 +140,7 @@ int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v
     int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, sizeof(double));
     if (rc) return rc;
     Opts o;
-    if ((rc = resolve(opts, 0, &o)) != 0) return rc;
+    if ((rc = resolve(opts, nbw, 0, &o)) != 0) return rc;
     size_t need = gb_trans_ev_host_buffer_bytes(n, nbw, nev, ldz, 0, opts);
     if (!dev_buf || ((uintptr_t)dev_buf % 256) != 0) return -8;
     if (dev_bytes < need) return -9;
@@ -144,15 +161,25 @@ int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v
                                      gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts), stream, opts);
     if (rc != GB_OK) return rc;
     if (cudaMemcpyAsync(Z, d_z, zbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GB_ERR_CUDA;
+    return gb_trans_ev_query(d_ws, gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts), stream);
+}
+
+int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
     if (cudaStreamSynchronize(st) != cudaSuccess) return GB_ERR_CUDA;
-    return GB_OK;
+    if (!workspace || ws_bytes < 256) return GB_OK;
+    int head[3] = {0, 0, 0};  // ticket, abort, error
+    if (cudaMemcpy(head, workspace, sizeof(head), cudaMemcpyDeviceToHost) != cudaSuccess) return GB_ERR_CUDA;
+    return head[2] ? head[2] : GB_OK;
 }
 
 long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
 {
     Opts o;
-    if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, is_complex, &o) != 0) return -1;
+    if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return -1;
     if (n == 1 || nev == 0) return 0;
+    if (o.variant == GB_VARIANT_PIPELINE) return 1;
     return gb::wavefront_launch_count(n, nbw, o.nb);
 }
 

@@ -38,4 +38,10 @@ cudaError_t wavefront_d(int n, int b, int nev, const double *hh_v, const double 
                         long long ldz, int nb, int threads, cudaStream_t st);
 long long wavefront_launch_count(int n, int b, int nb);
 
+size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads);
+bool pipeline_supported(int b);
+cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
+                       long long ldz, int nb, int threads, void *ws, size_t ws_bytes, long long spin_polls,
+                       long long timeout_ns, int hold_group, cudaStream_t st);
+
 }  // namespace gb
