@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "n16384": dict(n=16384, nev=4096, nbw=64),
+    "n6144": dict(n=6144, nev=2048, nbw=64),   # small case for ncu captures
     "n1024": dict(n=1024, nev=1024, nbw=32),
 }
 # FP64 DFMA: 2 lanes per clock per SM on GB300 (1.25 TFLOP/s nominal at the
@@ -305,6 +306,28 @@ def run_ours(args, wl):
     return 0
 
 
+def measure_fp64_peak():
+    """Build and run the FP64 microbenchmark (DFMA and f64 mma.sync) with the
+    SM clock sampled, and print one JSON line."""
+    src = os.path.join(ROOT, "paper_1811_01277_gb300", "microbench", "fp64_peak.cu")
+    exe = os.path.join(ROOT, "paper_1811_01277_gb300", "_build", "fp64_peak")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    out = subprocess.run([exe, "2.0"], capture_output=True, text=True, check=True).stdout
+    clocks = sampler.stop()
+    res = {}
+    for line in out.splitlines():
+        parts = line.split()
+        res[parts[0]] = {"tflops": float(parts[1]), "seconds": float(parts[2])}
+    mhz = clocks["sm_mhz"] if clocks else None
+    if mhz:
+        for v in res.values():
+            v["flop_per_clk_per_sm"] = v["tflops"] * 1e12 / (152 * mhz * 1e6)
+    print(json.dumps({"fp64_peak": res, "clocks": clocks}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,7 +340,10 @@ def main():
     ap.add_argument("--threads", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--measure-fp64-peak", action="store_true")
     args = ap.parse_args()
+    if args.measure_fp64_peak:
+        return measure_fp64_peak()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
