@@ -218,7 +218,10 @@ def run_ours(args, wl):
     gb.load()
     n, nev, nbw = wl["n"], wl["nev"], wl["nbw"]
     opts = {"variant": args.variant, "sweeps_per_tile": args.nb, "cols_per_block": args.threads}
-    variant_name = {0: "auto", 1: "wavefront", 2: "pipeline"}[args.variant]
+    if args.variant == 0 and args.nb == 0 and args.threads == 0:
+        opts = None  # the library's default choice
+    launches_per_call = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
+    variant_name = "pipeline" if launches_per_call == 1 else "wavefront"
 
     hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024 + 1000 * rank)
     Z = inputs.z_gaussian(n, nev, seed=2025 + 1000 * rank)
@@ -253,9 +256,9 @@ def run_ours(args, wl):
     value = world * args.steps / (el_ms / 1e3)
     F = algorithmic_flops(n, nev)
     achieved = F / (ms_per_step / 1e3) / 1e12
-    launches = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
+    launches = launches_per_call
     sha = kernel_sources_sha1()
-    kernel = "wavefront_tile_d" if args.variant in (0, 1) else "pipeline_d"
+    kernel = "pipeline_d" if variant_name == "pipeline" else "wavefront_tile_d"
     traffic = profile_traffic(kernel, args.workload, variant_name, sha)
 
     # end to end through the host-buffer entry point: H2D of reflectors and Z,
@@ -335,9 +338,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="n16384")
-    ap.add_argument("--variant", type=int, default=1)
-    ap.add_argument("--nb", type=int, default=16)
-    ap.add_argument("--threads", type=int, default=128)
+    ap.add_argument("--variant", type=int, default=0, help="0 library default, 1 wavefront, 2 pipeline")
+    ap.add_argument("--nb", type=int, default=0, help="sweeps per tile (0 = default)")
+    ap.add_argument("--threads", type=int, default=0, help="columns per block (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--measure-fp64-peak", action="store_true")

@@ -10,7 +10,9 @@
 
 namespace {
 
-constexpr int kMaxNbw = 64;
+constexpr int kMaxNbw = 256;       // shared-memory window kernels
+constexpr int kMaxRegNbw = 64;     // register-window kernels (real case)
+constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Opts {
     int variant, nb, threads, hold;
@@ -21,13 +23,12 @@ constexpr long long kDefaultSpinPolls = 1LL << 40;  // effectively bounded by th
 constexpr long long kTimeoutNs = 10LL * 1000 * 1000 * 1000;
 
 // Returns 0 or -11 (opts is the 11th argument of the device entry points).
-// The variant is resolved against nbw: PIPELINE needs nbw in {8,16,32,64}.
+// AUTO picks PIPELINE for real data with nbw in {8,16,32,64} (fastest in the
+// GB300 sweep: nb = 16, 64 columns per block) and WAVEFRONT otherwise;
+// PIPELINE requested for other cases runs as WAVEFRONT.
 int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
 {
-    (void)is_complex;
-    int variant = GB_VARIANT_AUTO;
-    r->nb = 16;
-    r->threads = 128;
+    int variant = GB_VARIANT_AUTO, nb = 0, threads = 0;
     r->spin = kDefaultSpinPolls;
     r->hold = 0;
     if (o) {
@@ -38,14 +39,28 @@ int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
             return -11;
         if (o->spin_limit < 0 || o->test_hold_group < 0) return -11;
         variant = o->variant;
-        if (o->sweeps_per_tile) r->nb = o->sweeps_per_tile;
-        if (o->cols_per_block) r->threads = o->cols_per_block;
+        nb = o->sweeps_per_tile;
+        threads = o->cols_per_block;
         if (o->spin_limit) r->spin = o->spin_limit;
         r->hold = o->test_hold_group;
     }
-    if (variant == GB_VARIANT_AUTO) variant = GB_VARIANT_WAVEFRONT;
-    if (variant == GB_VARIANT_PIPELINE && !gb::pipeline_supported(nbw)) variant = GB_VARIANT_WAVEFRONT;
+    const bool pipe_ok = !is_complex && gb::pipeline_supported(nbw);
+    if (variant == GB_VARIANT_AUTO) variant = pipe_ok ? GB_VARIANT_PIPELINE : GB_VARIANT_WAVEFRONT;
+    if (variant == GB_VARIANT_PIPELINE && !pipe_ok) variant = GB_VARIANT_WAVEFRONT;
     r->variant = variant;
+    const bool smem = is_complex || nbw > kMaxRegNbw;
+    r->nb = nb ? nb : (smem ? 8 : 16);
+    r->threads = threads ? threads : (variant == GB_VARIANT_PIPELINE || smem ? 64 : 128);
+    // the shared-memory kernels take 32 or 64 columns per block and shrink
+    // them or the tile depth until the window fits
+    if (smem) {
+        if (r->threads > 64) r->threads = 64;
+        while (gb::wavefront_smem_bytes(nbw, r->nb, r->threads, is_complex) > kMaxSmem) {
+            if (r->threads > 32) r->threads = 32;
+            else if (r->nb > 4) r->nb = r->nb > 8 ? 8 : 4;
+            else return -2;
+        }
+    }
     return 0;
 }
 
@@ -87,7 +102,7 @@ size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, cons
 {
     Opts o;
     if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return 0;
-    if (o.variant == GB_VARIANT_PIPELINE && n > 1 && nev > 0)
+    if (o.variant == GB_VARIANT_PIPELINE && !is_complex && n > 1 && nev > 0)
         return gb::pipeline_workspace_bytes(n, nev, o.nb, o.threads);
     return 0;  // the wavefront variant needs no workspace
 }
@@ -108,6 +123,8 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     if (o.variant == GB_VARIANT_PIPELINE)
         e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, workspace, need, o.spin,
                            kTimeoutNs, o.hold, (cudaStream_t)stream);
+    else if (nbw > kMaxRegNbw)
+        e = gb::wavefront_smem_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
     else
         e = gb::wavefront_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
     return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
@@ -119,8 +136,13 @@ int gb_trans_ev_tridi_to_band_z(int n, int nbw, int nev, const double *hh_v, con
 {
     int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, 2 * sizeof(double));
     if (rc) return rc;
-    (void)workspace; (void)ws_bytes; (void)stream; (void)opts;
-    return GB_ERR_UNSUPPORTED;
+    Opts o;
+    if ((rc = resolve(opts, nbw, 1, &o)) != 0) return rc;
+    (void)workspace;
+    (void)ws_bytes;  // the complex kernels need no workspace
+    if (n == 1 || nev == 0) return GB_OK;
+    cudaError_t e = gb::wavefront_smem_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 
 size_t gb_trans_ev_host_buffer_bytes(int n, int nbw, int nev, int ldz, int is_complex,

@@ -38,6 +38,12 @@ cudaError_t wavefront_d(int n, int b, int nev, const double *hh_v, const double 
                         long long ldz, int nb, int threads, cudaStream_t st);
 long long wavefront_launch_count(int n, int b, int nb);
 
+cudaError_t wavefront_smem_z(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
+                             long long ldz, int nb, int threads, cudaStream_t st);
+cudaError_t wavefront_smem_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
+                             long long ldz, int nb, int threads, cudaStream_t st);
+size_t wavefront_smem_bytes(int b, int nb, int threads, int is_complex);
+
 size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads);
 bool pipeline_supported(int b);
 cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,

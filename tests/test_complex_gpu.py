@@ -1,0 +1,92 @@
+"""Complex Hermitian back-transformation and real band widths above 64
+(shared-memory window kernels) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_01277_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_01277_gb300 as m
+    from paper_1811_01277_gb300 import build
+    build.build()
+    m.load()
+    return m
+
+
+def run(gb, n, b, hv, ht, Z, opts=None):
+    dev = torch.device("cuda")
+    cplx = np.iscomplexobj(Z)
+    ldz, nev = Z.shape
+    Zt = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)
+    hv_d = torch.from_numpy(np.ascontiguousarray(hv)).to(dev)
+    ht_d = torch.from_numpy(np.ascontiguousarray(ht)).to(dev)
+    wsb = gb.gb_trans_ev_workspace_bytes(n, b, nev, cplx, opts)
+    ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    f = gb.gb_trans_ev_tridi_to_band_z if cplx else gb.gb_trans_ev_tridi_to_band_d
+    f(n, b, nev, hv_d, ht_d, Zt, ldz, ws, wsb, st, opts)
+    assert gb.gb_trans_ev_query(ws if wsb else None, wsb, st) == 0
+    return np.asfortranarray(Zt.cpu().numpy().T)
+
+
+ZOPTS = [None, {"sweeps_per_tile": 4, "cols_per_block": 32}, {"sweeps_per_tile": 16, "cols_per_block": 64}]
+
+
+@pytest.mark.parametrize("opts", ZOPTS, ids=["default", "nb4t32", "nb16t64"])
+@pytest.mark.parametrize("n,b,nev", [(2, 1, 2), (3, 2, 3), (17, 3, 5), (60, 8, 33), (129, 16, 70),
+                                     (200, 64, 65), (150, 37, 31)])
+def test_complex_parity_bulge_chase(gb, n, b, nev, opts):
+    B = inputs.band_symmetric(n, b, seed=n + b, cplx=True)
+    _, _, hv, ht, _ = oracle.bulge_chase(B, b)
+    Z = inputs.z_gaussian(n, nev, seed=nev, cplx=True)
+    out = run(gb, n, b, hv, ht, Z, opts)
+    ref = oracle.trans_ev(n, b, hv, ht, Z)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
+
+
+def test_complex_eigenvectors_residual(gb):
+    n, b = 384, 32
+    B = inputs.band_symmetric(n, b, seed=77, cplx=True)
+    d, e, hv, ht, _ = oracle.bulge_chase(B, b)
+    w, V = oracle.tridiag_ql(d, e)
+    Z = np.asfortranarray(V.astype(np.complex128))
+    out = run(gb, n, b, hv, ht, Z)
+    assert np.linalg.norm(B @ out - out * w) / np.linalg.norm(B) <= 50 * n * U
+    assert np.abs(out.conj().T @ out - np.eye(n)).max() <= 50 * n * U
+
+
+def test_complex_config_size_sampled(gb):
+    """complex128 Hermitian n = 8192, nev = 2048 (25%), nbw = 64; 16 seeded
+    columns against the oracle, all columns for norm preservation."""
+    n, b, nev = 8192, 64, 2048
+    hv, ht = inputs.synthetic_reflectors(n, b, seed=81, cplx=True)
+    Z = inputs.z_gaussian(n, nev, seed=82, cplx=True)
+    out = run(gb, n, b, hv, ht, Z)
+    cols = np.sort(np.random.default_rng(3).choice(nev, 16, replace=False))
+    ref = oracle.trans_ev(n, b, hv, ht, np.asfortranarray(Z[:, cols]))
+    assert np.linalg.norm(out[:, cols] - ref) / np.linalg.norm(Z[:, cols]) <= 50 * n * U
+    nr = np.linalg.norm(out, axis=0) / np.linalg.norm(Z, axis=0)
+    assert np.abs(nr - 1).max() <= 50 * n * U
+
+
+@pytest.mark.parametrize("n,b,nev", [(300, 65, 40), (400, 100, 33), (600, 128, 70), (520, 256, 20)])
+def test_real_wide_band_parity(gb, n, b, nev):
+    if n <= 400:
+        B = inputs.band_symmetric(n, b, seed=n)
+        _, _, hv, ht, _ = oracle.bulge_chase(B, b)
+    else:
+        hv, ht = inputs.synthetic_reflectors(n, b, seed=n)
+    Z = inputs.z_gaussian(n, nev, seed=5)
+    out = run(gb, n, b, hv, ht, Z)
+    ref = oracle.trans_ev(n, b, hv, ht, Z)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
