@@ -129,6 +129,32 @@ int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream);
 long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex,
                                    const gb_trans_ev_opts *opts);
 
+/* No-allocation form of the real case, for callers that cannot call
+ * cudaMalloc (code running inside a memory pool or arena that owns all
+ * device memory, allocation-free service loops, hosts that forbid allocation
+ * after start-up).  The paper has no counterpart; it exists for such callers.
+ *
+ * Same operation and arguments 1-7 as gb_trans_ev_tridi_to_band_d, always
+ * with the pipeline kernel (nb = 16, 64 columns per block); nbw must be 8,
+ * 16, 32 or 64 (else -2).  Its scratch area (pipeline ticket, status words
+ * and progress flags) is a fixed array of GB_NOALLOC_SCRATCH_BYTES in device
+ * memory that every GPU loading the library holds until the process exits;
+ * a problem needing more (gb_trans_ev_workspace_bytes with variant PIPELINE,
+ * sweeps_per_tile 16, cols_per_block 64) is rejected with GB_ERR_WORKSPACE
+ * before anything is launched (n = 16384, nev = 4096 needs 256.25 KiB).
+ * The first call on a device looks the array's address up on that device
+ * (make it before any stream capture).  All calls share the array and it
+ * keeps the last call's contents; each call clears what must start at zero,
+ * and calls whose device work overlaps on the GPU race on it.
+ * status (argument 8) may be NULL, or a device or pinned-host int that
+ * receives, in stream order after the kernel, 0 or GB_ERR_TIMEOUT (a
+ * dependency wait gave up; Z is then unspecified).  stream (argument 9): the
+ * call is asynchronous on it.  Allocates nothing. */
+#define GB_NOALLOC_SCRATCH_BYTES (1 << 20)
+int gb_trans_ev_tridi_to_band_d_noalloc(int n, int nbw, int nev, const double *hh_v,
+                                        const double *hh_tau, double *Z, int ldz,
+                                        int *status, void *stream);
+
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);
 

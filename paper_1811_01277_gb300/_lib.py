@@ -26,7 +26,9 @@ EXPORTS = (
     "gb_trans_ev_tridi_to_band_d", "gb_trans_ev_tridi_to_band_z",
     "gb_trans_ev_host_buffer_bytes", "gb_trans_ev_tridi_to_band_d_host",
     "gb_trans_ev_launch_count", "gb_status_string", "gb_trans_ev_query",
+    "gb_trans_ev_tridi_to_band_d_noalloc",
 )
+GB_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 
 class gb_trans_ev_opts(ctypes.Structure):
@@ -71,6 +73,8 @@ def load(path=None):
     L.gb_trans_ev_launch_count.argtypes = [i, i, i, i, po]; L.gb_trans_ev_launch_count.restype = ll
     L.gb_status_string.argtypes = [i]; L.gb_status_string.restype = ctypes.c_char_p
     L.gb_trans_ev_query.argtypes = [p, sz, p]; L.gb_trans_ev_query.restype = i
+    L.gb_trans_ev_tridi_to_band_d_noalloc.argtypes = [i, i, i, p, p, p, i, p, p]
+    L.gb_trans_ev_tridi_to_band_d_noalloc.restype = i
     _lib = L
     return L
 
@@ -156,6 +160,17 @@ def gb_trans_ev_launch_count(n, nbw, nev, is_complex=0, opts=None):
 
 def gb_trans_ev_query(workspace=None, ws_bytes=0, stream=None):
     return load().gb_trans_ev_query(_p(workspace), ws_bytes, _stream(stream))
+
+
+def gb_trans_ev_tridi_to_band_d_noalloc(n, nbw, nev, hh_v, hh_tau, Z, ldz, status=None, stream=None,
+                                        check=True):
+    """No-allocation form for callers that cannot allocate device memory
+    (scratch in a fixed device array of GB_NOALLOC_SCRATCH_BYTES)."""
+    rc = load().gb_trans_ev_tridi_to_band_d_noalloc(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
+                                                    _p(status), _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_trans_ev_tridi_to_band_d_noalloc")
+    return rc
 
 
 def gb_status_string(status):
