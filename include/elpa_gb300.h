@@ -155,6 +155,24 @@ int gb_trans_ev_tridi_to_band_d_noalloc(int n, int nbw, int nev, const double *h
                                         const double *hh_tau, double *Z, int ldz,
                                         int *status, void *stream);
 
+/* Band -> tridiagonal reduction by bulge chasing (the second step of the
+ * two-stage reduction, Sec. 2), producing the reflectors that
+ * gb_trans_ev_tridi_to_band_d consumes.  B is real symmetric with nbw
+ * super-diagonals, given in LAPACK lower band storage: AB[(i-j) + j*ldab] =
+ * B(i,j) for 0 <= i-j <= nbw (device pointer, not modified).  Outputs
+ * (device pointers, caller-owned): d (n) and e (n-1), the diagonal and
+ * sub-diagonal of T = Q2^T B Q2; hh_v (gb_hh_count * nbw) and hh_tau
+ * (gb_hh_count) in the layout above (hh_v[idx*nbw] = 1, zero padding past
+ * len).  Arguments: 1 n >= 1; 2 nbw in 1..64; 3 AB; 4 ldab >= nbw+1; 5 d;
+ * 6 e; 7 hh_v; 8 hh_tau; 9 workspace (256-byte aligned); 10 ws_bytes >=
+ * gb_band_to_tridi_workspace_bytes(n, nbw); 11 stream.  Asynchronous;
+ * device-side status (a dependency wait that gave up after 10 s) through
+ * gb_trans_ev_query(workspace, ws_bytes, stream). */
+size_t gb_band_to_tridi_workspace_bytes(int n, int nbw);
+int gb_band_to_tridi_d(int n, int nbw, const double *AB, int ldab, double *d, double *e,
+                       double *hh_v, double *hh_tau, void *workspace, size_t ws_bytes,
+                       void *stream);
+
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);
 

@@ -26,7 +26,7 @@ EXPORTS = (
     "gb_trans_ev_tridi_to_band_d", "gb_trans_ev_tridi_to_band_z",
     "gb_trans_ev_host_buffer_bytes", "gb_trans_ev_tridi_to_band_d_host",
     "gb_trans_ev_launch_count", "gb_status_string", "gb_trans_ev_query",
-    "gb_trans_ev_tridi_to_band_d_noalloc",
+    "gb_trans_ev_tridi_to_band_d_noalloc", "gb_band_to_tridi_workspace_bytes", "gb_band_to_tridi_d",
 )
 GB_NOALLOC_SCRATCH_BYTES = 1 << 20
 
@@ -75,6 +75,8 @@ def load(path=None):
     L.gb_trans_ev_query.argtypes = [p, sz, p]; L.gb_trans_ev_query.restype = i
     L.gb_trans_ev_tridi_to_band_d_noalloc.argtypes = [i, i, i, p, p, p, i, p, p]
     L.gb_trans_ev_tridi_to_band_d_noalloc.restype = i
+    L.gb_band_to_tridi_workspace_bytes.argtypes = [i, i]; L.gb_band_to_tridi_workspace_bytes.restype = sz
+    L.gb_band_to_tridi_d.argtypes = [i, i, p, i, p, p, p, p, p, sz, p]; L.gb_band_to_tridi_d.restype = i
     _lib = L
     return L
 
@@ -170,6 +172,18 @@ def gb_trans_ev_tridi_to_band_d_noalloc(n, nbw, nev, hh_v, hh_tau, Z, ldz, statu
                                                     _p(status), _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_trans_ev_tridi_to_band_d_noalloc")
+    return rc
+
+
+def gb_band_to_tridi_workspace_bytes(n, nbw):
+    return load().gb_band_to_tridi_workspace_bytes(n, nbw)
+
+
+def gb_band_to_tridi_d(n, nbw, AB, ldab, d, e, hh_v, hh_tau, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_band_to_tridi_d(n, nbw, _p(AB), ldab, _p(d), _p(e), _p(hh_v), _p(hh_tau), _p(workspace),
+                                   ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_band_to_tridi_d")
     return rc
 
 

@@ -44,6 +44,10 @@ cudaError_t wavefront_smem_d(int n, int b, int nev, const double *hh_v, const do
                              long long ldz, int nb, int threads, cudaStream_t st);
 size_t wavefront_smem_bytes(int b, int nb, int threads, int is_complex);
 
+size_t band_to_tridi_workspace_bytes(int n, int b);
+cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
+                            double *hh_tau, void *ws, size_t ws_bytes, long long timeout_ns, cudaStream_t st);
+
 size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads);
 bool pipeline_supported(int b);
 cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
