@@ -43,11 +43,19 @@ def algorithmic_flops(n, nev, cplx=False):
     return (16 if cplx else 4) * nev * n * (n - 1) // 2
 
 
-def kernel_sources_sha1():
+KERNEL_SOURCES = {
+    "pipeline_d": ["trans_ev_pipeline.cu", "tile_apply.cuh", "layout.cuh"],
+    "wavefront_tile_d": ["trans_ev_wavefront.cu", "tile_apply.cuh", "layout.cuh"],
+}
+
+
+def kernel_sources_sha1(kernel):
+    """Hash of the source files a kernel is compiled from (traffic figures in
+    profiles/ are only reported while this matches)."""
     h = hashlib.sha1()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1811_01277_gb300", "csrc", "*.cu*"))):
-        with open(p, "rb") as f:
-            h.update(f.read())
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1811_01277_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:12]
 
 
@@ -263,8 +271,8 @@ def run_ours(args, wl):
     F = algorithmic_flops(n, nev)
     achieved = F / (ms_per_step / 1e3) / 1e12
     launches = launches_per_call
-    sha = kernel_sources_sha1()
     kernel = "pipeline_d" if variant_name == "pipeline" else "wavefront_tile_d"
+    sha = kernel_sources_sha1(kernel)
     traffic = profile_traffic(kernel, args.workload, variant_name, sha)
 
     # end to end through the host-buffer entry point: H2D of reflectors and Z,
@@ -315,6 +323,80 @@ def run_ours(args, wl):
     return 0
 
 
+def chase_flops(n, b):
+    """Algorithmic flops of the band -> tridiagonal bulge chase, summed over
+    tasks (s,k): left block 4*len*(r-c-1), below block 4*len*rows_below,
+    p = tau*A*v 2*len^2, symmetric rank-2 update 2*len*(len+1); the reflector
+    itself (O(len)) is not counted."""
+    import numpy as np
+    total = 0
+    for s_ in range(1, n):
+        nk = (n - s_ + b - 1) // b
+        k = np.arange(nk)
+        r = s_ + k * b
+        ln = np.minimum(b, n - r)
+        c = np.where(k == 0, s_ - 1, s_ + (k - 1) * b)
+        below = np.minimum(b, np.maximum(n - r - ln, 0))
+        active = ln > 1
+        total += int(np.sum(np.where(active, 4 * ln * (r - c - 1) + 4 * ln * below + 2 * ln * ln + 2 * ln * (ln + 1), 0)))
+    return total
+
+
+def run_stage_band_to_tridi(args):
+    """Time gb_band_to_tridi_d (device bulge chase) on an n x n band matrix
+    with U[-1,1] entries; one JSON line."""
+    import numpy as np
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    from paper_1811_01277_gb300 import inputs
+    gbuild.build()
+    gb.load()
+    n, b = args.chase_n, args.chase_b
+    dev = torch.device("cuda", 0)
+    g = np.random.default_rng(args.chase_n)
+    AB = np.zeros((n, b + 1))                      # row j = column j of the lower band storage
+    AB[:, :] = g.uniform(-1.0, 1.0, (n, b + 1))
+    for dd in range(b + 1):
+        AB[n - dd:, dd] = 0.0
+    AB_d = torch.from_numpy(AB).to(dev)
+    cnt = gb.gb_hh_count(n, b)
+    d = torch.empty(n, dtype=torch.float64, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev)
+    hv = torch.empty(cnt * b, dtype=torch.float64, device=dev)
+    ht = torch.empty(cnt, dtype=torch.float64, device=dev)
+    wsb = gb.gb_band_to_tridi_workspace_bytes(n, b)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        gb.gb_band_to_tridi_d(n, b, AB_d, b + 1, d, e, hv, ht, ws, wsb, st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    status = gb.gb_trans_ev_query(ws, wsb, st)
+    ms = e0.elapsed_time(e1) / args.steps
+    F = chase_flops(n, b)
+    ach = F / (ms / 1e3) / 1e12
+    print(json.dumps({
+        "stage": "band_to_tridi", "metric": f"band->tridiagonal bulge chase, n={n}, nbw={b}",
+        "value": 1e3 / ms, "unit": "reductions/s", "ms_per_step": ms, "steps": args.steps,
+        "warmup": args.warmup, "status": status, "dtype": "f64", "data": "synthetic U[-1,1] band",
+        "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach / FP64_PEAK_TFLOPS, "algorithmic_gflop": F / 1e9},
+        "gpu_launches": 3 * args.steps, "clocks": clocks}))
+    return 0
+
+
 def measure_fp64_peak():
     """Build and run the FP64 microbenchmark (DFMA and f64 mma.sync) with the
     SM clock sampled, and print one JSON line."""
@@ -350,7 +432,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--measure-fp64-peak", action="store_true")
+    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi"], default="trans_ev")
+    ap.add_argument("--chase-n", type=int, default=16384)
+    ap.add_argument("--chase-b", type=int, default=64)
     args = ap.parse_args()
+    if args.stage == "band_to_tridi":
+        return run_stage_band_to_tridi(args)
     if args.measure_fp64_peak:
         return measure_fp64_peak()
     wl = WORKLOADS[args.workload]
