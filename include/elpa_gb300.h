@@ -173,6 +173,34 @@ int gb_band_to_tridi_d(int n, int nbw, const double *AB, int ldab, double *d, do
                        double *hh_v, double *hh_tau, void *workspace, size_t ws_bytes,
                        void *stream);
 
+/* Two-stage symmetric eigensolver (Sec. 2): A = Z diag(ev) Z^T for the nev
+ * smallest eigenvalues of the real symmetric n x n matrix A.
+ *   full -> band (Householder panels; trailing updates as cuBLAS GEMMs),
+ *   band -> tridiagonal (gb_band_to_tridi_d's bulge chase),
+ *   eigenpairs of the tridiagonal (bisection, inverse iteration, one
+ *   Newton-Schulz orthogonalisation step),
+ *   tridiagonal -> band (gb_trans_ev_tridi_to_band_d, pipeline kernel),
+ *   band -> full (block reflectors as cuBLAS GEMMs).
+ * Arguments (device pointers): 1 n >= 2; 2 nev in 1..n; 3 nbw in 1..min(64,
+ * n-1), the intermediate band width; 4 A (column-major, lda; read only, both
+ * triangles used); 5 lda >= n; 6 ev (nev, ascending); 7 Z (n x nev,
+ * column-major); 8 ldz >= n; 9 workspace (256-byte aligned); 10 ws_bytes >=
+ * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0, or
+ * GB_SOLVE_FP64_EMULATED_GEMM to let cuBLAS use its fixed-point FP64
+ * emulation for the GEMMs where it supports it.  Asynchronous; device-side
+ * status of the dependency waits through gb_solve_query. */
+#define GB_SOLVE_FP64_EMULATED_GEMM 1
+size_t gb_solve_workspace_bytes(int n, int nev, int nbw);
+int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
+               void *workspace, size_t ws_bytes, void *stream, int flags);
+/* Synchronises the stream and returns GB_OK or the first device-side error
+ * (GB_ERR_TIMEOUT) of the last gb_solve_d that used this workspace. */
+int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream);
+/* Convenience form with host-side defaults: nbw = min(64, n-1), legacy
+ * default stream, and a workspace it allocates with cudaMalloc and frees
+ * before returning (synchronous).  All pointers are device pointers. */
+int elpa_b200_solve(int n, int nev, const double *A, int lda, double *ev, double *Z, int ldz);
+
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);
 

@@ -8,11 +8,11 @@ seeded input generators; PyTorch only provides device memory and streams.
 """
 from ._lib import (  # noqa: F401
     EXPORTS, GB_ERR_CUDA, GB_ERR_TIMEOUT, GB_ERR_UNSUPPORTED, GB_ERR_WORKSPACE, GB_OK,
-    GB_NOALLOC_SCRATCH_BYTES, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
+    GB_NOALLOC_SCRATCH_BYTES, GB_SOLVE_FP64_EMULATED_GEMM, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
     gb_band_to_tridi_d, gb_band_to_tridi_workspace_bytes, gb_hh_count, gb_hh_index, gb_max_nbw, gb_status_string, gb_trans_ev_host_buffer_bytes,
     gb_trans_ev_launch_count, gb_trans_ev_opts, gb_trans_ev_query, gb_trans_ev_tridi_to_band_d,
     gb_trans_ev_tridi_to_band_d_host, gb_trans_ev_tridi_to_band_d_noalloc, gb_trans_ev_tridi_to_band_z, gb_trans_ev_workspace_bytes,
-    load,
+    elpa_b200_solve, gb_solve_d, gb_solve_query, gb_solve_workspace_bytes, load,
 )
 
 

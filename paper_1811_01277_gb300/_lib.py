@@ -27,7 +27,9 @@ EXPORTS = (
     "gb_trans_ev_host_buffer_bytes", "gb_trans_ev_tridi_to_band_d_host",
     "gb_trans_ev_launch_count", "gb_status_string", "gb_trans_ev_query",
     "gb_trans_ev_tridi_to_band_d_noalloc", "gb_band_to_tridi_workspace_bytes", "gb_band_to_tridi_d",
+    "gb_solve_workspace_bytes", "gb_solve_d", "gb_solve_query", "elpa_b200_solve",
 )
+GB_SOLVE_FP64_EMULATED_GEMM = 1
 GB_NOALLOC_SCRATCH_BYTES = 1 << 20
 
 
@@ -77,6 +79,10 @@ def load(path=None):
     L.gb_trans_ev_tridi_to_band_d_noalloc.restype = i
     L.gb_band_to_tridi_workspace_bytes.argtypes = [i, i]; L.gb_band_to_tridi_workspace_bytes.restype = sz
     L.gb_band_to_tridi_d.argtypes = [i, i, p, i, p, p, p, p, p, sz, p]; L.gb_band_to_tridi_d.restype = i
+    L.gb_solve_workspace_bytes.argtypes = [i, i, i]; L.gb_solve_workspace_bytes.restype = sz
+    L.gb_solve_d.argtypes = [i, i, i, p, i, p, p, i, p, sz, p, i]; L.gb_solve_d.restype = i
+    L.gb_solve_query.argtypes = [p, i, i, i, p]; L.gb_solve_query.restype = i
+    L.elpa_b200_solve.argtypes = [i, i, p, i, p, p, i]; L.elpa_b200_solve.restype = i
     _lib = L
     return L
 
@@ -184,6 +190,29 @@ def gb_band_to_tridi_d(n, nbw, AB, ldab, d, e, hh_v, hh_tau, workspace, ws_bytes
                                    ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_band_to_tridi_d")
+    return rc
+
+
+def gb_solve_workspace_bytes(n, nev, nbw):
+    return load().gb_solve_workspace_bytes(n, nev, nbw)
+
+
+def gb_solve_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream=None, flags=0, check=True):
+    rc = load().gb_solve_d(n, nev, nbw, _p(A), lda, _p(ev), _p(Z), ldz, _p(workspace), ws_bytes,
+                           _stream(stream), flags)
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_d")
+    return rc
+
+
+def gb_solve_query(workspace, n, nev, nbw, stream=None):
+    return load().gb_solve_query(_p(workspace), n, nev, nbw, _stream(stream))
+
+
+def elpa_b200_solve(n, nev, A, lda, ev, Z, ldz, check=True):
+    rc = load().elpa_b200_solve(n, nev, _p(A), lda, _p(ev), _p(Z), ldz)
+    if check and rc != GB_OK:
+        raise GbError(rc, "elpa_b200_solve")
     return rc
 
 

@@ -52,7 +52,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results]
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(NVCC))), "lib64")
+    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + [
+        "-lcublas", "-Xlinker", "-rpath=" + cudalib]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

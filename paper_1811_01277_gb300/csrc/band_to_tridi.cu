@@ -12,8 +12,10 @@
 // The working matrix is kept in lower band storage of width 2b (entries up
 // to 2b-1 below the diagonal, where the bulges live), in a workspace.
 //
-// One block per sweep, sweeps taken by ticket in increasing s; the tasks of
-// a sweep run in order in that block.  Task (s,k) overlaps tasks of sweep
+// A persistent grid (one block per SM) takes sweeps by ticket in increasing
+// s; the tasks of a sweep run in order in the block that took it, each with
+// one round of loads into registers, the reductions, and one round of
+// stores.  Task (s,k) overlaps tasks of sweep
 // s-1 up to k+2, so it waits until sweep s-1 has finished min(k+3, nk(s-1))
 // tasks (progress flags, acquire/release, bounded waits as in the pipeline
 // back-transformation).
@@ -112,137 +114,124 @@ chase_d(int n, int b, Band A, double *__restrict__ hh_v, double *__restrict__ hh
         int *progress, long long timeout_ns)
 {
     __shared__ double v[64];
-    __shared__ double p[64];
+    __shared__ double q[64];
     __shared__ double red[kChaseThreads / 32];
-    __shared__ double s_tau, s_K;
+    __shared__ double s_tau, s_scal;
     __shared__ int s_sweep, s_abort;
     const int tid = threadIdx.x;
+    const int quad = tid >> 2, part = tid & 3;  // 64 quads of 4 lanes; lane 'part' owns rows/cols part+4t
 
-    if (tid == 0) s_sweep = 1 + atomicAdd(&state->ticket, 1);
-    __syncthreads();
-    const int s = s_sweep;
-    const int nk = sweep_count(n, b, s);
-    const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
-    const long long first = sweep_first(n, b, s);
+    for (;;) {  // persistent: sweeps by ticket, in increasing s
+        __syncthreads();
+        if (tid == 0) s_sweep = 1 + atomicAdd(&state->ticket, 1);
+        __syncthreads();
+        const int s = s_sweep;
+        if (s > n - 1) return;
+        const int nk = sweep_count(n, b, s);
+        const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
+        const long long first = sweep_first(n, b, s);
 
-    for (int k = 0; k < nk; k++) {
-        // ---- wait for sweep s-1 to be kLag tasks ahead (bounded)
-        if (tid == 0) {
-            int abort = 0;
-            if (s > 1) {
-                const int need = min(k + kLag, nk_prev);
-                const unsigned long long t0 = now_ns();
-                while (ld_acq(progress + (s - 2)) < need) {
-                    if (*(volatile int *)&state->abort) { abort = 1; break; }
-                    if ((long long)(now_ns() - t0) > timeout_ns) {
-                        atomicExch(&state->error, GB_ERR_TIMEOUT);
-                        atomicExch(&state->abort, 1);
-                        abort = 1;
-                        break;
+        for (int k = 0; k < nk; k++) {
+            // ---- wait for sweep s-1 to be kLag tasks ahead (bounded)
+            if (tid == 0) {
+                int abort = 0;
+                if (s > 1) {
+                    const int need = min(k + kLag, nk_prev);
+                    const unsigned long long t0 = now_ns();
+                    while (ld_acq(progress + (s - 2)) < need) {
+                        if (*(volatile int *)&state->abort) { abort = 1; break; }
+                        if ((long long)(now_ns() - t0) > timeout_ns) {
+                            atomicExch(&state->error, GB_ERR_TIMEOUT);
+                            atomicExch(&state->abort, 1);
+                            abort = 1;
+                            break;
+                        }
+                        __nanosleep(32);
                     }
-                    __nanosleep(64);
+                } else if (*(volatile int *)&state->abort) {
+                    abort = 1;
                 }
-            }
-            s_abort = abort;
-        }
-        __syncthreads();
-        if (s_abort) return;
-
-        const int r = s + k * b;             // 0-based first row of H(s,k)
-        const int len = min(b, n - r);
-        const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
-        const long long idx = first + k;
-
-        // ---- reflector from column c, rows r..r+len-1 (LAPACK form, v_0 = 1)
-        double xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : 0.0;
-        const double ss = block_sum(xi * xi, red);
-        if (tid == 0) {
-            const double alpha = A.get(r, c);
-            double tau = 0.0, scal = 0.0;
-            if (ss != 0.0) {
-                const double nrm = sqrt(alpha * alpha + ss);
-                const double beta = (alpha >= 0.0) ? -nrm : nrm;
-                tau = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
-                *A.at(r, c) = beta;
-            }
-            s_tau = tau;
-            s_K = scal;
-            hh_tau[idx] = tau;
-        }
-        __syncthreads();
-        const double tau = s_tau;
-        if (tid < b) {
-            double vi = 0.0;
-            if (tid == 0) vi = 1.0;
-            else if (tid < len) vi = (tau != 0.0) ? xi * s_K : 0.0;
-            if (tid < len) v[tid] = vi;
-            hh_v[idx * b + tid] = vi;
-            if (tau != 0.0 && tid >= 1 && tid < len) *A.at(r + tid, c) = 0.0;
-        }
-        __syncthreads();
-
-        if (tau != 0.0) {
-            const int quad = tid >> 2, part = tid & 3;  // 64 quads of 4 lanes
-            // Every lane runs the quad reductions (full-mask shuffles); only the
-            // memory accesses are guarded by the activity tests.
-            // ---- left block: columns c+1..r-1, w_j = v^T A[R,j], A[R,j] -= tau v w_j
-            {
-                const bool act = quad < r - c - 1;
-                const int j = c + 1 + quad;
-                double acc = 0.0;
-                if (act)
-                    for (int i = part; i < len; i += 4) acc = fma(v[i], A.get(r + i, j), acc);
-                const double tw = tau * quad_sum(acc);
-                if (act)
-                    for (int i = part; i < len; i += 4) {
-                        double *a = A.at(r + i, j);
-                        *a = fma(-tw, v[i], __ldcg(a));
-                    }
-            }
-            // ---- below block: rows r+len..min(r+len+b,n)-1, y_i = A[i,R] v, A[i,R] -= tau y_i v^T
-            {
-                const int rb = r + len;
-                const bool act = quad < min(b, n - rb);
-                const int i = rb + quad;
-                double acc = 0.0;
-                if (act)
-                    for (int j = part; j < len; j += 4) acc = fma(A.get(i, r + j), v[j], acc);
-                const double ty = tau * quad_sum(acc);
-                if (act)
-                    for (int j = part; j < len; j += 4) {
-                        double *a = A.at(i, r + j);
-                        *a = fma(-ty, v[j], __ldcg(a));
-                    }
-            }
-            // ---- diagonal block: p = tau A v (symmetric, read before any write)
-            {
-                const bool act = quad < len;
-                double acc = 0.0;
-                if (act)
-                    for (int j = part; j < len; j += 4) acc = fma(A.get(r + quad, r + j), v[j], acc);
-                acc = quad_sum(acc);
-                if (act && part == 0) p[quad] = tau * acc;
+                s_abort = abort;
             }
             __syncthreads();
-            double kv = (tid < len) ? v[tid] * p[tid] : 0.0;
-            const double K = 0.5 * tau * block_sum(kv, red);
-            // q = p - K v, A[R,R] -= v q^T + q v^T on the lower triangle
-            const int ntri = len * (len + 1) / 2;
-            for (int e = tid; e < ntri; e += kChaseThreads) {
-                // e -> (i, j), j <= i, row-major over the lower triangle
-                int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // FP32: keep the FP64 pipe free
-                while ((i + 1) * (i + 2) / 2 <= e) i++;
-                while (i * (i + 1) / 2 > e) i--;
-                const int j = e - i * (i + 1) / 2;
-                const double qi = p[i] - K * v[i], qj = p[j] - K * v[j];
-                double *a = A.at(r + i, r + j);
-                *a = __ldcg(a) - v[i] * qj - qi * v[j];
+            if (s_abort) return;
+
+            const int r = s + k * b;   // 0-based first row of H(s,k)
+            const int len = min(b, n - r);
+            const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
+            const int rb = r + len;
+            const int nleft = r - c - 1, nbelow = min(b, n - rb);
+            const long long idx = first + k;
+
+            // ---- one round of loads: the source column and the three blocks
+            const double xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : 0.0;
+            double L[16], Bl[16], D[16];
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const int i = part + 4 * t;
+                L[t] = (quad < nleft && i < len) ? A.get(r + i, c + 1 + quad) : 0.0;
+                Bl[t] = (quad < nbelow && i < len) ? A.get(rb + quad, r + i) : 0.0;
+                D[t] = (quad < len && i < len) ? A.get(r + quad, r + i) : 0.0;
             }
+
+            // ---- reflector from column c (LAPACK form, v_0 = 1)
+            const double ss = block_sum(xi * xi, red);
+            if (tid == 0) {
+                const double alpha = A.get(r, c);
+                double tau = 0.0, scal = 0.0, beta = alpha;
+                if (ss != 0.0) {
+                    const double nrm = sqrt(alpha * alpha + ss);
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    tau = (beta - alpha) / beta;
+                    scal = 1.0 / (alpha - beta);
+                }
+                s_tau = tau;
+                s_scal = scal;
+                hh_tau[idx] = tau;
+                if (tau != 0.0) *A.at(r, c) = beta;
+            }
+            __syncthreads();
+            const double tau = s_tau;
+            const double vt = (tid == 0) ? 1.0 : ((tid < len && tau != 0.0) ? xi * s_scal : 0.0);
+            if (tid < 64) v[tid] = vt;
+            if (tid < b) hh_v[idx * b + tid] = vt;
+            if (tau != 0.0 && tid >= 1 && tid < len) *A.at(r + tid, c) = 0.0;
+            __syncthreads();
+
+            if (tau != 0.0) {
+                // ---- the three reductions (every lane runs the quad shuffles)
+                double al = 0.0, ab = 0.0, ad = 0.0;
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const double vi = v[part + 4 * t];  // v is zero past len
+                    al = fma(vi, L[t], al);
+                    ab = fma(Bl[t], vi, ab);
+                    ad = fma(D[t], vi, ad);
+                }
+                const double tw = tau * quad_sum(al);   // left: tau v^T A[R, j]
+                const double ty = tau * quad_sum(ab);   // below: tau A[i, R] v
+                const double pi = tau * quad_sum(ad);   // diagonal: p_i = tau (A v)_i
+                // K = tau/2 v^T p, q = p - K v
+                const double K = 0.5 * tau * block_sum((part == 0 && quad < len) ? v[quad] * pi : 0.0, red);
+                if (part == 0 && quad < len) q[quad] = pi - K * v[quad];
+                __syncthreads();
+                const double vq = v[quad], qq = (quad < len) ? q[quad] : 0.0;
+                // ---- updates from registers, one store each
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int i = part + 4 * t;
+                    if (i < len) {
+                        const double vi = v[i];
+                        if (quad < nleft) *A.at(r + i, c + 1 + quad) = fma(-tw, vi, L[t]);
+                        if (quad < nbelow) *A.at(rb + quad, r + i) = fma(-ty, vi, Bl[t]);
+                        if (quad < len && i <= quad) *A.at(r + quad, r + i) = D[t] - vq * q[i] - qq * vi;
+                    }
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_rel(progress + (s - 1), k + 1);
         }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) st_rel(progress + (s - 1), k + 1);
     }
 }
 
@@ -270,8 +259,12 @@ cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d,
     band_init<<<1024, 256, 0, st>>>(n, b, AB, ldab, W, ldw);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (n > 1) {
-        chase_d<<<(unsigned)(n - 1), kChaseThreads, 0, st>>>(n, b, Band{W, ldw}, hh_v, hh_tau,
-                                                            (ChaseState *)flags, (int *)(flags + 256), timeout_ns);
+        int dev = 0, sms = 0;
+        if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+        const int grid = min(n - 1, sms);  // one persistent block per SM
+        chase_d<<<(unsigned)grid, kChaseThreads, 0, st>>>(n, b, Band{W, ldw}, hh_v, hh_tau, (ChaseState *)flags,
+                                                         (int *)(flags + 256), timeout_ns);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     band_extract<<<64, 256, 0, st>>>(n, W, ldw, d, e);

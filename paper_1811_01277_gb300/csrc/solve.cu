@@ -1,0 +1,227 @@
+// Two-stage symmetric eigensolver on one GPU (Sec. 2): full -> band ->
+// tridiagonal -> eigenpairs of T -> back-transformation to band
+// (trans_ev_tridi_to_band) -> back-transformation to full.
+//
+//   full -> band   panel p (columns j..j+b-1): Householder QR of A[j+b:, j:j+b]
+//                  (panel kernels), block reflector Q_p = I - Y T Y^T, and the
+//                  two-sided trailing update A2 <- Q_p^T A2 Q_p as GEMMs:
+//                  X = A2 (Y T), M = T^T (Y^T X), W = X - Y M / 2,
+//                  A2 -= W Y^T + Y W^T   (the whole symmetric matrix is kept)
+//   band -> tri    gb::band_to_tridi_d (bulge chasing)
+//   tridiagonal    gb::tridiag_eig_d (bisection + inverse iteration) and one
+//                  Newton-Schulz step Z <- Z (3I - Z^T Z)/2
+//   tri -> band    the pipeline trans_ev_tridi_to_band kernel
+//   band -> full   Z <- Q_0 Q_1 ... Q_{P-1} Z, last panel first:
+//                  Z_p -= Y (T (Y^T Z_p))
+// The plain GEMMs run in cuBLAS; everything else in this library's kernels.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "elpa_gb300.h"
+#include "layout.cuh"
+#include "trans_ev_kernels.cuh"
+
+namespace gb {
+
+int panel_chunks(int m);
+cudaError_t panel_qr(int m, int nb, double *P, long long lda, double *tau, double *part, cudaStream_t st);
+cudaError_t panel_y_and_t_prep(int m, int nb, const double *P, long long lda, double *Y, long long ldy,
+                               cudaStream_t st);
+cudaError_t panel_t(int nb, const double *G, long long ldg, const double *tau, double *T, long long ldt,
+                    cudaStream_t st);
+cudaError_t newton_schulz_matrix(int k, double *G, long long ldg, cudaStream_t st);
+cudaError_t band_from_full(int n, int b, const double *A, long long lda, double *AB, long long ldab, cudaStream_t st);
+size_t tridiag_eig_workspace_bytes(int n, int nev);
+cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, double *lam, double *Z, long long ldz,
+                          void *ws, cudaStream_t st);
+
+}  // namespace gb
+
+namespace {
+
+constexpr int kMaxDev = 64;
+std::mutex g_blas_mutex;
+cublasHandle_t g_blas[kMaxDev] = {nullptr};
+
+cublasHandle_t blas_handle()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
+    return g_blas[dev];
+}
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace carve-up (all pieces 256-byte aligned).
+struct SolveWs {
+    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2;
+    void *chase, *eig, *tev;
+    size_t chase_bytes, tev_bytes, total;
+};
+
+SolveWs carve(int n, int nev, int b, char *base)
+{
+    SolveWs w{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += a256(bytes);
+        return p;
+    };
+    const size_t P = (size_t)(n + b - 1) / b;
+    const size_t cnt = (size_t)gb::hh_total(n, b);
+    const size_t nch = (size_t)gb::panel_chunks(n);
+    w.Aw = (double *)take((size_t)n * n * 8);
+    w.tauP = (double *)take(P * b * 8);
+    w.Tall = (double *)take(P * b * b * 8);
+    w.Y = (double *)take((size_t)n * b * 8);
+    w.YT = (double *)take((size_t)n * b * 8);
+    w.X = (double *)take((size_t)n * b * 8);
+    w.Pm = (double *)take((size_t)b * b * 8);
+    w.M = (double *)take((size_t)b * b * 8);
+    w.G = (double *)take((size_t)b * b * 8);
+    w.part = (double *)take((2 * nch + 64 * nch) * 8);
+    w.AB = (double *)take((size_t)(b + 1) * n * 8);
+    w.d = (double *)take((size_t)n * 8);
+    w.e = (double *)take((size_t)n * 8);
+    w.hv = (double *)take((cnt ? cnt : 1) * b * 8);
+    w.ht = (double *)take((cnt ? cnt : 1) * 8);
+    w.Ztri = (double *)take((size_t)n * nev * 8);
+    w.Gns = (double *)take((size_t)nev * nev * 8);
+    w.S = (double *)take((size_t)b * nev * 8);
+    w.S2 = (double *)take((size_t)b * nev * 8);
+    w.chase_bytes = gb::band_to_tridi_workspace_bytes(n, b);
+    w.chase = take(w.chase_bytes);
+    w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
+    w.tev_bytes = gb_trans_ev_workspace_bytes(n, b, nev, 0, nullptr);
+    w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
+    w.total = off;
+    return w;
+}
+
+#define GB_CU(x)                                     \
+    do {                                             \
+        if ((x) != cudaSuccess) return GB_ERR_CUDA;  \
+    } while (0)
+#define GB_BL(x)                                               \
+    do {                                                       \
+        if ((x) != CUBLAS_STATUS_SUCCESS) return GB_ERR_CUDA;  \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+size_t gb_solve_workspace_bytes(int n, int nev, int nbw)
+{
+    if (n < 2 || nev < 1 || nev > n || nbw < 1 || nbw > 64 || nbw >= n) return 0;
+    return carve(n, nev, nbw, nullptr).total;
+}
+
+int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
+               size_t ws_bytes, void *stream, int flags)
+{
+    if (n < 2) return -1;
+    if (nev < 1 || nev > n) return -2;
+    if (nbw < 1 || nbw > 64 || nbw >= n) return -3;
+    if (!A || ((uintptr_t)A % 8) != 0) return -4;
+    if (lda < n) return -5;
+    if (!ev || ((uintptr_t)ev % 8) != 0) return -6;
+    if (!Z || ((uintptr_t)Z % 8) != 0) return -7;
+    if (ldz < n) return -8;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
+    const int b = nbw;
+    SolveWs w = carve(n, nev, b, (char *)workspace);
+    if (ws_bytes < w.total) return -10;
+    if (flags & ~GB_SOLVE_FP64_EMULATED_GEMM) return -12;
+    cudaStream_t st = (cudaStream_t)stream;
+    cublasHandle_t h = blas_handle();
+    if (!h) return GB_ERR_CUDA;
+    GB_BL(cublasSetStream(h, st));
+    GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
+                                                                       : CUBLAS_DEFAULT_MATH));
+    const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5;
+    const long long ldw = n;
+
+    // ---- full -> band
+    GB_CU(cudaMemcpy2DAsync(w.Aw, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice, st));
+    int P = 0;
+    for (int j = 0; j + b < n; j += b, P++) {
+        const int m = n - j - b;
+        double *panel = w.Aw + (long long)j * ldw + (j + b);
+        double *A2 = w.Aw + (long long)(j + b) * ldw + (j + b);
+        double *tau = w.tauP + (long long)P * b;
+        double *T = w.Tall + (long long)P * b * b;
+        GB_CU(gb::panel_qr(m, b, panel, ldw, tau, w.part, st));
+        GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, m, &one, w.Y, m, w.Y, m, &zero, w.G, b));
+        GB_CU(gb::panel_t(b, w.G, b, tau, T, b, st));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &one, w.Y, m, T, b, &zero, w.YT, m));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, m, &one, A2, ldw, w.YT, m, &zero, w.X, m));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, m, &one, w.Y, m, w.X, m, &zero, w.Pm, b));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, b, &one, T, b, w.Pm, b, &zero, w.M, b));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &mhalf, w.Y, m, w.M, b, &one, w.X, m));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, m, m, b, &mone, w.X, m, w.Y, m, &one, A2, ldw));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, m, m, b, &mone, w.Y, m, w.X, m, &one, A2, ldw));
+    }
+    GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
+
+    // ---- band -> tridiagonal
+    GB_CU(gb::band_to_tridi_d(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, w.chase_bytes,
+                              10LL * 1000 * 1000 * 1000, st));
+
+    // ---- eigenpairs of T, then one Newton-Schulz orthogonalisation step into Z
+    GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
+    GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nev, nev, n, &one, w.Ztri, n, w.Ztri, n, &zero, w.Gns, nev));
+    GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
+    GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, nev, nev, &one, w.Ztri, n, w.Gns, nev, &zero, Z, ldz));
+
+    // ---- tridiagonal -> band (the hot path)
+    int rc = gb_trans_ev_tridi_to_band_d(n, b, nev, w.hv, w.ht, Z, ldz, w.tev, w.tev_bytes, stream, nullptr);
+    if (rc != GB_OK) return rc;
+
+    // ---- band -> full, last panel first
+    for (int p = P - 1; p >= 0; p--) {
+        const int j = p * b, m = n - j - b;
+        const double *panel = w.Aw + (long long)j * ldw + (j + b);
+        const double *T = w.Tall + (long long)p * b * b;
+        double *Zr = Z + (j + b);
+        GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, nev, m, &one, w.Y, m, Zr, ldz, &zero, w.S, b));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, w.S, b, &zero, w.S2, b));
+        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, w.Y, m, w.S2, b, &one, Zr, ldz));
+    }
+    GB_CU(cudaGetLastError());
+    return GB_OK;
+}
+
+int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream)
+{
+    if (!workspace) return -1;
+    SolveWs w = carve(n, nev, nbw, (char *)workspace);
+    int rc = gb_trans_ev_query(w.chase, w.chase_bytes, stream);
+    if (rc != GB_OK) return rc;
+    return gb_trans_ev_query(w.tev, w.tev_bytes, stream);
+}
+
+int elpa_b200_solve(int n, int nev, const double *A, int lda, double *ev, double *Z, int ldz)
+{
+    const int nbw = n > 64 ? 64 : (n > 1 ? n - 1 : 1);
+    size_t bytes = gb_solve_workspace_bytes(n, nev, nbw);
+    if (bytes == 0) return n < 2 ? -1 : -2;
+    void *ws = nullptr;
+    if (cudaMalloc(&ws, bytes) != cudaSuccess) return GB_ERR_WORKSPACE;
+    int rc = gb_solve_d(n, nev, nbw, A, lda, ev, Z, ldz, ws, bytes, nullptr, 0);
+    if (rc == GB_OK) rc = gb_solve_query(ws, n, nev, nbw, nullptr);
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(ws);
+    if (rc == GB_OK && e != cudaSuccess) rc = GB_ERR_CUDA;
+    return rc;
+}
+
+}  // extern "C"

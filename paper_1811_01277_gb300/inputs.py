@@ -101,3 +101,32 @@ def synthetic_reflectors(n, b, seed, cplx=False):
     else:
         tau = 2.0 / nrm2
     return np.ascontiguousarray(V.reshape(-1)), np.ascontiguousarray(tau)
+
+
+def clustered_spectrum(n, seed, lo_exp=-3.0, hi=50.0, cluster_frac=0.1, cluster_size=8, width=1e-8):
+    """Eigenvalues in [-hi, hi]: magnitudes 10^U[lo_exp, log10(hi)] with random
+    signs, and cluster_frac of them in clusters of cluster_size spread over
+    `width` around centres drawn the same way.  Sorted ascending."""
+    g = _rng(seed + 31337)
+    ncl = int(round(n * cluster_frac / cluster_size))
+    nfree = n - ncl * cluster_size
+
+    def draw(k):
+        mag = 10.0 ** g.uniform(lo_exp, np.log10(hi), k)
+        return mag * np.where(g.uniform(size=k) < 0.5, -1.0, 1.0)
+
+    lam = list(draw(nfree))
+    for c in draw(ncl):
+        lam.extend(c + np.linspace(-0.5 * width, 0.5 * width, cluster_size))
+    return np.sort(np.array(lam[:n]))
+
+
+def symmetric_with_spectrum(lam, seed):
+    """A = Q diag(lam) Q^T with Q Haar-distributed (QR of a Gaussian matrix,
+    signs fixed by R's diagonal); exactly symmetric."""
+    n = len(lam)
+    g = _rng(seed + 271828)
+    Q, R = np.linalg.qr(g.standard_normal((n, n)))
+    Q = Q * np.sign(np.diag(R))[None, :]
+    A = (Q * lam[None, :]) @ Q.T
+    return np.asfortranarray(0.5 * (A + A.T))

@@ -26,7 +26,7 @@ def declared_functions():
         if f.endswith(".h"):
             src = open(os.path.join(inc, f)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"\b(gb_\w+)\s*\(", src)
+            names += re.findall(r"\b((?:gb|elpa)_\w+)\s*\(", src)
     return sorted(set(names))
 
 
