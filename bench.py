@@ -234,14 +234,40 @@ def run_ours(args, wl):
     opts = {"variant": args.variant, "sweeps_per_tile": args.nb, "cols_per_block": args.threads}
     if args.variant == 0 and args.nb == 0 and args.threads == 0:
         opts = None  # the library's default choice
-    launches_per_call = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
-    variant_name = "pipeline" if launches_per_call == 1 else "wavefront"
 
     hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024 + 1000 * rank)
     Z = inputs.z_gaussian(n, nev, seed=2025 + 1000 * rank)
     hv_d = torch.from_numpy(hv).to(dev)
     ht_d = torch.from_numpy(ht).to(dev)
     Z_d = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)  # (nev, n) row-major = column-major Z
+    tuned = None
+    if args.autotune:
+        # the paper's on-the-fly autotuning: one back-transformation per setting
+        level = gb.GB_AUTOTUNE_MEDIUM if args.autotune == "medium" else gb.GB_AUTOTUNE_FAST
+        t = gb.gb_autotune_create(level, n, nbw, nev)
+        st0 = torch.cuda.current_stream(dev)
+        trials = []
+        while True:
+            o = gb.gb_autotune_step(t)
+            if o is None:
+                break
+            wsb0 = gb.gb_trans_ev_workspace_bytes(n, nbw, nev, 0, o)
+            ws0 = torch.zeros(max(wsb0, 256), dtype=torch.uint8, device=dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(st0)
+            gb.gb_trans_ev_tridi_to_band_d(n, nbw, nev, hv_d, ht_d, Z_d, n, ws0, wsb0, st0, o)
+            a1.record(st0)
+            torch.cuda.synchronize(dev)
+            sec = a0.elapsed_time(a1) / 1e3
+            gb.gb_autotune_report(t, sec)
+            trials.append({"variant": o.variant, "nb": o.sweeps_per_tile, "cols": o.cols_per_block, "s": sec})
+        best, _ = gb.gb_autotune_best(t)
+        gb.gb_autotune_destroy(t)
+        opts = {"variant": best.variant, "sweeps_per_tile": best.sweeps_per_tile,
+                "cols_per_block": best.cols_per_block}
+        tuned = {"level": args.autotune, "chosen": opts, "trials": trials}
+    launches_per_call = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
+    variant_name = "pipeline" if launches_per_call == 1 else "wavefront"
     wsb = gb.gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts)
     ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -319,6 +345,8 @@ def run_ours(args, wl):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches) * args.steps,
             "clocks": clocks, "kernel_sources_sha1": sha,
         }
+        if tuned:
+            line["autotune"] = tuned
         print(json.dumps(line))
     return 0
 
@@ -474,6 +502,64 @@ def run_stage_solve(args):
     return 0
 
 
+def run_stage_batched(args):
+    """Many independent problems (sizes U[lo, hi], N(0,1) entries symmetrised,
+    all eigenpairs) through gb_solve_batched_d on several streams: solves/s
+    over the whole batch and p50/p99 of the per-solve times."""
+    import numpy as np
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    gbuild.build()
+    gb.load()
+    dev = torch.device("cuda", 0)
+    g = np.random.default_rng(512)
+    sizes = [int(x) for x in g.integers(args.batch_lo, args.batch_hi + 1, args.batch_count)]
+    gen = torch.Generator(device=dev).manual_seed(513)
+    A = []
+    for n in sizes:
+        R = torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64)
+        A.append(0.5 * (R + R.T))
+    ev = [torch.zeros(n, dtype=torch.float64, device=dev) for n in sizes]
+    Z = [torch.zeros((n, n), dtype=torch.float64, device=dev) for n in sizes]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(args.batch_streams)]
+    wsb = gb.gb_solve_batched_workspace_bytes(sizes, sizes, len(streams))
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    es = [torch.cuda.Event(enable_timing=True) for _ in sizes]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in sizes]
+
+    def batch(events):
+        gb.gb_solve_batched_d(sizes, sizes, A, sizes, ev, Z, sizes, ws, wsb, streams,
+                              es if events else None, ee if events else None)
+
+    for _ in range(args.warmup):
+        batch(False)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        batch(True)
+    torch.cuda.synchronize(dev)
+    el = time.perf_counter() - t0
+    clocks = sampler.stop()
+    per = np.array([a.elapsed_time(b) for a, b in zip(es, ee)])   # last batch, ms
+    # accuracy on a few problems
+    worst = 0.0
+    for i in range(0, len(sizes), max(1, len(sizes) // 8)):
+        n = sizes[i]
+        Zi = Z[i].T
+        r = torch.linalg.norm(A[i] @ Zi - Zi * ev[i][None, :]) / torch.linalg.norm(A[i])
+        o = (Zi.T @ Zi - torch.eye(n, dtype=torch.float64, device=dev)).abs().max()
+        worst = max(worst, float(r) / (50 * n * 2.0 ** -53), float(o) / (50 * n * 2.0 ** -53))
+    print(json.dumps({
+        "stage": "batched", "metric": f"batched eigensolves/s, {len(sizes)} problems n~U[{args.batch_lo},{args.batch_hi}], all eigenpairs",
+        "value": args.steps * len(sizes) / el, "unit": "solves/s", "seconds_per_batch": el / args.steps,
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "streams": len(streams), "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+        "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks}))
+    return 0
+
+
 def measure_fp64_peak():
     """Build and run the FP64 microbenchmark (DFMA and f64 mma.sync) with the
     SM clock sampled, and print one JSON line."""
@@ -508,8 +594,14 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="columns per block (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
+                    help="walk the autotuner first and time its fastest setting")
     ap.add_argument("--measure-fp64-peak", action="store_true")
-    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve"], default="trans_ev")
+    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve", "batched"], default="trans_ev")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-lo", type=int, default=128)
+    ap.add_argument("--batch-hi", type=int, default=2048)
+    ap.add_argument("--batch-streams", type=int, default=8)
     ap.add_argument("--solve-n", type=int, default=16384)
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
@@ -520,6 +612,8 @@ def main():
         return run_stage_band_to_tridi(args)
     if args.stage == "solve":
         return run_stage_solve(args)
+    if args.stage == "batched":
+        return run_stage_batched(args)
     if args.measure_fp64_peak:
         return measure_fp64_peak()
     wl = WORKLOADS[args.workload]

@@ -201,6 +201,51 @@ int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream)
  * before returning (synchronous).  All pointers are device pointers. */
 int elpa_b200_solve(int n, int nev, const double *A, int lda, double *ev, double *Z, int ldz);
 
+/* Batched form: count independent problems (A[i] n[i] x n[i], lda[i]; ev[i],
+ * Z[i] n[i] x nev[i], ldz[i]; all device pointers), each with band width
+ * gb_solve_default_nbw(n[i]).  Problem i runs on streams[i % nslots] in
+ * workspace slot i % nslots, so up to nslots solves overlap on the GPU; the
+ * host only enqueues (asynchronous).  If ev_start / ev_end are non-NULL,
+ * events ev_start[i] / ev_end[i] (cudaEvent_t, created by the caller) are
+ * recorded around problem i on its stream.  Arguments: 1 count >= 1; 2-8 the
+ * per-problem arrays; 9 workspace (256-byte aligned); 10 ws_bytes >=
+ * gb_solve_batched_workspace_bytes(count, n, nev, nslots); 11 nslots >= 1;
+ * 12 streams (nslots cudaStream_t); 13-14 event arrays or NULL. */
+int gb_solve_default_nbw(int n);
+size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev, int nslots);
+int gb_solve_batched_d(int count, const int *n, const int *nev, const double *const *A, const int *lda,
+                       double *const *ev, double *const *Z, const int *ldz, void *workspace,
+                       size_t ws_bytes, int nslots, void *const *streams, void *const *ev_start,
+                       void *const *ev_end);
+
+/* Autotuning of the back-transformation (modelled on the paper's autotuning,
+ * Sec. 4.3 and 5.3): a tuning object walks a fixed list of settings; the
+ * caller runs one back-transformation (or one solve) with each setting it
+ * is handed and reports the elapsed seconds; the fastest is kept.  The walk
+ * can be saved to a text file and resumed, so it can be spread over the
+ * iterations of a self-consistency loop.  Host-side only.
+ *   GB_AUTOTUNE_FAST   : kernel variant (wavefront, pipeline)
+ *   GB_AUTOTUNE_MEDIUM : variant and blocking (sweeps per tile, columns per block)
+ * gb_autotune_create returns NULL for invalid arguments.  gb_autotune_step
+ * returns 1 and fills *next with the setting to try, 0 when every setting has
+ * been handed out, -1 while the previous one is still unreported.
+ * gb_autotune_report records the seconds of the last setting handed out.
+ * gb_autotune_best returns GB_OK with the fastest measured setting (and its
+ * seconds if non-NULL) or GB_ERR_UNSUPPORTED if none has been measured.
+ * gb_autotune_save/_load write and read the state (a setting handed out but
+ * not reported is handed out again after loading). */
+#define GB_AUTOTUNE_FAST 1
+#define GB_AUTOTUNE_MEDIUM 2
+typedef struct gb_autotune gb_autotune;
+gb_autotune *gb_autotune_create(int level, int n, int nbw, int nev);
+void gb_autotune_destroy(gb_autotune *t);
+int gb_autotune_step(gb_autotune *t, gb_trans_ev_opts *next);
+int gb_autotune_report(gb_autotune *t, double seconds);
+int gb_autotune_best(const gb_autotune *t, gb_trans_ev_opts *best, double *seconds);
+int gb_autotune_progress(const gb_autotune *t, int *tried, int *total);
+int gb_autotune_save(const gb_autotune *t, const char *path);
+gb_autotune *gb_autotune_load(const char *path);
+
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);
 

@@ -28,7 +28,12 @@ EXPORTS = (
     "gb_trans_ev_launch_count", "gb_status_string", "gb_trans_ev_query",
     "gb_trans_ev_tridi_to_band_d_noalloc", "gb_band_to_tridi_workspace_bytes", "gb_band_to_tridi_d",
     "gb_solve_workspace_bytes", "gb_solve_d", "gb_solve_query", "elpa_b200_solve",
+    "gb_autotune_create", "gb_autotune_destroy", "gb_autotune_step", "gb_autotune_report",
+    "gb_autotune_best", "gb_autotune_progress", "gb_autotune_save", "gb_autotune_load",
+    "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d",
 )
+GB_AUTOTUNE_FAST = 1
+GB_AUTOTUNE_MEDIUM = 2
 GB_SOLVE_FP64_EMULATED_GEMM = 1
 GB_NOALLOC_SCRATCH_BYTES = 1 << 20
 
@@ -83,6 +88,22 @@ def load(path=None):
     L.gb_solve_d.argtypes = [i, i, i, p, i, p, p, i, p, sz, p, i]; L.gb_solve_d.restype = i
     L.gb_solve_query.argtypes = [p, i, i, i, p]; L.gb_solve_query.restype = i
     L.elpa_b200_solve.argtypes = [i, i, p, i, p, p, i]; L.elpa_b200_solve.restype = i
+    L.gb_autotune_create.argtypes = [i, i, i, i]; L.gb_autotune_create.restype = p
+    L.gb_autotune_destroy.argtypes = [p]; L.gb_autotune_destroy.restype = None
+    L.gb_autotune_step.argtypes = [p, po]; L.gb_autotune_step.restype = i
+    L.gb_autotune_report.argtypes = [p, ctypes.c_double]; L.gb_autotune_report.restype = i
+    L.gb_autotune_best.argtypes = [p, po, ctypes.POINTER(ctypes.c_double)]; L.gb_autotune_best.restype = i
+    L.gb_autotune_progress.argtypes = [p, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.gb_autotune_progress.restype = i
+    L.gb_autotune_save.argtypes = [p, ctypes.c_char_p]; L.gb_autotune_save.restype = i
+    L.gb_autotune_load.argtypes = [ctypes.c_char_p]; L.gb_autotune_load.restype = p
+    L.gb_solve_default_nbw.argtypes = [i]; L.gb_solve_default_nbw.restype = i
+    pi_ = ctypes.POINTER(ctypes.c_int)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.gb_solve_batched_workspace_bytes.argtypes = [i, pi_, pi_, i]
+    L.gb_solve_batched_workspace_bytes.restype = sz
+    L.gb_solve_batched_d.argtypes = [i, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
+    L.gb_solve_batched_d.restype = i
     _lib = L
     return L
 
@@ -213,6 +234,84 @@ def elpa_b200_solve(n, nev, A, lda, ev, Z, ldz, check=True):
     rc = load().elpa_b200_solve(n, nev, _p(A), lda, _p(ev), _p(Z), ldz)
     if check and rc != GB_OK:
         raise GbError(rc, "elpa_b200_solve")
+    return rc
+
+
+def gb_autotune_create(level, n, nbw, nev):
+    return load().gb_autotune_create(level, n, nbw, nev)
+
+
+def gb_autotune_destroy(t):
+    load().gb_autotune_destroy(t)
+
+
+def gb_autotune_step(t):
+    """Returns the next setting to try (a gb_trans_ev_opts) or None when done."""
+    o = gb_trans_ev_opts()
+    rc = load().gb_autotune_step(t, ctypes.byref(o))
+    if rc < 0:
+        raise GbError(rc, "gb_autotune_step")
+    return o if rc == 1 else None
+
+
+def gb_autotune_report(t, seconds):
+    return load().gb_autotune_report(t, seconds)
+
+
+def gb_autotune_best(t):
+    o = gb_trans_ev_opts()
+    s = ctypes.c_double()
+    rc = load().gb_autotune_best(t, ctypes.byref(o), ctypes.byref(s))
+    return (o, s.value) if rc == GB_OK else (None, None)
+
+
+def gb_autotune_progress(t):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    load().gb_autotune_progress(t, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def gb_autotune_save(t, path):
+    return load().gb_autotune_save(t, os.fsencode(path))
+
+
+def gb_autotune_load(path):
+    return load().gb_autotune_load(os.fsencode(path))
+
+
+def gb_solve_default_nbw(n):
+    return load().gb_solve_default_nbw(n)
+
+
+def _iarr(xs):
+    return (ctypes.c_int * len(xs))(*[int(x) for x in xs])
+
+
+def _parr(xs):
+    return (ctypes.c_void_p * len(xs))(*[_p(x) if x is not None else None for x in xs])
+
+
+def gb_solve_batched_workspace_bytes(n, nev, nslots):
+    return load().gb_solve_batched_workspace_bytes(len(n), _iarr(n), _iarr(nev), nslots)
+
+
+def gb_solve_batched_d(n, nev, A, lda, ev, Z, ldz, workspace, ws_bytes, streams, ev_start=None, ev_end=None,
+                       check=True):
+    """Lists of per-problem sizes and device buffers; streams / events are
+    torch.cuda.Stream / torch.cuda.Event objects or raw handles."""
+    def handle(x):
+        if hasattr(x, "cuda_stream"):
+            return x.cuda_stream
+        if hasattr(x, "cuda_event"):
+            return x.cuda_event
+        return int(x)
+    st = (ctypes.c_void_p * len(streams))(*[handle(s) for s in streams])
+    es = (ctypes.c_void_p * len(ev_start))(*[handle(e) for e in ev_start]) if ev_start else None
+    ee = (ctypes.c_void_p * len(ev_end))(*[handle(e) for e in ev_end]) if ev_end else None
+    rc = load().gb_solve_batched_d(len(n), _iarr(n), _iarr(nev), _parr(A), _iarr(lda), _parr(ev), _parr(Z),
+                                   _iarr(ldz), _p(workspace), ws_bytes, len(streams), st, es, ee)
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_batched_d")
     return rc
 
 

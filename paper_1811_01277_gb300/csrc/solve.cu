@@ -18,7 +18,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "elpa_gb300.h"
 #include "layout.cuh"
@@ -42,17 +44,28 @@ cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, doub
 
 namespace {
 
-constexpr int kMaxDev = 64;
+// One cuBLAS handle per (device, stream): solves that overlap on different
+// streams then never share a handle's internal workspace.  Handles live until
+// the process exits.
 std::mutex g_blas_mutex;
-cublasHandle_t g_blas[kMaxDev] = {nullptr};
+std::map<std::pair<int, cudaStream_t>, cublasHandle_t> g_blas;
 
-cublasHandle_t blas_handle()
+cublasHandle_t blas_handle(cudaStream_t st)
 {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> lock(g_blas_mutex);
-    if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
-    return g_blas[dev];
+    auto key = std::make_pair(dev, st);
+    auto it = g_blas.find(key);
+    if (it != g_blas.end()) return it->second;
+    cublasHandle_t h = nullptr;
+    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) {
+        cublasDestroy(h);
+        return nullptr;
+    }
+    g_blas[key] = h;
+    return h;
 }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -140,9 +153,8 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     if (ws_bytes < w.total) return -10;
     if (flags & ~GB_SOLVE_FP64_EMULATED_GEMM) return -12;
     cudaStream_t st = (cudaStream_t)stream;
-    cublasHandle_t h = blas_handle();
+    cublasHandle_t h = blas_handle(st);
     if (!h) return GB_ERR_CUDA;
-    GB_BL(cublasSetStream(h, st));
     GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
                                                                        : CUBLAS_DEFAULT_MATH));
     const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5;
@@ -207,6 +219,50 @@ int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream)
     int rc = gb_trans_ev_query(w.chase, w.chase_bytes, stream);
     if (rc != GB_OK) return rc;
     return gb_trans_ev_query(w.tev, w.tev_bytes, stream);
+}
+
+int gb_solve_default_nbw(int n)
+{
+    if (n < 2) return -1;
+    const int b = n >= 1024 ? 64 : 32;
+    return b < n ? b : n - 1;
+}
+
+size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev, int nslots)
+{
+    if (count < 1 || !n || !nev || nslots < 1) return 0;
+    size_t slot = 0;
+    for (int i = 0; i < count; i++) {
+        const size_t b = gb_solve_workspace_bytes(n[i], nev[i], gb_solve_default_nbw(n[i]));
+        if (b == 0) return 0;
+        if (b > slot) slot = b;
+    }
+    return a256(slot) * (size_t)nslots;
+}
+
+int gb_solve_batched_d(int count, const int *n, const int *nev, const double *const *A, const int *lda,
+                       double *const *ev, double *const *Z, const int *ldz, void *workspace, size_t ws_bytes,
+                       int nslots, void *const *streams, void *const *ev_start, void *const *ev_end)
+{
+    if (count < 1) return -1;
+    if (!n || !nev || !A || !lda || !ev || !Z || !ldz) return -2;
+    if (nslots < 1 || !streams) return -11;
+    const size_t need = gb_solve_batched_workspace_bytes(count, n, nev, nslots);
+    if (need == 0) return -2;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
+    if (ws_bytes < need) return -10;
+    const size_t slot = need / (size_t)nslots;
+    for (int i = 0; i < count; i++) {
+        const int s = i % nslots;
+        cudaStream_t st = (cudaStream_t)streams[s];
+        if (ev_start && cudaEventRecord((cudaEvent_t)ev_start[i], st) != cudaSuccess) return GB_ERR_CUDA;
+        const int b = gb_solve_default_nbw(n[i]);
+        int rc = gb_solve_d(n[i], nev[i], b, A[i], lda[i], ev[i], Z[i], ldz[i], (char *)workspace + s * slot, slot,
+                            (void *)st, 0);
+        if (rc != GB_OK) return rc;
+        if (ev_end && cudaEventRecord((cudaEvent_t)ev_end[i], st) != cudaSuccess) return GB_ERR_CUDA;
+    }
+    return GB_OK;
 }
 
 int elpa_b200_solve(int n, int nev, const double *A, int lda, double *ev, double *Z, int ldz)
