@@ -466,8 +466,8 @@ def run_stage_solve(args):
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
 
-    def step():
-        gb.gb_solve_d(n, nev, nbw, A, n, ev, Z, n, ws, wsb, st, 0)
+    def step(flags=0):
+        gb.gb_solve_d(n, nev, nbw, A, n, ev, Z, n, ws, wsb, st, flags)
 
     for _ in range(args.warmup):
         step()
@@ -482,6 +482,8 @@ def run_stage_solve(args):
     clocks = sampler.stop()
     status = gb.gb_solve_query(ws, n, nev, nbw, st)
     ms = e0.elapsed_time(e1) / args.steps
+    step(gb.GB_SOLVE_RECORD_STAGES)            # one more solve, outside the timed region
+    stages = gb.gb_solve_stage_ms(st)
     # accuracy: eigenvalues against the prescribed ones, residual and
     # orthogonality on all nev columns (GEMMs on the device)
     Zc = Z.T                                   # n x nev view, column-major data
@@ -496,6 +498,7 @@ def run_stage_solve(args):
         "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "seconds_per_solve": ms / 1e3,
         "steps": args.steps, "warmup": args.warmup, "status": status, "dtype": "f64",
         "data": "synthetic: A = Q diag(clustered spectrum) Q^T, Q a product of 256 seeded Householders",
+        "stage_ms": stages,
         "accuracy": {"max_dlambda_over_norm": dlam, "residual_rel_fro": resid, "orth_max": orth,
                      "bound_50nu": 50 * n * u, "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
         "clocks": clocks}))

@@ -190,12 +190,18 @@ int gb_band_to_tridi_d(int n, int nbw, const double *AB, int ldab, double *d, do
  * emulation for the GEMMs where it supports it.  Asynchronous; device-side
  * status of the dependency waits through gb_solve_query. */
 #define GB_SOLVE_FP64_EMULATED_GEMM 1
+#define GB_SOLVE_RECORD_STAGES 2 /* record CUDA events at the stage boundaries */
 size_t gb_solve_workspace_bytes(int n, int nev, int nbw);
 int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
                void *workspace, size_t ws_bytes, void *stream, int flags);
 /* Synchronises the stream and returns GB_OK or the first device-side error
  * (GB_ERR_TIMEOUT) of the last gb_solve_d that used this workspace. */
 int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream);
+/* Milliseconds of the six stages (full->band, band->tridiagonal, tridiagonal
+ * eigenpairs, orthogonalisation, tridiagonal->band, band->full) of the last
+ * gb_solve_d on this stream that had GB_SOLVE_RECORD_STAGES set; ms has 6
+ * entries.  Synchronises the stream. */
+int gb_solve_stage_ms(void *stream, float *ms);
 /* Convenience form with host-side defaults: nbw = min(64, n-1), legacy
  * default stream, and a workspace it allocates with cudaMalloc and frees
  * before returning (synchronous).  All pointers are device pointers. */

@@ -15,7 +15,7 @@ from ._lib import (  # noqa: F401
     GB_AUTOTUNE_FAST, GB_AUTOTUNE_MEDIUM, elpa_b200_solve, gb_autotune_best, gb_autotune_create,
     gb_autotune_destroy, gb_autotune_load, gb_autotune_progress, gb_autotune_report, gb_autotune_save,
     gb_autotune_step, gb_solve_batched_d, gb_solve_batched_workspace_bytes, gb_solve_d,
-    gb_solve_default_nbw, gb_solve_query, gb_solve_workspace_bytes, load,
+    gb_solve_default_nbw, gb_solve_stage_ms, GB_SOLVE_RECORD_STAGES, SOLVE_STAGES, gb_solve_query, gb_solve_workspace_bytes, load,
 )
 
 

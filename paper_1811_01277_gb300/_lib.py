@@ -30,8 +30,11 @@ EXPORTS = (
     "gb_solve_workspace_bytes", "gb_solve_d", "gb_solve_query", "elpa_b200_solve",
     "gb_autotune_create", "gb_autotune_destroy", "gb_autotune_step", "gb_autotune_report",
     "gb_autotune_best", "gb_autotune_progress", "gb_autotune_save", "gb_autotune_load",
-    "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d",
+    "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d", "gb_solve_stage_ms",
 )
+GB_SOLVE_RECORD_STAGES = 2
+SOLVE_STAGES = ("full_to_band", "band_to_tridi", "tridiag_eig", "orthogonalise", "trans_ev_tridi_to_band",
+                "band_to_full")
 GB_AUTOTUNE_FAST = 1
 GB_AUTOTUNE_MEDIUM = 2
 GB_SOLVE_FP64_EMULATED_GEMM = 1
@@ -98,6 +101,7 @@ def load(path=None):
     L.gb_autotune_save.argtypes = [p, ctypes.c_char_p]; L.gb_autotune_save.restype = i
     L.gb_autotune_load.argtypes = [ctypes.c_char_p]; L.gb_autotune_load.restype = p
     L.gb_solve_default_nbw.argtypes = [i]; L.gb_solve_default_nbw.restype = i
+    L.gb_solve_stage_ms.argtypes = [p, ctypes.POINTER(ctypes.c_float)]; L.gb_solve_stage_ms.restype = i
     pi_ = ctypes.POINTER(ctypes.c_int)
     pp = ctypes.POINTER(ctypes.c_void_p)
     L.gb_solve_batched_workspace_bytes.argtypes = [i, pi_, pi_, i]
@@ -277,6 +281,14 @@ def gb_autotune_save(t, path):
 
 def gb_autotune_load(path):
     return load().gb_autotune_load(os.fsencode(path))
+
+
+def gb_solve_stage_ms(stream=None):
+    ms = (ctypes.c_float * 6)()
+    rc = load().gb_solve_stage_ms(_stream(stream), ms)
+    if rc != GB_OK:
+        raise GbError(rc, "gb_solve_stage_ms")
+    return dict(zip(SOLVE_STAGES, [float(x) for x in ms]))
 
 
 def gb_solve_default_nbw(n):

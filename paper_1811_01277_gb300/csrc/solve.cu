@@ -70,6 +70,26 @@ cublasHandle_t blas_handle(cudaStream_t st)
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Stage boundaries recorded when GB_SOLVE_RECORD_STAGES is set: events
+// cached per (device, stream), created on first use.
+constexpr int kStages = 6;  // full->band, band->tri, tridiagonal, orthogonalise, tri->band, band->full
+std::map<std::pair<int, cudaStream_t>, cudaEvent_t *> g_stage_events;
+
+cudaEvent_t *stage_events(cudaStream_t st)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    auto key = std::make_pair(dev, st);
+    auto it = g_stage_events.find(key);
+    if (it != g_stage_events.end()) return it->second;
+    cudaEvent_t *ev = new cudaEvent_t[kStages + 1];
+    for (int i = 0; i <= kStages; i++)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) return nullptr;
+    g_stage_events[key] = ev;
+    return ev;
+}
+
 // Workspace carve-up (all pieces 256-byte aligned).
 struct SolveWs {
     double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2;
@@ -151,8 +171,17 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     const int b = nbw;
     SolveWs w = carve(n, nev, b, (char *)workspace);
     if (ws_bytes < w.total) return -10;
-    if (flags & ~GB_SOLVE_FP64_EMULATED_GEMM) return -12;
+    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES)) return -12;
     cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t *sev = nullptr;
+    if (flags & GB_SOLVE_RECORD_STAGES) {
+        sev = stage_events(st);
+        if (!sev) return GB_ERR_CUDA;
+    }
+#define GB_STAGE(i)                                                        \
+    do {                                                                   \
+        if (sev && cudaEventRecord(sev[i], st) != cudaSuccess) return GB_ERR_CUDA; \
+    } while (0)
     cublasHandle_t h = blas_handle(st);
     if (!h) return GB_ERR_CUDA;
     GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
@@ -161,6 +190,7 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     const long long ldw = n;
 
     // ---- full -> band
+    GB_STAGE(0);
     GB_CU(cudaMemcpy2DAsync(w.Aw, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice, st));
     int P = 0;
     for (int j = 0; j + b < n; j += b, P++) {
@@ -184,20 +214,25 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
 
     // ---- band -> tridiagonal
+    GB_STAGE(1);
     GB_CU(gb::band_to_tridi_d(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, w.chase_bytes,
                               10LL * 1000 * 1000 * 1000, st));
 
     // ---- eigenpairs of T, then one Newton-Schulz orthogonalisation step into Z
+    GB_STAGE(2);
     GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
+    GB_STAGE(3);
     GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nev, nev, n, &one, w.Ztri, n, w.Ztri, n, &zero, w.Gns, nev));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
     GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, nev, nev, &one, w.Ztri, n, w.Gns, nev, &zero, Z, ldz));
 
     // ---- tridiagonal -> band (the hot path)
+    GB_STAGE(4);
     int rc = gb_trans_ev_tridi_to_band_d(n, b, nev, w.hv, w.ht, Z, ldz, w.tev, w.tev_bytes, stream, nullptr);
     if (rc != GB_OK) return rc;
 
     // ---- band -> full, last panel first
+    GB_STAGE(5);
     for (int p = P - 1; p >= 0; p--) {
         const int j = p * b, m = n - j - b;
         const double *panel = w.Aw + (long long)j * ldw + (j + b);
@@ -208,7 +243,21 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, w.S, b, &zero, w.S2, b));
         GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, w.Y, m, w.S2, b, &one, Zr, ldz));
     }
+    GB_STAGE(6);
+#undef GB_STAGE
     GB_CU(cudaGetLastError());
+    return GB_OK;
+}
+
+int gb_solve_stage_ms(void *stream, float *ms)
+{
+    if (!ms) return -2;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t *sev = stage_events(st);
+    if (!sev) return GB_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GB_ERR_CUDA;
+    for (int i = 0; i < kStages; i++)
+        if (cudaEventElapsedTime(&ms[i], sev[i], sev[i + 1]) != cudaSuccess) return GB_ERR_CUDA;
     return GB_OK;
 }
 
