@@ -315,6 +315,8 @@ def gb_solve_batched_d(n, nev, A, lda, ev, Z, ldz, workspace, ws_bytes, streams,
         if hasattr(x, "cuda_stream"):
             return x.cuda_stream
         if hasattr(x, "cuda_event"):
+            if not x.cuda_event:      # torch creates the CUDA event on its first record
+                x.record()
             return x.cuda_event
         return int(x)
     st = (ctypes.c_void_p * len(streams))(*[handle(s) for s in streams])
