@@ -81,11 +81,22 @@ __global__ void __launch_bounds__(kChunk) panel_refl_dots(int m, int nb, int i, 
     else if (r > i && r < m) {
         v = (t != 0.0) ? col[r] * s_scal : 0.0;
     }
-    // partial v^T A[:, j], j > i
+    // partial v^T A[:, j] for every j > i in one pass: warp sums, then one
+    // shared-memory sum over the block's warps
+    __shared__ double wsum[kChunk / 32][kPanelMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = i + 1; j < nb; j++) {
-        const double a = (r >= i && r < m) ? P[(long long)j * lda + r] : 0.0;
-        const double s = block_reduce_sum(v * a, red);
-        if (threadIdx.x == 0) part_dot[(long long)blockIdx.x * kPanelMax + j] = s;
+        double a = (r >= i && r < m) ? P[(long long)j * lda + r] : 0.0;
+        double x = v * a;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) wsum[warp][j] = x;
+    }
+    __syncthreads();
+    for (int j = i + 1 + threadIdx.x; j < nb; j += blockDim.x) {
+        double t2 = 0.0;
+        for (int w2 = 0; w2 < kChunk / 32; w2++) t2 += wsum[w2][j];
+        part_dot[(long long)blockIdx.x * kPanelMax + j] = t2;
     }
     __syncthreads();
     // store v below the diagonal (needs every block to have read col[i] first:

@@ -96,7 +96,7 @@ __device__ int sturm_count(int n, const double *__restrict__ d, const double *__
     return cnt;
 }
 
-__global__ void __launch_bounds__(128) tridiag_bisect(int n, int nev, const double *__restrict__ d,
+__global__ void __launch_bounds__(32) tridiag_bisect(int n, int nev, const double *__restrict__ d,
                                                       const double *__restrict__ e2, const double *bounds,
                                                       const double *pivmin_p, double *__restrict__ lam)
 {
@@ -126,7 +126,7 @@ __device__ __forceinline__ double start_value(int k, int i)
 
 // One thread per cluster leader k (lam[k] - lam[k-1] > gap, or k = 0): the
 // cluster's eigenvectors, written to Z (n x nev, column-major, ldz).
-__global__ void __launch_bounds__(64) tridiag_invit(int n, int nev, const double *__restrict__ d,
+__global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double *__restrict__ d,
                                                     const double *__restrict__ e, const double *__restrict__ lam,
                                                     const double *bounds, double gap_rel, double *__restrict__ A,
                                                     double *__restrict__ Bs, double *__restrict__ C,
@@ -253,8 +253,10 @@ cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, doub
     unsigned char *piv = (unsigned char *)(X + per);
     tridiag_bounds<<<1, 256, 0, st>>>(n, d, e, bounds);
     square_offdiag<<<1, 256, 0, st>>>(n, e, e2, pivmin);
-    tridiag_bisect<<<(nev + 127) / 128, 128, 0, st>>>(n, nev, d, e2, bounds, pivmin, lam);
-    tridiag_invit<<<(nev + 63) / 64, 64, 0, st>>>(n, nev, d, e, lam, bounds, 1e-7, A, Bs, C, D2, piv, X, Z, ldz);
+    // one warp per block: the per-eigenvalue chains are latency-bound, so
+    // they are spread over as many SMs as possible
+    tridiag_bisect<<<(nev + 31) / 32, 32, 0, st>>>(n, nev, d, e2, bounds, pivmin, lam);
+    tridiag_invit<<<(nev + 31) / 32, 32, 0, st>>>(n, nev, d, e, lam, bounds, 1e-7, A, Bs, C, D2, piv, X, Z, ldz);
     return cudaGetLastError();
 }
 
