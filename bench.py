@@ -425,25 +425,29 @@ def run_stage_band_to_tridi(args):
     return 0
 
 
-def prescribed_symmetric_gpu(lam, k, seed, dev):
-    """A = Q diag(lam) Q^T on the device, Q = H_1 ... H_k a product of k seeded
-    random Householder reflectors, built in O(n^2 k) from the compact form
-    Q = I - Y T Y^T (input synthesis; eigenvalues known exactly)."""
+def prescribed_symmetric_gpu(lam, k, seed, dev, cplx=False):
+    """A = Q diag(lam) Q^H on the device, Q = H_1 ... H_k a product of k seeded
+    random Householder reflectors (tau = 2/||y||^2), built in O(n^2 k) from the
+    compact form Q = I - Y T Y^H (input synthesis; eigenvalues known exactly)."""
     import torch
     n = lam.numel()
     g = torch.Generator(device=dev).manual_seed(seed)
+    dt = torch.complex128 if cplx else torch.float64
     Y = torch.randn(n, k, generator=g, device=dev, dtype=torch.float64)
-    tau = 2.0 / (Y * Y).sum(0)
-    G = Y.T @ Y
-    T = torch.zeros(k, k, dtype=torch.float64, device=dev)
+    if cplx:
+        Y = torch.complex(Y, torch.randn(n, k, generator=g, device=dev, dtype=torch.float64))
+    tau = (2.0 / (Y.abs() ** 2).sum(0)).to(dt)
+    G = Y.conj().T @ Y
+    T = torch.zeros(k, k, dtype=dt, device=dev)
     for j in range(k):
         if j:
             T[:j, j] = -tau[j] * (T[:j, :j] @ G[:j, j])
         T[j, j] = tau[j]
-    U = Y @ T                                   # Q = I - U Y^T
-    LY = lam[:, None] * Y                       # Lambda Y
-    A = torch.diag(lam) - U @ LY.T - LY @ U.T + U @ ((Y.T @ LY) @ U.T)
-    return 0.5 * (A + A.T)
+    U = Y @ T                                   # Q = I - U Y^H
+    L = lam.to(dt)
+    LY = L[:, None] * Y                         # Lambda Y
+    A = torch.diag(L) - U @ LY.conj().T - LY @ U.conj().T + U @ ((Y.conj().T @ LY) @ U.conj().T)
+    return 0.5 * (A + A.conj().T)
 
 
 def run_stage_solve(args):
@@ -457,17 +461,22 @@ def run_stage_solve(args):
     gbuild.build()
     gb.load()
     n, nev, nbw = args.solve_n, args.solve_nev, args.solve_nbw
+    cplx = args.complex
     dev = torch.device("cuda", 0)
     lam = torch.from_numpy(inputs.clustered_spectrum(n, seed=n)).to(dev)
-    A = prescribed_symmetric_gpu(lam, 256, seed=n + 1, dev=dev)   # symmetric: row-major = column-major
+    A = prescribed_symmetric_gpu(lam, 256, seed=n + 1, dev=dev, cplx=cplx)
+    Acm = A.T.contiguous() if cplx else A       # column-major storage (A Hermitian: A^T = conj(A))
     ev = torch.zeros(nev, dtype=torch.float64, device=dev)
-    Z = torch.zeros((nev, n), dtype=torch.float64, device=dev)
-    wsb = gb.gb_solve_workspace_bytes(n, nev, nbw)
+    Z = torch.zeros((nev, n), dtype=torch.complex128 if cplx else torch.float64, device=dev)
+    wsb = (gb.gb_solve_workspace_bytes_z if cplx else gb.gb_solve_workspace_bytes)(n, nev, nbw)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
 
     def step(flags=0):
-        gb.gb_solve_d(n, nev, nbw, A, n, ev, Z, n, ws, wsb, st, flags)
+        if cplx:
+            gb.gb_solve_z(n, nev, nbw, Acm, n, ev, Z, n, ws, wsb, st, flags & ~gb.GB_SOLVE_RECORD_STAGES)
+        else:
+            gb.gb_solve_d(n, nev, nbw, Acm, n, ev, Z, n, ws, wsb, st, flags)
 
     for _ in range(args.warmup):
         step()
@@ -480,21 +489,24 @@ def run_stage_solve(args):
     e1.record(st)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
-    status = gb.gb_solve_query(ws, n, nev, nbw, st)
+    status = (gb.gb_solve_query_z if cplx else gb.gb_solve_query)(ws, n, nev, nbw, st)
     ms = e0.elapsed_time(e1) / args.steps
-    step(gb.GB_SOLVE_RECORD_STAGES)            # one more solve, outside the timed region
-    stages = gb.gb_solve_stage_ms(st)
+    stages = None
+    if not cplx:
+        step(gb.GB_SOLVE_RECORD_STAGES)        # one more solve, outside the timed region
+        stages = gb.gb_solve_stage_ms(st)
     # accuracy: eigenvalues against the prescribed ones, residual and
     # orthogonality on all nev columns (GEMMs on the device)
     Zc = Z.T                                   # n x nev view, column-major data
     anorm = lam.abs().max().item()
     dlam = (ev - lam[:nev]).abs().max().item() / anorm
-    R = A @ Zc - Zc * ev[None, :]
+    R = A @ Zc - Zc * ev[None, :].to(Zc.dtype)
     resid = (torch.linalg.norm(R) / torch.linalg.norm(A)).item()
-    orth = (Zc.T @ Zc - torch.eye(nev, dtype=torch.float64, device=dev)).abs().max().item()
+    orth = (Zc.conj().T @ Zc - torch.eye(nev, dtype=Zc.dtype, device=dev)).abs().max().item()
     u = 2.0 ** -53
     print(json.dumps({
-        "stage": "solve", "metric": f"two-stage eigensolve s at n={n} ({100 * nev // n}% vecs), nbw={nbw}",
+        "stage": "solve", "metric": f"two-stage eigensolve s at n={n} ({100 * nev // n}% vecs), nbw={nbw}, "
+                                    f"{'complex128 Hermitian' if cplx else 'real FP64'}",
         "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "seconds_per_solve": ms / 1e3,
         "steps": args.steps, "warmup": args.warmup, "status": status, "dtype": "f64",
         "data": "synthetic: A = Q diag(clustered spectrum) Q^T, Q a product of 256 seeded Householders",
@@ -608,6 +620,7 @@ def main():
     ap.add_argument("--solve-n", type=int, default=16384)
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
+    ap.add_argument("--complex", action="store_true", help="solve stage: complex128 Hermitian")
     ap.add_argument("--chase-n", type=int, default=16384)
     ap.add_argument("--chase-b", type=int, default=64)
     args = ap.parse_args()

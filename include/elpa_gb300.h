@@ -173,6 +173,16 @@ int gb_band_to_tridi_d(int n, int nbw, const double *AB, int ldab, double *d, do
                        double *hh_v, double *hh_tau, void *workspace, size_t ws_bytes,
                        void *stream);
 
+/* Complex Hermitian form of gb_band_to_tridi_d: AB holds complex128 entries
+ * (interleaved re, im) of the lower band, hh_v / hh_tau complex128 in the
+ * same layout; d and e are real (every kept sub-diagonal entry is made real
+ * by the reflector generation, length-1 reflectors included).  Arguments and
+ * status as for gb_band_to_tridi_d, with ldab counted in complex elements. */
+size_t gb_band_to_tridi_workspace_bytes_z(int n, int nbw);
+int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, double *e,
+                       double *hh_v, double *hh_tau, void *workspace, size_t ws_bytes,
+                       void *stream);
+
 /* Two-stage symmetric eigensolver (Sec. 2): A = Z diag(ev) Z^T for the nev
  * smallest eigenvalues of the real symmetric n x n matrix A.
  *   full -> band (Householder panels; trailing updates as cuBLAS GEMMs),
@@ -197,10 +207,20 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
 /* Synchronises the stream and returns GB_OK or the first device-side error
  * (GB_ERR_TIMEOUT) of the last gb_solve_d that used this workspace. */
 int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream);
-/* Milliseconds of the six stages (full->band, band->tridiagonal, tridiagonal
- * eigenpairs, orthogonalisation, tridiagonal->band, band->full) of the last
- * gb_solve_d on this stream that had GB_SOLVE_RECORD_STAGES set; ms has 6
- * entries.  Synchronises the stream. */
+/* Complex Hermitian two-stage solve: A (complex128, interleaved, lda) =
+ * Z diag(ev) Z^H with real ev (nev, ascending) and complex Z (n x nev, ldz);
+ * same arguments, workspace rule (gb_solve_workspace_bytes_z) and flags as
+ * gb_solve_d (GB_SOLVE_RECORD_STAGES is ignored).  Device-side status of
+ * the bulge chase's waits through gb_solve_query_z. */
+size_t gb_solve_workspace_bytes_z(int n, int nev, int nbw);
+int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
+               void *workspace, size_t ws_bytes, void *stream, int flags);
+int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *stream);
+
+/* Milliseconds of the seven stages (full->band, band->tridiagonal,
+ * bisection, inverse iteration, orthogonalisation, tridiagonal->band,
+ * band->full) of the last gb_solve_d on this stream that had
+ * GB_SOLVE_RECORD_STAGES set; ms has 7 entries.  Synchronises the stream. */
 int gb_solve_stage_ms(void *stream, float *ms);
 /* Convenience form with host-side defaults: nbw = min(64, n-1), legacy
  * default stream, and a workspace it allocates with cudaMalloc and frees

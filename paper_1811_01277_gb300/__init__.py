@@ -9,13 +9,13 @@ seeded input generators; PyTorch only provides device memory and streams.
 from ._lib import (  # noqa: F401
     EXPORTS, GB_ERR_CUDA, GB_ERR_TIMEOUT, GB_ERR_UNSUPPORTED, GB_ERR_WORKSPACE, GB_OK,
     GB_NOALLOC_SCRATCH_BYTES, GB_SOLVE_FP64_EMULATED_GEMM, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
-    gb_band_to_tridi_d, gb_band_to_tridi_workspace_bytes, gb_hh_count, gb_hh_index, gb_max_nbw, gb_status_string, gb_trans_ev_host_buffer_bytes,
+    gb_band_to_tridi_d, gb_band_to_tridi_workspace_bytes, gb_band_to_tridi_workspace_bytes_z, gb_band_to_tridi_z, gb_hh_count, gb_hh_index, gb_max_nbw, gb_status_string, gb_trans_ev_host_buffer_bytes,
     gb_trans_ev_launch_count, gb_trans_ev_opts, gb_trans_ev_query, gb_trans_ev_tridi_to_band_d,
     gb_trans_ev_tridi_to_band_d_host, gb_trans_ev_tridi_to_band_d_noalloc, gb_trans_ev_tridi_to_band_z, gb_trans_ev_workspace_bytes,
     GB_AUTOTUNE_FAST, GB_AUTOTUNE_MEDIUM, elpa_b200_solve, gb_autotune_best, gb_autotune_create,
     gb_autotune_destroy, gb_autotune_load, gb_autotune_progress, gb_autotune_report, gb_autotune_save,
     gb_autotune_step, gb_solve_batched_d, gb_solve_batched_workspace_bytes, gb_solve_d,
-    gb_solve_default_nbw, gb_solve_stage_ms, GB_SOLVE_RECORD_STAGES, SOLVE_STAGES, gb_solve_query, gb_solve_workspace_bytes, load,
+    gb_solve_default_nbw, gb_solve_stage_ms, gb_solve_workspace_bytes_z, gb_solve_z, gb_solve_query_z, GB_SOLVE_RECORD_STAGES, SOLVE_STAGES, gb_solve_query, gb_solve_workspace_bytes, load,
 )
 
 

@@ -31,10 +31,12 @@ EXPORTS = (
     "gb_autotune_create", "gb_autotune_destroy", "gb_autotune_step", "gb_autotune_report",
     "gb_autotune_best", "gb_autotune_progress", "gb_autotune_save", "gb_autotune_load",
     "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d", "gb_solve_stage_ms",
+    "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
+    "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
 )
 GB_SOLVE_RECORD_STAGES = 2
-SOLVE_STAGES = ("full_to_band", "band_to_tridi", "tridiag_eig", "orthogonalise", "trans_ev_tridi_to_band",
-                "band_to_full")
+SOLVE_STAGES = ("full_to_band", "band_to_tridi", "bisection", "inverse_iteration", "orthogonalise",
+                "trans_ev_tridi_to_band", "band_to_full")
 GB_AUTOTUNE_FAST = 1
 GB_AUTOTUNE_MEDIUM = 2
 GB_SOLVE_FP64_EMULATED_GEMM = 1
@@ -102,6 +104,11 @@ def load(path=None):
     L.gb_autotune_load.argtypes = [ctypes.c_char_p]; L.gb_autotune_load.restype = p
     L.gb_solve_default_nbw.argtypes = [i]; L.gb_solve_default_nbw.restype = i
     L.gb_solve_stage_ms.argtypes = [p, ctypes.POINTER(ctypes.c_float)]; L.gb_solve_stage_ms.restype = i
+    L.gb_band_to_tridi_workspace_bytes_z.argtypes = [i, i]; L.gb_band_to_tridi_workspace_bytes_z.restype = sz
+    L.gb_band_to_tridi_z.argtypes = [i, i, p, i, p, p, p, p, p, sz, p]; L.gb_band_to_tridi_z.restype = i
+    L.gb_solve_workspace_bytes_z.argtypes = [i, i, i]; L.gb_solve_workspace_bytes_z.restype = sz
+    L.gb_solve_z.argtypes = [i, i, i, p, i, p, p, i, p, sz, p, i]; L.gb_solve_z.restype = i
+    L.gb_solve_query_z.argtypes = [p, i, i, i, p]; L.gb_solve_query_z.restype = i
     pi_ = ctypes.POINTER(ctypes.c_int)
     pp = ctypes.POINTER(ctypes.c_void_p)
     L.gb_solve_batched_workspace_bytes.argtypes = [i, pi_, pi_, i]
@@ -283,8 +290,36 @@ def gb_autotune_load(path):
     return load().gb_autotune_load(os.fsencode(path))
 
 
+def gb_band_to_tridi_workspace_bytes_z(n, nbw):
+    return load().gb_band_to_tridi_workspace_bytes_z(n, nbw)
+
+
+def gb_band_to_tridi_z(n, nbw, AB, ldab, d, e, hh_v, hh_tau, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_band_to_tridi_z(n, nbw, _p(AB), ldab, _p(d), _p(e), _p(hh_v), _p(hh_tau), _p(workspace),
+                                   ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_band_to_tridi_z")
+    return rc
+
+
+def gb_solve_workspace_bytes_z(n, nev, nbw):
+    return load().gb_solve_workspace_bytes_z(n, nev, nbw)
+
+
+def gb_solve_z(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream=None, flags=0, check=True):
+    rc = load().gb_solve_z(n, nev, nbw, _p(A), lda, _p(ev), _p(Z), ldz, _p(workspace), ws_bytes,
+                           _stream(stream), flags)
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_z")
+    return rc
+
+
+def gb_solve_query_z(workspace, n, nev, nbw, stream=None):
+    return load().gb_solve_query_z(_p(workspace), n, nev, nbw, _stream(stream))
+
+
 def gb_solve_stage_ms(stream=None):
-    ms = (ctypes.c_float * 6)()
+    ms = (ctypes.c_float * 7)()
     rc = load().gb_solve_stage_ms(_stream(stream), ms)
     if rc != GB_OK:
         raise GbError(rc, "gb_solve_stage_ms")

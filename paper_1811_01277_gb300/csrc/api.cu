@@ -230,6 +230,30 @@ int gb_band_to_tridi_d(int n, int nbw, const double *AB, int ldab, double *d, do
     return err == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 
+size_t gb_band_to_tridi_workspace_bytes_z(int n, int nbw)
+{
+    if (n < 1 || nbw < 1 || nbw > kMaxRegNbw) return 0;
+    return gb::band_to_tridi_workspace_bytes_z(n, nbw);
+}
+
+int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, double *e, double *hh_v,
+                       double *hh_tau, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (n < 1) return -1;
+    if (nbw < 1 || nbw > kMaxRegNbw) return -2;
+    if (!AB || ((uintptr_t)AB % 16) != 0) return -3;
+    if (ldab < nbw + 1) return -4;
+    if (!d || ((uintptr_t)d % sizeof(double)) != 0) return -5;
+    if (n > 1 && (!e || ((uintptr_t)e % sizeof(double)) != 0)) return -6;
+    if (n > 1 && (!hh_v || ((uintptr_t)hh_v % 16) != 0)) return -7;
+    if (n > 1 && (!hh_tau || ((uintptr_t)hh_tau % 16) != 0)) return -8;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
+    if (ws_bytes < gb::band_to_tridi_workspace_bytes_z(n, nbw)) return -10;
+    cudaError_t err = gb::band_to_tridi_z(n, nbw, AB, ldab, d, e, hh_v, hh_tau, workspace, kTimeoutNs,
+                                          (cudaStream_t)stream);
+    return err == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
 const char *gb_status_string(int status)
 {
     switch (status) {

@@ -235,6 +235,250 @@ chase_d(int n, int b, Band A, double *__restrict__ hh_v, double *__restrict__ hh
     }
 }
 
+// ---------------------------------------------------------------- complex
+// Hermitian band (lower storage, complex entries): the same task structure
+// with H = I - tau v v^H applied as H^H from the left and H from the right;
+// the sub-diagonal comes out real because every kept entry is a real beta.
+struct Zc {
+    double re, im;
+};
+__device__ __forceinline__ Zc zmul(Zc a, Zc b) { return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)}; }
+__device__ __forceinline__ Zc zconj(Zc a) { return {a.re, -a.im}; }
+// acc += conj(a) * b
+__device__ __forceinline__ void zdotc(Zc &acc, Zc a, Zc b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+// acc += a * b
+__device__ __forceinline__ void zfma(Zc &acc, Zc a, Zc b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+
+struct BandZ {
+    Zc *W;
+    long long ldw;
+    __device__ __forceinline__ Zc *at_lower(int i, int j) const { return W + (i - j) + (long long)j * ldw; }
+    __device__ __forceinline__ Zc get(int i, int j) const
+    {
+        if (i >= j) {
+            const double2 t = __ldcg(reinterpret_cast<const double2 *>(at_lower(i, j)));
+            return {t.x, t.y};
+        }
+        const double2 t = __ldcg(reinterpret_cast<const double2 *>(at_lower(j, i)));
+        return {t.x, -t.y};
+    }
+    __device__ __forceinline__ void set_lower(int i, int j, Zc v) const { *at_lower(i, j) = v; }
+};
+
+__device__ __forceinline__ Zc quad_sum_z(Zc x)
+{
+    x.re = quad_sum(x.re);
+    x.im = quad_sum(x.im);
+    return x;
+}
+
+__global__ void __launch_bounds__(kChaseThreads)
+chase_z(int n, int b, BandZ A, Zc *__restrict__ hh_v, Zc *__restrict__ hh_tau, ChaseState *state, int *progress,
+        long long timeout_ns)
+{
+    __shared__ Zc v[64];
+    __shared__ Zc q[64];
+    __shared__ double red[kChaseThreads / 32];
+    __shared__ Zc s_tau, s_scal;
+    __shared__ int s_sweep, s_abort;
+    const int tid = threadIdx.x;
+    const int quad = tid >> 2, part = tid & 3;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_sweep = 1 + atomicAdd(&state->ticket, 1);
+        __syncthreads();
+        const int s = s_sweep;
+        if (s > n - 1) return;
+        const int nk = sweep_count(n, b, s);
+        const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
+        const long long first = sweep_first(n, b, s);
+
+        for (int k = 0; k < nk; k++) {
+            if (tid == 0) {
+                int abort = 0;
+                if (s > 1) {
+                    const int need = min(k + kLag, nk_prev);
+                    const unsigned long long t0 = now_ns();
+                    while (ld_acq(progress + (s - 2)) < need) {
+                        if (*(volatile int *)&state->abort) { abort = 1; break; }
+                        if ((long long)(now_ns() - t0) > timeout_ns) {
+                            atomicExch(&state->error, GB_ERR_TIMEOUT);
+                            atomicExch(&state->abort, 1);
+                            abort = 1;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                } else if (*(volatile int *)&state->abort) {
+                    abort = 1;
+                }
+                s_abort = abort;
+            }
+            __syncthreads();
+            if (s_abort) return;
+
+            const int r = s + k * b;
+            const int len = min(b, n - r);
+            const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
+            const int rb = r + len;
+            const int nleft = r - c - 1, nbelow = min(b, n - rb);
+            const long long idx = first + k;
+
+            // ---- reflector (complex, beta real)
+            const Zc xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : Zc{0.0, 0.0};
+            const double ss = block_sum(xi.re * xi.re + xi.im * xi.im, red);
+            if (tid == 0) {
+                const Zc alpha = A.get(r, c);
+                Zc tau{0.0, 0.0}, scal{0.0, 0.0};
+                if (!(ss == 0.0 && alpha.im == 0.0)) {
+                    const double nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + ss);
+                    const double beta = (alpha.re >= 0.0) ? -nrm : nrm;
+                    tau = {(beta - alpha.re) / beta, -alpha.im / beta};
+                    const Zc den{alpha.re - beta, alpha.im};           // 1 / (alpha - beta)
+                    const double dd = den.re * den.re + den.im * den.im;
+                    scal = {den.re / dd, -den.im / dd};
+                    A.set_lower(r, c, Zc{beta, 0.0});
+                }
+                s_tau = tau;
+                s_scal = scal;
+                hh_tau[idx] = tau;
+            }
+            __syncthreads();
+            const Zc tau = s_tau;
+            const bool active = !(tau.re == 0.0 && tau.im == 0.0);
+            Zc vt{0.0, 0.0};
+            if (tid == 0) vt = {1.0, 0.0};
+            else if (tid < len && active) vt = zmul(xi, s_scal);
+            if (tid < 64) v[tid] = vt;
+            if (tid < b) hh_v[idx * b + tid] = vt;
+            if (active && tid >= 1 && tid < len) A.set_lower(r + tid, c, Zc{0.0, 0.0});
+            __syncthreads();
+
+            if (active) {
+                const Zc ctau = zconj(tau);
+                // ---- left block: A[R,j] -= conj(tau) v (v^H A[R,j])
+                {
+                    const bool act = quad < nleft;
+                    const int j = c + 1 + quad;
+                    Zc Lr[16];
+                    Zc acc{0.0, 0.0};
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int i = part + 4 * t;
+                        Lr[t] = (act && i < len) ? A.get(r + i, j) : Zc{0.0, 0.0};
+                        zdotc(acc, v[i], Lr[t]);
+                    }
+                    const Zc w = zmul(ctau, quad_sum_z(acc));
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int i = part + 4 * t;
+                        if (act && i < len) {
+                            Zc a = Lr[t];
+                            const Zc vw = zmul(v[i], w);
+                            a.re -= vw.re;
+                            a.im -= vw.im;
+                            A.set_lower(r + i, j, a);
+                        }
+                    }
+                }
+                // ---- below block: A[i,R] -= tau (A[i,R] v) v^H
+                {
+                    const bool act = quad < nbelow;
+                    const int i = rb + quad;
+                    Zc Br[16];
+                    Zc acc{0.0, 0.0};
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int j = part + 4 * t;
+                        Br[t] = (act && j < len) ? A.get(i, r + j) : Zc{0.0, 0.0};
+                        zfma(acc, Br[t], v[j]);
+                    }
+                    const Zc y = zmul(tau, quad_sum_z(acc));
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int j = part + 4 * t;
+                        if (act && j < len) {
+                            Zc a = Br[t];
+                            const Zc yv = zmul(y, zconj(v[j]));
+                            a.re -= yv.re;
+                            a.im -= yv.im;
+                            A.set_lower(i, r + j, a);
+                        }
+                    }
+                }
+                // ---- diagonal block: p = tau A v, K = conj(tau)/2 v^H p, q = p - K v,
+                //      A -= q v^H + v q^H on the lower triangle
+                Zc Dr[16];
+                Zc pa{0.0, 0.0};
+                const bool actd = quad < len;
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int j = part + 4 * t;
+                    Dr[t] = (actd && j < len) ? A.get(r + quad, r + j) : Zc{0.0, 0.0};
+                    zfma(pa, Dr[t], v[j]);
+                }
+                const Zc pi = zmul(tau, quad_sum_z(pa));
+                Zc vp{0.0, 0.0};
+                if (part == 0 && actd) zdotc(vp, v[quad], pi);
+                const double kre = block_sum(vp.re, red), kim = block_sum(vp.im, red);
+                const Zc K = zmul(Zc{0.5 * ctau.re, 0.5 * ctau.im}, Zc{kre, kim});
+                if (part == 0 && actd) {
+                    const Zc kv = zmul(K, v[quad]);
+                    q[quad] = Zc{pi.re - kv.re, pi.im - kv.im};
+                }
+                __syncthreads();
+                if (actd) {
+                    const Zc vq = v[quad], qq = q[quad];
+#pragma unroll
+                    for (int t = 0; t < 16; t++) {
+                        const int j = part + 4 * t;
+                        if (j < len && j <= quad) {
+                            const Zc t1 = zmul(qq, zconj(v[j])), t2 = zmul(vq, zconj(q[j]));
+                            A.set_lower(r + quad, r + j, Zc{Dr[t].re - t1.re - t2.re, Dr[t].im - t1.im - t2.im});
+                        }
+                    }
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_rel(progress + (s - 1), k + 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) band_init_z(int n, int b, const Zc *__restrict__ AB, long long ldab,
+                                                   Zc *__restrict__ W, long long ldw)
+{
+    const long long total = (long long)n * ldw;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long j = e / ldw, d = e - j * ldw;
+        W[e] = (d <= b && j + d < n) ? AB[d + j * ldab] : Zc{0.0, 0.0};
+    }
+}
+
+__global__ void __launch_bounds__(256) band_extract_z(int n, const Zc *__restrict__ W, long long ldw,
+                                                      double *__restrict__ dd, double *__restrict__ ee)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        dd[j] = W[(long long)j * ldw].re;
+        if (j < n - 1) ee[j] = W[1 + (long long)j * ldw].re;
+    }
+}
+
 }  // namespace
 
 // Workspace: [256-byte head {ticket, abort, error}][progress: n ints] then,
@@ -245,6 +489,35 @@ size_t band_to_tridi_workspace_bytes(int n, int b)
 {
     size_t band = 2 * (size_t)b * (size_t)n * sizeof(double);
     return flags_bytes(n) + ((band + 255) & ~(size_t)255);
+}
+
+size_t band_to_tridi_workspace_bytes_z(int n, int b)
+{
+    size_t band = 2 * (size_t)b * (size_t)n * 2 * sizeof(double);
+    return flags_bytes(n) + ((band + 255) & ~(size_t)255);
+}
+
+cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
+                            double *hh_tau, void *ws, long long timeout_ns, cudaStream_t st)
+{
+    const long long ldw = 2LL * b;
+    char *flags = (char *)ws;
+    Zc *W = (Zc *)(flags + flags_bytes(n));
+    cudaError_t err = cudaMemsetAsync(flags, 0, flags_bytes(n), st);
+    if (err != cudaSuccess) return err;
+    band_init_z<<<1024, 256, 0, st>>>(n, b, (const Zc *)AB, ldab, W, ldw);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (n > 1) {
+        int dev = 0, sms = 0;
+        if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+        if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+        const int grid = min(n - 1, sms);
+        chase_z<<<(unsigned)grid, kChaseThreads, 0, st>>>(n, b, BandZ{W, ldw}, (Zc *)hh_v, (Zc *)hh_tau,
+                                                         (ChaseState *)flags, (int *)(flags + 256), timeout_ns);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    band_extract_z<<<64, 256, 0, st>>>(n, W, ldw, d, e);
+    return cudaGetLastError();
 }
 
 cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,

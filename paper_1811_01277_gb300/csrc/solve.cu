@@ -4,9 +4,9 @@
 //
 //   full -> band   panel p (columns j..j+b-1): Householder QR of A[j+b:, j:j+b]
 //                  (panel kernels), block reflector Q_p = I - Y T Y^T, and the
-//                  two-sided trailing update A2 <- Q_p^T A2 Q_p as GEMMs:
-//                  X = A2 (Y T), M = T^T (Y^T X), W = X - Y M / 2,
-//                  A2 -= W Y^T + Y W^T   (the whole symmetric matrix is kept)
+//                  two-sided trailing update A2 <- Q_p^T A2 Q_p on the lower
+//                  triangle: X = A2 (Y T) (SYMM), M = T^T (Y^T X),
+//                  W = X - Y M / 2, A2 -= W Y^T + Y W^T (SYR2K)
 //   band -> tri    gb::band_to_tridi_d (bulge chasing)
 //   tridiagonal    gb::tridiag_eig_d (bisection + inverse iteration) and one
 //                  Newton-Schulz step Z <- Z (3I - Z^T Z)/2
@@ -39,6 +39,18 @@ cudaError_t band_from_full(int n, int b, const double *A, long long lda, double 
 size_t tridiag_eig_workspace_bytes(int n, int nev);
 cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, double *lam, double *Z, long long ldz,
                           void *ws, cudaStream_t st);
+cudaError_t tridiag_bisect_d(int n, int nev, const double *d, const double *e, double *lam, void *ws, cudaStream_t st);
+cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, const double *lam, double *Z,
+                            long long ldz, void *ws, cudaStream_t st);
+
+cudaError_t zpanel_qr(int m, int nb, double *P, long long lda, double *tau, double *part, cudaStream_t st);
+cudaError_t zpanel_y(int m, int nb, const double *P, long long lda, double *Y, long long ldy, cudaStream_t st);
+cudaError_t zpanel_t(int nb, const double *G, long long ldg, const double *tau, double *T, long long ldt,
+                     cudaStream_t st);
+cudaError_t zband_from_full(int n, int b, const double *A, long long lda, double *AB, long long ldab,
+                            cudaStream_t st);
+cudaError_t promote_real(long long rows, long long cols, const double *X, long long ldx, double *Z, long long ldz,
+                         cudaStream_t st);
 
 }  // namespace gb
 
@@ -72,7 +84,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Stage boundaries recorded when GB_SOLVE_RECORD_STAGES is set: events
 // cached per (device, stream), created on first use.
-constexpr int kStages = 6;  // full->band, band->tri, tridiagonal, orthogonalise, tri->band, band->full
+constexpr int kStages = 7;  // full->band, band->tri, bisection, inverse iteration, orthogonalise, tri->band, band->full
 std::map<std::pair<int, cudaStream_t>, cudaEvent_t *> g_stage_events;
 
 cudaEvent_t *stage_events(cudaStream_t st)
@@ -133,6 +145,52 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
     w.tev_bytes = gb_trans_ev_workspace_bytes(n, b, nev, 0, nullptr);
     w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
+    w.total = off;
+    return w;
+}
+
+// Complex workspace: complex pieces hold 2 doubles per entry.
+struct SolveWsZ {
+    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Zre, *Gns, *Zns, *S, *S2;
+    void *chase, *eig;
+    size_t chase_bytes, total;
+};
+
+SolveWsZ carve_z(int n, int nev, int b, char *base)
+{
+    SolveWsZ w{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off += a256(bytes);
+        return p;
+    };
+    const size_t P = (size_t)(n + b - 1) / b;
+    const size_t cnt = (size_t)gb::hh_total(n, b);
+    const size_t nch = (size_t)gb::panel_chunks(n);
+    w.Aw = (double *)take((size_t)n * n * 16);
+    w.tauP = (double *)take(P * b * 16);
+    w.Tall = (double *)take(P * b * b * 16);
+    w.Y = (double *)take((size_t)n * b * 16);
+    w.YT = (double *)take((size_t)n * b * 16);
+    w.X = (double *)take((size_t)n * b * 16);
+    w.Pm = (double *)take((size_t)b * b * 16);
+    w.M = (double *)take((size_t)b * b * 16);
+    w.G = (double *)take((size_t)b * b * 16);
+    w.part = (double *)take((2 * nch + 128 * nch) * 8);
+    w.AB = (double *)take((size_t)(b + 1) * n * 16);
+    w.d = (double *)take((size_t)n * 8);
+    w.e = (double *)take((size_t)n * 8);
+    w.hv = (double *)take((cnt ? cnt : 1) * b * 16);
+    w.ht = (double *)take((cnt ? cnt : 1) * 16);
+    w.Zre = (double *)take((size_t)n * nev * 8);
+    w.Gns = (double *)take((size_t)nev * nev * 8);
+    w.Zns = (double *)take((size_t)n * nev * 8);
+    w.S = (double *)take((size_t)b * nev * 16);
+    w.S2 = (double *)take((size_t)b * nev * 16);
+    w.chase_bytes = gb::band_to_tridi_workspace_bytes_z(n, b);
+    w.chase = take(w.chase_bytes);
+    w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
     w.total = off;
     return w;
 }
@@ -204,12 +262,13 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, m, &one, w.Y, m, w.Y, m, &zero, w.G, b));
         GB_CU(gb::panel_t(b, w.G, b, tau, T, b, st));
         GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &one, w.Y, m, T, b, &zero, w.YT, m));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, m, &one, A2, ldw, w.YT, m, &zero, w.X, m));
+        // only the lower triangle of A2 is kept: X = A2 (Y T) by SYMM, the
+        // rank-2b update by SYR2K (half the flops of updating both triangles)
+        GB_BL(cublasDsymm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, m, b, &one, A2, ldw, w.YT, m, &zero, w.X, m));
         GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, m, &one, w.Y, m, w.X, m, &zero, w.Pm, b));
         GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, b, &one, T, b, w.Pm, b, &zero, w.M, b));
         GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &mhalf, w.Y, m, w.M, b, &one, w.X, m));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, m, m, b, &mone, w.X, m, w.Y, m, &one, A2, ldw));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, m, m, b, &mone, w.Y, m, w.X, m, &one, A2, ldw));
+        GB_BL(cublasDsyr2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, m, b, &mone, w.X, m, w.Y, m, &one, A2, ldw));
     }
     GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
 
@@ -220,19 +279,21 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
 
     // ---- eigenpairs of T, then one Newton-Schulz orthogonalisation step into Z
     GB_STAGE(2);
-    GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
+    GB_CU(gb::tridiag_bisect_d(n, nev, w.d, w.e, ev, w.eig, st));
     GB_STAGE(3);
+    GB_CU(gb::tridiag_invit_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
+    GB_STAGE(4);
     GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nev, nev, n, &one, w.Ztri, n, w.Ztri, n, &zero, w.Gns, nev));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
     GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, nev, nev, &one, w.Ztri, n, w.Gns, nev, &zero, Z, ldz));
 
     // ---- tridiagonal -> band (the hot path)
-    GB_STAGE(4);
+    GB_STAGE(5);
     int rc = gb_trans_ev_tridi_to_band_d(n, b, nev, w.hv, w.ht, Z, ldz, w.tev, w.tev_bytes, stream, nullptr);
     if (rc != GB_OK) return rc;
 
     // ---- band -> full, last panel first
-    GB_STAGE(5);
+    GB_STAGE(6);
     for (int p = P - 1; p >= 0; p--) {
         const int j = p * b, m = n - j - b;
         const double *panel = w.Aw + (long long)j * ldw + (j + b);
@@ -243,10 +304,103 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, w.S, b, &zero, w.S2, b));
         GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, w.Y, m, w.S2, b, &one, Zr, ldz));
     }
-    GB_STAGE(6);
+    GB_STAGE(7);
 #undef GB_STAGE
     GB_CU(cudaGetLastError());
     return GB_OK;
+}
+
+size_t gb_solve_workspace_bytes_z(int n, int nev, int nbw)
+{
+    if (n < 2 || nev < 1 || nev > n || nbw < 1 || nbw > 64 || nbw >= n) return 0;
+    return carve_z(n, nev, nbw, nullptr).total;
+}
+
+int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
+               size_t ws_bytes, void *stream, int flags)
+{
+    if (n < 2) return -1;
+    if (nev < 1 || nev > n) return -2;
+    if (nbw < 1 || nbw > 64 || nbw >= n) return -3;
+    if (!A || ((uintptr_t)A % 16) != 0) return -4;
+    if (lda < n) return -5;
+    if (!ev || ((uintptr_t)ev % 8) != 0) return -6;
+    if (!Z || ((uintptr_t)Z % 16) != 0) return -7;
+    if (ldz < n) return -8;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
+    const int b = nbw;
+    SolveWsZ w = carve_z(n, nev, b, (char *)workspace);
+    if (ws_bytes < w.total) return -10;
+    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES)) return -12;
+    cudaStream_t st = (cudaStream_t)stream;
+    cublasHandle_t h = blas_handle(st);
+    if (!h) return GB_ERR_CUDA;
+    GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
+                                                                       : CUBLAS_DEFAULT_MATH));
+    const cuDoubleComplex one{1.0, 0.0}, zero{0.0, 0.0}, mone{-1.0, 0.0}, mhalf{-0.5, 0.0};
+    const double done = 1.0, dzero = 0.0;
+    const long long ldw = n;
+    typedef cuDoubleComplex C;
+    C *Aw = (C *)w.Aw, *Y = (C *)w.Y, *YT = (C *)w.YT, *X = (C *)w.X, *Pm = (C *)w.Pm, *M = (C *)w.M,
+      *G = (C *)w.G, *S = (C *)w.S, *S2 = (C *)w.S2, *Zc = (C *)Z;
+
+    // ---- full -> band: A2 <- Q^H A2 Q, Q = I - Y T Y^H
+    GB_CU(cudaMemcpy2DAsync(Aw, (size_t)n * 16, A, (size_t)lda * 16, (size_t)n * 16, n, cudaMemcpyDeviceToDevice, st));
+    int P = 0;
+    for (int j = 0; j + b < n; j += b, P++) {
+        const int m = n - j - b;
+        C *panel = Aw + (long long)j * ldw + (j + b);
+        C *A2 = Aw + (long long)(j + b) * ldw + (j + b);
+        double *tau = w.tauP + (long long)P * b * 2;
+        C *T = (C *)(w.Tall + (long long)P * b * b * 2);
+        GB_CU(gb::zpanel_qr(m, b, (double *)panel, ldw, tau, w.part, st));
+        GB_CU(gb::zpanel_y(m, b, (const double *)panel, ldw, (double *)Y, m, st));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, m, &one, Y, m, Y, m, &zero, G, b));
+        GB_CU(gb::zpanel_t(b, (const double *)G, b, tau, (double *)T, b, st));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &one, Y, m, T, b, &zero, YT, m));
+        GB_BL(cublasZhemm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, m, b, &one, A2, ldw, YT, m, &zero, X, m));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, m, &one, Y, m, X, m, &zero, Pm, b));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, b, &one, T, b, Pm, b, &zero, M, b));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &mhalf, Y, m, M, b, &one, X, m));
+        const double rone = 1.0;  // ZHER2K: C = alpha A B^H + conj(alpha) B A^H + beta C, beta real
+        GB_BL(cublasZher2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, m, b, &mone, X, m, Y, m, &rone, A2, ldw));
+    }
+    GB_CU(gb::zband_from_full(n, b, (const double *)Aw, ldw, w.AB, b + 1, st));
+
+    // ---- band -> tridiagonal (complex reflectors, real T)
+    GB_CU(gb::band_to_tridi_z(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, 10LL * 1000 * 1000 * 1000, st));
+
+    // ---- real tridiagonal eigenpairs, Newton-Schulz, promote to complex Z
+    GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Zre, n, w.eig, st));
+    GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nev, nev, n, &done, w.Zre, n, w.Zre, n, &dzero, w.Gns, nev));
+    GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
+    GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, nev, nev, &done, w.Zre, n, w.Gns, nev, &dzero, w.Zns, n));
+    GB_CU(gb::promote_real(n, nev, w.Zns, n, Z, ldz, st));
+
+    // ---- tridiagonal -> band (complex back-transformation)
+    int rc = gb_trans_ev_tridi_to_band_z(n, b, nev, w.hv, w.ht, Z, ldz, nullptr, 0, stream, nullptr);
+    if (rc != GB_OK) return rc;
+
+    // ---- band -> full: Z_p -= Y (T (Y^H Z_p)), last panel first
+    for (int p = P - 1; p >= 0; p--) {
+        const int j = p * b, m = n - j - b;
+        const C *panel = Aw + (long long)j * ldw + (j + b);
+        const C *T = (const C *)(w.Tall + (long long)p * b * b * 2);
+        C *Zr = Zc + (j + b);
+        GB_CU(gb::zpanel_y(m, b, (const double *)panel, ldw, (double *)Y, m, st));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, nev, m, &one, Y, m, Zr, ldz, &zero, S, b));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, S, b, &zero, S2, b));
+        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, Y, m, S2, b, &one, Zr, ldz));
+    }
+    GB_CU(cudaGetLastError());
+    return GB_OK;
+}
+
+int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *stream)
+{
+    if (!workspace) return -1;
+    SolveWsZ w = carve_z(n, nev, nbw, (char *)workspace);
+    return gb_trans_ev_query(w.chase, w.chase_bytes, stream);
 }
 
 int gb_solve_stage_ms(void *stream, float *ms)

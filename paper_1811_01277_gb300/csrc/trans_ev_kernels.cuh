@@ -21,6 +21,10 @@ size_t band_to_tridi_workspace_bytes(int n, int b);
 cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
                             double *hh_tau, void *ws, size_t ws_bytes, long long timeout_ns, cudaStream_t st);
 
+size_t band_to_tridi_workspace_bytes_z(int n, int b);
+cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
+                            double *hh_tau, void *ws, long long timeout_ns, cudaStream_t st);
+
 size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads);
 bool pipeline_supported(int b);
 cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,

@@ -144,55 +144,67 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
     do {
         const double lk = lam[k];
         // ---- LU with partial pivoting of T - lk I (A: diag of U, Bs: first
-        // super-diagonal, D2: second super-diagonal, C: multipliers)
-        for (int i = 0; i < n; i++) {
-            A[i * S + k0] = d[i] - lk;
-            Bs[i * S + k0] = (i < n - 1) ? e[i] : 0.0;
-            C[i * S + k0] = (i < n - 1) ? e[i] : 0.0;
-            D2[i * S + k0] = 0.0;
-        }
-        for (int i = 0; i < n - 1; i++) {
-            double a = A[i * S + k0], c = C[i * S + k0];
-            if (dabs(a) >= dabs(c)) {
-                if (a == 0.0) a = tiny;
-                A[i * S + k0] = a;
-                const double m = c / a;
-                C[i * S + k0] = m;
-                A[(i + 1) * S + k0] -= m * Bs[i * S + k0];
-                piv[i * S + k0] = 0;
-            } else {
-                const double m = a / c;
-                const double a1 = A[(i + 1) * S + k0];
-                const double b0 = Bs[i * S + k0];
-                A[i * S + k0] = c;
-                A[(i + 1) * S + k0] = b0 - m * a1;
-                Bs[i * S + k0] = a1;
-                if (i < n - 2) {
-                    const double b1 = Bs[(i + 1) * S + k0];
+        // super-diagonal, D2: second super-diagonal, C: multipliers).  The
+        // row below the pivot is untouched before its step, so the running
+        // diagonal and super-diagonal entries are carried in registers.
+        {
+            double a_cur = d[0] - lk;
+            double b_cur = (n > 1) ? e[0] : 0.0;
+            for (int i = 0; i < n - 1; i++) {
+                const double c = e[i];
+                const double a1 = d[i + 1] - lk;
+                const double b1 = (i < n - 2) ? e[i + 1] : 0.0;
+                double a = a_cur;
+                if (dabs(a) >= dabs(c)) {
+                    if (a == 0.0) a = tiny;
+                    const double m = c / a;
+                    A[i * S + k0] = a;
+                    Bs[i * S + k0] = b_cur;
+                    D2[i * S + k0] = 0.0;
+                    C[i * S + k0] = m;
+                    piv[i * S + k0] = 0;
+                    a_cur = a1 - m * b_cur;
+                    b_cur = b1;
+                } else {
+                    const double m = a / c;
+                    A[i * S + k0] = c;
+                    Bs[i * S + k0] = a1;
                     D2[i * S + k0] = b1;
-                    Bs[(i + 1) * S + k0] = -m * b1;
+                    C[i * S + k0] = m;
+                    piv[i * S + k0] = 1;
+                    a_cur = b_cur - m * a1;
+                    b_cur = -m * b1;
                 }
-                C[i * S + k0] = m;
-                piv[i * S + k0] = 1;
             }
+            A[(n - 1) * S + k0] = (a_cur == 0.0) ? tiny : a_cur;
+            Bs[(n - 1) * S + k0] = 0.0;
+            D2[(n - 1) * S + k0] = 0.0;
         }
-        if (A[(n - 1) * S + k0] == 0.0) A[(n - 1) * S + k0] = tiny;
         for (int i = 0; i < n; i++) X[i * S + k0] = start_value(k, i);
         for (int iter = 0; iter < 3; iter++) {
-            // forward: apply the row interchanges and L^-1
-            for (int i = 0; i < n - 1; i++) {
-                double xi = X[i * S + k0], xj = X[(i + 1) * S + k0];
-                if (piv[i * S + k0]) { double t = xi; xi = xj; xj = t; X[i * S + k0] = xi; }
-                X[(i + 1) * S + k0] = xj - C[i * S + k0] * xi;
+            // forward: row interchanges and L^-1, the running entry in a register
+            {
+                double x_cur = X[k0];
+                for (int i = 0; i < n - 1; i++) {
+                    double x_next = X[(i + 1) * S + k0];
+                    if (piv[i * S + k0]) { const double t = x_cur; x_cur = x_next; x_next = t; }
+                    X[i * S + k0] = x_cur;
+                    x_cur = x_next - C[i * S + k0] * x_cur;
+                }
+                X[(n - 1) * S + k0] = x_cur;
             }
-            // backward: U^-1 (tiny pivots perturbed)
-            for (int i = n - 1; i >= 0; i--) {
-                double s = X[i * S + k0];
-                if (i + 1 < n) s -= Bs[i * S + k0] * X[(i + 1) * S + k0];
-                if (i + 2 < n) s -= D2[i * S + k0] * X[(i + 2) * S + k0];
-                double a = A[i * S + k0];
-                if (dabs(a) < tiny) a = (a < 0 ? -tiny : tiny);
-                X[i * S + k0] = s / a;
+            // backward: U^-1 (tiny pivots perturbed), the two later entries in registers
+            {
+                double x1 = 0.0, x2 = 0.0;
+                for (int i = n - 1; i >= 0; i--) {
+                    double sv = X[i * S + k0] - Bs[i * S + k0] * x1 - D2[i * S + k0] * x2;
+                    double a = A[i * S + k0];
+                    if (dabs(a) < tiny) a = (a < 0 ? -tiny : tiny);
+                    const double xi = sv / a;
+                    X[i * S + k0] = xi;
+                    x2 = x1;
+                    x1 = xi;
+                }
             }
             // Gram-Schmidt against the cluster's earlier vectors (already in Z)
             for (int j = k0; j < k; j++) {
@@ -236,28 +248,53 @@ size_t tridiag_eig_workspace_bytes(int n, int nev)
 }
 
 // lam (nev) and Z (n x nev, ldz) of the tridiagonal (d, e); before the final
-// orthogonalisation step, which the caller applies.
-cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, double *lam, double *Z, long long ldz,
-                          void *ws, cudaStream_t st)
+// orthogonalisation step, which the caller applies.  Two phases so that the
+// caller can time them separately.
+static void carve_eig(int n, int nev, void *ws, double **bounds, double **pivmin, double **e2, double **A,
+                      double **Bs, double **C, double **D2, double **X, unsigned char **piv)
 {
     char *p = (char *)ws;
-    double *bounds = (double *)p;            // lo, hi, ||T||
-    double *pivmin = (double *)(p + 256);
-    double *e2 = (double *)(p + 512);
     size_t per = (size_t)n * (size_t)nev;
-    double *A = e2 + n;
-    double *Bs = A + per;
-    double *C = Bs + per;
-    double *D2 = C + per;
-    double *X = D2 + per;
-    unsigned char *piv = (unsigned char *)(X + per);
+    *bounds = (double *)p;            // lo, hi, ||T||
+    *pivmin = (double *)(p + 256);
+    *e2 = (double *)(p + 512);
+    *A = *e2 + n;
+    *Bs = *A + per;
+    *C = *Bs + per;
+    *D2 = *C + per;
+    *X = *D2 + per;
+    *piv = (unsigned char *)(*X + per);
+}
+
+cudaError_t tridiag_bisect_d(int n, int nev, const double *d, const double *e, double *lam, void *ws, cudaStream_t st)
+{
+    double *bounds, *pivmin, *e2, *A, *Bs, *C, *D2, *X;
+    unsigned char *piv;
+    carve_eig(n, nev, ws, &bounds, &pivmin, &e2, &A, &Bs, &C, &D2, &X, &piv);
     tridiag_bounds<<<1, 256, 0, st>>>(n, d, e, bounds);
     square_offdiag<<<1, 256, 0, st>>>(n, e, e2, pivmin);
     // one warp per block: the per-eigenvalue chains are latency-bound, so
     // they are spread over as many SMs as possible
     tridiag_bisect<<<(nev + 31) / 32, 32, 0, st>>>(n, nev, d, e2, bounds, pivmin, lam);
+    return cudaGetLastError();
+}
+
+cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, const double *lam, double *Z,
+                            long long ldz, void *ws, cudaStream_t st)
+{
+    double *bounds, *pivmin, *e2, *A, *Bs, *C, *D2, *X;
+    unsigned char *piv;
+    carve_eig(n, nev, ws, &bounds, &pivmin, &e2, &A, &Bs, &C, &D2, &X, &piv);
     tridiag_invit<<<(nev + 31) / 32, 32, 0, st>>>(n, nev, d, e, lam, bounds, 1e-7, A, Bs, C, D2, piv, X, Z, ldz);
     return cudaGetLastError();
+}
+
+cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, double *lam, double *Z, long long ldz,
+                          void *ws, cudaStream_t st)
+{
+    cudaError_t err = tridiag_bisect_d(n, nev, d, e, lam, ws, st);
+    if (err != cudaSuccess) return err;
+    return tridiag_invit_d(n, nev, d, e, lam, Z, ldz, ws, st);
 }
 
 }  // namespace gb

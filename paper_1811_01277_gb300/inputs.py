@@ -121,12 +121,16 @@ def clustered_spectrum(n, seed, lo_exp=-3.0, hi=50.0, cluster_frac=0.1, cluster_
     return np.sort(np.array(lam[:n]))
 
 
-def symmetric_with_spectrum(lam, seed):
-    """A = Q diag(lam) Q^T with Q Haar-distributed (QR of a Gaussian matrix,
-    signs fixed by R's diagonal); exactly symmetric."""
+def symmetric_with_spectrum(lam, seed, cplx=False):
+    """A = Q diag(lam) Q^H with Q Haar-distributed (QR of a Gaussian matrix,
+    phases fixed by R's diagonal); exactly symmetric (Hermitian)."""
     n = len(lam)
     g = _rng(seed + 271828)
-    Q, R = np.linalg.qr(g.standard_normal((n, n)))
-    Q = Q * np.sign(np.diag(R))[None, :]
-    A = (Q * lam[None, :]) @ Q.T
-    return np.asfortranarray(0.5 * (A + A.T))
+    G = g.standard_normal((n, n))
+    if cplx:
+        G = G + 1j * g.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    dg = np.diag(R)
+    Q = Q * (dg / np.abs(dg))[None, :]
+    A = (Q * lam[None, :]) @ Q.conj().T
+    return np.asfortranarray(0.5 * (A + A.conj().T))

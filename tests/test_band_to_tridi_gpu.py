@@ -125,3 +125,55 @@ def test_chase_large_eigenvalues(gb):
     lam_B = scipy.linalg.eig_banded(lower_band(B, b), lower=True, eigvals_only=True)
     nrm = np.abs(lam_B).max()
     assert np.abs(np.sort(lam_T) - np.sort(lam_B)).max() <= 50 * n * U * nrm
+
+
+def chase_gpu_z(gb, B, b):
+    n = B.shape[0]
+    dev = torch.device("cuda")
+    AB = np.zeros((b + 1, n), dtype=np.complex128, order="F")
+    for dd in range(b + 1):
+        AB[dd, :n - dd] = np.diag(B, -dd)
+    AB_d = torch.from_numpy(np.ascontiguousarray(AB.T)).to(dev)
+    cnt = gb.gb_hh_count(n, b)
+    d = torch.zeros(n, dtype=torch.float64, device=dev)
+    e = torch.zeros(max(n - 1, 1), dtype=torch.float64, device=dev)
+    hv = torch.full((max(cnt * b, 1),), complex(np.nan, np.nan), dtype=torch.complex128, device=dev)
+    ht = torch.full((max(cnt, 1),), complex(np.nan, np.nan), dtype=torch.complex128, device=dev)
+    wsb = gb.gb_band_to_tridi_workspace_bytes_z(n, b)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    gb.gb_band_to_tridi_z(n, b, AB_d, b + 1, d, e, hv, ht, ws, wsb, st)
+    assert gb.gb_trans_ev_query(ws, wsb, st) == 0
+    return (d.cpu().numpy(), e.cpu().numpy()[:n - 1], hv.cpu().numpy()[:cnt * b], ht.cpu().numpy()[:cnt])
+
+
+@pytest.mark.parametrize("n,b", [(2, 1), (5, 2), (17, 3), (60, 7), (130, 33), (200, 64)])
+def test_chase_complex_matches_oracle(gb, n, b):
+    B = inputs.band_symmetric(n, b, seed=n + 3 * b, cplx=True)
+    d, e, hv, ht = chase_gpu_z(gb, B, b)
+    d0, e0, hv0, ht0, _ = oracle.bulge_chase(B, b)
+    nrm = np.linalg.norm(B, 2)
+    lam_T = scipy.linalg.eigvalsh_tridiagonal(d, e) if n > 1 else d
+    assert np.abs(np.sort(lam_T) - np.linalg.eigvalsh(B)).max() <= 50 * n * U * nrm
+    Q = oracle.trans_ev(n, b, hv, ht, np.eye(n, dtype=np.complex128))
+    T = np.diag(d) + np.diag(e, -1) + np.diag(e, 1)
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() <= 50 * n * U
+    assert np.abs(Q.conj().T @ B @ Q - T).max() <= 50 * n * U * nrm
+    assert np.abs(d - d0).max() <= 1e-9 * nrm and np.abs(e - e0).max() <= 1e-9 * nrm
+    assert np.abs(hv - hv0).max() <= 1e-9 and np.abs(ht - ht0).max() <= 1e-9
+
+
+def test_two_stage_tail_complex_on_gpu(gb):
+    n, b = 512, 32
+    B = inputs.band_symmetric(n, b, seed=2, cplx=True)
+    d, e, hv, ht = chase_gpu_z(gb, B, b)
+    w, V = oracle.tridiag_ql(d, e)
+    dev = torch.device("cuda")
+    Zt = torch.from_numpy(np.ascontiguousarray(V.T.astype(np.complex128))).to(dev)
+    st = torch.cuda.current_stream()
+    gb.gb_trans_ev_tridi_to_band_z(n, b, n, torch.from_numpy(hv).to(dev), torch.from_numpy(ht).to(dev), Zt, n,
+                                   None, 0, st)
+    torch.cuda.synchronize()
+    Z = Zt.cpu().numpy().T
+    assert np.linalg.norm(B @ Z - Z * w) / np.linalg.norm(B) <= 50 * n * U
+    assert np.abs(Z.conj().T @ Z - np.eye(n)).max() <= 50 * n * U

@@ -1,0 +1,61 @@
+"""Complex Hermitian two-stage solve (gb_solve_z): eigenvalues within 1e-11
+||A||_2 of LAPACK's, residual ||A Z - Z L||_F / ||A||_F and orthogonality
+||Z^H Z - I||_max within 50 n u."""
+import numpy as np
+import pytest
+
+from paper_1811_01277_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def gb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_01277_gb300 as m
+    from paper_1811_01277_gb300 import build
+    build.build()
+    m.load()
+    return m
+
+
+def solve_z(gb, A, nev, nbw):
+    n = A.shape[0]
+    dev = torch.device("cuda")
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev)
+    ev = torch.zeros(nev, dtype=torch.float64, device=dev)
+    Z = torch.zeros((nev, n), dtype=torch.complex128, device=dev)
+    wsb = gb.gb_solve_workspace_bytes_z(n, nev, nbw)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    gb.gb_solve_z(n, nev, nbw, A_d, n, ev, Z, n, ws, wsb, st, 0)
+    assert gb.gb_solve_query_z(ws, n, nev, nbw, st) == 0
+    return ev.cpu().numpy(), Z.cpu().numpy().T
+
+
+def check(A, w, Z, nev):
+    n = A.shape[0]
+    nrm = np.linalg.norm(A, 2)
+    assert np.abs(w - np.linalg.eigvalsh(A)[:nev]).max() / nrm <= 1e-11
+    assert np.linalg.norm(A @ Z - Z * w) / np.linalg.norm(A) <= 50 * n * U
+    assert np.abs(Z.conj().T @ Z - np.eye(nev)).max() <= 50 * n * U
+
+
+@pytest.mark.parametrize("n,nev,nbw", [(2, 2, 1), (5, 3, 2), (64, 64, 8), (150, 40, 16), (300, 75, 32), (400, 100, 64)])
+def test_solve_hermitian_random(gb, n, nev, nbw):
+    A = inputs.band_symmetric(n, n, seed=n + 7, cplx=True)
+    w, Z = solve_z(gb, A, nev, nbw)
+    check(A, w, Z, nev)
+
+
+def test_solve_hermitian_clustered(gb):
+    n, nev = 384, 120
+    lam = inputs.clustered_spectrum(n, seed=11)
+    A = inputs.symmetric_with_spectrum(lam, seed=12, cplx=True)
+    w, Z = solve_z(gb, A, nev, 32)
+    assert np.abs(w - lam[:nev]).max() / np.abs(lam).max() <= 1e-11
+    check(A, w, Z, nev)
