@@ -575,6 +575,59 @@ def run_stage_batched(args):
     return 0
 
 
+def run_stage_serve(args):
+    """Poisson stream of complex Hermitian requests through the
+    continuous-batching server: `systems` systems with sizes drawn from
+    --serve-sizes, each re-submitted --serve-repeats times as
+    A <- A + 1e-3 E (E Hermitian, ||E||_2 = 1, kept on the device), nev = 30%."""
+    import numpy as np
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    from paper_1811_01277_gb300 import serve
+    gbuild.build()
+    gb.load()
+    dev = torch.device("cuda", 0)
+    g = np.random.default_rng(200)
+    sizes = [int(x) for x in args.serve_sizes.split(",")]
+    gen = torch.Generator(device=dev).manual_seed(201)
+    reqs, t, rid = [], 0.0, 0
+    systems = []
+    for k in range(args.serve_systems):
+        n = int(g.choice(sizes))
+        R = torch.complex(torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64),
+                          torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64))
+        A = 0.5 * (R + R.conj().T)
+        R = torch.complex(torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64),
+                          torch.randn(n, n, generator=gen, device=dev, dtype=torch.float64))
+        E = 0.5 * (R + R.conj().T)
+        E = E / torch.linalg.matrix_norm(E, ord=2)
+        systems.append((n, A, E))
+    arrivals = np.cumsum(g.exponential(1.0 / args.serve_rate, args.serve_systems * args.serve_repeats))
+    for j in range(args.serve_repeats):
+        for k, (n, A, E) in enumerate(systems):
+            M = A + (1e-3 * j) * E
+            reqs.append(serve.Request(rid=rid, A=M.T.contiguous(), nev=int(0.3 * n), arrival=float(arrivals[rid])))
+            rid += 1
+    torch.cuda.synchronize(dev)
+    warm = serve.EigenServer(slots=args.serve_slots)
+    warm.run([serve.Request(rid=-1, A=reqs[0].A, nev=reqs[0].nev, arrival=0.0)])
+    srv = serve.EigenServer(slots=args.serve_slots, hbm_budget_bytes=args.serve_budget_gb << 30)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    done = srv.run(reqs)
+    clocks = sampler.stop()
+    summ = serve.latency_summary(done)
+    print(json.dumps({
+        "stage": "serve", "metric": "served complex Hermitian eigensolves: solves/s and latency",
+        "value": summ["solves_per_s"], "unit": "solves/s", "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+        "max_ms": summ["max_ms"], "requests": summ["requests"], "arrival_rate_per_s": args.serve_rate,
+        "sizes": sizes, "systems": args.serve_systems, "repeats": args.serve_repeats, "slots": args.serve_slots,
+        "hbm_budget_gb": args.serve_budget_gb, "failed": sum(1 for r in done if r.status != 0),
+        "dtype": "complex128", "data": "synthetic Hermitian, A <- A + 1e-3 E per re-submission",
+        "clocks": clocks}))
+    return 0
+
+
 def measure_fp64_peak():
     """Build and run the FP64 microbenchmark (DFMA and f64 mma.sync) with the
     SM clock sampled, and print one JSON line."""
@@ -612,7 +665,7 @@ def main():
     ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
                     help="walk the autotuner first and time its fastest setting")
     ap.add_argument("--measure-fp64-peak", action="store_true")
-    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve", "batched"], default="trans_ev")
+    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve", "batched", "serve"], default="trans_ev")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-lo", type=int, default=128)
     ap.add_argument("--batch-hi", type=int, default=2048)
@@ -621,6 +674,12 @@ def main():
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
     ap.add_argument("--complex", action="store_true", help="solve stage: complex128 Hermitian")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-sizes", default="512,1024,2048")
+    ap.add_argument("--serve-systems", type=int, default=6)
+    ap.add_argument("--serve-repeats", type=int, default=10)
+    ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--chase-n", type=int, default=16384)
     ap.add_argument("--chase-b", type=int, default=64)
     args = ap.parse_args()
@@ -630,6 +689,8 @@ def main():
         return run_stage_solve(args)
     if args.stage == "batched":
         return run_stage_batched(args)
+    if args.stage == "serve":
+        return run_stage_serve(args)
     if args.measure_fp64_peak:
         return measure_fp64_peak()
     wl = WORKLOADS[args.workload]

@@ -88,6 +88,7 @@ __device__ int sturm_count(int n, const double *__restrict__ d, const double *__
     double q = d[0] - x;
     if (dabs(q) < pivmin) q = -pivmin;
     cnt += q < 0.0;
+#pragma unroll 4
     for (int i = 1; i < n; i++) {
         q = (d[i] - x) - e2[i - 1] / q;
         if (dabs(q) < pivmin) q = -pivmin;
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
         {
             double a_cur = d[0] - lk;
             double b_cur = (n > 1) ? e[0] : 0.0;
+#pragma unroll 8
             for (int i = 0; i < n - 1; i++) {
                 const double c = e[i];
                 const double a1 = d[i + 1] - lk;
@@ -185,6 +187,7 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
             // forward: row interchanges and L^-1, the running entry in a register
             {
                 double x_cur = X[k0];
+#pragma unroll 8
                 for (int i = 0; i < n - 1; i++) {
                     double x_next = X[(i + 1) * S + k0];
                     if (piv[i * S + k0]) { const double t = x_cur; x_cur = x_next; x_next = t; }
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
             // backward: U^-1 (tiny pivots perturbed), the two later entries in registers
             {
                 double x1 = 0.0, x2 = 0.0;
+#pragma unroll 8
                 for (int i = n - 1; i >= 0; i--) {
                     double sv = X[i * S + k0] - Bs[i * S + k0] * x1 - D2[i * S + k0] * x2;
                     double a = A[i * S + k0];
