@@ -472,7 +472,10 @@ def run_stage_solve(args):
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
 
+    base_flags = gb.GB_SOLVE_FP64_EMULATED_GEMM if args.emulated_gemm else 0
+
     def step(flags=0):
+        flags |= base_flags
         if cplx:
             gb.gb_solve_z(n, nev, nbw, Acm, n, ev, Z, n, ws, wsb, st, flags & ~gb.GB_SOLVE_RECORD_STAGES)
         else:
@@ -505,6 +508,7 @@ def run_stage_solve(args):
     orth = (Zc.conj().T @ Zc - torch.eye(nev, dtype=Zc.dtype, device=dev)).abs().max().item()
     u = 2.0 ** -53
     print(json.dumps({
+        "emulated_gemm": bool(args.emulated_gemm),
         "stage": "solve", "metric": f"two-stage eigensolve s at n={n} ({100 * nev // n}% vecs), nbw={nbw}, "
                                     f"{'complex128 Hermitian' if cplx else 'real FP64'}",
         "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "seconds_per_solve": ms / 1e3,
@@ -674,6 +678,8 @@ def main():
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
     ap.add_argument("--complex", action="store_true", help="solve stage: complex128 Hermitian")
+    ap.add_argument("--emulated-gemm", action="store_true",
+                    help="solve stage: let cuBLAS use its fixed-point FP64 emulation for the GEMMs")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-sizes", default="512,1024,2048")
     ap.add_argument("--serve-systems", type=int, default=6)

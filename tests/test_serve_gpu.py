@@ -74,8 +74,10 @@ def test_mix_equals_alone(serve):
 
 def test_hbm_budget_limits_admission(serve):
     reqs, mats = make_requests(serve)
-    need = max(serve.request_bytes(r.n, r.nev, True, 32) for r in reqs)
-    srv = serve.EigenServer(slots=4, hbm_budget_bytes=need)   # room for one request at a time
+    # any two requests together exceed the smallest footprint: one at a time
+    # (a request larger than the budget is still admitted when nothing runs)
+    need = min(serve.request_bytes(r.n, r.nev, True, 32) for r in reqs)
+    srv = serve.EigenServer(slots=4, hbm_budget_bytes=need)
     peak = 0
     orig = srv._admit
 
