@@ -425,6 +425,22 @@ def run_stage_band_to_tridi(args):
     return 0
 
 
+def solve_flops(n, nev, nbw, cplx=False):
+    """Algorithmic flops of the two-stage solve by stage (real flops; a
+    complex multiply-add counts 8): full->band (4/3) n^3 (two-sided panel
+    reduction), the bulge chase (chase_flops), the back-transformations
+    trans_ev (algorithmic_flops) and band->full 2 n^2 nev, and the
+    Newton-Schulz step n nev^2 (Z^T Z, one triangle) + 2 n nev^2 (Z M).
+    Bisection and inverse iteration are O(n nev) per round and not counted."""
+    f = 4 if cplx else 1
+    st = {"full_to_band": f * 4 * n ** 3 // 3,
+          "band_to_tridi": f * chase_flops(n, nbw),
+          "orthogonalise": f * 3 * n * nev * nev,
+          "trans_ev_tridi_to_band": algorithmic_flops(n, nev, cplx),
+          "band_to_full": f * 2 * n * n * nev}
+    return sum(st.values()), st
+
+
 def prescribed_symmetric_gpu(lam, k, seed, dev, cplx=False):
     """A = Q diag(lam) Q^H on the device, Q = H_1 ... H_k a product of k seeded
     random Householder reflectors (tau = 2/||y||^2), built in O(n^2 k) from the
@@ -494,6 +510,7 @@ def run_stage_solve(args):
     clocks = sampler.stop()
     status = (gb.gb_solve_query_z if cplx else gb.gb_solve_query)(ws, n, nev, nbw, st)
     ms = e0.elapsed_time(e1) / args.steps
+    F, Fst = solve_flops(n, nev, nbw, cplx)
     stages = None
     if not cplx:
         step(gb.GB_SOLVE_RECORD_STAGES)        # one more solve, outside the timed region
@@ -515,6 +532,11 @@ def run_stage_solve(args):
         "steps": args.steps, "warmup": args.warmup, "status": status, "dtype": "f64",
         "data": "synthetic: A = Q diag(clustered spectrum) Q^T, Q a product of 256 seeded Householders",
         "stage_ms": stages,
+        "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12,
+                     "by_stage_tflop": {k_: v_ / 1e12 for k_, v_ in Fst.items()},
+                     "note": "whole solve against the FP64 DFMA peak; the GEMM stages run in cuBLAS DGEMM/DSYMM/"
+                             "DSYR2K, whose own ceiling on this part is 1.10 TFLOP/s"},
         "accuracy": {"max_dlambda_over_norm": dlam, "residual_rel_fro": resid, "orth_max": orth,
                      "bound_50nu": 50 * n * u, "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
         "clocks": clocks}))

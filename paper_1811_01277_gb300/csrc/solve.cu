@@ -25,6 +25,7 @@
 #include "elpa_gb300.h"
 #include "layout.cuh"
 #include "trans_ev_kernels.cuh"
+#include "tridiag_eig.cuh"
 
 namespace gb {
 
@@ -36,12 +37,6 @@ cudaError_t panel_t(int nb, const double *G, long long ldg, const double *tau, d
                     cudaStream_t st);
 cudaError_t newton_schulz_matrix(int k, double *G, long long ldg, cudaStream_t st);
 cudaError_t band_from_full(int n, int b, const double *A, long long lda, double *AB, long long ldab, cudaStream_t st);
-size_t tridiag_eig_workspace_bytes(int n, int nev);
-cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, double *lam, double *Z, long long ldz,
-                          void *ws, cudaStream_t st);
-cudaError_t tridiag_bisect_d(int n, int nev, const double *d, const double *e, double *lam, void *ws, cudaStream_t st);
-cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, const double *lam, double *Z,
-                            long long ldz, void *ws, cudaStream_t st);
 
 cudaError_t zpanel_qr(int m, int nb, double *P, long long lda, double *tau, double *part, cudaStream_t st);
 cudaError_t zpanel_y(int m, int nb, const double *P, long long lda, double *Y, long long ldy, cudaStream_t st);
@@ -283,9 +278,11 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_STAGE(3);
     GB_CU(gb::tridiag_invit_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
     GB_STAGE(4);
-    GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nev, nev, n, &one, w.Ztri, n, w.Ztri, n, &zero, w.Gns, nev));
+    // G = Z^T Z (lower triangle), M = (3I - G)/2, Z <- Z M
+    GB_BL(cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, nev, n, &one, w.Ztri, n, &zero, w.Gns, nev));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, nev, nev, &one, w.Ztri, n, w.Gns, nev, &zero, Z, ldz));
+    GB_BL(cublasDsymm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, n, nev, &one, w.Gns, nev, w.Ztri, n, &zero, Z,
+                      ldz));
 
     // ---- tridiagonal -> band (the hot path)
     GB_STAGE(5);
@@ -372,9 +369,10 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
 
     // ---- real tridiagonal eigenpairs, Newton-Schulz, promote to complex Z
     GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Zre, n, w.eig, st));
-    GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, nev, nev, n, &done, w.Zre, n, w.Zre, n, &dzero, w.Gns, nev));
+    GB_BL(cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, nev, n, &done, w.Zre, n, &dzero, w.Gns, nev));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n, nev, nev, &done, w.Zre, n, w.Gns, nev, &dzero, w.Zns, n));
+    GB_BL(cublasDsymm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, n, nev, &done, w.Gns, nev, w.Zre, n, &dzero, w.Zns,
+                      n));
     GB_CU(gb::promote_real(n, nev, w.Zns, n, Z, ldz, st));
 
     // ---- tridiagonal -> band (complex back-transformation)

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tridiag_eig.cuh"
+
 namespace gb {
 
 namespace {
@@ -80,40 +82,102 @@ __global__ void __launch_bounds__(256) square_offdiag(int n, const double *__res
     if (threadIdx.x == 0) *pivmin_out = 0x1p-1022 * sm[0];
 }
 
-// Number of eigenvalues of T below x.
-__device__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e2, double x,
-                           double pivmin)
+// |x| as an ordered integer key: for finite a, b, |a| < |b| iff
+// abs_key(a) < abs_key(b).  Comparisons and sign tests on the bit pattern run
+// on the integer pipes, not on the (narrow) FP64 pipe.
+__device__ __forceinline__ unsigned long long abs_key(double x)
 {
-    int cnt = 0;
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__device__ __forceinline__ int sign_bit(double x) { return (int)((unsigned)__double2hiint(x) >> 31); }
+
+// 1/q by Newton-Raphson refinement r <- r + r(1 - q r) (each step squares the
+// relative error) of the hardware's approximate FP64 reciprocal
+// (rcp.approx.ftz.f64): two steps give the reciprocal to about one ulp with
+// four FMAs.  Outside 2^-1000 <= |q| < 2^1000, where the approximation
+// flushes to zero or overflows, the IEEE division is used.
+__device__ __forceinline__ double recip(double q)
+{
+    const unsigned ex = ((unsigned)__double2hiint(q) >> 20) & 0x7FFu;
+    if (ex - 23u < 2000u) {
+        double r;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
+        double t = fma(-q, r, 1.0);
+        r = fma(r, t, r);
+        t = fma(-q, r, 1.0);
+        return fma(r, t, r);
+    }
+    return 1.0 / q;
+}
+
+// Number of eigenvalues of T below x: negative pivots of the LDL^T
+// factorisation of T - xI (Sylvester's law of inertia), pivots smaller than
+// pivmin in magnitude replaced by -pivmin.
+__device__ __forceinline__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e2,
+                                           double x, double pivmin, unsigned long long pivkey)
+{
     double q = d[0] - x;
-    if (dabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    if (abs_key(q) < pivkey) q = -pivmin;
+    int cnt = sign_bit(q);
 #pragma unroll 4
     for (int i = 1; i < n; i++) {
-        q = (d[i] - x) - e2[i - 1] / q;
-        if (dabs(q) < pivmin) q = -pivmin;
-        cnt += q < 0.0;
+        q = fma(-e2[i - 1], recip(q), d[i] - x);
+        if (abs_key(q) < pivkey) q = -pivmin;
+        cnt += sign_bit(q);
     }
     return cnt;
 }
 
-__global__ void __launch_bounds__(32) tridiag_bisect(int n, int nev, const double *__restrict__ d,
-                                                      const double *__restrict__ e2, const double *bounds,
-                                                      const double *pivmin_p, double *__restrict__ lam)
+// Multisection: kMultisect lanes per eigenvalue k (0-based, ascending).  In
+// each round the lanes evaluate the Sturm count at the kMultisect points that
+// split [lo, hi] into kMultisect + 1 equal parts, exchange the counts, and the
+// group keeps the part in which the count passes k.  Rounds stop when the
+// interval is within max(u ||T||, 2 (kMultisect + 1) u |x|) or cannot shrink.
+constexpr int kMultisect = 4;
+
+__global__ void __launch_bounds__(128) tridiag_bisect(int n, int nev, const double *__restrict__ d,
+                                                       const double *__restrict__ e2, const double *bounds,
+                                                       const double *pivmin_p, double *__restrict__ lam)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nev) return;
+    constexpr int P = kMultisect;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = gt / P;
+    const int j = gt % P;
+    const int lane0 = (threadIdx.x & 31) & ~(P - 1);  // first lane of this group in the warp
     const double pivmin = *pivmin_p;
+    const unsigned long long pivkey = abs_key(pivmin);
+    const double abstol = 0x1p-53 * bounds[2];
     double lo = bounds[0], hi = bounds[1];
-    for (int it = 0; it < 200; it++) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;  // interval cannot shrink further
-        if (sturm_count(n, d, e2, mid, pivmin) <= k) lo = mid;
-        else hi = mid;
+    bool done = k >= nev;
+    for (int round = 0; round < 400; round++) {
+        const double w = hi - lo;
+        if (!done) {
+            const double tol = fmax(abstol, (2.0 * (P + 1) * 0x1p-53) * fmax(fabs(lo), fabs(hi)));
+            done = !(w > tol);
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        const double h = w * (1.0 / (P + 1));
+        const int c = done ? 0 : sturm_count(n, d, e2, fma((double)(j + 1), h, lo), pivmin, pivkey);
+        int first = P;  // first point whose count exceeds k
+#pragma unroll
+        for (int m = P - 1; m >= 0; m--) {
+            const int cm = __shfl_sync(0xffffffffu, c, lane0 + m);
+            if (cm > k) first = m;
+        }
+        if (!done) {
+            const double nlo = (first == 0) ? lo : fma((double)first, h, lo);
+            const double nhi = (first == P) ? hi : fma((double)(first + 1), h, lo);
+            if (nlo <= lo && nhi >= hi) done = true;  // no progress in FP64
+            lo = nlo;
+            hi = nhi;
+        }
     }
-    lam[k] = 0.5 * (lo + hi);
+    if (j == 0 && k < nev) lam[k] = 0.5 * (lo + hi);
 }
 
+// Deterministic pseudo-random start vector entry in [-0.5, 0.5): 52 hashed
+// bits placed in the mantissa of a number in [1, 2), then shifted.
 __device__ __forceinline__ double start_value(int k, int i)
 {
     uint32_t x = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)i * 0x85EBCA77u ^ 0x1811u;
@@ -122,17 +186,34 @@ __device__ __forceinline__ double start_value(int k, int i)
     x ^= x >> 12;
     x *= 0x297A2D39u;
     x ^= x >> 15;
-    return (double)(x >> 8) * 0x1p-24 - 0.5;  // uniform in [-0.5, 0.5)
+    const uint32_t y = x * 0x9E3779B1u ^ (x >> 16);
+    return __hiloint2double(0x3FF00000 | (int)(x >> 12), (int)(y ^ (x << 20))) - 1.5;
 }
 
 // One thread per cluster leader k (lam[k] - lam[k-1] > gap, or k = 0): the
 // cluster's eigenvectors, written to Z (n x nev, column-major, ldz).
+//
+// Per eigenvalue: one pass factors P(T - lk I) = LU with partial pivoting
+// (U0 = 1/pivot, U1 = first super-diagonal of U, Cm = multiplier, piv =
+// interchange; the second super-diagonal is e[i+1] where piv[i] = 1, else 0)
+// and applies L^-1 P to the start vector on the fly (Y); then three rounds of
+// back substitution U^-1 (Y -> X, tracking max |x|), Gram-Schmidt against the
+// cluster's earlier vectors, and -- for the next round -- L^-1 P applied to X
+// (X -> Y, scaled by 1/max|x| only when max|x| leaves [2^-200, 2^200]).
+// Inputs and outputs of a pass are different arrays, so the loads of later
+// rows do not wait on the chain of the current one; pivoting decisions and
+// magnitude tracking use integer compares of the bit patterns, and each pivot
+// costs one reciprocal, so the FP64 pipe sees about 20 operations per row.
+// Work arrays are interleaved by thread ([i * S + k0]).
+__device__ __forceinline__ double select(bool c, double a, double b) { return c ? a : b; }
+
 __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double *__restrict__ d,
                                                     const double *__restrict__ e, const double *__restrict__ lam,
-                                                    const double *bounds, double gap_rel, double *__restrict__ A,
-                                                    double *__restrict__ Bs, double *__restrict__ C,
-                                                    double *__restrict__ D2, unsigned char *__restrict__ piv,
-                                                    double *__restrict__ X, double *__restrict__ Z, long long ldz)
+                                                    const double *__restrict__ bounds, double gap_rel,
+                                                    double *__restrict__ U0, double *__restrict__ U1,
+                                                    double *__restrict__ Cm, unsigned char *__restrict__ piv,
+                                                    double *__restrict__ Y, double *__restrict__ X,
+                                                    double *__restrict__ Z, long long ldz)
 {
     const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (k0 >= nev) return;
@@ -140,104 +221,116 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
     const double gap = gap_rel * tnorm;
     if (k0 > 0 && lam[k0] - lam[k0 - 1] <= gap) return;  // not a cluster leader
     const long long S = nev;                                // interleave stride
-    const double tiny = 0x1p-52 * tnorm;                    // pivot perturbation
+    const double tiny = 0x1p-52 * tnorm;                    // smallest pivot magnitude used
+    const unsigned long long tiny_key = abs_key(tiny);
+    const double inv_tiny = 1.0 / tiny;
+    U0 += k0;
+    U1 += k0;
+    Cm += k0;
+    piv += k0;
+    Y += k0;
+    X += k0;
     int k = k0;
     do {
         const double lk = lam[k];
-        // ---- LU with partial pivoting of T - lk I (A: diag of U, Bs: first
-        // super-diagonal, D2: second super-diagonal, C: multipliers).  The
-        // row below the pivot is untouched before its step, so the running
-        // diagonal and super-diagonal entries are carried in registers.
+        // ---- factor and apply L^-1 P to the start vector
         {
             double a_cur = d[0] - lk;
             double b_cur = (n > 1) ? e[0] : 0.0;
+            double y_cur = start_value(k, 0);
 #pragma unroll 8
             for (int i = 0; i < n - 1; i++) {
                 const double c = e[i];
                 const double a1 = d[i + 1] - lk;
                 const double b1 = (i < n - 2) ? e[i + 1] : 0.0;
-                double a = a_cur;
-                if (dabs(a) >= dabs(c)) {
-                    if (a == 0.0) a = tiny;
-                    const double m = c / a;
-                    A[i * S + k0] = a;
-                    Bs[i * S + k0] = b_cur;
-                    D2[i * S + k0] = 0.0;
-                    C[i * S + k0] = m;
-                    piv[i * S + k0] = 0;
-                    a_cur = a1 - m * b_cur;
-                    b_cur = b1;
-                } else {
-                    const double m = a / c;
-                    A[i * S + k0] = c;
-                    Bs[i * S + k0] = a1;
-                    D2[i * S + k0] = b1;
-                    C[i * S + k0] = m;
-                    piv[i * S + k0] = 1;
-                    a_cur = b_cur - m * a1;
-                    b_cur = -m * b1;
-                }
+                const double y_next = start_value(k, i + 1);
+                const unsigned long long ka = abs_key(a_cur), kc = abs_key(c);
+                const bool sw = kc > ka;  // interchange rows i and i+1
+                const double p = sw ? c : (ka == 0 ? tiny : a_cur);
+                const double r = recip(p);
+                const double m = (sw ? a_cur : c) * r;
+                U0[i * S] = (abs_key(p) < tiny_key) ? (sign_bit(p) ? -inv_tiny : inv_tiny) : r;
+                U1[i * S] = select(sw, a1, b_cur);
+                Cm[i * S] = m;
+                piv[i * S] = sw;
+                Y[i * S] = select(sw, y_next, y_cur);
+                y_cur = fma(-m, select(sw, y_next, y_cur), select(sw, y_cur, y_next));
+                a_cur = fma(-m, select(sw, a1, b_cur), select(sw, b_cur, a1));
+                b_cur = b1 * select(sw, -m, 1.0);
             }
-            A[(n - 1) * S + k0] = (a_cur == 0.0) ? tiny : a_cur;
-            Bs[(n - 1) * S + k0] = 0.0;
-            D2[(n - 1) * S + k0] = 0.0;
+            const double p = (abs_key(a_cur) == 0) ? tiny : a_cur;
+            U0[(n - 1) * S] = (abs_key(p) < tiny_key) ? (sign_bit(p) ? -inv_tiny : inv_tiny) : recip(p);
+            U1[(n - 1) * S] = 0.0;
+            piv[(n - 1) * S] = 0;
+            Y[(n - 1) * S] = y_cur;
         }
-        for (int i = 0; i < n; i++) X[i * S + k0] = start_value(k, i);
+        unsigned long long mx_key = 0;
         for (int iter = 0; iter < 3; iter++) {
-            // forward: row interchanges and L^-1, the running entry in a register
-            {
-                double x_cur = X[k0];
+            if (iter > 0) {
+                // L^-1 P X -> Y (X rescaled if its magnitude drifted far)
+                const double mx = __longlong_as_double((long long)mx_key);
+                const bool rescale = mx_key < abs_key(0x1p-200) || mx_key > abs_key(0x1p200);
+                const double sc = (mx_key == 0) ? 1.0 : recip(mx);
+                if (rescale) {
+                    for (int i = 0; i < n; i++) X[i * S] *= sc;
+                }
+                double y_cur = X[0];
 #pragma unroll 8
                 for (int i = 0; i < n - 1; i++) {
-                    double x_next = X[(i + 1) * S + k0];
-                    if (piv[i * S + k0]) { const double t = x_cur; x_cur = x_next; x_next = t; }
-                    X[i * S + k0] = x_cur;
-                    x_cur = x_next - C[i * S + k0] * x_cur;
+                    const double y_next = X[(i + 1) * S];
+                    const bool sw = piv[i * S];
+                    Y[i * S] = select(sw, y_next, y_cur);
+                    y_cur = fma(-Cm[i * S], select(sw, y_next, y_cur), select(sw, y_cur, y_next));
                 }
-                X[(n - 1) * S + k0] = x_cur;
+                Y[(n - 1) * S] = y_cur;
             }
-            // backward: U^-1 (tiny pivots perturbed), the two later entries in registers
+            // U^-1 Y -> X, with max |x|
             {
                 double x1 = 0.0, x2 = 0.0;
+                mx_key = 0;
 #pragma unroll 8
                 for (int i = n - 1; i >= 0; i--) {
-                    double sv = X[i * S + k0] - Bs[i * S + k0] * x1 - D2[i * S + k0] * x2;
-                    double a = A[i * S + k0];
-                    if (dabs(a) < tiny) a = (a < 0 ? -tiny : tiny);
-                    const double xi = sv / a;
-                    X[i * S + k0] = xi;
+                    const double d2 = (piv[i * S] && i < n - 2) ? e[i + 1] : 0.0;
+                    const double t = fma(-d2, x2, Y[i * S]);
+                    const double xi = fma(-U1[i * S], x1, t) * U0[i * S];
+                    X[i * S] = xi;
                     x2 = x1;
                     x1 = xi;
+                    const unsigned long long kx = abs_key(xi);
+                    mx_key = kx > mx_key ? kx : mx_key;
                 }
             }
-            // Gram-Schmidt against the cluster's earlier vectors (already in Z)
-            for (int j = k0; j < k; j++) {
-                const double *zj = Z + (long long)j * ldz;
-                double dot = 0.0;
-                for (int i = 0; i < n; i++) dot = fma(zj[i], X[i * S + k0], dot);
-                for (int i = 0; i < n; i++) X[i * S + k0] = fma(-dot, zj[i], X[i * S + k0]);
+            if (k > k0) {
+                // Gram-Schmidt against the cluster's earlier vectors (unit
+                // columns of Z), then max |x| again
+                for (int j = k0; j < k; j++) {
+                    const double *zj = Z + (long long)j * ldz;
+                    double dot = 0.0;
+                    for (int i = 0; i < n; i++) dot = fma(zj[i], X[i * S], dot);
+                    for (int i = 0; i < n; i++) X[i * S] = fma(-dot, zj[i], X[i * S]);
+                }
+                mx_key = 0;
+                for (int i = 0; i < n; i++) {
+                    const unsigned long long kx = abs_key(X[i * S]);
+                    mx_key = kx > mx_key ? kx : mx_key;
+                }
             }
-            // normalise (scale by the largest entry first to avoid overflow)
-            double mx = 0.0;
-            for (int i = 0; i < n; i++) mx = fmax(mx, dabs(X[i * S + k0]));
-            const double sc = mx > 0 ? 1.0 / mx : 1.0;
-            double nrm2 = 0.0;
-            for (int i = 0; i < n; i++) {
-                const double t = X[i * S + k0] * sc;
-                nrm2 = fma(t, t, nrm2);
-            }
-            const double inv = sc / sqrt(nrm2);
-            for (int i = 0; i < n; i++) X[i * S + k0] *= inv;
         }
-        // deterministic sign: the entry of largest magnitude is positive
-        double big = 0.0;
+        // ---- normalise (sum of squares of X / max|x|); the entry of largest
+        // magnitude (the first, scanning upwards from row 0) is made positive
+        const double sc = (mx_key == 0) ? 1.0 : recip(__longlong_as_double((long long)mx_key));
+        double ssq = 0.0, big = 0.0;
         for (int i = 0; i < n; i++) {
-            const double t = X[i * S + k0];
-            if (dabs(t) > dabs(big)) big = t;
+            const double xi = X[i * S];
+            const double t = xi * sc;
+            ssq = fma(t, t, ssq);
+            if (abs_key(xi) == mx_key && big == 0.0) big = xi;
         }
-        const double sgn = big < 0 ? -1.0 : 1.0;
+        const double nrm = sqrt(ssq) * __longlong_as_double((long long)(mx_key == 0 ? abs_key(1.0) : mx_key));
+        const double f = nrm > 0.0 ? (sign_bit(big) ? -1.0 : 1.0) / nrm : 0.0;
         double *zk = Z + (long long)k * ldz;
-        for (int i = 0; i < n; i++) zk[i] = sgn * X[i * S + k0];
+#pragma unroll 8
+        for (int i = 0; i < n; i++) zk[i] = X[i * S] * f;
         k++;
     } while (k < nev && lam[k] - lam[k - 1] <= gap);
 }
@@ -251,45 +344,59 @@ size_t tridiag_eig_workspace_bytes(int n, int nev)
     return (bytes + 255) & ~(size_t)255;
 }
 
-// lam (nev) and Z (n x nev, ldz) of the tridiagonal (d, e); before the final
-// orthogonalisation step, which the caller applies.  Two phases so that the
-// caller can time them separately.
-static void carve_eig(int n, int nev, void *ws, double **bounds, double **pivmin, double **e2, double **A,
-                      double **Bs, double **C, double **D2, double **X, unsigned char **piv)
+namespace {
+
+struct EigWork {
+    double *bounds;  // lo, hi, ||T||
+    double *pivmin;
+    double *e2;
+    double *U0, *U1, *Cm, *Y, *X;  // n x nev each, interleaved
+    unsigned char *piv;
+};
+
+EigWork carve_eig(int n, int nev, void *ws)
 {
+    EigWork w;
     char *p = (char *)ws;
     size_t per = (size_t)n * (size_t)nev;
-    *bounds = (double *)p;            // lo, hi, ||T||
-    *pivmin = (double *)(p + 256);
-    *e2 = (double *)(p + 512);
-    *A = *e2 + n;
-    *Bs = *A + per;
-    *C = *Bs + per;
-    *D2 = *C + per;
-    *X = *D2 + per;
-    *piv = (unsigned char *)(*X + per);
+    w.bounds = (double *)p;
+    w.pivmin = (double *)(p + 256);
+    w.e2 = (double *)(p + 512);
+    w.U0 = w.e2 + n;
+    w.U1 = w.U0 + per;
+    w.Cm = w.U1 + per;
+    w.Y = w.Cm + per;
+    w.X = w.Y + per;
+    w.piv = (unsigned char *)(w.X + per);
+    return w;
 }
 
+int clamp_threads(int threads) { return threads < 1 ? 1 : threads > 32 ? 32 : threads; }
+
+}  // namespace
+
+// lam (nev) and Z (n x nev, ldz) of the tridiagonal (d, e); before the final
+// orthogonalisation step, which the caller applies.  Two phases so that the
+// caller can time them separately.  `threads` = threads per block (1..32):
+// the per-eigenvalue chains are latency-bound, so they are spread over as
+// many SMs and schedulers as possible.
 cudaError_t tridiag_bisect_d(int n, int nev, const double *d, const double *e, double *lam, void *ws, cudaStream_t st)
 {
-    double *bounds, *pivmin, *e2, *A, *Bs, *C, *D2, *X;
-    unsigned char *piv;
-    carve_eig(n, nev, ws, &bounds, &pivmin, &e2, &A, &Bs, &C, &D2, &X, &piv);
-    tridiag_bounds<<<1, 256, 0, st>>>(n, d, e, bounds);
-    square_offdiag<<<1, 256, 0, st>>>(n, e, e2, pivmin);
-    // one warp per block: the per-eigenvalue chains are latency-bound, so
-    // they are spread over as many SMs as possible
-    tridiag_bisect<<<(nev + 31) / 32, 32, 0, st>>>(n, nev, d, e2, bounds, pivmin, lam);
+    EigWork w = carve_eig(n, nev, ws);
+    tridiag_bounds<<<1, 256, 0, st>>>(n, d, e, w.bounds);
+    square_offdiag<<<1, 256, 0, st>>>(n, e, w.e2, w.pivmin);
+    const long long lanes = (long long)nev * kMultisect;
+    tridiag_bisect<<<(unsigned)((lanes + 127) / 128), 128, 0, st>>>(n, nev, d, w.e2, w.bounds, w.pivmin, lam);
     return cudaGetLastError();
 }
 
 cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, const double *lam, double *Z,
-                            long long ldz, void *ws, cudaStream_t st)
+                            long long ldz, void *ws, cudaStream_t st, int threads)
 {
-    double *bounds, *pivmin, *e2, *A, *Bs, *C, *D2, *X;
-    unsigned char *piv;
-    carve_eig(n, nev, ws, &bounds, &pivmin, &e2, &A, &Bs, &C, &D2, &X, &piv);
-    tridiag_invit<<<(nev + 31) / 32, 32, 0, st>>>(n, nev, d, e, lam, bounds, 1e-7, A, Bs, C, D2, piv, X, Z, ldz);
+    EigWork w = carve_eig(n, nev, ws);
+    threads = clamp_threads(threads);
+    tridiag_invit<<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, 1e-7, w.U0, w.U1,
+                                                                      w.Cm, w.piv, w.Y, w.X, Z, ldz);
     return cudaGetLastError();
 }
 
@@ -298,7 +405,7 @@ cudaError_t tridiag_eig_d(int n, int nev, const double *d, const double *e, doub
 {
     cudaError_t err = tridiag_bisect_d(n, nev, d, e, lam, ws, st);
     if (err != cudaSuccess) return err;
-    return tridiag_invit_d(n, nev, d, e, lam, Z, ldz, ws, st);
+    return tridiag_invit_d(n, nev, d, e, lam, Z, ldz, ws, st, kTridiagThreads);
 }
 
 }  // namespace gb
