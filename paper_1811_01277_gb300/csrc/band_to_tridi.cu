@@ -12,8 +12,8 @@
 // The working matrix is kept in lower band storage of width 2b (entries up
 // to 2b-1 below the diagonal, where the bulges live), in a workspace.
 //
-// A persistent grid (one block per SM) takes sweeps by ticket in increasing
-// s; the tasks of a sweep run in order in the block that took it, each with
+// A persistent grid (at most one block per SM) takes sweeps by ticket in
+// increasing s; the tasks of a sweep run in order in the block that took it, each with
 // one round of loads into registers, the reductions, and one round of
 // stores.  Task (s,k) overlaps tasks of sweep
 // s-1 up to k+2, so it waits until sweep s-1 has finished min(k+3, nk(s-1))
@@ -497,6 +497,17 @@ size_t band_to_tridi_workspace_bytes_z(int n, int b)
     return flags_bytes(n) + ((band + 255) & ~(size_t)255);
 }
 
+// Persistent blocks for the chase: at most one per SM, and no more than the
+// sweeps that can be in flight at once (sweep s trails sweep s-1 by kLag
+// tasks, so about nk(1)/kLag sweeps are active); further blocks would only
+// poll, holding SM slots that concurrent work on other streams could use.
+static int chase_grid(int n, int b, int sms)
+{
+    const int nk1 = (n - 1 + b - 1) / b;
+    const int active = (nk1 + kLag - 1) / kLag + 2;
+    return max(1, min(min(n - 1, sms), active));
+}
+
 cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
                             double *hh_tau, void *ws, long long timeout_ns, cudaStream_t st)
 {
@@ -511,7 +522,7 @@ cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d,
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-        const int grid = min(n - 1, sms);
+        const int grid = chase_grid(n, b, sms);
         chase_z<<<(unsigned)grid, kChaseThreads, 0, st>>>(n, b, BandZ{W, ldw}, (Zc *)hh_v, (Zc *)hh_tau,
                                                          (ChaseState *)flags, (int *)(flags + 256), timeout_ns);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -535,7 +546,7 @@ cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d,
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
         if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-        const int grid = min(n - 1, sms);  // one persistent block per SM
+        const int grid = chase_grid(n, b, sms);
         chase_d<<<(unsigned)grid, kChaseThreads, 0, st>>>(n, b, Band{W, ldw}, hh_v, hh_tau, (ChaseState *)flags,
                                                          (int *)(flags + 256), timeout_ns);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;

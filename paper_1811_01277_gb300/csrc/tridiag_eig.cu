@@ -207,6 +207,14 @@ __device__ __forceinline__ double start_value(int k, int i)
 // Work arrays are interleaved by thread ([i * S + k0]).
 __device__ __forceinline__ double select(bool c, double a, double b) { return c ? a : b; }
 
+// L2 prefetch hint for a row PD rows ahead of the one being processed (the
+// passes are chains over rows, so the row loads would otherwise each pay the
+// DRAM latency once per unrolled group).
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+constexpr int kInvitPrefetch = 64;  // rows
+
+template <int PD>
 __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double *__restrict__ d,
                                                     const double *__restrict__ e, const double *__restrict__ lam,
                                                     const double *__restrict__ bounds, double gap_rel,
@@ -277,6 +285,12 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
                 double y_cur = X[0];
 #pragma unroll 8
                 for (int i = 0; i < n - 1; i++) {
+                    if (PD > 0) {
+                        const long long ip = (long long)min(i + PD, n - 1) * S;
+                        prefetch_l2(X + ip);
+                        prefetch_l2(Cm + ip);
+                        prefetch_l2(piv + ip);
+                    }
                     const double y_next = X[(i + 1) * S];
                     const bool sw = piv[i * S];
                     Y[i * S] = select(sw, y_next, y_cur);
@@ -290,6 +304,13 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
                 mx_key = 0;
 #pragma unroll 8
                 for (int i = n - 1; i >= 0; i--) {
+                    if (PD > 0) {
+                        const long long ip = (long long)max(i - PD, 0) * S;
+                        prefetch_l2(Y + ip);
+                        prefetch_l2(U1 + ip);
+                        prefetch_l2(U0 + ip);
+                        prefetch_l2(piv + ip);
+                    }
                     const double d2 = (piv[i * S] && i < n - 2) ? e[i + 1] : 0.0;
                     const double t = fma(-d2, x2, Y[i * S]);
                     const double xi = fma(-U1[i * S], x1, t) * U0[i * S];
@@ -306,8 +327,22 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
                 for (int j = k0; j < k; j++) {
                     const double *zj = Z + (long long)j * ldz;
                     double dot = 0.0;
-                    for (int i = 0; i < n; i++) dot = fma(zj[i], X[i * S], dot);
-                    for (int i = 0; i < n; i++) X[i * S] = fma(-dot, zj[i], X[i * S]);
+#pragma unroll 8
+                    for (int i = 0; i < n; i++) {
+                        if (PD > 0) {
+                            prefetch_l2(zj + min(i + PD, n - 1));
+                            prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
+                        }
+                        dot = fma(zj[i], X[i * S], dot);
+                    }
+#pragma unroll 8
+                    for (int i = 0; i < n; i++) {
+                        if (PD > 0) {
+                            prefetch_l2(zj + min(i + PD, n - 1));
+                            prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
+                        }
+                        X[i * S] = fma(-dot, zj[i], X[i * S]);
+                    }
                 }
                 mx_key = 0;
                 for (int i = 0; i < n; i++) {
@@ -320,7 +355,9 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
         // magnitude (the first, scanning upwards from row 0) is made positive
         const double sc = (mx_key == 0) ? 1.0 : recip(__longlong_as_double((long long)mx_key));
         double ssq = 0.0, big = 0.0;
+#pragma unroll 8
         for (int i = 0; i < n; i++) {
+            if (PD > 0) prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
             const double xi = X[i * S];
             const double t = xi * sc;
             ssq = fma(t, t, ssq);
@@ -330,7 +367,10 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
         const double f = nrm > 0.0 ? (sign_bit(big) ? -1.0 : 1.0) / nrm : 0.0;
         double *zk = Z + (long long)k * ldz;
 #pragma unroll 8
-        for (int i = 0; i < n; i++) zk[i] = X[i * S] * f;
+        for (int i = 0; i < n; i++) {
+            if (PD > 0) prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
+            zk[i] = X[i * S] * f;
+        }
         k++;
     } while (k < nev && lam[k] - lam[k - 1] <= gap);
 }
@@ -395,7 +435,7 @@ cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, co
 {
     EigWork w = carve_eig(n, nev, ws);
     threads = clamp_threads(threads);
-    tridiag_invit<<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, 1e-7, w.U0, w.U1,
+    tridiag_invit<kInvitPrefetch><<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, 1e-7, w.U0, w.U1,
                                                                       w.Cm, w.piv, w.Y, w.X, Z, ldz);
     return cudaGetLastError();
 }
