@@ -199,22 +199,29 @@ __device__ __forceinline__ double start_value(int k, int i)
 // and applies L^-1 P to the start vector on the fly (Y); then three rounds of
 // back substitution U^-1 (Y -> X, tracking max |x|), Gram-Schmidt against the
 // cluster's earlier vectors, and -- for the next round -- L^-1 P applied to X
-// (X -> Y, scaled by 1/max|x| only when max|x| leaves [2^-200, 2^200]).
-// Inputs and outputs of a pass are different arrays, so the loads of later
-// rows do not wait on the chain of the current one; pivoting decisions and
-// magnitude tracking use integer compares of the bit patterns, and each pivot
-// costs one reciprocal, so the FP64 pipe sees about 20 operations per row.
-// Work arrays are interleaved by thread ([i * S + k0]).
+// (X -> Y, X first rescaled by 1/max|x| only when max|x| leaves
+// [2^-200, 2^200]).
+//
+// Every pass is a chain over rows, so memory latency, not arithmetic, bounds
+// it: rows are processed in blocks of kRows, all loads of a block are issued
+// before its chain steps (and an L2 prefetch runs kPrefetch rows ahead), so a
+// block pays one memory latency.  Pivoting decisions and magnitude tracking
+// use integer compares of the bit patterns, and each pivot costs one
+// reciprocal.  Work arrays are interleaved by thread ([i * S + k0]) so that a
+// warp's accesses to one row are contiguous.
 __device__ __forceinline__ double select(bool c, double a, double b) { return c ? a : b; }
 
-// L2 prefetch hint for a row PD rows ahead of the one being processed (the
-// passes are chains over rows, so the row loads would otherwise each pay the
-// DRAM latency once per unrolled group).
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-constexpr int kInvitPrefetch = 64;  // rows
+constexpr int kRows = 8;        // rows per staged block
+constexpr int kRowsLU = 8;      // rows per staged block of the factorisation pass
+constexpr int kPrefetch = 64;   // L2 prefetch distance, rows
 
-template <int PD>
+__device__ __forceinline__ double rcp_pivot(double p, unsigned long long tiny_key, double inv_tiny)
+{
+    return (abs_key(p) < tiny_key) ? (sign_bit(p) ? -inv_tiny : inv_tiny) : recip(p);
+}
+
 __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double *__restrict__ d,
                                                     const double *__restrict__ e, const double *__restrict__ lam,
                                                     const double *__restrict__ bounds, double gap_rel,
@@ -223,6 +230,7 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
                                                     double *__restrict__ Y, double *__restrict__ X,
                                                     double *__restrict__ Z, long long ldz)
 {
+    constexpr int R = kRows;
     const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (k0 >= nev) return;
     const double tnorm = bounds[2];
@@ -241,33 +249,45 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
     int k = k0;
     do {
         const double lk = lam[k];
-        // ---- factor and apply L^-1 P to the start vector
+        // ---- factor and apply L^-1 P to the start vector (step i eliminates
+        // row i+1 with rows i, i+1 pivoted)
         {
             double a_cur = d[0] - lk;
             double b_cur = (n > 1) ? e[0] : 0.0;
             double y_cur = start_value(k, 0);
-#pragma unroll 8
-            for (int i = 0; i < n - 1; i++) {
-                const double c = e[i];
-                const double a1 = d[i + 1] - lk;
-                const double b1 = (i < n - 2) ? e[i + 1] : 0.0;
-                const double y_next = start_value(k, i + 1);
-                const unsigned long long ka = abs_key(a_cur), kc = abs_key(c);
-                const bool sw = kc > ka;  // interchange rows i and i+1
-                const double p = sw ? c : (ka == 0 ? tiny : a_cur);
-                const double r = recip(p);
-                const double m = (sw ? a_cur : c) * r;
-                U0[i * S] = (abs_key(p) < tiny_key) ? (sign_bit(p) ? -inv_tiny : inv_tiny) : r;
-                U1[i * S] = select(sw, a1, b_cur);
-                Cm[i * S] = m;
-                piv[i * S] = sw;
-                Y[i * S] = select(sw, y_next, y_cur);
-                y_cur = fma(-m, select(sw, y_next, y_cur), select(sw, y_cur, y_next));
-                a_cur = fma(-m, select(sw, a1, b_cur), select(sw, b_cur, a1));
-                b_cur = b1 * select(sw, -m, 1.0);
+            constexpr int RL = kRowsLU;
+            for (int i0 = 0; i0 < n - 1; i0 += RL) {
+                double cv[RL], av[RL], bv[RL];
+#pragma unroll
+                for (int r = 0; r < RL; r++) {
+                    const int i = i0 + r;
+                    cv[r] = (i < n - 1) ? e[i] : 0.0;
+                    av[r] = (i < n - 1) ? d[i + 1] : 0.0;
+                    bv[r] = (i < n - 2) ? e[i + 1] : 0.0;
+                }
+#pragma unroll
+                for (int r = 0; r < RL; r++) {
+                    const int i = i0 + r;
+                    if (i < n - 1) {
+                        const double c = cv[r], a1 = av[r] - lk, b1 = bv[r];
+                        const double y_next = start_value(k, i + 1);
+                        const unsigned long long ka = abs_key(a_cur), kc = abs_key(c);
+                        const bool sw = kc > ka;  // interchange rows i and i+1
+                        const double p = sw ? c : (ka == 0 ? tiny : a_cur);
+                        const double rp = recip(p);
+                        const double m = (sw ? a_cur : c) * rp;
+                        U0[i * S] = (abs_key(p) < tiny_key) ? (sign_bit(p) ? -inv_tiny : inv_tiny) : rp;
+                        U1[i * S] = select(sw, a1, b_cur);
+                        Cm[i * S] = m;
+                        piv[i * S] = sw;
+                        Y[i * S] = select(sw, y_next, y_cur);
+                        y_cur = fma(-m, select(sw, y_next, y_cur), select(sw, y_cur, y_next));
+                        a_cur = fma(-m, select(sw, a1, b_cur), select(sw, b_cur, a1));
+                        b_cur = b1 * select(sw, -m, 1.0);
+                    }
+                }
             }
-            const double p = (abs_key(a_cur) == 0) ? tiny : a_cur;
-            U0[(n - 1) * S] = (abs_key(p) < tiny_key) ? (sign_bit(p) ? -inv_tiny : inv_tiny) : recip(p);
+            U0[(n - 1) * S] = rcp_pivot((abs_key(a_cur) == 0) ? tiny : a_cur, tiny_key, inv_tiny);
             U1[(n - 1) * S] = 0.0;
             piv[(n - 1) * S] = 0;
             Y[(n - 1) * S] = y_cur;
@@ -275,26 +295,43 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
         unsigned long long mx_key = 0;
         for (int iter = 0; iter < 3; iter++) {
             if (iter > 0) {
-                // L^-1 P X -> Y (X rescaled if its magnitude drifted far)
-                const double mx = __longlong_as_double((long long)mx_key);
-                const bool rescale = mx_key < abs_key(0x1p-200) || mx_key > abs_key(0x1p200);
-                const double sc = (mx_key == 0) ? 1.0 : recip(mx);
-                if (rescale) {
+                // L^-1 P X -> Y (X rescaled first if its magnitude drifted far)
+                if (mx_key < abs_key(0x1p-200) || mx_key > abs_key(0x1p200)) {
+                    const double sc = (mx_key == 0) ? 1.0 : recip(__longlong_as_double((long long)mx_key));
                     for (int i = 0; i < n; i++) X[i * S] *= sc;
                 }
                 double y_cur = X[0];
-#pragma unroll 8
-                for (int i = 0; i < n - 1; i++) {
-                    if (PD > 0) {
-                        const long long ip = (long long)min(i + PD, n - 1) * S;
-                        prefetch_l2(X + ip);
-                        prefetch_l2(Cm + ip);
-                        prefetch_l2(piv + ip);
+                for (int i0 = 0; i0 < n - 1; i0 += R) {
+                    double xv[R], mv[R];
+                    bool pv[R];
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int i = i0 + r;
+                        if (i < n - 1) {
+                            xv[r] = X[(i + 1) * S];
+                            mv[r] = Cm[i * S];
+                            pv[r] = piv[i * S];
+                        }
                     }
-                    const double y_next = X[(i + 1) * S];
-                    const bool sw = piv[i * S];
-                    Y[i * S] = select(sw, y_next, y_cur);
-                    y_cur = fma(-Cm[i * S], select(sw, y_next, y_cur), select(sw, y_cur, y_next));
+                    {
+                        const long long ip = (long long)min(i0 + kPrefetch, n - 1) * S;
+#pragma unroll
+                        for (int r = 0; r < R; r += 4) {
+                            const long long q = ip + (long long)min(r, n - 1 - min(i0 + kPrefetch, n - 1)) * S;
+                            prefetch_l2(X + q);
+                            prefetch_l2(Cm + q);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int i = i0 + r;
+                        if (i < n - 1) {
+                            const bool sw = pv[r];
+                            const double y_next = xv[r];
+                            Y[i * S] = select(sw, y_next, y_cur);
+                            y_cur = fma(-mv[r], select(sw, y_next, y_cur), select(sw, y_cur, y_next));
+                        }
+                    }
                 }
                 Y[(n - 1) * S] = y_cur;
             }
@@ -302,23 +339,41 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
             {
                 double x1 = 0.0, x2 = 0.0;
                 mx_key = 0;
-#pragma unroll 8
-                for (int i = n - 1; i >= 0; i--) {
-                    if (PD > 0) {
-                        const long long ip = (long long)max(i - PD, 0) * S;
-                        prefetch_l2(Y + ip);
-                        prefetch_l2(U1 + ip);
-                        prefetch_l2(U0 + ip);
-                        prefetch_l2(piv + ip);
+                for (int i0 = n - 1; i0 >= 0; i0 -= R) {
+                    double yv[R], u1v[R], u0v[R], d2v[R];
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int i = i0 - r;
+                        if (i >= 0) {
+                            yv[r] = Y[i * S];
+                            u1v[r] = U1[i * S];
+                            u0v[r] = U0[i * S];
+                            d2v[r] = (i < n - 2 && piv[i * S]) ? e[i + 1] : 0.0;
+                        }
                     }
-                    const double d2 = (piv[i * S] && i < n - 2) ? e[i + 1] : 0.0;
-                    const double t = fma(-d2, x2, Y[i * S]);
-                    const double xi = fma(-U1[i * S], x1, t) * U0[i * S];
-                    X[i * S] = xi;
-                    x2 = x1;
-                    x1 = xi;
-                    const unsigned long long kx = abs_key(xi);
-                    mx_key = kx > mx_key ? kx : mx_key;
+                    {
+                        const int ib = max(i0 - kPrefetch, 0);
+#pragma unroll
+                        for (int r = 0; r < R; r += 4) {
+                            const long long q = (long long)max(ib - r, 0) * S;
+                            prefetch_l2(Y + q);
+                            prefetch_l2(U1 + q);
+                            prefetch_l2(U0 + q);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int i = i0 - r;
+                        if (i >= 0) {
+                            const double t = fma(-d2v[r], x2, yv[r]);
+                            const double xi = fma(-u1v[r], x1, t) * u0v[r];
+                            X[i * S] = xi;
+                            x2 = x1;
+                            x1 = xi;
+                            const unsigned long long kx = abs_key(xi);
+                            mx_key = kx > mx_key ? kx : mx_key;
+                        }
+                    }
                 }
             }
             if (k > k0) {
@@ -326,50 +381,75 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
                 // columns of Z), then max |x| again
                 for (int j = k0; j < k; j++) {
                     const double *zj = Z + (long long)j * ldz;
-                    double dot = 0.0;
-#pragma unroll 8
-                    for (int i = 0; i < n; i++) {
-                        if (PD > 0) {
-                            prefetch_l2(zj + min(i + PD, n - 1));
-                            prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
+                    double dp[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int i0 = 0; i0 < n; i0 += R) {
+                        double zv[R], xv[R];
+#pragma unroll
+                        for (int r = 0; r < R; r++) {
+                            const int i = i0 + r;
+                            zv[r] = (i < n) ? zj[i] : 0.0;
+                            xv[r] = (i < n) ? X[i * S] : 0.0;
                         }
-                        dot = fma(zj[i], X[i * S], dot);
+#pragma unroll
+                        for (int r = 0; r < R; r++) dp[r & 3] = fma(zv[r], xv[r], dp[r & 3]);
                     }
-#pragma unroll 8
-                    for (int i = 0; i < n; i++) {
-                        if (PD > 0) {
-                            prefetch_l2(zj + min(i + PD, n - 1));
-                            prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
+                    const double dot = (dp[0] + dp[1]) + (dp[2] + dp[3]);
+                    for (int i0 = 0; i0 < n; i0 += R) {
+                        double zv[R], xv[R];
+#pragma unroll
+                        for (int r = 0; r < R; r++) {
+                            const int i = i0 + r;
+                            if (i < n) {
+                                zv[r] = zj[i];
+                                xv[r] = X[i * S];
+                            }
                         }
-                        X[i * S] = fma(-dot, zj[i], X[i * S]);
+#pragma unroll
+                        for (int r = 0; r < R; r++) {
+                            const int i = i0 + r;
+                            if (i < n) X[i * S] = fma(-dot, zv[r], xv[r]);
+                        }
                     }
                 }
                 mx_key = 0;
-                for (int i = 0; i < n; i++) {
-                    const unsigned long long kx = abs_key(X[i * S]);
-                    mx_key = kx > mx_key ? kx : mx_key;
+                for (int i0 = 0; i0 < n; i0 += R) {
+                    double xv[R];
+#pragma unroll
+                    for (int r = 0; r < R; r++) xv[r] = (i0 + r < n) ? X[(i0 + r) * S] : 0.0;
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const unsigned long long kx = abs_key(xv[r]);
+                        mx_key = kx > mx_key ? kx : mx_key;
+                    }
                 }
             }
         }
         // ---- normalise (sum of squares of X / max|x|); the entry of largest
         // magnitude (the first, scanning upwards from row 0) is made positive
         const double sc = (mx_key == 0) ? 1.0 : recip(__longlong_as_double((long long)mx_key));
-        double ssq = 0.0, big = 0.0;
-#pragma unroll 8
-        for (int i = 0; i < n; i++) {
-            if (PD > 0) prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
-            const double xi = X[i * S];
-            const double t = xi * sc;
-            ssq = fma(t, t, ssq);
-            if (abs_key(xi) == mx_key && big == 0.0) big = xi;
+        double ssq[4] = {0.0, 0.0, 0.0, 0.0}, big = 0.0;
+        for (int i0 = 0; i0 < n; i0 += R) {
+            double xv[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) xv[r] = (i0 + r < n) ? X[(i0 + r) * S] : 0.0;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const double t = xv[r] * sc;
+                ssq[r & 3] = fma(t, t, ssq[r & 3]);
+                if (abs_key(xv[r]) == mx_key && big == 0.0) big = xv[r];
+            }
         }
-        const double nrm = sqrt(ssq) * __longlong_as_double((long long)(mx_key == 0 ? abs_key(1.0) : mx_key));
+        const double nrm = sqrt((ssq[0] + ssq[1]) + (ssq[2] + ssq[3])) *
+                           __longlong_as_double((long long)(mx_key == 0 ? abs_key(1.0) : mx_key));
         const double f = nrm > 0.0 ? (sign_bit(big) ? -1.0 : 1.0) / nrm : 0.0;
         double *zk = Z + (long long)k * ldz;
-#pragma unroll 8
-        for (int i = 0; i < n; i++) {
-            if (PD > 0) prefetch_l2(X + (long long)min(i + PD, n - 1) * S);
-            zk[i] = X[i * S] * f;
+        for (int i0 = 0; i0 < n; i0 += R) {
+            double xv[R];
+#pragma unroll
+            for (int r = 0; r < R; r++) xv[r] = (i0 + r < n) ? X[(i0 + r) * S] : 0.0;
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (i0 + r < n) zk[i0 + r] = xv[r] * f;
         }
         k++;
     } while (k < nev && lam[k] - lam[k - 1] <= gap);
@@ -435,7 +515,7 @@ cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, co
 {
     EigWork w = carve_eig(n, nev, ws);
     threads = clamp_threads(threads);
-    tridiag_invit<kInvitPrefetch><<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, 1e-7, w.U0, w.U1,
+    tridiag_invit<<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, 1e-7, w.U0, w.U1,
                                                                       w.Cm, w.piv, w.Y, w.X, Z, ldz);
     return cudaGetLastError();
 }
