@@ -535,8 +535,9 @@ def run_stage_solve(args):
         "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12,
                      "by_stage_tflop": {k_: v_ / 1e12 for k_, v_ in Fst.items()},
-                     "note": "whole solve against the FP64 DFMA peak; the GEMM stages run in cuBLAS DGEMM/DSYMM/"
-                             "DSYR2K, whose own ceiling on this part is 1.10 TFLOP/s"},
+                     "note": "whole solve against the FP64 DFMA peak; real solve: every product in this "
+                             "library's DFMA kernels (1.19-1.25 TFLOP/s on these shapes); complex solve: "
+                             "cuBLAS ZGEMM/ZHEMM/ZHER2K for the complex products"},
         "accuracy": {"max_dlambda_over_norm": dlam, "residual_rel_fro": resid, "orth_max": orth,
                      "bound_50nu": 50 * n * u, "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
         "clocks": clocks}))

@@ -185,20 +185,23 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
 
 /* Two-stage symmetric eigensolver (Sec. 2): A = Z diag(ev) Z^T for the nev
  * smallest eigenvalues of the real symmetric n x n matrix A.
- *   full -> band (Householder panels; trailing updates as cuBLAS GEMMs),
+ *   full -> band (Householder panels; trailing updates as symmetric
+ *   products on the lower triangle),
  *   band -> tridiagonal (gb_band_to_tridi_d's bulge chase),
- *   eigenpairs of the tridiagonal (bisection, inverse iteration, one
+ *   eigenpairs of the tridiagonal (multisection, inverse iteration, one
  *   Newton-Schulz orthogonalisation step),
  *   tridiagonal -> band (gb_trans_ev_tridi_to_band_d, pipeline kernel),
- *   band -> full (block reflectors as cuBLAS GEMMs).
+ *   band -> full (block reflectors as matrix products).
+ * All FP64 matrix products run in this library's DFMA-tiled kernels.
  * Arguments (device pointers): 1 n >= 2; 2 nev in 1..n; 3 nbw in 1..min(64,
  * n-1), the intermediate band width; 4 A (column-major, lda; read only, both
  * triangles used); 5 lda >= n; 6 ev (nev, ascending); 7 Z (n x nev,
  * column-major); 8 ldz >= n; 9 workspace (256-byte aligned); 10 ws_bytes >=
- * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0, or
- * GB_SOLVE_FP64_EMULATED_GEMM to let cuBLAS use its fixed-point FP64
- * emulation for the GEMMs where it supports it.  Asynchronous; device-side
- * status of the dependency waits through gb_solve_query. */
+ * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0,
+ * GB_SOLVE_RECORD_STAGES, or GB_SOLVE_FP64_EMULATED_GEMM (accepted, no effect
+ * here: it selects cuBLAS's fixed-point FP64 emulation for the complex
+ * solve's cuBLAS products).  Asynchronous; device-side status of the
+ * dependency waits through gb_solve_query. */
 #define GB_SOLVE_FP64_EMULATED_GEMM 1
 #define GB_SOLVE_RECORD_STAGES 2 /* record CUDA events at the stage boundaries */
 size_t gb_solve_workspace_bytes(int n, int nev, int nbw);

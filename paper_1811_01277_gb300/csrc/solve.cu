@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -25,6 +26,7 @@
 #include "elpa_gb300.h"
 #include "layout.cuh"
 #include "trans_ev_kernels.cuh"
+#include "dgemm_dfma.cuh"
 #include "tridiag_eig.cuh"
 
 namespace gb {
@@ -99,10 +101,14 @@ cudaEvent_t *stage_events(cudaStream_t st)
 
 // Workspace carve-up (all pieces 256-byte aligned).
 struct SolveWs {
-    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2;
+    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2, *gw;
     void *chase, *eig, *tev;
-    size_t chase_bytes, tev_bytes, total;
+    size_t chase_bytes, tev_bytes, gw_elems, total;
 };
+
+// Split-K partials of the DFMA products (the kernels split only as far as
+// this holds).
+size_t gemm_work_elems(int n, int b) { return std::max((size_t)8 * n * b, (size_t)1 << 22); }
 
 SolveWs carve(int n, int nev, int b, char *base)
 {
@@ -135,6 +141,8 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.Gns = (double *)take((size_t)nev * nev * 8);
     w.S = (double *)take((size_t)b * nev * 8);
     w.S2 = (double *)take((size_t)b * nev * 8);
+    w.gw_elems = gemm_work_elems(n, b);
+    w.gw = (double *)take(w.gw_elems * 8);
     w.chase_bytes = gb::band_to_tridi_workspace_bytes(n, b);
     w.chase = take(w.chase_bytes);
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
@@ -146,9 +154,9 @@ SolveWs carve(int n, int nev, int b, char *base)
 
 // Complex workspace: complex pieces hold 2 doubles per entry.
 struct SolveWsZ {
-    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Zre, *Gns, *Zns, *S, *S2;
+    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Zre, *Gns, *Zns, *S, *S2, *gw;
     void *chase, *eig;
-    size_t chase_bytes, total;
+    size_t chase_bytes, gw_elems, total;
 };
 
 SolveWsZ carve_z(int n, int nev, int b, char *base)
@@ -183,6 +191,8 @@ SolveWsZ carve_z(int n, int nev, int b, char *base)
     w.Zns = (double *)take((size_t)n * nev * 8);
     w.S = (double *)take((size_t)b * nev * 16);
     w.S2 = (double *)take((size_t)b * nev * 16);
+    w.gw_elems = gemm_work_elems(n, b);
+    w.gw = (double *)take(w.gw_elems * 8);
     w.chase_bytes = gb::band_to_tridi_workspace_bytes_z(n, b);
     w.chase = take(w.chase_bytes);
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
@@ -235,11 +245,8 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     do {                                                                   \
         if (sev && cudaEventRecord(sev[i], st) != cudaSuccess) return GB_ERR_CUDA; \
     } while (0)
-    cublasHandle_t h = blas_handle(st);
-    if (!h) return GB_ERR_CUDA;
-    GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
-                                                                       : CUBLAS_DEFAULT_MATH));
-    const double one = 1.0, zero = 0.0, mone = -1.0, mhalf = -0.5;
+    // the real path's products run in this library's DFMA kernels; the
+    // cuBLAS emulation flag only concerns the complex path
     const long long ldw = n;
 
     // ---- full -> band
@@ -254,16 +261,16 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         double *T = w.Tall + (long long)P * b * b;
         GB_CU(gb::panel_qr(m, b, panel, ldw, tau, w.part, st));
         GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, m, &one, w.Y, m, w.Y, m, &zero, w.G, b));
+        GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, w.Y, m, w.Y, m, 0.0, w.G, b, w.gw, w.gw_elems, st));
         GB_CU(gb::panel_t(b, w.G, b, tau, T, b, st));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &one, w.Y, m, T, b, &zero, w.YT, m));
-        // only the lower triangle of A2 is kept: X = A2 (Y T) by SYMM, the
-        // rank-2b update by SYR2K (half the flops of updating both triangles)
-        GB_BL(cublasDsymm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, m, b, &one, A2, ldw, w.YT, m, &zero, w.X, m));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, m, &one, w.Y, m, w.X, m, &zero, w.Pm, b));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, b, b, &one, T, b, w.Pm, b, &zero, w.M, b));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &mhalf, w.Y, m, w.M, b, &one, w.X, m));
-        GB_BL(cublasDsyr2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, m, b, &mone, w.X, m, w.Y, m, &one, A2, ldw));
+        GB_CU(gb::dfma_gemm('N', 'N', m, b, b, 1.0, w.Y, m, T, b, 0.0, w.YT, m, w.gw, w.gw_elems, st));
+        // only the lower triangle of A2 is kept: X = A2 (Y T) (symmetric
+        // product), the rank-2b update on the lower triangle only
+        GB_CU(gb::dfma_symm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, w.Y, m, w.X, m, 0.0, w.Pm, b, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_gemm('T', 'N', b, b, b, 1.0, T, b, w.Pm, b, 0.0, w.M, b, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_gemm('N', 'N', m, b, b, -0.5, w.Y, m, w.M, b, 1.0, w.X, m, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_syr2k_lower(m, b, -1.0, w.X, m, w.Y, m, 1.0, A2, ldw, st));
     }
     GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
 
@@ -279,10 +286,9 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_CU(gb::tridiag_invit_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
     GB_STAGE(4);
     // G = Z^T Z (lower triangle), M = (3I - G)/2, Z <- Z M
-    GB_BL(cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, nev, n, &one, w.Ztri, n, &zero, w.Gns, nev));
+    GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, st));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    GB_BL(cublasDsymm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, n, nev, &one, w.Gns, nev, w.Ztri, n, &zero, Z,
-                      ldz));
+    GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.gw, w.gw_elems, st));
 
     // ---- tridiagonal -> band (the hot path)
     GB_STAGE(5);
@@ -297,9 +303,9 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         const double *T = w.Tall + (long long)p * b * b;
         double *Zr = Z + (j + b);
         GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, b, nev, m, &one, w.Y, m, Zr, ldz, &zero, w.S, b));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, w.S, b, &zero, w.S2, b));
-        GB_BL(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, w.Y, m, w.S2, b, &one, Zr, ldz));
+        GB_CU(gb::dfma_gemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_gemm('N', 'N', b, nev, b, 1.0, T, b, w.S, b, 0.0, w.S2, b, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_gemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.gw, w.gw_elems, st));
     }
     GB_STAGE(7);
 #undef GB_STAGE
@@ -335,7 +341,6 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
                                                                        : CUBLAS_DEFAULT_MATH));
     const cuDoubleComplex one{1.0, 0.0}, zero{0.0, 0.0}, mone{-1.0, 0.0}, mhalf{-0.5, 0.0};
-    const double done = 1.0, dzero = 0.0;
     const long long ldw = n;
     typedef cuDoubleComplex C;
     C *Aw = (C *)w.Aw, *Y = (C *)w.Y, *YT = (C *)w.YT, *X = (C *)w.X, *Pm = (C *)w.Pm, *M = (C *)w.M,
@@ -369,10 +374,9 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
 
     // ---- real tridiagonal eigenpairs, Newton-Schulz, promote to complex Z
     GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Zre, n, w.eig, st));
-    GB_BL(cublasDsyrk(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, nev, n, &done, w.Zre, n, &dzero, w.Gns, nev));
+    GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, st));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    GB_BL(cublasDsymm(h, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, n, nev, &done, w.Gns, nev, w.Zre, n, &dzero, w.Zns,
-                      n));
+    GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.gw, w.gw_elems, st));
     GB_CU(gb::promote_real(n, nev, w.Zns, n, Z, ldz, st));
 
     // ---- tridiagonal -> band (complex back-transformation)
