@@ -544,6 +544,73 @@ def run_stage_solve(args):
     return 0
 
 
+def run_stage_gemm(args):
+    """The solver's FP64 products at the shapes of an n = 16384, nev = 4096,
+    nbw = 64 solve: this library's DFMA kernels (gb_dgemm / gb_dsymm /
+    gb_dsyr2k / gb_dsyrk) against torch's float64 products on the same
+    device (cuBLAS); one JSON line with TFLOP/s and the fraction of the FP64
+    DFMA peak for each."""
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    gbuild.build()
+    gb.load()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev).manual_seed(77)
+    n, nev, b = 16384, 4096, 64
+    m = n - b
+    A = torch.rand(n, n, generator=g, device=dev, dtype=torch.float64) - 0.5      # column-major view: A.T
+    Y = torch.rand(b, m, generator=g, device=dev, dtype=torch.float64) - 0.5      # m x b column-major
+    X = torch.rand(b, m, generator=g, device=dev, dtype=torch.float64) - 0.5
+    Zt = torch.rand(nev, n, generator=g, device=dev, dtype=torch.float64) - 0.5   # n x nev column-major
+    Cb = torch.empty(b, m, device=dev, dtype=torch.float64)
+    G = torch.empty(nev, nev, device=dev, dtype=torch.float64)
+    Zo = torch.empty(nev, n, device=dev, dtype=torch.float64)
+    wsb = gb.gb_dgemm_workspace_bytes(n, b)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    Asym = A.T                                  # only the lower triangle matters to gb_dsymm
+    cases = [
+        ("symm_L m=16320 n=64 (full->band X = A2 YT)", 2.0 * m * m * b,
+         lambda: gb.gb_dsymm("L", m, b, 1.0, A, n, Y, m, 0.0, Cb, m, ws, wsb, st),
+         lambda: torch.mm(Asym[:m, :m], Y.T)),
+        ("syr2k m=16320 k=64 (full->band rank-2b update)", 2.0 * m * m * b,
+         lambda: gb.gb_dsyr2k(m, b, -1.0, X, m, Y, m, 1.0, A, n, st),
+         lambda: A[:m, :m].addmm_(X.T, Y, alpha=-1.0).addmm_(Y.T, X, alpha=-1.0)),
+        ("gemm TN 64 x 4096 k=16384 (band->full Y^T Z)", 2.0 * b * nev * n,
+         lambda: gb.gb_dgemm("T", "N", b, nev, n, 1.0, A, n, Zt, n, 0.0, G, b, ws, wsb, st),
+         lambda: torch.mm(A[:b, :], Zt.T)),
+        ("gemm NN 16384 x 4096 k=64 (band->full Z -= Y S2)", 2.0 * n * nev * b,
+         lambda: gb.gb_dgemm("N", "N", n, nev, b, -1.0, A, n, G, b, 1.0, Zo, n, ws, wsb, st),
+         lambda: Zo.T.addmm_(A[:b, :].T, G.view(-1)[:b * nev].view(nev, b).T, alpha=-1.0)),
+        ("syrk 4096 k=16384 (Newton-Schulz Z^T Z)", 1.0 * nev * nev * n,
+         lambda: gb.gb_dsyrk(nev, n, 1.0, Zt, n, 0.0, G, nev, st),
+         lambda: torch.mm(Zt, Zt.T, out=G)),
+    ]
+    res = {}
+    for name, flops, ours, ref in cases:
+        out = {}
+        for label, f in (("dfma", ours), ("torch_cublas", ref)):
+            for _ in range(max(1, args.warmup)):
+                f()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(args.steps):
+                f()
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / args.steps
+            out[label] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+        out["frac_of_fp64_peak"] = out["dfma"]["tflops"] / FP64_PEAK_TFLOPS
+        out["cublas_note"] = "torch float64 matmul (cuBLAS DGEMM); syr2k as two full GEMMs, so twice the flops"
+        res[name] = out
+    print(json.dumps({"stage": "gemm", "metric": "FP64 products of the n=16384 solve, TFLOP/s",
+                      "peak_tflops": FP64_PEAK_TFLOPS, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f64", "data": "synthetic U[-0.5,0.5]", "cases": res}))
+    return 0
+
+
 def run_stage_batched(args):
     """Many independent problems (sizes U[lo, hi], N(0,1) entries symmetrised,
     all eigenpairs) through gb_solve_batched_d on several streams: solves/s
@@ -692,7 +759,8 @@ def main():
     ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
                     help="walk the autotuner first and time its fastest setting")
     ap.add_argument("--measure-fp64-peak", action="store_true")
-    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve", "batched", "serve"], default="trans_ev")
+    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve", "batched", "serve", "gemm"],
+                    default="trans_ev")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-lo", type=int, default=128)
     ap.add_argument("--batch-hi", type=int, default=2048)
@@ -716,6 +784,8 @@ def main():
         return run_stage_band_to_tridi(args)
     if args.stage == "solve":
         return run_stage_solve(args)
+    if args.stage == "gemm":
+        return run_stage_gemm(args)
     if args.stage == "batched":
         return run_stage_batched(args)
     if args.stage == "serve":

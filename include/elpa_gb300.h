@@ -275,6 +275,35 @@ int gb_autotune_progress(const gb_autotune *t, int *tried, int *total);
 int gb_autotune_save(const gb_autotune *t, const char *path);
 gb_autotune *gb_autotune_load(const char *path);
 
+/* FP64 matrix products (column-major, device pointers, asynchronous on
+ * `stream`).  The paper's solver hands these steps to BLAS (Sec. 3.2: the
+ * GPU version calls cuBLAS for the matrix products of the reduction and the
+ * back-transformations); here they run in this library's DFMA-tiled kernels,
+ * which the solver uses internally.  `workspace` (8-byte aligned, or NULL
+ * with ws_bytes 0) holds split-K partial products: a call splits the
+ * reduction only as far as ws_bytes allows (gb_dgemm_workspace_bytes(m, n)
+ * is always enough).  Returns GB_OK, -i for invalid argument i (nothing
+ * launched), or GB_ERR_CUDA.
+ *   gb_dgemm : C (m x n) = alpha op(A) op(B) + beta C, trans = 'N' or 'T',
+ *              op(A) m x k, op(B) k x n; lda >= rows of A as stored, etc.
+ *   gb_dsymm : side 'L': C (m x n) = alpha S B + beta C, S (m x m);
+ *              side 'R': C = alpha B S + beta C, S (n x n); S symmetric,
+ *              only its lower triangle is read.
+ *   gb_dsyr2k: lower triangle of C (n x n) = alpha (A B^T + B A^T) + beta C,
+ *              A, B n x k; the strict upper triangle of C is not touched.
+ *   gb_dsyrk : lower triangle of C (n x n) = alpha A^T A + beta C, A k x n.
+ * beta = 0 does not read C. */
+size_t gb_dgemm_workspace_bytes(int m, int n);
+int gb_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+             const double *B, int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes,
+             void *stream);
+int gb_dsymm(char side, int m, int n, double alpha, const double *S, int lds, const double *B, int ldb,
+             double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);
+int gb_dsyr2k(int n, int k, double alpha, const double *A, int lda, const double *B, int ldb, double beta,
+              double *C, int ldc, void *stream);
+int gb_dsyrk(int n, int k, double alpha, const double *A, int lda, double beta, double *C, int ldc,
+             void *stream);
+
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);
 

@@ -33,6 +33,7 @@ EXPORTS = (
     "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d", "gb_solve_stage_ms",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
+    "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
 )
 GB_SOLVE_RECORD_STAGES = 2
 SOLVE_STAGES = ("full_to_band", "band_to_tridi", "bisection", "inverse_iteration", "orthogonalise",
@@ -115,6 +116,12 @@ def load(path=None):
     L.gb_solve_batched_workspace_bytes.restype = sz
     L.gb_solve_batched_d.argtypes = [i, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
     L.gb_solve_batched_d.restype = i
+    ch, dd = ctypes.c_char, ctypes.c_double
+    L.gb_dgemm_workspace_bytes.argtypes = [i, i]; L.gb_dgemm_workspace_bytes.restype = sz
+    L.gb_dgemm.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dgemm.restype = i
+    L.gb_dsymm.argtypes = [ch, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dsymm.restype = i
+    L.gb_dsyr2k.argtypes = [i, i, dd, p, i, p, i, dd, p, i, p]; L.gb_dsyr2k.restype = i
+    L.gb_dsyrk.argtypes = [i, i, dd, p, i, dd, p, i, p]; L.gb_dsyrk.restype = i
     _lib = L
     return L
 
@@ -361,6 +368,46 @@ def gb_solve_batched_d(n, nev, A, lda, ev, Z, ldz, workspace, ws_bytes, streams,
                                    _iarr(ldz), _p(workspace), ws_bytes, len(streams), st, es, ee)
     if check and rc != GB_OK:
         raise GbError(rc, "gb_solve_batched_d")
+    return rc
+
+
+def gb_dgemm_workspace_bytes(m, n):
+    return load().gb_dgemm_workspace_bytes(m, n)
+
+
+def _c(ch):
+    return ch.encode() if isinstance(ch, str) else ch
+
+
+def gb_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace=None, ws_bytes=0,
+             stream=None, check=True):
+    rc = load().gb_dgemm(_c(transa), _c(transb), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc,
+                         _p(workspace), ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dgemm")
+    return rc
+
+
+def gb_dsymm(side, m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace=None, ws_bytes=0, stream=None,
+             check=True):
+    rc = load().gb_dsymm(_c(side), m, n, alpha, _p(S), lds, _p(B), ldb, beta, _p(C), ldc, _p(workspace),
+                         ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dsymm")
+    return rc
+
+
+def gb_dsyr2k(n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None, check=True):
+    rc = load().gb_dsyr2k(n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dsyr2k")
+    return rc
+
+
+def gb_dsyrk(n, k, alpha, A, lda, beta, C, ldc, stream=None, check=True):
+    rc = load().gb_dsyrk(n, k, alpha, _p(A), lda, beta, _p(C), ldc, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dsyrk")
     return rc
 
 

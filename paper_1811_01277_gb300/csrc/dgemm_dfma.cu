@@ -15,7 +15,10 @@
 // crosses the diagonal is read element by element.
 #include <cuda_runtime.h>
 
+#include <stdint.h>
+
 #include "dgemm_dfma.cuh"
+#include "elpa_gb300.h"
 
 namespace gb {
 
@@ -338,3 +341,87 @@ cudaError_t dfma_syrk_lower_t(int n, int k, double alpha, const double *A, long 
 }
 
 }  // namespace gb
+
+extern "C" {
+
+size_t gb_dgemm_workspace_bytes(int m, int n)
+{
+    if (m < 0 || n < 0) return 0;
+    return (size_t)512 * (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1) * 8;
+}
+
+static bool bad_ptr(const void *p) { return !p || ((uintptr_t)p % 8) != 0; }
+
+int gb_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+             const double *B, int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes,
+             void *stream)
+{
+    const bool ta = transa == 'T' || transa == 't', tb = transb == 'T' || transb == 't';
+    if (!ta && transa != 'N' && transa != 'n') return -1;
+    if (!tb && transb != 'N' && transb != 'n') return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    if (m == 0 || n == 0) return GB_OK;
+    if (k > 0 && bad_ptr(A)) return -7;
+    if (lda < (ta ? (k > 1 ? k : 1) : m)) return -8;
+    if (k > 0 && bad_ptr(B)) return -9;
+    if (ldb < (tb ? n : (k > 1 ? k : 1))) return -10;
+    if (bad_ptr(C)) return -12;
+    if (ldc < m) return -13;
+    if (ws_bytes > 0 && bad_ptr(workspace)) return -14;
+    cudaError_t e = gb::dfma_gemm(ta ? 'T' : 'N', tb ? 'T' : 'N', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                  ws_bytes ? (double *)workspace : nullptr, ws_bytes / 8, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+int gb_dsymm(char side, int m, int n, double alpha, const double *S, int lds, const double *B, int ldb,
+             double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream)
+{
+    const bool left = side == 'L' || side == 'l';
+    if (!left && side != 'R' && side != 'r') return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (m == 0 || n == 0) return GB_OK;
+    if (bad_ptr(S)) return -5;
+    if (lds < (left ? m : n)) return -6;
+    if (bad_ptr(B)) return -7;
+    if (ldb < m) return -8;
+    if (bad_ptr(C)) return -10;
+    if (ldc < m) return -11;
+    if (ws_bytes > 0 && bad_ptr(workspace)) return -12;
+    cudaError_t e = gb::dfma_symm(left ? 'L' : 'R', m, n, alpha, S, lds, B, ldb, beta, C, ldc,
+                                  ws_bytes ? (double *)workspace : nullptr, ws_bytes / 8, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+int gb_dsyr2k(int n, int k, double alpha, const double *A, int lda, const double *B, int ldb, double beta,
+              double *C, int ldc, void *stream)
+{
+    if (n < 0) return -1;
+    if (k < 0) return -2;
+    if (n == 0) return GB_OK;
+    if (k > 0 && bad_ptr(A)) return -4;
+    if (lda < n) return -5;
+    if (k > 0 && bad_ptr(B)) return -6;
+    if (ldb < n) return -7;
+    if (bad_ptr(C)) return -9;
+    if (ldc < n) return -10;
+    cudaError_t e = gb::dfma_syr2k_lower(n, k, alpha, A, lda, B, ldb, beta, C, ldc, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+int gb_dsyrk(int n, int k, double alpha, const double *A, int lda, double beta, double *C, int ldc, void *stream)
+{
+    if (n < 0) return -1;
+    if (k < 0) return -2;
+    if (n == 0) return GB_OK;
+    if (k > 0 && bad_ptr(A)) return -4;
+    if (lda < (k > 1 ? k : 1)) return -5;
+    if (bad_ptr(C)) return -7;
+    if (ldc < n) return -8;
+    cudaError_t e = gb::dfma_syrk_lower_t(n, k, alpha, A, lda, beta, C, ldc, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+}  // extern "C"
