@@ -234,7 +234,8 @@ int elpa_b200_solve(int n, int nev, const double *A, int lda, double *ev, double
  * Z[i] n[i] x nev[i], ldz[i]; all device pointers), each with band width
  * gb_solve_default_nbw(n[i]).  Problem i runs on streams[i % nslots] in
  * workspace slot i % nslots, so up to nslots solves overlap on the GPU; the
- * host only enqueues (asynchronous).  If ev_start / ev_end are non-NULL,
+ * host only enqueues (asynchronous), one host thread per slot, and returns
+ * when every problem is enqueued.  If ev_start / ev_end are non-NULL,
  * events ev_start[i] / ev_end[i] (cudaEvent_t, created by the caller) are
  * recorded around problem i on its stream.  Arguments: 1 count >= 1; 2-8 the
  * per-problem arrays; 9 workspace (256-byte aligned); 10 ws_bytes >=

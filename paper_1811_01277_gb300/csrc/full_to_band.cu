@@ -16,9 +16,12 @@
 // Each block reduces the (few) partials itself, so no atomics are needed.
 // On exit the panel holds R on and above the diagonal and v below it
 // (LAPACK layout, v_0 = 1 implicit); tau holds the nb scalars.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 namespace gb {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -39,8 +42,7 @@ __device__ double block_reduce_sum(double x, double *red)
 }
 
 // partial squared norm of column 0 below its first row, per chunk
-__global__ void __launch_bounds__(kChunk) panel_first_norm(int m, const double *__restrict__ P, long long lda,
-                                                           double *__restrict__ part)
+__device__ __forceinline__ void first_norm_phase(int m, const double *__restrict__ P, double *__restrict__ part)
 {
     __shared__ double red[kChunk / 32];
     const int r = blockIdx.x * kChunk + threadIdx.x;
@@ -49,9 +51,15 @@ __global__ void __launch_bounds__(kChunk) panel_first_norm(int m, const double *
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kChunk) panel_refl_dots(int m, int nb, int i, double *__restrict__ P, long long lda,
-                                                          const double *__restrict__ part_norm, int nchunks,
-                                                          double *__restrict__ part_dot, double *__restrict__ tau)
+__global__ void __launch_bounds__(kChunk) panel_first_norm(int m, const double *__restrict__ P, long long lda,
+                                                           double *__restrict__ part)
+{
+    first_norm_phase(m, P, part);
+}
+
+__device__ __forceinline__ void refl_dots_phase(int m, int nb, int i, double *__restrict__ P, long long lda,
+                                                const double *__restrict__ part_norm, int nchunks,
+                                                double *__restrict__ part_dot, double *__restrict__ tau)
 {
     __shared__ double red[kChunk / 32];
     __shared__ double s_tau, s_scal;
@@ -105,10 +113,17 @@ __global__ void __launch_bounds__(kChunk) panel_refl_dots(int m, int nb, int i, 
     if (r > i && r < m && t != 0.0) col[r] = v;
 }
 
-__global__ void __launch_bounds__(kChunk) panel_update(int m, int nb, int i, double *__restrict__ P, long long lda,
-                                                       const double *__restrict__ part_dot, int nchunks,
-                                                       const double *__restrict__ tau, double *__restrict__ part_norm,
-                                                       const double *__restrict__ part_norm_prev)
+__global__ void __launch_bounds__(kChunk) panel_refl_dots(int m, int nb, int i, double *__restrict__ P, long long lda,
+                                                          const double *__restrict__ part_norm, int nchunks,
+                                                          double *__restrict__ part_dot, double *__restrict__ tau)
+{
+    refl_dots_phase(m, nb, i, P, lda, part_norm, nchunks, part_dot, tau);
+}
+
+__device__ __forceinline__ void update_phase(int m, int nb, int i, double *__restrict__ P, long long lda,
+                                             const double *__restrict__ part_dot, int nchunks,
+                                             const double *__restrict__ tau, double *__restrict__ part_norm,
+                                             const double *__restrict__ part_norm_prev)
 {
     __shared__ double red[kChunk / 32];
     __shared__ double w[kPanelMax];
@@ -153,6 +168,35 @@ __global__ void __launch_bounds__(kChunk) panel_update(int m, int nb, int i, dou
         if (threadIdx.x == 0) part_norm[blockIdx.x] = s;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) col[i] = s_beta;  // R's diagonal entry
+}
+
+__global__ void __launch_bounds__(kChunk) panel_update(int m, int nb, int i, double *__restrict__ P, long long lda,
+                                                       const double *__restrict__ part_dot, int nchunks,
+                                                       const double *__restrict__ tau, double *__restrict__ part_norm,
+                                                       const double *__restrict__ part_norm_prev)
+{
+    update_phase(m, nb, i, P, lda, part_dot, nchunks, tau, part_norm, part_norm_prev);
+}
+
+// The whole panel in one cooperative launch: the same phases, separated by
+// grid-wide barriers instead of kernel boundaries (2 nb + 1 launches become
+// one).  Launched only when every block of the grid can be resident.
+__global__ void __launch_bounds__(kChunk) panel_qr_fused(int m, int nb, double *__restrict__ P, long long lda,
+                                                         double *__restrict__ tau, double *__restrict__ norm_a,
+                                                         double *__restrict__ norm_b, double *__restrict__ dots,
+                                                         int nchunks)
+{
+    cg::grid_group grid = cg::this_grid();
+    first_norm_phase(m, P, norm_a);
+    grid.sync();
+    for (int i = 0; i < nb && i < m; i++) {
+        double *cur = (i % 2 == 0) ? norm_a : norm_b;
+        double *nxt = (i % 2 == 0) ? norm_b : norm_a;
+        refl_dots_phase(m, nb, i, P, lda, cur, nchunks, dots, tau);
+        grid.sync();
+        update_phase(m, nb, i, P, lda, dots, nchunks, tau, nxt, cur);
+        grid.sync();
+    }
 }
 
 // Y (m x nb, explicit unit lower trapezoidal) from the QR'd panel.
@@ -244,6 +288,18 @@ cudaError_t panel_qr(int m, int nb, double *P, long long lda, double *tau, doubl
     // columns past the last reflector (m < nb) keep tau = 0
     cudaError_t e = cudaMemsetAsync(tau, 0, sizeof(double) * nb, st);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_fused, kChunk, 0)) != cudaSuccess)
+        return e;
+    // a quarter of the co-resident capacity at most, so that concurrent
+    // solves on other streams keep room beside it
+    if (coop && (long long)nch * 4 <= (long long)per_sm * sms) {
+        void *args[] = {&m, &nb, &P, &lda, &tau, &norm_a, &norm_b, &dots, (void *)&nch};
+        return cudaLaunchCooperativeKernel((const void *)panel_qr_fused, dim3(nch), dim3(kChunk), args, 0, st);
+    }
     panel_first_norm<<<nch, kChunk, 0, st>>>(m, P, lda, norm_a);
     for (int i = 0; i < nb && i < m; i++) {
         double *cur = (i % 2 == 0) ? norm_a : norm_b;

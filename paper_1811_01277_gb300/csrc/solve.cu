@@ -21,7 +21,9 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <utility>
+#include <vector>
 
 #include "elpa_gb300.h"
 #include "layout.cuh"
@@ -79,6 +81,37 @@ cublasHandle_t blas_handle(cudaStream_t st)
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Look-ahead helper per (device, caller stream): a high-priority stream on
+// which the next panel is factored while the caller's stream runs the
+// current trailing update, and the events that order the two.  Created on
+// first use, kept until the process exits.
+struct Lookahead {
+    cudaStream_t side;
+    cudaEvent_t start, ready, factored;
+};
+std::map<std::pair<int, cudaStream_t>, Lookahead> g_lookahead;
+
+const Lookahead *lookahead(cudaStream_t st)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    auto key = std::make_pair(dev, st);
+    auto it = g_lookahead.find(key);
+    if (it != g_lookahead.end()) return &it->second;
+    Lookahead la{};
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return nullptr;
+    if (cudaStreamCreateWithPriority(&la.side, cudaStreamNonBlocking, hi) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&la.start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&la.ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&la.factored, cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    return &(g_lookahead[key] = la);
+}
+
+
+
 // Stage boundaries recorded when GB_SOLVE_RECORD_STAGES is set: events
 // cached per (device, stream), created on first use.
 constexpr int kStages = 7;  // full->band, band->tri, bisection, inverse iteration, orthogonalise, tri->band, band->full
@@ -101,9 +134,10 @@ cudaEvent_t *stage_events(cudaStream_t st)
 
 // Workspace carve-up (all pieces 256-byte aligned).
 struct SolveWs {
-    double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2, *gw;
+    double *Aw, *tauP, *Tall, *Y, *Y2, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2, *gw,
+        *gw2;
     void *chase, *eig, *tev;
-    size_t chase_bytes, tev_bytes, gw_elems, total;
+    size_t chase_bytes, tev_bytes, gw_elems, gw2_elems, total;
 };
 
 // Split-K partials of the DFMA products (the kernels split only as far as
@@ -126,6 +160,7 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.tauP = (double *)take(P * b * 8);
     w.Tall = (double *)take(P * b * b * 8);
     w.Y = (double *)take((size_t)n * b * 8);
+    w.Y2 = (double *)take((size_t)n * b * 8);
     w.YT = (double *)take((size_t)n * b * 8);
     w.X = (double *)take((size_t)n * b * 8);
     w.Pm = (double *)take((size_t)b * b * 8);
@@ -143,6 +178,8 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.S2 = (double *)take((size_t)b * nev * 8);
     w.gw_elems = gemm_work_elems(n, b);
     w.gw = (double *)take(w.gw_elems * 8);
+    w.gw2_elems = (size_t)512 * b * b;  // split-K partials of the panel's Y^T Y on the helper stream
+    w.gw2 = (double *)take(w.gw2_elems * 8);
     w.chase_bytes = gb::band_to_tridi_workspace_bytes(n, b);
     w.chase = take(w.chase_bytes);
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
@@ -249,28 +286,64 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     // cuBLAS emulation flag only concerns the complex path
     const long long ldw = n;
 
-    // ---- full -> band
+    // ---- full -> band, with look-ahead: panel p+1 is factored on the helper
+    // stream as soon as its columns have received panel p's update, while
+    // the caller's stream applies the rest of that update (the rank-2b update
+    // of the trailing lower triangle, the bulk of the flops)
     GB_STAGE(0);
     GB_CU(cudaMemcpy2DAsync(w.Aw, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice, st));
+    const Lookahead *la = lookahead(st);
+    if (!la) return GB_ERR_CUDA;
+    double *Ybuf[2] = {w.Y, w.Y2};
+    auto factor = [&](int p) -> cudaError_t {  // on the helper stream
+        const int j = p * b, m = n - j - b;
+        double *panel = w.Aw + (long long)j * ldw + (j + b);
+        double *Yp = Ybuf[p & 1];
+        cudaError_t e;
+        if ((e = gb::panel_qr(m, b, panel, ldw, w.tauP + (long long)p * b, w.part, la->side)) != cudaSuccess) return e;
+        if ((e = gb::panel_y_and_t_prep(m, b, panel, ldw, Yp, m, la->side)) != cudaSuccess) return e;
+        if ((e = gb::dfma_gemm('T', 'N', b, b, m, 1.0, Yp, m, Yp, m, 0.0, w.G, b, w.gw2, w.gw2_elems, la->side)) !=
+            cudaSuccess)
+            return e;
+        if ((e = gb::panel_t(b, w.G, b, w.tauP + (long long)p * b, w.Tall + (long long)p * b * b, b, la->side)) !=
+            cudaSuccess)
+            return e;
+        return cudaEventRecord(la->factored, la->side);
+    };
     int P = 0;
+    if (b < n) {
+        GB_CU(cudaEventRecord(la->start, st));
+        GB_CU(cudaStreamWaitEvent(la->side, la->start, 0));
+        GB_CU(factor(0));
+    }
     for (int j = 0; j + b < n; j += b, P++) {
         const int m = n - j - b;
-        double *panel = w.Aw + (long long)j * ldw + (j + b);
         double *A2 = w.Aw + (long long)(j + b) * ldw + (j + b);
-        double *tau = w.tauP + (long long)P * b;
-        double *T = w.Tall + (long long)P * b * b;
-        GB_CU(gb::panel_qr(m, b, panel, ldw, tau, w.part, st));
-        GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
-        GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, w.Y, m, w.Y, m, 0.0, w.G, b, w.gw, w.gw_elems, st));
-        GB_CU(gb::panel_t(b, w.G, b, tau, T, b, st));
-        GB_CU(gb::dfma_gemm('N', 'N', m, b, b, 1.0, w.Y, m, T, b, 0.0, w.YT, m, w.gw, w.gw_elems, st));
+        const double *T = w.Tall + (long long)P * b * b;
+        const double *Yp = Ybuf[P & 1];
+        GB_CU(cudaStreamWaitEvent(st, la->factored, 0));
+        GB_CU(gb::dfma_gemm('N', 'N', m, b, b, 1.0, Yp, m, T, b, 0.0, w.YT, m, w.gw, w.gw_elems, st));
         // only the lower triangle of A2 is kept: X = A2 (Y T) (symmetric
-        // product), the rank-2b update on the lower triangle only
+        // product), W = X - Y M / 2, then A2 -= W Y^T + Y W^T on the lower triangle
         GB_CU(gb::dfma_symm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.gw, w.gw_elems, st));
-        GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, w.Y, m, w.X, m, 0.0, w.Pm, b, w.gw, w.gw_elems, st));
+        GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, Yp, m, w.X, m, 0.0, w.Pm, b, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('T', 'N', b, b, b, 1.0, T, b, w.Pm, b, 0.0, w.M, b, w.gw, w.gw_elems, st));
-        GB_CU(gb::dfma_gemm('N', 'N', m, b, b, -0.5, w.Y, m, w.M, b, 1.0, w.X, m, w.gw, w.gw_elems, st));
-        GB_CU(gb::dfma_syr2k_lower(m, b, -1.0, w.X, m, w.Y, m, 1.0, A2, ldw, st));
+        GB_CU(gb::dfma_gemm('N', 'N', m, b, b, -0.5, Yp, m, w.M, b, 1.0, w.X, m, w.gw, w.gw_elems, st));
+        if (m > b) {
+            // the next panel's columns first (all m rows; the upper triangle
+            // of their diagonal block is updated too and never read), then
+            // the next panel is factored on the helper stream while the rest
+            // of the trailing update runs here
+            GB_CU(gb::dfma_gemm('N', 'T', m, b, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, w.gw, w.gw_elems, st));
+            GB_CU(gb::dfma_gemm('N', 'T', m, b, b, -1.0, Yp, m, w.X, m, 1.0, A2, ldw, w.gw, w.gw_elems, st));
+            GB_CU(cudaEventRecord(la->ready, st));
+            GB_CU(cudaStreamWaitEvent(la->side, la->ready, 0));
+            GB_CU(factor(P + 1));
+            GB_CU(gb::dfma_syr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b, ldw,
+                                       st));
+        } else {
+            GB_CU(gb::dfma_syr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, st));
+        }
     }
     GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
 
@@ -457,16 +530,43 @@ int gb_solve_batched_d(int count, const int *n, const int *nev, const double *co
     if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
     if (ws_bytes < need) return -10;
     const size_t slot = need / (size_t)nslots;
-    for (int i = 0; i < count; i++) {
-        const int s = i % nslots;
+    // One host thread per slot issues that slot's problems in order: a solve
+    // is thousands of launches, and a single issuing thread would block on
+    // one stream's full launch queue while the other streams run dry.
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    const int nthreads = nslots < count ? nslots : count;
+    std::vector<int> rcs(nthreads, GB_OK);
+    auto issue = [&](int s) {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            rcs[s] = GB_ERR_CUDA;
+            return;
+        }
         cudaStream_t st = (cudaStream_t)streams[s];
-        if (ev_start && cudaEventRecord((cudaEvent_t)ev_start[i], st) != cudaSuccess) return GB_ERR_CUDA;
-        const int b = gb_solve_default_nbw(n[i]);
-        int rc = gb_solve_d(n[i], nev[i], b, A[i], lda[i], ev[i], Z[i], ldz[i], (char *)workspace + s * slot, slot,
-                            (void *)st, 0);
+        for (int i = s; i < count; i += nslots) {
+            if (ev_start && cudaEventRecord((cudaEvent_t)ev_start[i], st) != cudaSuccess) {
+                rcs[s] = GB_ERR_CUDA;
+                return;
+            }
+            const int b = gb_solve_default_nbw(n[i]);
+            const int rc = gb_solve_d(n[i], nev[i], b, A[i], lda[i], ev[i], Z[i], ldz[i], (char *)workspace + s * slot,
+                                      slot, (void *)st, 0);
+            if (rc != GB_OK) {
+                rcs[s] = rc;
+                return;
+            }
+            if (ev_end && cudaEventRecord((cudaEvent_t)ev_end[i], st) != cudaSuccess) {
+                rcs[s] = GB_ERR_CUDA;
+                return;
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int s = 1; s < nthreads; s++) pool.emplace_back(issue, s);
+    issue(0);
+    for (auto &t : pool) t.join();
+    for (int rc : rcs)
         if (rc != GB_OK) return rc;
-        if (ev_end && cudaEventRecord((cudaEvent_t)ev_end[i], st) != cudaSuccess) return GB_ERR_CUDA;
-    }
     return GB_OK;
 }
 

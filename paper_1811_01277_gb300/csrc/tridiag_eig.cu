@@ -190,24 +190,31 @@ __device__ __forceinline__ double start_value(int k, int i)
     return __hiloint2double(0x3FF00000 | (int)(x >> 12), (int)(y ^ (x << 20))) - 1.5;
 }
 
-// One thread per cluster leader k (lam[k] - lam[k-1] > gap, or k = 0): the
-// cluster's eigenvectors, written to Z (n x nev, column-major, ldz).
+// One thread per eigenvalue k: its inverse-iteration vector, normalised
+// (largest entry positive), written to column k of Z (n x nev, column-major,
+// ldz).  Eigenvalues closer than the cluster gap are orthogonalised
+// afterwards by cluster_orthonormalise.
 //
 // Per eigenvalue: one pass factors P(T - lk I) = LU with partial pivoting
 // (U0 = 1/pivot, U1 = first super-diagonal of U, Cm = multiplier, piv =
 // interchange; the second super-diagonal is e[i+1] where piv[i] = 1, else 0)
 // and applies L^-1 P to the start vector on the fly (Y); then three rounds of
-// back substitution U^-1 (Y -> X, tracking max |x|), Gram-Schmidt against the
-// cluster's earlier vectors, and -- for the next round -- L^-1 P applied to X
-// (X -> Y, X first rescaled by 1/max|x| only when max|x| leaves
-// [2^-200, 2^200]).
+// back substitution U^-1 (Y -> X, tracking max |x|) and -- for the next
+// round -- L^-1 P applied to X (X -> Y, X first rescaled by 1/max|x| only
+// when max|x| leaves [2^-200, 2^200]).  Each vector uses its own eigenvalue
+// as the shift, so components along other eigenvectors shrink by
+// (|lk - lambda_k| / |lk - lambda_i|)^3 in three rounds: vectors of close
+// but distinct eigenvalues separate by themselves, and those of eigenvalues
+// equal to working accuracy are independent combinations (different start
+// vectors) of the same invariant subspace, which the cluster step makes
+// orthonormal.
 //
 // Every pass is a chain over rows, so memory latency, not arithmetic, bounds
 // it: rows are processed in blocks of kRows, all loads of a block are issued
 // before its chain steps (and an L2 prefetch runs kPrefetch rows ahead), so a
 // block pays one memory latency.  Pivoting decisions and magnitude tracking
 // use integer compares of the bit patterns, and each pivot costs one
-// reciprocal.  Work arrays are interleaved by thread ([i * S + k0]) so that a
+// reciprocal.  Work arrays are interleaved by thread ([i * S + k]) so that a
 // warp's accesses to one row are contiguous.
 __device__ __forceinline__ double select(bool c, double a, double b) { return c ? a : b; }
 
@@ -216,6 +223,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefe
 constexpr int kRows = 8;        // rows per staged block
 constexpr int kRowsLU = 8;      // rows per staged block of the factorisation pass
 constexpr int kPrefetch = 64;   // L2 prefetch distance, rows
+constexpr double kClusterGap = 1e-7;  // relative to ||T||
 
 __device__ __forceinline__ double rcp_pivot(double p, unsigned long long tiny_key, double inv_tiny)
 {
@@ -224,30 +232,27 @@ __device__ __forceinline__ double rcp_pivot(double p, unsigned long long tiny_ke
 
 __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double *__restrict__ d,
                                                     const double *__restrict__ e, const double *__restrict__ lam,
-                                                    const double *__restrict__ bounds, double gap_rel,
+                                                    const double *__restrict__ bounds,
                                                     double *__restrict__ U0, double *__restrict__ U1,
                                                     double *__restrict__ Cm, unsigned char *__restrict__ piv,
                                                     double *__restrict__ Y, double *__restrict__ X,
                                                     double *__restrict__ Z, long long ldz)
 {
     constexpr int R = kRows;
-    const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k0 >= nev) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nev) return;
     const double tnorm = bounds[2];
-    const double gap = gap_rel * tnorm;
-    if (k0 > 0 && lam[k0] - lam[k0 - 1] <= gap) return;  // not a cluster leader
     const long long S = nev;                                // interleave stride
     const double tiny = 0x1p-52 * tnorm;                    // smallest pivot magnitude used
     const unsigned long long tiny_key = abs_key(tiny);
     const double inv_tiny = 1.0 / tiny;
-    U0 += k0;
-    U1 += k0;
-    Cm += k0;
-    piv += k0;
-    Y += k0;
-    X += k0;
-    int k = k0;
-    do {
+    U0 += k;
+    U1 += k;
+    Cm += k;
+    piv += k;
+    Y += k;
+    X += k;
+    {
         const double lk = lam[k];
         // ---- factor and apply L^-1 P to the start vector (step i eliminates
         // row i+1 with rows i, i+1 pivoted)
@@ -376,53 +381,6 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
                     }
                 }
             }
-            if (k > k0) {
-                // Gram-Schmidt against the cluster's earlier vectors (unit
-                // columns of Z), then max |x| again
-                for (int j = k0; j < k; j++) {
-                    const double *zj = Z + (long long)j * ldz;
-                    double dp[4] = {0.0, 0.0, 0.0, 0.0};
-                    for (int i0 = 0; i0 < n; i0 += R) {
-                        double zv[R], xv[R];
-#pragma unroll
-                        for (int r = 0; r < R; r++) {
-                            const int i = i0 + r;
-                            zv[r] = (i < n) ? zj[i] : 0.0;
-                            xv[r] = (i < n) ? X[i * S] : 0.0;
-                        }
-#pragma unroll
-                        for (int r = 0; r < R; r++) dp[r & 3] = fma(zv[r], xv[r], dp[r & 3]);
-                    }
-                    const double dot = (dp[0] + dp[1]) + (dp[2] + dp[3]);
-                    for (int i0 = 0; i0 < n; i0 += R) {
-                        double zv[R], xv[R];
-#pragma unroll
-                        for (int r = 0; r < R; r++) {
-                            const int i = i0 + r;
-                            if (i < n) {
-                                zv[r] = zj[i];
-                                xv[r] = X[i * S];
-                            }
-                        }
-#pragma unroll
-                        for (int r = 0; r < R; r++) {
-                            const int i = i0 + r;
-                            if (i < n) X[i * S] = fma(-dot, zv[r], xv[r]);
-                        }
-                    }
-                }
-                mx_key = 0;
-                for (int i0 = 0; i0 < n; i0 += R) {
-                    double xv[R];
-#pragma unroll
-                    for (int r = 0; r < R; r++) xv[r] = (i0 + r < n) ? X[(i0 + r) * S] : 0.0;
-#pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        const unsigned long long kx = abs_key(xv[r]);
-                        mx_key = kx > mx_key ? kx : mx_key;
-                    }
-                }
-            }
         }
         // ---- normalise (sum of squares of X / max|x|); the entry of largest
         // magnitude (the first, scanning upwards from row 0) is made positive
@@ -451,8 +409,100 @@ __global__ void __launch_bounds__(32) tridiag_invit(int n, int nev, const double
             for (int r = 0; r < R; r++)
                 if (i0 + r < n) zk[i0 + r] = xv[r] * f;
         }
-        k++;
-    } while (k < nev && lam[k] - lam[k - 1] <= gap);
+    }
+}
+
+// Sum over a block of 256 threads (all threads get the result).
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();  // red is free (previous use finished)
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long block_max_key(unsigned long long v, unsigned long long *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    unsigned long long t = (l < (int)(blockDim.x >> 5)) ? red[l] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, t, o);
+        t = u > t ? u : t;
+    }
+    return t;
+}
+
+// One block per cluster of eigenvalues closer than the gap (consecutive
+// differences <= gap, two or more members): modified Gram-Schmidt of the
+// members' columns of Z in order, each member orthogonalised twice against
+// the earlier ones, then normalised with its largest entry positive.  Rows
+// are spread over the block, so each dot product is one block reduction.
+__global__ void __launch_bounds__(256) cluster_orthonormalise(int n, int nev, const double *__restrict__ lam,
+                                                              const double *__restrict__ bounds, double gap_rel,
+                                                              double *__restrict__ Z, long long ldz)
+{
+    __shared__ double red[32];
+    __shared__ unsigned long long redk[32];
+    const int k0 = blockIdx.x;
+    const double gap = gap_rel * bounds[2];
+    if (k0 > 0 && lam[k0] - lam[k0 - 1] <= gap) return;   // not the first member
+    if (k0 + 1 >= nev || lam[k0 + 1] - lam[k0] > gap) return;  // a single eigenvalue
+    int k1 = k0 + 1;
+    while (k1 + 1 < nev && lam[k1 + 1] - lam[k1] <= gap) k1++;
+    for (int k = k0 + 1; k <= k1; k++) {
+        double *zk = Z + (long long)k * ldz;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int j = k0; j < k; j++) {
+                const double *zj = Z + (long long)j * ldz;
+                double s = 0.0;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(zj[i], zk[i], s);
+                const double dot = block_sum(s, red);
+                for (int i = threadIdx.x; i < n; i += blockDim.x) zk[i] = fma(-dot, zj[i], zk[i]);
+            }
+        }
+        unsigned long long mk = 0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long t = abs_key(zk[i]);
+            mk = t > mk ? t : mk;
+        }
+        mk = block_max_key(mk, redk);
+        const double sc = (mk == 0) ? 1.0 : recip(__longlong_as_double((long long)mk));
+        double s2 = 0.0;
+        int first = n;  // first row holding the largest magnitude
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double t = zk[i] * sc;
+            s2 = fma(t, t, s2);
+            if (abs_key(zk[i]) == mk && i < first) first = i;
+        }
+        const double nrm = sqrt(block_sum(s2, red)) * __longlong_as_double((long long)(mk == 0 ? abs_key(1.0) : mk));
+        // smallest such row over the block
+        __syncthreads();
+        if (threadIdx.x < 32) redk[threadIdx.x] = ~0ull;
+        __syncthreads();
+        atomicMin(&redk[0], (unsigned long long)first);
+        __syncthreads();
+        const int f0 = (int)redk[0];
+        const double big = (f0 < n) ? zk[f0] : 1.0;
+        const double f = nrm > 0.0 ? (sign_bit(big) ? -1.0 : 1.0) / nrm : 0.0;
+        __syncthreads();  // every thread has read zk[f0]
+        for (int i = threadIdx.x; i < n; i += blockDim.x) zk[i] *= f;
+        __syncthreads();  // column k final before the next member reads it
+    }
 }
 
 }  // namespace
@@ -515,8 +565,11 @@ cudaError_t tridiag_invit_d(int n, int nev, const double *d, const double *e, co
 {
     EigWork w = carve_eig(n, nev, ws);
     threads = clamp_threads(threads);
-    tridiag_invit<<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, 1e-7, w.U0, w.U1,
-                                                                      w.Cm, w.piv, w.Y, w.X, Z, ldz);
+    tridiag_invit<<<(nev + threads - 1) / threads, threads, 0, st>>>(n, nev, d, e, lam, w.bounds, w.U0, w.U1, w.Cm,
+                                                                      w.piv, w.Y, w.X, Z, ldz);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    cluster_orthonormalise<<<nev, 256, 0, st>>>(n, nev, lam, w.bounds, kClusterGap, Z, ldz);
     return cudaGetLastError();
 }
 
