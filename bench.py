@@ -23,6 +23,10 @@ import subprocess
 import sys
 import time
 
+# Solves overlapping on many streams (batched and serve stages) need as many
+# hardware work queues; the driver reads this before the CUDA context exists.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

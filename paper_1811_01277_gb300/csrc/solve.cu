@@ -90,6 +90,7 @@ struct Lookahead {
     cudaEvent_t start, ready, factored;
 };
 std::map<std::pair<int, cudaStream_t>, Lookahead> g_lookahead;
+constexpr int kLookaheadMinN = 4096;
 
 const Lookahead *lookahead(cudaStream_t st)
 {
@@ -292,28 +293,35 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     // of the trailing lower triangle, the bulk of the flops)
     GB_STAGE(0);
     GB_CU(cudaMemcpy2DAsync(w.Aw, (size_t)n * 8, A, (size_t)lda * 8, (size_t)n * 8, n, cudaMemcpyDeviceToDevice, st));
-    const Lookahead *la = lookahead(st);
-    if (!la) return GB_ERR_CUDA;
+    // small problems factor their panels in line: the helper stream would
+    // gain little there and would double the streams concurrent solves use
+    // (streams beyond the device's hardware queues share them)
+    const bool ahead = n >= kLookaheadMinN;
+    const Lookahead *la = ahead ? lookahead(st) : nullptr;
+    if (ahead && !la) return GB_ERR_CUDA;
+    const cudaStream_t fst = ahead ? la->side : st;  // stream that factors panels
     double *Ybuf[2] = {w.Y, w.Y2};
-    auto factor = [&](int p) -> cudaError_t {  // on the helper stream
+    auto factor = [&](int p) -> cudaError_t {  // on the panel stream
         const int j = p * b, m = n - j - b;
         double *panel = w.Aw + (long long)j * ldw + (j + b);
         double *Yp = Ybuf[p & 1];
         cudaError_t e;
-        if ((e = gb::panel_qr(m, b, panel, ldw, w.tauP + (long long)p * b, w.part, la->side)) != cudaSuccess) return e;
-        if ((e = gb::panel_y_and_t_prep(m, b, panel, ldw, Yp, m, la->side)) != cudaSuccess) return e;
-        if ((e = gb::dfma_gemm('T', 'N', b, b, m, 1.0, Yp, m, Yp, m, 0.0, w.G, b, w.gw2, w.gw2_elems, la->side)) !=
+        if ((e = gb::panel_qr(m, b, panel, ldw, w.tauP + (long long)p * b, w.part, fst)) != cudaSuccess) return e;
+        if ((e = gb::panel_y_and_t_prep(m, b, panel, ldw, Yp, m, fst)) != cudaSuccess) return e;
+        if ((e = gb::dfma_gemm('T', 'N', b, b, m, 1.0, Yp, m, Yp, m, 0.0, w.G, b, w.gw2, w.gw2_elems, fst)) !=
             cudaSuccess)
             return e;
-        if ((e = gb::panel_t(b, w.G, b, w.tauP + (long long)p * b, w.Tall + (long long)p * b * b, b, la->side)) !=
+        if ((e = gb::panel_t(b, w.G, b, w.tauP + (long long)p * b, w.Tall + (long long)p * b * b, b, fst)) !=
             cudaSuccess)
             return e;
-        return cudaEventRecord(la->factored, la->side);
+        return ahead ? cudaEventRecord(la->factored, fst) : cudaSuccess;
     };
     int P = 0;
     if (b < n) {
-        GB_CU(cudaEventRecord(la->start, st));
-        GB_CU(cudaStreamWaitEvent(la->side, la->start, 0));
+        if (ahead) {
+            GB_CU(cudaEventRecord(la->start, st));
+            GB_CU(cudaStreamWaitEvent(la->side, la->start, 0));
+        }
         GB_CU(factor(0));
     }
     for (int j = 0; j + b < n; j += b, P++) {
@@ -321,7 +329,7 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         double *A2 = w.Aw + (long long)(j + b) * ldw + (j + b);
         const double *T = w.Tall + (long long)P * b * b;
         const double *Yp = Ybuf[P & 1];
-        GB_CU(cudaStreamWaitEvent(st, la->factored, 0));
+        if (ahead) GB_CU(cudaStreamWaitEvent(st, la->factored, 0));
         GB_CU(gb::dfma_gemm('N', 'N', m, b, b, 1.0, Yp, m, T, b, 0.0, w.YT, m, w.gw, w.gw_elems, st));
         // only the lower triangle of A2 is kept: X = A2 (Y T) (symmetric
         // product), W = X - Y M / 2, then A2 -= W Y^T + Y W^T on the lower triangle
@@ -336,8 +344,10 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
             // of the trailing update runs here
             GB_CU(gb::dfma_gemm('N', 'T', m, b, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, w.gw, w.gw_elems, st));
             GB_CU(gb::dfma_gemm('N', 'T', m, b, b, -1.0, Yp, m, w.X, m, 1.0, A2, ldw, w.gw, w.gw_elems, st));
-            GB_CU(cudaEventRecord(la->ready, st));
-            GB_CU(cudaStreamWaitEvent(la->side, la->ready, 0));
+            if (ahead) {
+                GB_CU(cudaEventRecord(la->ready, st));
+                GB_CU(cudaStreamWaitEvent(la->side, la->ready, 0));
+            }
             GB_CU(factor(P + 1));
             GB_CU(gb::dfma_syr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b, ldw,
                                        st));
