@@ -1,16 +1,17 @@
 // Eigenpairs of the real symmetric tridiagonal T = tridiag(e, d, e) (Sec. 2,
 // Eq. 5) for the nev smallest eigenvalues, on the device.
 //
-// 1. Bisection on the Sturm count: the number of negative pivots of the
-//    LDL^T factorisation of T - xI is the number of eigenvalues below x.  One
-//    thread per eigenvalue, starting from the Gershgorin interval, halving
-//    until the interval stops shrinking in FP64.
-// 2. Inverse iteration, one thread per cluster: T - lambda I is factored by
-//    Gaussian elimination with partial pivoting (a tridiagonal LU with one
+// 1. Multisection on the Sturm count: the number of negative pivots of the
+//    LDL^T factorisation of T - xI is the number of eigenvalues below x.
+//    Four lanes per eigenvalue evaluate the count at four interior points of
+//    the current interval (which shrinks five-fold per round), starting from
+//    the Gershgorin interval, until it stops shrinking in FP64.
+// 2. Inverse iteration, one thread per eigenvalue: T - lambda I is factored
+//    by Gaussian elimination with partial pivoting (a tridiagonal LU with one
 //    extra super-diagonal from the interchanges); three solves from a
-//    deterministic pseudo-random start, each followed by Gram-Schmidt
-//    against the cluster's earlier vectors and normalisation.  Eigenvalues
-//    closer than the cluster gap are treated together, so nearly equal
+//    deterministic pseudo-random start, each followed by normalisation.
+// 3. One block per cluster of eigenvalues closer than the cluster gap:
+//    modified Gram-Schmidt (twice) of the cluster's vectors, so nearly equal
 //    eigenvalues get orthogonal vectors.
 // The caller finishes with one Newton-Schulz step Z <- Z (3I - Z^T Z)/2
 // (two GEMMs), which makes all columns orthonormal to rounding level; it

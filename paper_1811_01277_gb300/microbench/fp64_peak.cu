@@ -1,6 +1,8 @@
 // FP64 pipe throughput on the local GPU: DFMA (8 independent chains per
-// thread) and the f64 mma.sync shapes, each run for about a second so that
-// clocks settle.  Prints one line per test: name, TFLOP/s, seconds.
+// thread), the f64 mma.sync shape m8n8k4, and kernels that issue both from
+// the same warps (to see whether the FP64 tensor path and DFMA share one
+// unit).  Each test runs for about target_s seconds so that clocks settle.
+// Prints one line per test: name, TFLOP/s, seconds.
 #include <cstdio>
 #include <cstdlib>
 #include <cuda_runtime.h>
@@ -37,47 +39,115 @@ __global__ void dmma_m8n8k4(double *out, long long iters)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Per iteration every thread issues 8 DFMA (16 flops; 512 per warp) and the
+// warp issues NM m8n8k4 f64 MMAs (512 flops each).  If the tensor path had
+// its own FP64 units the sum would exceed the DFMA-only rate.
+template <int NM>
+__global__ void dfma_dmma_mix(double *out, long long iters, double x, double y)
+{
+    double a[8], ma = 1.0 + threadIdx.x * 1e-6, mb = 0.5, c[NM][2];
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = threadIdx.x * 1e-3 + k;
+#pragma unroll
+    for (int k = 0; k < NM; k++) { c[k][0] = k; c[k][1] = k + 1; }
+    for (long long i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = fma(a[k], x, y);
+#pragma unroll
+        for (int k = 0; k < NM; k++)
+            asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                         : "+d"(c[k][0]), "+d"(c[k][1]) : "d"(ma), "d"(mb));
+    }
+    double s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += a[k];
+#pragma unroll
+    for (int k = 0; k < NM; k++) s += c[k][0] + c[k][1];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Half the warps of a block run DFMA chains, the other half m8n8k4 MMAs.
+__global__ void dfma_dmma_split(double *out, long long iters_f, long long iters_m, double x, double y)
+{
+    double s = 0;
+    if ((threadIdx.x >> 5) & 1) {
+        double ma = 1.0 + threadIdx.x * 1e-6, mb = 0.5, c[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; k++) { c[k][0] = k; c[k][1] = k + 1; }
+        for (long long i = 0; i < iters_m; i++) {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                             : "+d"(c[k][0]), "+d"(c[k][1]) : "d"(ma), "d"(mb));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) s += c[k][0] + c[k][1];
+    } else {
+        double a[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = threadIdx.x * 1e-3 + k;
+        for (long long i = 0; i < iters_f; i++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) a[k] = fma(a[k], x, y);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) s += a[k];
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+static cudaEvent_t e0, e1;
+
+template <class F>
+static float timed(F launch)
+{
+    float ms = 0;
+    cudaEventRecord(e0);
+    launch();
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+}
+
+// Calibrates the iteration count on a short run, then times about target_s.
+template <class F>
+static void run(const char *name, double target_s, double flops_per_iter, F launch_with_iters)
+{
+    long long it = 100;
+    launch_with_iters(it);
+    float ms = timed([&] { launch_with_iters(it); });
+    it = (long long)(it * target_s * 1000.0 / (ms > 0.01f ? ms : 0.01f));
+    if (it < 1) it = 1;
+    ms = timed([&] { launch_with_iters(it); });
+    printf("%s %.4f %.3f\n", name, flops_per_iter * it / (ms * 1e-3) / 1e12, ms * 1e-3);
+}
+
 int main(int argc, char **argv)
 {
     double target_s = argc > 1 ? atof(argv[1]) : 1.0;
     cudaDeviceProp p;
     if (cudaGetDeviceProperties(&p, 0) != cudaSuccess) { printf("no device\n"); return 1; }
-    const int sms = p.multiProcessorCount, block = 256, grid = sms * 8;
+    const int grid = p.multiProcessorCount * 8;
     double *out;
-    if (cudaMalloc(&out, sizeof(double) * grid * block) != cudaSuccess) return 1;
-    cudaEvent_t e0, e1;
+    if (cudaMalloc(&out, sizeof(double) * grid * 256) != cudaSuccess) return 1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float ms;
-    // calibrate then run for ~target_s
-    long long it = 1000;
-    dfma8<<<grid, block>>>(out, it, 1.0000001, 1e-9);
-    cudaEventRecord(e0);
-    dfma8<<<grid, block>>>(out, it, 1.0000001, 1e-9);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    it = (long long)(it * target_s * 1000.0 / ms);
-    cudaEventRecord(e0);
-    dfma8<<<grid, block>>>(out, it, 1.0000001, 1e-9);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    printf("dfma %.4f %.3f sms=%d\n", 2.0 * 8 * it * (double)grid * block / (ms * 1e-3) / 1e12, ms * 1e-3, sms);
-    long long jt = 200;
-    dmma_m8n8k4<<<grid, 128>>>(out, jt);
-    cudaEventRecord(e0);
-    dmma_m8n8k4<<<grid, 128>>>(out, jt);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    jt = (long long)(jt * target_s * 1000.0 / ms);
-    cudaEventRecord(e0);
-    dmma_m8n8k4<<<grid, 128>>>(out, jt);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    printf("dmma_m8n8k4 %.4f %.3f\n", 512.0 * 4 * jt * grid * 4.0 / (ms * 1e-3) / 1e12, ms * 1e-3);
+    const double X = 1.0000001, Y = 1e-9;
+
+    run("dfma", target_s, 16.0 * grid * 256,
+        [&](long long it) { dfma8<<<grid, 256>>>(out, it, X, Y); });
+    run("dmma_m8n8k4", target_s, 512.0 * 4 * grid * 4,
+        [&](long long it) { dmma_m8n8k4<<<grid, 128>>>(out, it); });
+    // 8 warps per block: 8 x 512 DFMA flops + NM x 8 x 512 MMA flops per iteration
+    run("mix_dfma_dmma1", target_s, (512.0 + 512.0 * 1) * 8 * grid,
+        [&](long long it) { dfma_dmma_mix<1><<<grid, 256>>>(out, it, X, Y); });
+    run("mix_dfma_dmma2", target_s, (512.0 + 512.0 * 2) * 8 * grid,
+        [&](long long it) { dfma_dmma_mix<2><<<grid, 256>>>(out, it, X, Y); });
+    // split warps: DFMA warps run 4x the iterations of MMA warps so both take
+    // about the same time alone (8 chains x 512 flops vs 4 MMAs x 512 flops)
+    run("split_dfma_dmma", target_s, (4.0 * 512.0 + 4.0 * 512.0) * 4 * grid,
+        [&](long long it) { dfma_dmma_split<<<grid, 256>>>(out, 4 * it, it, X, Y); });
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { printf("cuda error %s\n", cudaGetErrorString(e)); return 1; }
     return 0;
