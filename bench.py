@@ -235,8 +235,9 @@ def run_ours(args, wl):
     gbuild.build()
     gb.load()
     n, nev, nbw = wl["n"], wl["nev"], wl["nbw"]
-    opts = {"variant": args.variant, "sweeps_per_tile": args.nb, "cols_per_block": args.threads}
-    if args.variant == 0 and args.nb == 0 and args.threads == 0:
+    opts = {"variant": args.variant, "sweeps_per_tile": args.nb, "cols_per_block": args.threads,
+            "column_batch": args.column_batch, "lead_tiles": args.lead_tiles}
+    if args.variant == 0 and args.nb == 0 and args.threads == 0 and args.column_batch == 0 and args.lead_tiles == 0:
         opts = None  # the library's default choice
 
     hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024 + 1000 * rank)
@@ -303,7 +304,8 @@ def run_ours(args, wl):
     launches = launches_per_call
     kernel = "pipeline_d" if variant_name == "pipeline" else "wavefront_tile_d"
     sha = kernel_sources_sha1(kernel)
-    traffic = profile_traffic(kernel, args.workload, variant_name, sha)
+    # the committed ncu figure is for the default configuration only
+    traffic = profile_traffic(kernel, args.workload, variant_name, sha) if opts is None else None
 
     # end to end through the host-buffer entry point: H2D of reflectors and Z,
     # the kernels, D2H of Z, per step
@@ -349,6 +351,9 @@ def run_ours(args, wl):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches) * args.steps,
             "clocks": clocks, "kernel_sources_sha1": sha,
         }
+        if opts is not None:
+            line["opts"] = dict(opts) if isinstance(opts, dict) else {
+                f: getattr(opts, f) for f, _ in gb.gb_trans_ev_opts._fields_}
         if tuned:
             line["autotune"] = tuned
         print(json.dumps(line))
@@ -493,6 +498,8 @@ def run_stage_solve(args):
     st = torch.cuda.current_stream(dev)
 
     base_flags = gb.GB_SOLVE_FP64_EMULATED_GEMM if args.emulated_gemm else 0
+    if args.dfma_products:
+        base_flags |= gb.GB_SOLVE_DFMA_PRODUCTS
 
     def step(flags=0):
         flags |= base_flags
@@ -529,7 +536,7 @@ def run_stage_solve(args):
     orth = (Zc.conj().T @ Zc - torch.eye(nev, dtype=Zc.dtype, device=dev)).abs().max().item()
     u = 2.0 ** -53
     print(json.dumps({
-        "emulated_gemm": bool(args.emulated_gemm),
+        "emulated_gemm": bool(args.emulated_gemm), "products": "dfma" if args.dfma_products else "sliced",
         "stage": "solve", "metric": f"two-stage eigensolve s at n={n} ({100 * nev // n}% vecs), nbw={nbw}, "
                                     f"{'complex128 Hermitian' if cplx else 'real FP64'}",
         "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "seconds_per_solve": ms / 1e3,
@@ -539,9 +546,10 @@ def run_stage_solve(args):
         "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12,
                      "by_stage_tflop": {k_: v_ / 1e12 for k_, v_ in Fst.items()},
-                     "note": "whole solve against the FP64 DFMA peak; real solve: every product in this "
-                             "library's DFMA kernels (1.19-1.25 TFLOP/s on these shapes); complex solve: "
-                             "cuBLAS ZGEMM/ZHEMM/ZHER2K for the complex products"},
+                     "note": "algorithmic FP64 flops of the whole solve against the FP64 DFMA peak; real "
+                             "solve: large products on the bf16 tensor cores by exact digit slicing (FP64 "
+                             "accuracy; the DFMA kernels with --dfma-products), the rest in DFMA kernels; "
+                             "complex solve: cuBLAS ZGEMM/ZHEMM/ZHER2K for the complex products"},
         "accuracy": {"max_dlambda_over_norm": dlam, "residual_rel_fro": resid, "orth_max": orth,
                      "bound_50nu": 50 * n * u, "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
         "clocks": clocks}))
@@ -551,9 +559,11 @@ def run_stage_solve(args):
 def run_stage_gemm(args):
     """The solver's FP64 products at the shapes of an n = 16384, nev = 4096,
     nbw = 64 solve: this library's DFMA kernels (gb_dgemm / gb_dsymm /
-    gb_dsyr2k / gb_dsyrk) against torch's float64 products on the same
-    device (cuBLAS); one JSON line with TFLOP/s and the fraction of the FP64
-    DFMA peak for each."""
+    gb_dsyr2k / gb_dsyrk), its sliced bf16 tensor-core forms (gb_*_sliced)
+    and torch's float64 products on the same device (cuBLAS); one JSON line
+    with TFLOP/s (FP64 flops of the product) for each, the fraction of the
+    FP64 DFMA peak, and the largest difference of the sliced result from the
+    DFMA one relative to the largest entry."""
     import torch
     import paper_1811_01277_gb300 as gb
     from paper_1811_01277_gb300 import build as gbuild
@@ -573,28 +583,50 @@ def run_stage_gemm(args):
     Zo = torch.empty(nev, n, device=dev, dtype=torch.float64)
     wsb = gb.gb_dgemm_workspace_bytes(n, b)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    swb = max(gb.gb_dsymm_sliced_workspace_bytes("L", m, b), gb.gb_dsyr2k_sliced_workspace_bytes(m, b),
+              gb.gb_dgemm_sliced_workspace_bytes(b, nev, n), gb.gb_dgemm_sliced_workspace_bytes(n, nev, b),
+              gb.gb_dsyrk_sliced_workspace_bytes(nev, n), gb.gb_dsymm_sliced_workspace_bytes("R", n, nev))
+    sws = torch.empty(swb, dtype=torch.uint8, device=dev)
+    G2 = torch.empty(nev, nev, device=dev, dtype=torch.float64)
+    Zs = torch.empty(nev, n, device=dev, dtype=torch.float64)
     Asym = A.T                                  # only the lower triangle matters to gb_dsymm
+    # (name, flops, DFMA call, sliced call, cuBLAS call, (DFMA output, sliced output) or None)
     cases = [
         ("symm_L m=16320 n=64 (full->band X = A2 YT)", 2.0 * m * m * b,
          lambda: gb.gb_dsymm("L", m, b, 1.0, A, n, Y, m, 0.0, Cb, m, ws, wsb, st),
-         lambda: torch.mm(Asym[:m, :m], Y.T)),
+         lambda: gb.gb_dsymm_sliced("L", m, b, 1.0, A, n, Y, m, 0.0, X, m, sws, swb, st),
+         lambda: torch.mm(Asym[:m, :m], Y.T), (Cb, X)),
         ("syr2k m=16320 k=64 (full->band rank-2b update)", 2.0 * m * m * b,
          lambda: gb.gb_dsyr2k(m, b, -1.0, X, m, Y, m, 1.0, A, n, st),
-         lambda: A[:m, :m].addmm_(X.T, Y, alpha=-1.0).addmm_(Y.T, X, alpha=-1.0)),
+         lambda: gb.gb_dsyr2k_sliced(m, b, -1.0, X, m, Y, m, 1.0, A, n, sws, swb, st),
+         lambda: A[:m, :m].addmm_(X.T, Y, alpha=-1.0).addmm_(Y.T, X, alpha=-1.0), None),
         ("gemm TN 64 x 4096 k=16384 (band->full Y^T Z)", 2.0 * b * nev * n,
          lambda: gb.gb_dgemm("T", "N", b, nev, n, 1.0, A, n, Zt, n, 0.0, G, b, ws, wsb, st),
-         lambda: torch.mm(A[:b, :], Zt.T)),
+         lambda: gb.gb_dgemm_sliced("T", "N", b, nev, n, 1.0, A, n, Zt, n, 0.0, G2, b, sws, swb, st),
+         lambda: torch.mm(A[:b, :], Zt.T), (G.view(-1)[:b * nev], G2.view(-1)[:b * nev])),
         ("gemm NN 16384 x 4096 k=64 (band->full Z -= Y S2)", 2.0 * n * nev * b,
          lambda: gb.gb_dgemm("N", "N", n, nev, b, -1.0, A, n, G, b, 1.0, Zo, n, ws, wsb, st),
-         lambda: Zo.T.addmm_(A[:b, :].T, G.view(-1)[:b * nev].view(nev, b).T, alpha=-1.0)),
+         lambda: gb.gb_dgemm_sliced("N", "N", n, nev, b, -1.0, A, n, G, b, 1.0, Zo, n, sws, swb, st),
+         lambda: Zo.T.addmm_(A[:b, :].T, G.view(-1)[:b * nev].view(nev, b).T, alpha=-1.0), None),
         ("syrk 4096 k=16384 (Newton-Schulz Z^T Z)", 1.0 * nev * nev * n,
          lambda: gb.gb_dsyrk(nev, n, 1.0, Zt, n, 0.0, G, nev, st),
-         lambda: torch.mm(Zt, Zt.T, out=G)),
+         lambda: gb.gb_dsyrk_sliced(nev, n, 1.0, Zt, n, 0.0, G2, nev, sws, swb, st),
+         lambda: torch.mm(Zt, Zt.T, out=G), (lambda: G.tril(), lambda: G2.tril())),
+        ("symm_R 16384 x 4096 (Newton-Schulz Z M)", 2.0 * n * nev * nev,
+         lambda: gb.gb_dsymm("R", n, nev, 1.0, G2, nev, Zt, n, 0.0, Zo, n, ws, wsb, st),
+         lambda: gb.gb_dsymm_sliced("R", n, nev, 1.0, G2, nev, Zt, n, 0.0, Zs, n, sws, swb, st),
+         lambda: torch.mm(G2, Zt, out=Zo), (Zo, Zs)),
     ]
     res = {}
-    for name, flops, ours, ref in cases:
+    for name, flops, ours, sliced, ref, outs in cases:
         out = {}
-        for label, f in (("dfma", ours), ("torch_cublas", ref)):
+        if outs is not None:               # accuracy of the sliced form against the DFMA form
+            ours()
+            sliced()
+            torch.cuda.synchronize(dev)
+            d, s_ = (o() if callable(o) else o for o in outs)
+            out["sliced_vs_dfma_maxdiff_rel"] = float((s_ - d).abs().max() / d.abs().max().clamp_min(1e-300))
+        for label, f in (("dfma", ours), ("sliced", sliced), ("torch_cublas", ref)):
             for _ in range(max(1, args.warmup)):
                 f()
             torch.cuda.synchronize(dev)
@@ -607,6 +639,7 @@ def run_stage_gemm(args):
             ms = e0.elapsed_time(e1) / args.steps
             out[label] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
         out["frac_of_fp64_peak"] = out["dfma"]["tflops"] / FP64_PEAK_TFLOPS
+        out["sliced_speedup_over_dfma"] = out["dfma"]["ms"] / out["sliced"]["ms"]
         out["cublas_note"] = "torch float64 matmul (cuBLAS DGEMM); syr2k as two full GEMMs, so twice the flops"
         res[name] = out
     print(json.dumps({"stage": "gemm", "metric": "FP64 products of the n=16384 solve, TFLOP/s",
@@ -760,6 +793,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="0 library default, 1 wavefront, 2 pipeline")
     ap.add_argument("--nb", type=int, default=0, help="sweeps per tile (0 = default)")
     ap.add_argument("--threads", type=int, default=0, help="columns per block (0 = default)")
+    ap.add_argument("--column-batch", type=int, default=0, help="pipeline: column blocks per ticket batch (0 = default)")
+    ap.add_argument("--lead-tiles", type=int, default=0, help="pipeline: tiles a sweep group may lead the next (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
@@ -775,6 +810,8 @@ def main():
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
     ap.add_argument("--complex", action="store_true", help="solve stage: complex128 Hermitian")
+    ap.add_argument("--dfma-products", action="store_true",
+                    help="solve stage: run the real solve's products on the FP64 FMA pipe (not sliced)")
     ap.add_argument("--emulated-gemm", action="store_true",
                     help="solve stage: let cuBLAS use its fixed-point FP64 emulation for the GEMMs")
     ap.add_argument("--serve-rate", type=float, default=200.0)

@@ -71,6 +71,16 @@ typedef struct gb_trans_ev_opts {
     int test_hold_group; /* fault-injection hook for tests: when g+1 > 0, sweep
                             group g never publishes its progress so that the
                             next group's wait must give up; 0 = off */
+    int column_batch;    /* PIPELINE only: column blocks per ticket batch,
+                            1..1024 (0 = default 16).  Items of one batch run
+                            group after group; smaller batches keep fewer
+                            eigenvector rows live in L2, larger ones read the
+                            reflectors fewer times. */
+    int lead_tiles;      /* PIPELINE only: how many tiles a sweep group may run
+                            ahead of the next group of the same columns, 1..65536
+                            (0 = default: no limit).  Small leads keep the rows
+                            passed from group to group in L2 but hold groups
+                            back. */
 } gb_trans_ev_opts;
 
 /* Number of reflectors of the layout above (-1 if n < 1 or nbw < 1). */
@@ -197,13 +207,18 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
  * n-1), the intermediate band width; 4 A (column-major, lda; read only, both
  * triangles used); 5 lda >= n; 6 ev (nev, ascending); 7 Z (n x nev,
  * column-major); 8 ldz >= n; 9 workspace (256-byte aligned); 10 ws_bytes >=
- * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0,
- * GB_SOLVE_RECORD_STAGES, or GB_SOLVE_FP64_EMULATED_GEMM (accepted, no effect
- * here: it selects cuBLAS's fixed-point FP64 emulation for the complex
- * solve's cuBLAS products).  Asynchronous; device-side status of the
- * dependency waits through gb_solve_query. */
+ * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0 or an OR
+ * of GB_SOLVE_RECORD_STAGES, GB_SOLVE_DFMA_PRODUCTS and
+ * GB_SOLVE_FP64_EMULATED_GEMM (accepted, no effect here: it selects cuBLAS's
+ * fixed-point FP64 emulation for the complex solve's cuBLAS products).  By
+ * default the large products (the full->band SYMM and SYR2K, the band->full
+ * GEMMs, the Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by
+ * exact digit slicing (gb_dgemm_sliced below); GB_SOLVE_DFMA_PRODUCTS runs
+ * them on the FP64 FMA pipe instead.  Asynchronous; device-side status of
+ * the dependency waits through gb_solve_query. */
 #define GB_SOLVE_FP64_EMULATED_GEMM 1
 #define GB_SOLVE_RECORD_STAGES 2 /* record CUDA events at the stage boundaries */
+#define GB_SOLVE_DFMA_PRODUCTS 4 /* products on the FP64 FMA pipe, not sliced */
 size_t gb_solve_workspace_bytes(int n, int nev, int nbw);
 int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
                void *workspace, size_t ws_bytes, void *stream, int flags);
@@ -304,6 +319,35 @@ int gb_dsyr2k(int n, int k, double alpha, const double *A, int lda, const double
               double *C, int ldc, void *stream);
 int gb_dsyrk(int n, int k, double alpha, const double *A, int lda, double beta, double *C, int ldc,
              void *stream);
+
+/* The same products computed on the bf16 tensor cores: every row of op(A)
+ * and every column of op(B) is scaled by a power of two and cut exactly into
+ * eight 7-bit digits (error-free splitting, Ozaki, Ogita, Oishi and Rump,
+ * Numer. Algorithms 59, 2012); digit-plane products are formed with
+ * mma.sync bf16 and accumulated exactly in integers (FP32 only for the
+ * pairs whose weight is below 2^-35 of the leading ones), and the result is
+ * rounded to FP64 once.  Accuracy is that of an FP64 product measured
+ * against the scaled maxima: |C - alpha op(A) op(B)| <~ 2^-53 k |alpha|
+ * max_j |op(A)_ij| max_i |op(B)_ij| per entry.  Inputs must be finite;
+ * subnormal inputs are read as zero.  The paper's products are BLAS calls
+ * (Sec. 3.2); this is how they run fastest on a part whose FP64 pipe is
+ * narrow.  `workspace` (256-byte aligned) must hold the *_workspace_bytes
+ * figure: the digit planes of both operands and split-K partials.  Same
+ * argument numbering as the DFMA forms, then workspace, ws_bytes, stream;
+ * -i for invalid argument i, GB_ERR_CUDA for a launch error. */
+size_t gb_dgemm_sliced_workspace_bytes(int m, int n, int k);
+int gb_dgemm_sliced(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc, void *workspace,
+                    size_t ws_bytes, void *stream);
+size_t gb_dsymm_sliced_workspace_bytes(char side, int m, int n);
+int gb_dsymm_sliced(char side, int m, int n, double alpha, const double *S, int lds, const double *B, int ldb,
+                    double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);
+size_t gb_dsyr2k_sliced_workspace_bytes(int n, int k);
+int gb_dsyr2k_sliced(int n, int k, double alpha, const double *A, int lda, const double *B, int ldb,
+                     double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);
+size_t gb_dsyrk_sliced_workspace_bytes(int n, int k);
+int gb_dsyrk_sliced(int n, int k, double alpha, const double *A, int lda, double beta, double *C, int ldc,
+                    void *workspace, size_t ws_bytes, void *stream);
 
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);

@@ -34,8 +34,11 @@ EXPORTS = (
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
+    "gb_dgemm_sliced_workspace_bytes", "gb_dgemm_sliced", "gb_dsymm_sliced_workspace_bytes", "gb_dsymm_sliced",
+    "gb_dsyr2k_sliced_workspace_bytes", "gb_dsyr2k_sliced", "gb_dsyrk_sliced_workspace_bytes", "gb_dsyrk_sliced",
 )
 GB_SOLVE_RECORD_STAGES = 2
+GB_SOLVE_DFMA_PRODUCTS = 4
 SOLVE_STAGES = ("full_to_band", "band_to_tridi", "bisection", "inverse_iteration", "orthogonalise",
                 "trans_ev_tridi_to_band", "band_to_full")
 GB_AUTOTUNE_FAST = 1
@@ -47,7 +50,8 @@ GB_NOALLOC_SCRATCH_BYTES = 1 << 20
 class gb_trans_ev_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("sweeps_per_tile", ctypes.c_int),
                 ("cols_per_block", ctypes.c_int), ("spin_limit", ctypes.c_int),
-                ("test_hold_group", ctypes.c_int)]
+                ("test_hold_group", ctypes.c_int), ("column_batch", ctypes.c_int),
+                ("lead_tiles", ctypes.c_int)]
 
 
 class GbError(RuntimeError):
@@ -122,6 +126,15 @@ def load(path=None):
     L.gb_dsymm.argtypes = [ch, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dsymm.restype = i
     L.gb_dsyr2k.argtypes = [i, i, dd, p, i, p, i, dd, p, i, p]; L.gb_dsyr2k.restype = i
     L.gb_dsyrk.argtypes = [i, i, dd, p, i, dd, p, i, p]; L.gb_dsyrk.restype = i
+    L.gb_dgemm_sliced_workspace_bytes.argtypes = [i, i, i]; L.gb_dgemm_sliced_workspace_bytes.restype = sz
+    L.gb_dgemm_sliced.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]
+    L.gb_dgemm_sliced.restype = i
+    L.gb_dsymm_sliced_workspace_bytes.argtypes = [ch, i, i]; L.gb_dsymm_sliced_workspace_bytes.restype = sz
+    L.gb_dsymm_sliced.argtypes = [ch, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dsymm_sliced.restype = i
+    L.gb_dsyr2k_sliced_workspace_bytes.argtypes = [i, i]; L.gb_dsyr2k_sliced_workspace_bytes.restype = sz
+    L.gb_dsyr2k_sliced.argtypes = [i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dsyr2k_sliced.restype = i
+    L.gb_dsyrk_sliced_workspace_bytes.argtypes = [i, i]; L.gb_dsyrk_sliced_workspace_bytes.restype = sz
+    L.gb_dsyrk_sliced.argtypes = [i, i, dd, p, i, dd, p, i, p, sz, p]; L.gb_dsyrk_sliced.restype = i
     _lib = L
     return L
 
@@ -408,6 +421,56 @@ def gb_dsyrk(n, k, alpha, A, lda, beta, C, ldc, stream=None, check=True):
     rc = load().gb_dsyrk(n, k, alpha, _p(A), lda, beta, _p(C), ldc, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsyrk")
+    return rc
+
+
+def gb_dgemm_sliced_workspace_bytes(m, n, k):
+    return load().gb_dgemm_sliced_workspace_bytes(m, n, k)
+
+
+def gb_dgemm_sliced(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes,
+                    stream=None, check=True):
+    rc = load().gb_dgemm_sliced(_c(transa), _c(transb), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc,
+                                _p(workspace), ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dgemm_sliced")
+    return rc
+
+
+def gb_dsymm_sliced_workspace_bytes(side, m, n):
+    return load().gb_dsymm_sliced_workspace_bytes(_c(side), m, n)
+
+
+def gb_dsymm_sliced(side, m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None,
+                    check=True):
+    rc = load().gb_dsymm_sliced(_c(side), m, n, alpha, _p(S), lds, _p(B), ldb, beta, _p(C), ldc, _p(workspace),
+                                ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dsymm_sliced")
+    return rc
+
+
+def gb_dsyr2k_sliced_workspace_bytes(n, k):
+    return load().gb_dsyr2k_sliced_workspace_bytes(n, k)
+
+
+def gb_dsyr2k_sliced(n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_dsyr2k_sliced(n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc, _p(workspace), ws_bytes,
+                                 _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dsyr2k_sliced")
+    return rc
+
+
+def gb_dsyrk_sliced_workspace_bytes(n, k):
+    return load().gb_dsyrk_sliced_workspace_bytes(n, k)
+
+
+def gb_dsyrk_sliced(n, k, alpha, A, lda, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_dsyrk_sliced(n, k, alpha, _p(A), lda, beta, _p(C), ldc, _p(workspace), ws_bytes,
+                                _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dsyrk_sliced")
     return rc
 
 

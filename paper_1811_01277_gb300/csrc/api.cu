@@ -15,7 +15,7 @@ constexpr int kMaxRegNbw = 64;     // register-window kernels (real case)
 constexpr size_t kMaxSmem = 227 * 1024;
 
 struct Opts {
-    int variant, nb, threads, hold;
+    int variant, nb, threads, hold, column_batch, lead_tiles;
     long long spin;
 };
 
@@ -31,6 +31,8 @@ int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
     int variant = GB_VARIANT_AUTO, nb = 0, threads = 0;
     r->spin = kDefaultSpinPolls;
     r->hold = 0;
+    r->column_batch = 0;
+    r->lead_tiles = 0;
     if (o) {
         if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE) return -11;
         if (o->sweeps_per_tile < 0 || o->sweeps_per_tile > 32) return -11;
@@ -38,6 +40,10 @@ int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
             o->cols_per_block != 128)
             return -11;
         if (o->spin_limit < 0 || o->test_hold_group < 0) return -11;
+        if (o->column_batch < 0 || o->column_batch > 1024) return -11;
+        r->column_batch = o->column_batch;
+        if (o->lead_tiles < 0 || o->lead_tiles > 65536) return -11;
+        r->lead_tiles = o->lead_tiles;
         variant = o->variant;
         nb = o->sweeps_per_tile;
         threads = o->cols_per_block;
@@ -121,8 +127,8 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     if (n == 1 || nev == 0) return GB_OK;
     cudaError_t e;
     if (o.variant == GB_VARIANT_PIPELINE)
-        e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, workspace, need, o.spin,
-                           kTimeoutNs, o.hold, (cudaStream_t)stream);
+        e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, o.column_batch, o.lead_tiles, workspace, need,
+                           o.spin, kTimeoutNs, o.hold, (cudaStream_t)stream);
     else if (nbw > kMaxRegNbw)
         e = gb::wavefront_smem_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
     else

@@ -1,0 +1,623 @@
+// FP64 products on the bf16 tensor cores by exact digit slicing; the scheme
+// and its accuracy are described in dgemm_sliced.cuh.
+//
+// Slicing: two passes over 32 x 32 tiles of the slice-row view, staged in
+// shared memory so that global reads follow the source's contiguous index;
+// pass 1 takes each row's largest magnitude (atomicMax on the bit pattern),
+// pass 2 cuts every entry into digits with integer arithmetic on its bit
+// pattern (no FP64 instructions) and writes the bf16 planes, k fastest.
+//
+// Product: one 256-thread block per 64 x 64 tile of C, warps 4 (rows) x 2
+// (columns), each warp 16 x 32 = four m16n8 accumulator tiles per bucket.
+// K advances 32 at a time through a two-stage cp.async pipeline holding all
+// digit planes of the A and B tiles (rows padded to 80 bytes so that the
+// ldmatrix row addresses of a phase fall in distinct banks).  Per k16 step
+// the warp loads the eight A-plane fragments once and, per B plane j, issues
+// mma.sync m16n8k16 bf16 for every A plane i with i + j < kSlices into
+// bucket min(i + j, kExactLevels).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dgemm_sliced.cuh"
+
+namespace gb {
+
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 32;
+constexpr int kRowPad = 40;  // bf16 per staged row (32 used)
+constexpr int kThreads = 256;
+constexpr int kStages = 2;
+constexpr int kBuckets = kExactLevels + 1;
+constexpr size_t kStageElems = (size_t)kSlices * (kBM + kBN) * kRowPad;  // bf16 per stage
+constexpr size_t kProductSmem = kStages * kStageElems * sizeof(uint16_t);
+
+static_assert(kSlices * kDigitBits <= 56, "digits come from the 56-bit fixed-point magnitude");
+static_assert((kExactLevels + 1) * 127 * 127 * kFlushK < (1 << 24), "exact levels must stay below 2^24 units");
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct SliceLayout {
+    size_t planes, e, rmax, total;
+};
+
+SliceLayout slice_layout(int R, int K)
+{
+    const size_t Rp = (size_t)round_up(R > 0 ? R : 1, kBM), Kp = (size_t)round_up(K > 0 ? K : 1, kBK);
+    SliceLayout L;
+    L.planes = 0;
+    L.e = a256(L.planes + (size_t)kSlices * Rp * Kp * sizeof(uint16_t));
+    L.rmax = a256(L.e + Rp * sizeof(int));
+    L.total = a256(L.rmax + Rp * sizeof(unsigned long long));
+    return L;
+}
+
+// element (r, k) of the view (r < R, k < K)
+__device__ __forceinline__ double view_at(int view, const double *__restrict__ src, long long ld, int r, int k)
+{
+    if (view == kViewRow) return src[r + (long long)k * ld];
+    if (view == kViewCol) return src[k + (long long)r * ld];
+    return r >= k ? src[r + (long long)k * ld] : src[k + (long long)r * ld];
+}
+
+// Loads the 32 x 32 tile at (r0, k0) into t[r][k] (zero outside R x K), with
+// the thread index running along the source's contiguous index.
+__device__ __forceinline__ void load_tile(int view, const double *__restrict__ src, long long ld, int R, int K,
+                                          int r0, int k0, double (*t)[33])
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // which index is contiguous in memory for this tile
+    bool along_r;
+    if (view == kViewRow) along_r = true;
+    else if (view == kViewCol) along_r = false;
+    else along_r = (r0 >= k0 + 31) || !(r0 + 31 < k0);  // lower or diagonal tiles: read src[r + k ld]
+    for (int i = ty; i < 32; i += 8) {
+        const int a = along_r ? i : tx, bb = along_r ? tx : i;  // a: k offset, bb: r offset
+        const int r = r0 + bb, k = k0 + a;
+        double v = 0.0;
+        if (r < R && k < K) v = view_at(view, src, ld, r, k);
+        t[bb][a] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) slice_rowmax(int view, const double *__restrict__ src, long long ld, int R,
+                                                     int K, unsigned long long *__restrict__ rmax)
+{
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    load_tile(view, src, ld, R, K, r0, k0, t);
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        unsigned long long m = (unsigned long long)__double_as_longlong(t[i][threadIdx.x]) & 0x7fffffffffffffffull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+            m = u > m ? u : m;
+        }
+        if (threadIdx.x == 0 && r0 + i < R && m) atomicMax(rmax + r0 + i, m);
+    }
+}
+
+// Row exponent e with max|row| < 2^e (0 for an all-zero row).
+__device__ __forceinline__ int row_exponent(unsigned long long maxbits)
+{
+    const int ex = (int)(maxbits >> 52);
+    return ex ? ex - 1022 : 0;
+}
+
+__global__ void __launch_bounds__(256) slice_digits(int view, const double *__restrict__ src, long long ld, int R,
+                                                     int K, int Rp, int Kp, const unsigned long long *__restrict__ rmax,
+                                                     uint16_t *__restrict__ planes, int *__restrict__ e_out)
+{
+    __shared__ double t[32][33];
+    const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    load_tile(view, src, ld, R, K, r0, k0, t);
+    __syncthreads();
+    const size_t plane = (size_t)Rp * Kp;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, k = k0 + threadIdx.x;
+        if (r >= Rp || k >= Kp) continue;
+        const int er = r < R ? row_exponent(rmax[r]) : 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) e_out[r] = er;
+        const unsigned long long u = (unsigned long long)__double_as_longlong(t[i][threadIdx.x]);
+        const int ex = (int)((u >> 52) & 0x7ff);
+        // Y = floor(|x| 2^(56 - er)): the 56-bit fixed-point magnitude
+        unsigned long long Y = 0;
+        if (ex != 0) {
+            const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
+            const int sh = ex - 1075 - er + 56;
+            Y = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+        }
+        const bool neg = (u >> 63) != 0;
+#pragma unroll
+        for (int s = 0; s < kSlices; s++) {
+            const int d = (int)((Y >> (kDigitBits * (kSlices - 1 - s))) & 127u);
+            // bf16 of +-d 2^(-7 s): exact (d has at most 7 significant bits)
+            uint16_t h = 0;
+            if (d) {
+                const int p = 31 - __clz(d);                  // d = 1.f x 2^p
+                const unsigned frac = ((unsigned)d << (7 - p)) & 0x7fu;
+                const unsigned expo = (unsigned)(127 + p - kDigitBits * s);
+                h = (uint16_t)((neg ? 0x8000u : 0u) | (expo << 7) | frac);
+            }
+            planes[s * plane + (size_t)r * Kp + k] = h;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ double pow2(int e)  // 2^e for -1022 <= e <= 1023
+{
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// 2^e for any e the products can produce, as two factors
+__device__ __forceinline__ double scale_by_pow2(double v, int e)
+{
+    const int e1 = e / 2, e2 = e - e1;
+    return v * pow2(e1) * pow2(e2);
+}
+
+// Stage loader: all digit planes of the A rows [m0, m0+64) and B rows
+// [n0, n0+64) for k in [kt, kt+32).
+__device__ __forceinline__ void load_stage(uint16_t *stage, const uint16_t *__restrict__ Ap, size_t a_plane,
+                                           int a_kp, const uint16_t *__restrict__ Bp, size_t b_plane, int b_kp,
+                                           int m0, int n0, int kt)
+{
+    // per operand kSlices x 64 rows x 4 chunks of 16 bytes
+    constexpr int kChunks = kSlices * 64 * 4;
+#pragma unroll
+    for (int it = 0; it < 2 * kChunks / kThreads; it++) {
+        const int c = threadIdx.x + it * kThreads;
+        const int op = c / kChunks;  // 0 = A, 1 = B
+        const int rem = c - op * kChunks;
+        const int s = rem / 256, row = (rem / 4) % 64, part = rem % 4;
+        const uint16_t *g = op == 0 ? Ap + s * a_plane + (size_t)(m0 + row) * a_kp + kt + part * 8
+                                    : Bp + s * b_plane + (size_t)(n0 + row) * b_kp + kt + part * 8;
+        uint16_t *d = stage + ((size_t)(op * kSlices + s) * 64 + row) * kRowPad + part * 8;
+        cp_async16(d, g);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One 64 x 64 tile of C (or of split z's partial product).
+__global__ void __launch_bounds__(kThreads, 1)
+sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int a_rp, int a_kp,
+               const uint16_t *__restrict__ Bp, const int *__restrict__ eb, int b_rp, int b_kp, int m, int n,
+               int ksplit, int K, double alpha, double beta, double *__restrict__ C, long long ldc, int lower,
+               double *__restrict__ part)
+{
+    extern __shared__ __align__(16) uint16_t smem[];
+    const int tm = blockIdx.y, tn = blockIdx.x;
+    if (lower && tm < tn) return;  // tile wholly above the diagonal
+    const int m0 = tm * kBM, n0 = tn * kBN;
+    const int kbeg = blockIdx.z * ksplit, kend = min(K, kbeg + ksplit);
+    const size_t a_plane = (size_t)a_rp * a_kp, b_plane = (size_t)b_rp * b_kp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp & 3, wn = warp >> 2;
+
+    float acc[kBuckets][4][4];
+    long long T[4][4];
+#pragma unroll
+    for (int b = 0; b < kBuckets; b++)
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[b][t][q] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; t++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) T[t][q] = 0;
+
+    // ldmatrix lane offsets (elements within a stage's operand block)
+    const int a_row = wm * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
+    const int b_row = wn * 32 + (lane & 7) + (lane >> 4) * 8, b_k = ((lane >> 3) & 1) * 8;
+
+    int stage = 0;
+    if (kbeg < kend) load_stage(smem, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0, kbeg);
+    int steps = 0;
+    for (int kt = kbeg; kt < kend; kt += kBK, steps++) {
+        const bool more = kt + kBK < kend;
+        if (more)
+            load_stage(smem + (size_t)(stage ^ 1) * kStageElems, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0,
+                       kt + kBK);
+        if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const uint16_t *As = smem + (size_t)stage * kStageElems;
+        const uint16_t *Bs = As + (size_t)kSlices * 64 * kRowPad;
+#pragma unroll
+        for (int ks = 0; ks < kBK / 16; ks++) {
+            unsigned af[kSlices][4];
+#pragma unroll
+            for (int s = 0; s < kSlices; s++)
+                ldsm_x4(af[s][0], af[s][1], af[s][2], af[s][3],
+                        As + ((size_t)s * 64 + a_row) * kRowPad + ks * 16 + a_k);
+#pragma unroll
+            for (int j = 0; j < kSlices; j++) {
+                unsigned bf[4][2];
+#pragma unroll
+                for (int p = 0; p < 2; p++)
+                    ldsm_x4(bf[2 * p][0], bf[2 * p][1], bf[2 * p + 1][0], bf[2 * p + 1][1],
+                            Bs + ((size_t)j * 64 + b_row + p * 16) * kRowPad + ks * 16 + b_k);
+#pragma unroll
+                for (int i = 0; i + j < kSlices; i++) {
+                    constexpr int kLast = kBuckets - 1;
+                    const int bucket = (i + j) < kLast ? (i + j) : kLast;
+#pragma unroll
+                    for (int t = 0; t < 4; t++) mma_bf16(acc[bucket][t], af[i], bf[t][0], bf[t][1]);
+                }
+            }
+        }
+        __syncthreads();  // this stage's buffer is refilled two steps later
+        stage ^= 1;
+        // fold the exact levels into the integer accumulators every kFlushK
+        if ((steps + 1) % (kFlushK / kBK) == 0 || !more) {
+#pragma unroll
+            for (int b = 0; b < kExactLevels; b++)
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        // level b holds an integer multiple of 2^(-7b) below 2^24 units
+                        const int iv = __float2int_rn(acc[b][t][q] * (float)(1 << (kDigitBits * b)));
+                        T[t][q] += (long long)iv << (kDigitBits * (kExactLevels - 1 - b));
+                        acc[b][t][q] = 0.f;
+                    }
+        }
+    }
+
+    // epilogue: value = (T 2^-28 + low) 2^(ea + eb - 14)
+    const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int t = 0; t < 4; t++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int r = m0 + wm * 16 + g + (q >> 1) * 8;
+            const int c = n0 + wn * 32 + t * 8 + tig * 2 + (q & 1);
+            if (r >= m || c >= n || (lower && r < c)) continue;
+            double v = (double)T[t][q] * 0x1p-28 + (double)acc[kExactLevels][t][q];
+            v = scale_by_pow2(v, ea[r] + eb[c] - 2 * kDigitBits);
+            if (part) {
+                part[(size_t)blockIdx.z * m * n + (size_t)c * m + r] = v;
+            } else {
+                double *cp = C + r + (long long)c * ldc;
+                *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
+            }
+        }
+}
+
+__global__ void __launch_bounds__(256) sliced_reduce(int m, int n, int splits, const double *__restrict__ part,
+                                                      double alpha, double beta, double *__restrict__ C,
+                                                      long long ldc, int lower)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * n) return;
+    const int r = (int)(idx % m), c = (int)(idx / m);
+    if (lower && r < c) return;
+    double s = 0.0;
+    for (int z = 0; z < splits; z++) s += part[(size_t)z * m * n + idx];
+    double *cp = C + r + (long long)c * ldc;
+    *cp = beta == 0.0 ? alpha * s : fma(alpha, s, beta * *cp);
+}
+
+}  // namespace
+
+size_t sliced_bytes(int R, int K) { return slice_layout(R, K).total; }
+
+cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long long ld, void *buf, SlicedOp *out,
+                         cudaStream_t st)
+{
+    const SliceLayout L = slice_layout(R, K);
+    const int Rp = round_up(R > 0 ? R : 1, kBM), Kp = round_up(K > 0 ? K : 1, kBK);
+    char *base = (char *)buf;
+    uint16_t *planes = (uint16_t *)(base + L.planes);
+    int *e = (int *)(base + L.e);
+    unsigned long long *rmax = (unsigned long long *)(base + L.rmax);
+    out->planes = planes;
+    out->e = e;
+    out->R = R;
+    out->K = K;
+    out->Rp = Rp;
+    out->Kp = Kp;
+    cudaError_t err = cudaMemsetAsync(rmax, 0, (size_t)Rp * sizeof(unsigned long long), st);
+    if (err != cudaSuccess) return err;
+    const dim3 block(32, 8);
+    if (R > 0 && K > 0) {
+        const dim3 grid((K + 31) / 32, (R + 31) / 32);
+        slice_rowmax<<<grid, block, 0, st>>>((int)view, src, ld, R, K, rmax);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    // digits over the padded extent (zeros outside R x K)
+    const dim3 grid2(Kp / 32, Rp / 32);
+    slice_digits<<<grid2, block, 0, st>>>((int)view, src, ld, R, K, Rp, Kp, rmax, planes, e);
+    return cudaGetLastError();
+}
+
+cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, double alpha, double beta, double *C,
+                        long long ldc, bool lower, double *work, size_t work_elems, cudaStream_t st)
+{
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (A.K != B.K || A.Kp != B.Kp || m > A.R || n > B.R) return cudaErrorInvalidValue;
+    // opt in to the large dynamic shared memory (cheap; per device, so every call)
+    cudaError_t ea = cudaFuncSetAttribute(sliced_product, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kProductSmem);
+    if (ea != cudaSuccess) return ea;
+    const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
+    const long long tiles = lower ? (long long)tiles_m * (tiles_m + 1) / 2 : (long long)tiles_m * tiles_n;
+    const int Kp = A.Kp;
+    // split the reduction when the tiles alone cannot fill the device
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int splits = 1;
+    if (tiles < 2LL * sms && work) {
+        splits = (int)((2LL * sms + tiles - 1) / tiles);
+        const int max_by_k = Kp / (4 * kFlushK);  // keep at least 4 flush chunks per split
+        if (splits > max_by_k) splits = max_by_k > 1 ? max_by_k : 1;
+        while (splits > 1 && (size_t)splits * m * n > work_elems) splits--;
+    }
+    int ksplit = Kp;
+    if (splits > 1) {
+        ksplit = round_up((Kp + splits - 1) / splits, kFlushK);
+        splits = (Kp + ksplit - 1) / ksplit;
+    }
+    const dim3 grid(tiles_n, tiles_m, splits);
+    sliced_product<<<grid, kThreads, kProductSmem, st>>>(A.planes, A.e, A.Rp, A.Kp, B.planes, B.e, B.Rp, B.Kp, m, n,
+                                                         ksplit, Kp, alpha, beta, C, ldc, lower ? 1 : 0,
+                                                         splits > 1 ? work : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    const long long total = (long long)m * n;
+    sliced_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(m, n, splits, work, alpha, beta, C, ldc,
+                                                                    lower ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace gb
+
+// ---- whole products: slice both operands into the workspace, multiply ----
+
+namespace gb {
+
+namespace {
+
+constexpr size_t kPartialElems = (size_t)4 << 20;  // split-K partials (32 MB)
+
+struct SlicedWs {
+    char *a, *b, *cat1, *cat2;
+    double *part;
+    size_t total;
+};
+
+// Workspace of a product whose slice-row operands are Ra x K and Rb x K; cat
+// holds two Rc x Kc FP64 concatenation buffers (SYR2K), or nothing.
+SlicedWs sliced_ws(int Ra, int Rb, int K, int Rc, int Kc, void *base)
+{
+    SlicedWs w{};
+    size_t off = 0;
+    char *p = (char *)base;
+    auto take = [&](size_t bytes) {
+        char *q = p ? p + off : nullptr;
+        off += a256(bytes);
+        return q;
+    };
+    w.a = take(sliced_bytes(Ra, K));
+    w.b = Rb > 0 ? take(sliced_bytes(Rb, K)) : nullptr;
+    w.cat1 = Rc > 0 ? take((size_t)Rc * Kc * 8) : nullptr;
+    w.cat2 = Rc > 0 ? take((size_t)Rc * Kc * 8) : nullptr;
+    w.part = (double *)take(kPartialElems * 8);
+    w.total = off;
+    return w;
+}
+
+}  // namespace
+
+size_t sliced_gemm_ws_bytes(int m, int n, int k) { return sliced_ws(m, n, k, 0, 0, nullptr).total; }
+size_t sliced_symm_ws_bytes(char side, int m, int n)
+{
+    return side == 'L' ? sliced_ws(m, n, m, 0, 0, nullptr).total : sliced_ws(m, n, n, 0, 0, nullptr).total;
+}
+size_t sliced_syr2k_ws_bytes(int n, int k) { return sliced_ws(n, n, 2 * k, n, 2 * k, nullptr).total; }
+size_t sliced_syrk_ws_bytes(int n, int k) { return sliced_ws(n, 0, k, 0, 0, nullptr).total; }
+
+cudaError_t sliced_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double *A, long long lda,
+                         const double *B, long long ldb, double beta, double *C, long long ldc, void *ws,
+                         cudaStream_t st)
+{
+    SlicedWs w = sliced_ws(m, n, k, 0, 0, ws);
+    SlicedOp a, b;
+    cudaError_t e = slice_matrix(transa == 'N' ? kViewRow : kViewCol, m, k, A, lda, w.a, &a, st);
+    if (e != cudaSuccess) return e;
+    if ((e = slice_matrix(transb == 'N' ? kViewCol : kViewRow, n, k, B, ldb, w.b, &b, st)) != cudaSuccess) return e;
+    return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, false, w.part, kPartialElems, st);
+}
+
+cudaError_t sliced_dsymm(char side, int m, int n, double alpha, const double *S, long long lds, const double *B,
+                         long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st)
+{
+    const int K = side == 'L' ? m : n;
+    SlicedWs w = sliced_ws(m, n, K, 0, 0, ws);
+    SlicedOp a, b;
+    cudaError_t e;
+    if (side == 'L') {  // C = S B: rows of S, columns of B
+        if ((e = slice_matrix(kViewSym, m, m, S, lds, w.a, &a, st)) != cudaSuccess) return e;
+        if ((e = slice_matrix(kViewCol, n, m, B, ldb, w.b, &b, st)) != cudaSuccess) return e;
+    } else {            // C = B S: rows of B, columns (= rows) of S
+        if ((e = slice_matrix(kViewRow, m, n, B, ldb, w.a, &a, st)) != cudaSuccess) return e;
+        if ((e = slice_matrix(kViewSym, n, n, S, lds, w.b, &b, st)) != cudaSuccess) return e;
+    }
+    return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, false, w.part, kPartialElems, st);
+}
+
+cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, long long lda, const double *B,
+                                long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st)
+{
+    // A B^T + B A^T = [A B] [B A]^T
+    SlicedWs w = sliced_ws(n, n, 2 * k, n, 2 * k, ws);
+    double *AB = (double *)w.cat1, *BA = (double *)w.cat2;
+    const size_t row = (size_t)n * 8;
+    cudaError_t e;
+    if (k > 0) {
+        if ((e = cudaMemcpy2DAsync(AB, row, A, lda * 8, row, k, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(AB + (size_t)n * k, row, B, ldb * 8, row, k, cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy2DAsync(BA, row, B, ldb * 8, row, k, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(BA + (size_t)n * k, row, A, lda * 8, row, k, cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess)
+            return e;
+    }
+    SlicedOp a, b;
+    if ((e = slice_matrix(kViewRow, n, 2 * k, AB, n, w.a, &a, st)) != cudaSuccess) return e;
+    if ((e = slice_matrix(kViewRow, n, 2 * k, BA, n, w.b, &b, st)) != cudaSuccess) return e;
+    return sliced_gemm(a, b, n, n, alpha, beta, C, ldc, true, w.part, kPartialElems, st);
+}
+
+cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
+                                 long long ldc, void *ws, cudaStream_t st)
+{
+    // A^T A: both operands are the columns of A
+    SlicedWs w = sliced_ws(n, 0, k, 0, 0, ws);
+    SlicedOp a;
+    cudaError_t e = slice_matrix(kViewCol, n, k, A, lda, w.a, &a, st);
+    if (e != cudaSuccess) return e;
+    return sliced_gemm(a, a, n, n, alpha, beta, C, ldc, true, w.part, kPartialElems, st);
+}
+
+}  // namespace gb
+
+#include "elpa_gb300.h"
+
+extern "C" {
+
+static bool sl_bad_ptr(const void *p) { return !p || ((uintptr_t)p % 8) != 0; }
+static bool sl_bad_ws(const void *p) { return !p || ((uintptr_t)p % 256) != 0; }
+
+size_t gb_dgemm_sliced_workspace_bytes(int m, int n, int k)
+{
+    if (m < 0 || n < 0 || k < 0) return 0;
+    return gb::sliced_gemm_ws_bytes(m, n, k);
+}
+
+int gb_dgemm_sliced(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes,
+                    void *stream)
+{
+    const bool ta = transa == 'T' || transa == 't', tb = transb == 'T' || transb == 't';
+    if (!ta && transa != 'N' && transa != 'n') return -1;
+    if (!tb && transb != 'N' && transb != 'n') return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (k < 0) return -5;
+    if (m == 0 || n == 0) return GB_OK;
+    if (k > 0 && sl_bad_ptr(A)) return -7;
+    if (lda < (ta ? (k > 1 ? k : 1) : m)) return -8;
+    if (k > 0 && sl_bad_ptr(B)) return -9;
+    if (ldb < (tb ? n : (k > 1 ? k : 1))) return -10;
+    if (sl_bad_ptr(C)) return -12;
+    if (ldc < m) return -13;
+    if (sl_bad_ws(workspace)) return -14;
+    if (ws_bytes < gb::sliced_gemm_ws_bytes(m, n, k)) return -15;
+    cudaError_t e = gb::sliced_dgemm(ta ? 'T' : 'N', tb ? 'T' : 'N', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                     workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+size_t gb_dsymm_sliced_workspace_bytes(char side, int m, int n)
+{
+    const bool left = side == 'L' || side == 'l';
+    if ((!left && side != 'R' && side != 'r') || m < 0 || n < 0) return 0;
+    return gb::sliced_symm_ws_bytes(left ? 'L' : 'R', m, n);
+}
+
+int gb_dsymm_sliced(char side, int m, int n, double alpha, const double *S, int lds, const double *B, int ldb,
+                    double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream)
+{
+    const bool left = side == 'L' || side == 'l';
+    if (!left && side != 'R' && side != 'r') return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (m == 0 || n == 0) return GB_OK;
+    if (sl_bad_ptr(S)) return -5;
+    if (lds < (left ? m : n)) return -6;
+    if (sl_bad_ptr(B)) return -7;
+    if (ldb < m) return -8;
+    if (sl_bad_ptr(C)) return -10;
+    if (ldc < m) return -11;
+    if (sl_bad_ws(workspace)) return -12;
+    if (ws_bytes < gb::sliced_symm_ws_bytes(left ? 'L' : 'R', m, n)) return -13;
+    cudaError_t e = gb::sliced_dsymm(left ? 'L' : 'R', m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace,
+                                     (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+size_t gb_dsyr2k_sliced_workspace_bytes(int n, int k)
+{
+    if (n < 0 || k < 0) return 0;
+    return gb::sliced_syr2k_ws_bytes(n, k);
+}
+
+int gb_dsyr2k_sliced(int n, int k, double alpha, const double *A, int lda, const double *B, int ldb, double beta,
+                     double *C, int ldc, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (n < 0) return -1;
+    if (k < 0) return -2;
+    if (n == 0) return GB_OK;
+    if (k > 0 && sl_bad_ptr(A)) return -4;
+    if (lda < n) return -5;
+    if (k > 0 && sl_bad_ptr(B)) return -6;
+    if (ldb < n) return -7;
+    if (sl_bad_ptr(C)) return -9;
+    if (ldc < n) return -10;
+    if (sl_bad_ws(workspace)) return -11;
+    if (ws_bytes < gb::sliced_syr2k_ws_bytes(n, k)) return -12;
+    cudaError_t e = gb::sliced_dsyr2k_lower(n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace,
+                                            (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+size_t gb_dsyrk_sliced_workspace_bytes(int n, int k)
+{
+    if (n < 0 || k < 0) return 0;
+    return gb::sliced_syrk_ws_bytes(n, k);
+}
+
+int gb_dsyrk_sliced(int n, int k, double alpha, const double *A, int lda, double beta, double *C, int ldc,
+                    void *workspace, size_t ws_bytes, void *stream)
+{
+    if (n < 0) return -1;
+    if (k < 0) return -2;
+    if (n == 0) return GB_OK;
+    if (k > 0 && sl_bad_ptr(A)) return -4;
+    if (lda < (k > 1 ? k : 1)) return -5;
+    if (sl_bad_ptr(C)) return -7;
+    if (ldc < n) return -8;
+    if (sl_bad_ws(workspace)) return -9;
+    if (ws_bytes < gb::sliced_syrk_ws_bytes(n, k)) return -10;
+    cudaError_t e = gb::sliced_dsyrk_lower_t(n, k, alpha, A, lda, beta, C, ldc, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// FP64 matrix products on the bf16 tensor cores by exact digit slicing (the
+// error-free splitting idea of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 59 (2012), in its fixed-point form).
+//
+// Every row of op(A) and every column of op(B) is scaled by a power of two
+// so that its largest entry is below one, and each entry's magnitude is cut
+// into kSlices digits of kDigitBits bits (|digit| <= 127, all digits carry
+// the entry's sign).  Digit t is stored as the bf16 value d * 2^(-7t), which
+// bf16 holds exactly.  The product of digit planes i (of A) and j (of B) is
+// an exact multiple of 2^(-7(i+j)) and lands in "level" i+j.  Pairs with
+// i+j < kSlices are formed (the rest lie below FP64's resolution of the
+// scaled row/column maxima).  Levels 0..kExactLevels-1 are accumulated
+// exactly: each level's FP32 tensor-core sum over kFlushK consecutive k is an
+// integer multiple of 2^(-7 level) below 2^24 units, so it is exact, and it
+// is folded into a 64-bit integer per output every kFlushK.  The higher
+// levels, whose weight is below 2^-35 of level 0, share one FP32
+// accumulator.  The result is rounded to FP64 once, at the end.
+//
+// Accuracy is that of an FP64 product measured against the scaled maxima:
+// |C - AB| <~ 2^-53 k max_j|a_ij| max_i|b_ij| per entry.  Inputs must be
+// finite; subnormal inputs are read as zero.
+//
+// A sliced operand is an R x K "slice-row" matrix; its rows are the rows of
+// op(A) (for the left operand) or the columns of op(B) (for the right).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gb {
+
+constexpr int kSlices = 8;
+constexpr int kDigitBits = 7;
+constexpr int kExactLevels = 5;
+constexpr int kFlushK = 128;
+
+// How a slice-row matrix reads a column-major FP64 source `src` (leading
+// dimension ld): element (r, k) is
+//   kViewRow: src[r + k ld]     (slice rows are the source's rows)
+//   kViewCol: src[k + r ld]     (slice rows are the source's columns)
+//   kViewSym: the symmetric matrix whose lower triangle src holds.
+enum SliceView { kViewRow = 0, kViewCol = 1, kViewSym = 2 };
+
+struct SlicedOp {
+    const uint16_t *planes;  // kSlices planes of Rp x Kp bf16, row-major (k fastest)
+    const int *e;            // Rp row exponents: the row's entries are below 2^e
+    int R, K, Rp, Kp;        // Rp: R rounded up to 64; Kp: K rounded up to 32
+};
+
+// Bytes a sliced R x K operand occupies (planes, exponents and a reduction
+// scratch), 256-byte multiple.
+size_t sliced_bytes(int R, int K);
+
+// Slices an R x K view of src into buf (sliced_bytes(R, K) bytes, 256-byte
+// aligned); fills *out.  Two launches and a memset on st.
+cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long long ld, void *buf, SlicedOp *out,
+                         cudaStream_t st);
+
+// C (m x n, column-major) = alpha A B^T + beta C where A, B are sliced
+// (A.R >= m, B.R >= n, A.K == B.K): row r of A times row c of B.  lower:
+// only C's lower triangle (r >= c) is written.  `work` (doubles) holds
+// split-K partials; the reduction splits while splits * m * n <= work_elems.
+cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, double alpha, double beta, double *C,
+                        long long ldc, bool lower, double *work, size_t work_elems, cudaStream_t st);
+
+// Whole products (slice both operands into ws, multiply), with the DFMA
+// forms' conventions (dgemm_dfma.cuh); ws must hold the matching *_ws_bytes.
+size_t sliced_gemm_ws_bytes(int m, int n, int k);
+size_t sliced_symm_ws_bytes(char side, int m, int n);
+size_t sliced_syr2k_ws_bytes(int n, int k);
+size_t sliced_syrk_ws_bytes(int n, int k);
+cudaError_t sliced_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double *A, long long lda,
+                         const double *B, long long ldb, double beta, double *C, long long ldc, void *ws,
+                         cudaStream_t st);
+cudaError_t sliced_dsymm(char side, int m, int n, double alpha, const double *S, long long lds, const double *B,
+                         long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
+cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, long long lda, const double *B,
+                                long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
+cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
+                                 long long ldc, void *ws, cudaStream_t st);
+
+}  // namespace gb

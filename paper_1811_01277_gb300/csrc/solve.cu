@@ -13,7 +13,10 @@
 //   tri -> band    the pipeline trans_ev_tridi_to_band kernel
 //   band -> full   Z <- Q_0 Q_1 ... Q_{P-1} Z, last panel first:
 //                  Z_p -= Y (T (Y^T Z_p))
-// The plain GEMMs run in cuBLAS; everything else in this library's kernels.
+// The real solve's large products (SYMM, SYR2K, the band->full GEMMs, the
+// Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by exact digit
+// slicing (dgemm_sliced.cuh), the small ones in the DFMA kernels
+// (dgemm_dfma.cuh); the complex solve's products in cuBLAS.
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,6 +32,7 @@
 #include "layout.cuh"
 #include "trans_ev_kernels.cuh"
 #include "dgemm_dfma.cuh"
+#include "dgemm_sliced.cuh"
 #include "tridiag_eig.cuh"
 
 namespace gb {
@@ -137,9 +141,27 @@ cudaEvent_t *stage_events(cudaStream_t st)
 struct SolveWs {
     double *Aw, *tauP, *Tall, *Y, *Y2, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2, *gw,
         *gw2;
-    void *chase, *eig, *tev;
-    size_t chase_bytes, tev_bytes, gw_elems, gw2_elems, total;
+    void *chase, *eig, *tev, *sl;
+    size_t chase_bytes, tev_bytes, gw_elems, gw2_elems, sl_bytes, total;
 };
+
+// Products of at least this many flops go to the sliced tensor-core kernels
+// (below it the extra launches of slicing cost more than they save).
+constexpr double kSlicedMinFlops = 2.5e8;
+
+bool sliced_pays(double m, double n, double k) { return 2.0 * m * n * k >= kSlicedMinFlops; }
+
+// Workspace of the largest sliced product of a solve (0 if none is large).
+size_t sliced_region_bytes(int n, int nev, int b)
+{
+    if (!sliced_pays(n, b, n)) return 0;
+    size_t s = std::max(gb::sliced_symm_ws_bytes('L', n, b), gb::sliced_syr2k_ws_bytes(n, b));
+    s = std::max(s, gb::sliced_gemm_ws_bytes(b, nev, n));
+    s = std::max(s, gb::sliced_gemm_ws_bytes(n, nev, b));
+    s = std::max(s, gb::sliced_syrk_ws_bytes(nev, n));
+    s = std::max(s, gb::sliced_symm_ws_bytes('R', n, nev));
+    return s;
+}
 
 // Split-K partials of the DFMA products (the kernels split only as far as
 // this holds).
@@ -186,6 +208,8 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
     w.tev_bytes = gb_trans_ev_workspace_bytes(n, b, nev, 0, nullptr);
     w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
+    w.sl_bytes = sliced_region_bytes(n, nev, b);
+    w.sl = w.sl_bytes ? take(w.sl_bytes) : nullptr;
     w.total = off;
     return w;
 }
@@ -272,7 +296,10 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     const int b = nbw;
     SolveWs w = carve(n, nev, b, (char *)workspace);
     if (ws_bytes < w.total) return -10;
-    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES)) return -12;
+    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS)) return -12;
+    // large products on the tensor cores unless the caller asks for DFMA
+    const bool slice_ok = w.sl && !(flags & GB_SOLVE_DFMA_PRODUCTS);
+    auto use_sliced = [&](double m_, double n_, double k_) { return slice_ok && sliced_pays(m_, n_, k_); };
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t *sev = nullptr;
     if (flags & GB_SOLVE_RECORD_STAGES) {
@@ -333,7 +360,10 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         GB_CU(gb::dfma_gemm('N', 'N', m, b, b, 1.0, Yp, m, T, b, 0.0, w.YT, m, w.gw, w.gw_elems, st));
         // only the lower triangle of A2 is kept: X = A2 (Y T) (symmetric
         // product), W = X - Y M / 2, then A2 -= W Y^T + Y W^T on the lower triangle
-        GB_CU(gb::dfma_symm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.gw, w.gw_elems, st));
+        if (use_sliced(m, b, m))
+            GB_CU(gb::sliced_dsymm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.sl, st));
+        else
+            GB_CU(gb::dfma_symm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, Yp, m, w.X, m, 0.0, w.Pm, b, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('T', 'N', b, b, b, 1.0, T, b, w.Pm, b, 0.0, w.M, b, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('N', 'N', m, b, b, -0.5, Yp, m, w.M, b, 1.0, w.X, m, w.gw, w.gw_elems, st));
@@ -349,10 +379,17 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
                 GB_CU(cudaStreamWaitEvent(la->side, la->ready, 0));
             }
             GB_CU(factor(P + 1));
-            GB_CU(gb::dfma_syr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b, ldw,
-                                       st));
+            if (use_sliced(m - b, m - b, b))
+                GB_CU(gb::sliced_dsyr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b,
+                                              ldw, w.sl, st));
+            else
+                GB_CU(gb::dfma_syr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b,
+                                           ldw, st));
         } else {
-            GB_CU(gb::dfma_syr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, st));
+            if (use_sliced(m, m, b))
+                GB_CU(gb::sliced_dsyr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, w.sl, st));
+            else
+                GB_CU(gb::dfma_syr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, st));
         }
     }
     GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
@@ -369,9 +406,15 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_CU(gb::tridiag_invit_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
     GB_STAGE(4);
     // G = Z^T Z (lower triangle), M = (3I - G)/2, Z <- Z M
-    GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, st));
+    if (use_sliced(nev, nev, n))
+        GB_CU(gb::sliced_dsyrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, w.sl, st));
+    else
+        GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, st));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.gw, w.gw_elems, st));
+    if (use_sliced(n, nev, nev))
+        GB_CU(gb::sliced_dsymm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.sl, st));
+    else
+        GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.gw, w.gw_elems, st));
 
     // ---- tridiagonal -> band (the hot path)
     GB_STAGE(5);
@@ -386,9 +429,15 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         const double *T = w.Tall + (long long)p * b * b;
         double *Zr = Z + (j + b);
         GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
-        GB_CU(gb::dfma_gemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.gw, w.gw_elems, st));
+        if (use_sliced(b, nev, m))
+            GB_CU(gb::sliced_dgemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.sl, st));
+        else
+            GB_CU(gb::dfma_gemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('N', 'N', b, nev, b, 1.0, T, b, w.S, b, 0.0, w.S2, b, w.gw, w.gw_elems, st));
-        GB_CU(gb::dfma_gemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.gw, w.gw_elems, st));
+        if (use_sliced(m, nev, b))
+            GB_CU(gb::sliced_dgemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.sl, st));
+        else
+            GB_CU(gb::dfma_gemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.gw, w.gw_elems, st));
     }
     GB_STAGE(7);
 #undef GB_STAGE

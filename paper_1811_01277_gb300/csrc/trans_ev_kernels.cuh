@@ -27,8 +27,10 @@ cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d,
 
 size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads);
 bool pipeline_supported(int b);
+// column_batch: column blocks per ticket batch; lead_tiles: how far a sweep
+// group may run ahead of the next (0 = defaults)
 cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
-                       long long ldz, int nb, int threads, void *ws, size_t ws_bytes, long long spin_polls,
-                       long long timeout_ns, int hold_group, cudaStream_t st);
+                       long long ldz, int nb, int threads, int column_batch, int lead_tiles, void *ws,
+                       size_t ws_bytes, long long spin_polls, long long timeout_ns, int hold_group, cudaStream_t st);
 
 }  // namespace gb

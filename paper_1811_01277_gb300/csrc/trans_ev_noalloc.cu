@@ -87,7 +87,7 @@ extern "C" int gb_trans_ev_tridi_to_band_d_noalloc(int n, int nbw, int nev, cons
             return GB_ERR_CUDA;
         return GB_OK;
     }
-    cudaError_t e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, kNoallocNb, kNoallocThreads, scratch, need,
+    cudaError_t e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, kNoallocNb, kNoallocThreads, 0, 0, scratch, need,
                                    kNoallocSpinPolls, kNoallocTimeoutNs, 0, (cudaStream_t)stream);
     if (e != cudaSuccess) return GB_ERR_CUDA;
     if (status) {

@@ -20,6 +20,17 @@
 // Rows that group g overwrites have already been read by group g+1, which
 // is at least one tile ahead.
 //
+// Lead limit: once group g-1 of the same column block has started, group g
+// runs tile k only after g-1 has completed k - lead tiles.  Without it the
+// groups of a batch drift many tiles apart, the live rows of a batch span
+// the whole column height, and rows round-trip through DRAM between
+// consecutive groups.  Progress words start at -1 ("not started"); an item
+// publishes 0 when it starts.  No deadlock for lead >= 1: the lowest started
+// group of a column block has no started successor, so it is never held by
+// the limit, and if it waits for its predecessor then that one is not held
+// by the limit either (it is less than one tile ahead), and so on up to the
+// highest unfinished group, whose predecessor has finished.
+//
 // Waits are bounded: thread 0 polls with an acquire load and a short sleep;
 // after spin_polls polls or timeout_ns nanoseconds it records
 // GB_ERR_TIMEOUT, raises an abort flag that every other waiter also checks,
@@ -51,9 +62,12 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Column blocks per ticket batch (a schedule simulation of n = 16384 gave a
-// one-tile lag between consecutive groups at 98% slot utilisation for 16).
+// Default column blocks per ticket batch, and no lead limit: on GB300 at
+// n = 16384 every limit that cut the DRAM traffic (2 tiles: 175 -> 50 GB per
+// launch) also stalled the chains (1.97 -> 4.4 s), because a group that
+// starts at tile 0 holds back the groups started before it.
 constexpr int kColumnBatch = 16;
+constexpr int kLeadTiles = 1 << 30;
 
 struct PipeState {  // head of the workspace (zeroed before every launch)
     int ticket;
@@ -64,8 +78,8 @@ struct PipeState {  // head of the workspace (zeroed before every launch)
 template <int B, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 pipeline_d(int n, int nev, const double *__restrict__ hh_v, const double *__restrict__ hh_tau,
-           double *__restrict__ Z, long long ldz, int G, int C, int CB, PipeState *state, int *progress,
-           long long spin_polls, long long timeout_ns, int hold_group)
+           double *__restrict__ Z, long long ldz, int G, int C, int CB, int lead, PipeState *state,
+           int *progress, long long spin_polls, long long timeout_ns, int hold_group)
 {
     constexpr int L = B + NB - 1;
     constexpr int b = B;
@@ -91,29 +105,37 @@ pipeline_d(int n, int nev, const double *__restrict__ hh_v, const double *__rest
     double w[L];
 #pragma unroll
     for (int i = 0; i < L; i++) w[i] = 0.0;
+    if (threadIdx.x == 0 && g + 1 != hold_group) st_release_gpu(progress + (long long)g * C + c, 0);
 
     for (int k = 0; k < K; k++) {
-        // ---- wait for group g+1 to have finalised the rows this tile reads
+        // ---- wait for group g+1 to have finalised the rows this tile reads,
+        // and for group g-1 (once started) to be at most `lead` tiles behind
         if (threadIdx.x == 0) {
             int abort = 0;
-            if (g + 1 < G) {
-                const int need = min(k + 1, Knext);
-                const int *flag = progress + (long long)(g + 1) * C + c;
-                unsigned long long t0 = global_ns();
-                long long polls = 0;
-                while (ld_acquire_gpu(flag) < need) {
-                    if (*(volatile int *)&state->abort) { abort = 1; break; }
-                    if (++polls >= spin_polls || (long long)(global_ns() - t0) > timeout_ns) {
-                        atomicExch(&state->error, GB_ERR_TIMEOUT);
-                        atomicExch(&state->abort, 1);
-                        abort = 1;
-                        break;
-                    }
-                    __nanosleep(128);
+            const int need = (g + 1 < G) ? min(k + 1, Knext) : 0;
+            const int *flag = progress + (long long)(g + 1) * C + c;
+            const int behind = k - lead;  // tiles g-1 must have completed
+            const int *succ = progress + (long long)(g - 1) * C + c;
+            unsigned long long t0 = 0;
+            long long polls = 0;
+            for (;;) {
+                bool ok = need == 0 || ld_acquire_gpu(flag) >= need;
+                if (ok && g > 0 && behind > 0) {
+                    const int p = *(volatile const int *)succ;
+                    ok = p < 0 || p >= behind;
                 }
-            } else if (*(volatile int *)&state->abort) {
-                abort = 1;
+                if (ok) break;
+                if (*(volatile int *)&state->abort) { abort = 1; break; }
+                if (polls == 0) t0 = global_ns();
+                if (++polls >= spin_polls || (long long)(global_ns() - t0) > timeout_ns) {
+                    atomicExch(&state->error, GB_ERR_TIMEOUT);
+                    atomicExch(&state->abort, 1);
+                    abort = 1;
+                    break;
+                }
+                __nanosleep(128);
             }
+            if (!abort && *(volatile int *)&state->abort) abort = 1;
             s_abort = abort;
         }
         // ---- stage the tile's reflectors (v_0 = 1, zero past len)
@@ -167,19 +189,23 @@ pipeline_d(int n, int nev, const double *__restrict__ hh_v, const double *__rest
 
 template <int B, int NB, int THREADS>
 static cudaError_t run_pipeline_d(int n, int nev, const double *hh_v, const double *hh_tau, double *Z,
-                                  long long ldz, void *ws, size_t ws_bytes, long long spin_polls,
-                                  long long timeout_ns, int hold_group, cudaStream_t st)
+                                  long long ldz, int column_batch, int lead_tiles, void *ws, size_t ws_bytes,
+                                  long long spin_polls, long long timeout_ns, int hold_group, cudaStream_t st)
 {
     const int G = group_count(n, NB);
     const int C = (nev + THREADS - 1) / THREADS;
     if (G <= 0 || nev <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(ws, 0, ws_bytes, st);
+    // head zeroed, progress words set to -1 ("not started")
+    cudaError_t e = cudaMemsetAsync(ws, 0, 256, st);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync((char *)ws + 256, 0xff, ws_bytes - 256, st)) != cudaSuccess) return e;
     PipeState *state = (PipeState *)ws;
     int *progress = (int *)((char *)ws + 256);
-    const int CB = C < kColumnBatch ? C : kColumnBatch;
+    const int lead = lead_tiles > 0 ? lead_tiles : kLeadTiles;
+    const int want = column_batch > 0 ? column_batch : kColumnBatch;
+    const int CB = C < want ? C : want;
     pipeline_d<B, NB, THREADS><<<(unsigned)G * (unsigned)C, THREADS, 0, st>>>(
-        n, nev, hh_v, hh_tau, Z, ldz, G, C, CB, state, progress, spin_polls, timeout_ns, hold_group);
+        n, nev, hh_v, hh_tau, Z, ldz, G, C, CB, lead, state, progress, spin_polls, timeout_ns, hold_group);
     return cudaGetLastError();
 }
 
@@ -195,12 +221,12 @@ size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads)
 bool pipeline_supported(int b) { return b == 8 || b == 16 || b == 32 || b == 64; }
 
 cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
-                       long long ldz, int nb, int threads, void *ws, size_t ws_bytes, long long spin_polls,
-                       long long timeout_ns, int hold_group, cudaStream_t st)
+                       long long ldz, int nb, int threads, int column_batch, int lead_tiles, void *ws,
+                       size_t ws_bytes, long long spin_polls, long long timeout_ns, int hold_group, cudaStream_t st)
 {
-#define GB_PL(BB, NBB, TT)                                                                              \
-    return run_pipeline_d<BB, NBB, TT>(n, nev, hh_v, hh_tau, Z, ldz, ws, ws_bytes, spin_polls, timeout_ns, \
-                                       hold_group, st)
+#define GB_PL(BB, NBB, TT)                                                                                \
+    return run_pipeline_d<BB, NBB, TT>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, lead_tiles, ws, ws_bytes, \
+                                       spin_polls, timeout_ns, hold_group, st)
 #define GB_PL_T(BB, NBB)                        \
     do {                                        \
         if (threads <= 64) GB_PL(BB, NBB, 64);  \

@@ -1,7 +1,7 @@
 // FP64 pipe throughput on the local GPU: DFMA (8 independent chains per
 // thread), the f64 mma.sync shape m8n8k4, and kernels that issue both from
 // the same warps (to see whether the FP64 tensor path and DFMA share one
-// unit).  Each test runs for about target_s seconds so that clocks settle.
+// unit), and the bf16 / int8 mma.sync rates.  Each test runs for about target_s seconds so that clocks settle.
 // Prints one line per test: name, TFLOP/s, seconds.
 #include <cstdio>
 #include <cstdlib>
@@ -96,6 +96,59 @@ __global__ void dfma_dmma_split(double *out, long long iters_f, long long iters_
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+
+// Legacy warp-level tensor path (mma.sync), for the FP64-emulation design:
+// 8 independent accumulator chains per warp.
+__global__ void hmma_bf16(float *out, long long iters)
+{
+    unsigned a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; i++) a[i] = 0x3f803f80u ^ (threadIdx.x << 3);
+    b[0] = 0x3f003f00u;
+    b[1] = 0x3e803e80u;
+    float c[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) c[k][i] = 0.f;
+    for (long long it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                         : "+f"(c[k][0]), "+f"(c[k][1]), "+f"(c[k][2]), "+f"(c[k][3])
+                         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += c[k][0] + c[k][1] + c[k][2] + c[k][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void imma_s8(int *out, long long iters)
+{
+    unsigned a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; i++) a[i] = 0x01020304u ^ threadIdx.x;
+    b[0] = 0x05060708u;
+    b[1] = 0x0102fefdu;
+    int c[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) c[k][i] = 0;
+    for (long long it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                         : "+r"(c[k][0]), "+r"(c[k][1]), "+r"(c[k][2]), "+r"(c[k][3])
+                         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += c[k][0] + c[k][1] + c[k][2] + c[k][3];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 static cudaEvent_t e0, e1;
 
 template <class F>
@@ -148,6 +201,11 @@ int main(int argc, char **argv)
     // about the same time alone (8 chains x 512 flops vs 4 MMAs x 512 flops)
     run("split_dfma_dmma", target_s, (4.0 * 512.0 + 4.0 * 512.0) * 4 * grid,
         [&](long long it) { dfma_dmma_split<<<grid, 256>>>(out, 4 * it, it, X, Y); });
+    // 8 warps per block, 8 MMAs per warp and iteration
+    run("hmma_bf16_m16n8k16", target_s, 4096.0 * 8 * 8 * grid,
+        [&](long long it) { hmma_bf16<<<grid, 256>>>((float *)out, it); });
+    run("imma_s8_m16n8k32", target_s, 8192.0 * 8 * 8 * grid,
+        [&](long long it) { imma_s8<<<grid, 256>>>((int *)out, it); });
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { printf("cuda error %s\n", cudaGetErrorString(e)); return 1; }
     return 0;

@@ -69,6 +69,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert call(ldz=9) == -7
     assert f(10, 3, 2, 256, 256, 256, 10, opts={"variant": 7}, check=False) == -11
     assert f(10, 3, 2, 256, 256, 256, 10, opts={"variant": 1, "cols_per_block": 48}, check=False) == -11
+    for bad in ({"column_batch": -1}, {"column_batch": 1025}, {"lead_tiles": -1}, {"lead_tiles": 65537}):
+        assert f(10, 16, 2, 256, 256, 256, 10, opts=dict({"variant": 2}, **bad), check=False) == -11
+        assert gb.gb_trans_ev_workspace_bytes(100, 16, 10, 0, dict({"variant": 2}, **bad)) == 0
     # no-op cases return success without touching memory or a GPU
     assert f(1, 3, 5, None, None, 256, 1, check=False) == 0
     assert f(10, 3, 0, 256, 256, None, 10, check=False) == 0

@@ -62,6 +62,29 @@ def test_pipeline_parity(gb, n, b, nev, opts):
     assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
 
 
+SCHED = [{"column_batch": 1, "lead_tiles": 1}, {"column_batch": 3, "lead_tiles": 1},
+         {"column_batch": 3, "lead_tiles": 2}, {"column_batch": 1024, "lead_tiles": 3},
+         {"column_batch": 2, "lead_tiles": 65536}]
+
+
+@pytest.mark.parametrize("sched", SCHED, ids=["cb1l1", "cb3l1", "cb3l2", "cb1024l3", "cb2unbounded"])
+@pytest.mark.parametrize("n,b,nev", [(300, 32, 200), (1000, 64, 300), (777, 16, 129)])
+def test_pipeline_schedule_options(gb, n, b, nev, sched):
+    """Column batching and the lead limit only reorder independent work:
+    every column sees the same operations in the same order, so the result
+    is bit-identical to the default schedule (and within tolerance of the
+    oracle).  lead_tiles = 1 is the lock-step extreme of the lead limit."""
+    hv, ht = inputs.synthetic_reflectors(n, b, seed=n + 7)
+    Z = inputs.z_gaussian(n, nev, seed=nev + 7)
+    base = {"variant": 2, "sweeps_per_tile": 16, "cols_per_block": 64}
+    rc0, q0, out0 = run(gb, n, b, hv, ht, Z, base)
+    rc, q, out = run(gb, n, b, hv, ht, Z, dict(base, **sched))
+    assert rc0 == 0 and q0 == 0 and rc == 0 and q == 0
+    assert np.array_equal(out, out0)
+    ref = oracle.trans_ev(n, b, hv, ht, Z)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
+
+
 def test_pipeline_unsupported_nbw_falls_back(gb):
     n, b, nev = 200, 13, 40
     opts = {"variant": 2}

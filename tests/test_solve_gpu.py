@@ -80,6 +80,20 @@ def test_solve_clustered_spectrum(gb):
     check(A, w, Z, nev)
 
 
+@pytest.mark.parametrize("flags", [0, 4], ids=["sliced_products", "dfma_products"])
+def test_solve_large_products_both_paths(gb, flags):
+    """n = 2048 (large enough that the solve's big products take the sliced
+    tensor-core path by default): both product paths meet the bounds, and
+    their eigenvalues agree with LAPACK to 1e-11 ||A||."""
+    assert gb.GB_SOLVE_DFMA_PRODUCTS == 4
+    n, nev = 2048, 512
+    lam = inputs.clustered_spectrum(n, seed=21)
+    A = inputs.symmetric_with_spectrum(lam, seed=22)
+    w, Z = solve_gpu(gb, A, nev, 64, flags)
+    assert np.abs(w - lam[:nev]).max() / np.abs(lam).max() <= 1e-11
+    check(A, w, Z, nev)
+
+
 def test_solve_toeplitz_closed_form(gb):
     n, nev = 200, 50
     A = inputs.toeplitz_band(n, 1)
