@@ -56,6 +56,11 @@ extern "C" {
 #define GB_VARIANT_AUTO 0      /* library picks */
 #define GB_VARIANT_WAVEFRONT 1 /* one launch per anti-diagonal of the tile DAG */
 #define GB_VARIANT_PIPELINE 2  /* one persistent launch, tiles ordered by flags */
+#define GB_VARIANT_PIPELINE_TC 3 /* the pipeline's schedule with every tile applied in
+                                    compact WY form on the bf16 tensor cores (exact
+                                    digit slicing, Z in per-column 64-bit fixed point
+                                    during the call); real data, nbw in {16,32,64},
+                                    otherwise runs as PIPELINE */
 
 /* Tuning knobs (the paper's MEDIUM autotuning level tunes the blocking of the
  * back transformation, Sec. 4.3 and Sec. 5.3).  Zero fields mean "default". */
@@ -324,9 +329,9 @@ int gb_dsyrk(int n, int k, double alpha, const double *A, int lda, double beta, 
  * and every column of op(B) is scaled by a power of two and cut exactly into
  * eight 7-bit digits (error-free splitting, Ozaki, Ogita, Oishi and Rump,
  * Numer. Algorithms 59, 2012); digit-plane products are formed with
- * mma.sync bf16 and accumulated exactly in integers (FP32 only for the
- * pairs whose weight is below 2^-35 of the leading ones), and the result is
- * rounded to FP64 once.  Accuracy is that of an FP64 product measured
+ * mma.sync bf16, accumulated exactly (one FP32 accumulator per digit level,
+ * exact over 128 values of k, folded into 64-bit integers), and the result
+ * is rounded to FP64 once.  Accuracy is that of an FP64 product measured
  * against the scaled maxima: |C - alpha op(A) op(B)| <~ 2^-53 k |alpha|
  * max_j |op(A)_ij| max_i |op(B)_ij| per entry.  Inputs must be finite;
  * subnormal inputs are read as zero.  The paper's products are BLAS calls

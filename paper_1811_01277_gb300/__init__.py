@@ -8,7 +8,7 @@ seeded input generators; PyTorch only provides device memory and streams.
 """
 from ._lib import (  # noqa: F401
     EXPORTS, GB_ERR_CUDA, GB_ERR_TIMEOUT, GB_ERR_UNSUPPORTED, GB_ERR_WORKSPACE, GB_OK,
-    GB_NOALLOC_SCRATCH_BYTES, GB_SOLVE_FP64_EMULATED_GEMM, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
+    GB_NOALLOC_SCRATCH_BYTES, GB_SOLVE_FP64_EMULATED_GEMM, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_PIPELINE_TC, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
     gb_band_to_tridi_d, gb_band_to_tridi_workspace_bytes, gb_band_to_tridi_workspace_bytes_z, gb_band_to_tridi_z, gb_hh_count, gb_hh_index, gb_max_nbw, gb_status_string, gb_trans_ev_host_buffer_bytes,
     gb_trans_ev_launch_count, gb_trans_ev_opts, gb_trans_ev_query, gb_trans_ev_tridi_to_band_d,
     gb_trans_ev_tridi_to_band_d_host, gb_trans_ev_tridi_to_band_d_noalloc, gb_trans_ev_tridi_to_band_z, gb_trans_ev_workspace_bytes,
@@ -17,6 +17,9 @@ from ._lib import (  # noqa: F401
     gb_autotune_step, gb_solve_batched_d, gb_solve_batched_workspace_bytes, gb_solve_d,
     gb_solve_default_nbw, gb_solve_stage_ms, gb_solve_workspace_bytes_z, gb_solve_z, gb_solve_query_z, GB_SOLVE_RECORD_STAGES, SOLVE_STAGES, gb_solve_query, gb_solve_workspace_bytes, load,
     gb_dgemm, gb_dgemm_workspace_bytes, gb_dsymm, gb_dsyr2k, gb_dsyrk,
+    GB_SOLVE_DFMA_PRODUCTS, gb_dgemm_sliced, gb_dgemm_sliced_workspace_bytes, gb_dsymm_sliced,
+    gb_dsymm_sliced_workspace_bytes, gb_dsyr2k_sliced, gb_dsyr2k_sliced_workspace_bytes, gb_dsyrk_sliced,
+    gb_dsyrk_sliced_workspace_bytes,
 )
 
 

@@ -20,6 +20,7 @@ GB_ERR_UNSUPPORTED = 4
 GB_VARIANT_AUTO = 0
 GB_VARIANT_WAVEFRONT = 1
 GB_VARIANT_PIPELINE = 2
+GB_VARIANT_PIPELINE_TC = 3
 
 EXPORTS = (
     "gb_hh_count", "gb_hh_index", "gb_max_nbw", "gb_trans_ev_workspace_bytes",

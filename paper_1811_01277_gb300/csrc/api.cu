@@ -34,7 +34,7 @@ int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
     r->column_batch = 0;
     r->lead_tiles = 0;
     if (o) {
-        if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE) return -11;
+        if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE_TC) return -11;
         if (o->sweeps_per_tile < 0 || o->sweeps_per_tile > 32) return -11;
         if (o->cols_per_block != 0 && o->cols_per_block != 32 && o->cols_per_block != 64 &&
             o->cols_per_block != 128)
@@ -51,6 +51,8 @@ int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
         r->hold = o->test_hold_group;
     }
     const bool pipe_ok = !is_complex && gb::pipeline_supported(nbw);
+    if (variant == GB_VARIANT_PIPELINE_TC && (is_complex || !gb::pipeline_tc_supported(nbw)))
+        variant = GB_VARIANT_PIPELINE;
     if (variant == GB_VARIANT_AUTO) variant = pipe_ok ? GB_VARIANT_PIPELINE : GB_VARIANT_WAVEFRONT;
     if (variant == GB_VARIANT_PIPELINE && !pipe_ok) variant = GB_VARIANT_WAVEFRONT;
     r->variant = variant;
@@ -108,6 +110,7 @@ size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, cons
 {
     Opts o;
     if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return 0;
+    if (o.variant == GB_VARIANT_PIPELINE_TC && n > 1 && nev > 0) return gb::pipeline_tc_workspace_bytes(n, nbw, nev);
     if (o.variant == GB_VARIANT_PIPELINE && !is_complex && n > 1 && nev > 0)
         return gb::pipeline_workspace_bytes(n, nev, o.nb, o.threads);
     return 0;  // the wavefront variant needs no workspace
@@ -126,7 +129,10 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     if (ws_bytes < need) return -9;
     if (n == 1 || nev == 0) return GB_OK;
     cudaError_t e;
-    if (o.variant == GB_VARIANT_PIPELINE)
+    if (o.variant == GB_VARIANT_PIPELINE_TC)
+        e = gb::pipeline_tc_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.column_batch, workspace, need, o.spin, kTimeoutNs,
+                              o.hold, (cudaStream_t)stream);
+    else if (o.variant == GB_VARIANT_PIPELINE)
         e = gb::pipeline_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, o.column_batch, o.lead_tiles, workspace, need,
                            o.spin, kTimeoutNs, o.hold, (cudaStream_t)stream);
     else if (nbw > kMaxRegNbw)
@@ -208,6 +214,7 @@ long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex, cons
     if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return -1;
     if (n == 1 || nev == 0) return 0;
     if (o.variant == GB_VARIANT_PIPELINE) return 1;
+    if (o.variant == GB_VARIANT_PIPELINE_TC) return 6;  // scales, to fixed, offsets, tile prep, pipeline, back
     return gb::wavefront_launch_count(n, nbw, o.nb);
 }
 

@@ -7,16 +7,18 @@
 // pass 2 cuts every entry into digits with integer arithmetic on its bit
 // pattern (no FP64 instructions) and writes the bf16 planes, k fastest.
 //
-// Product: one 256-thread block per 64 x 64 tile of C, warps 4 (rows) x 2
-// (columns), each warp 16 x 32 = four m16n8 accumulator tiles per bucket.
+// Product: one 256-thread block per 64 x 32 tile of C, warps 4 (rows) x 2
+// (columns), each warp 16 x 16 = two m16n8 accumulator tiles per level.
 // K advances 32 at a time through a two-stage cp.async pipeline holding all
 // digit planes of the A and B tiles (rows padded to 80 bytes so that the
 // ldmatrix row addresses of a phase fall in distinct banks).  Per k16 step
 // the warp loads the eight A-plane fragments once and, per B plane j, issues
-// mma.sync m16n8k16 bf16 for every A plane i with i + j < kSlices into
-// bucket min(i + j, kExactLevels).
+// mma.sync m16n8k16 bf16 for every A plane i with i + j < kSlices into the
+// accumulator of level i + j.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "dgemm_sliced.cuh"
 
@@ -24,16 +26,16 @@ namespace gb {
 
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 32;
+constexpr int kBM = 64, kBN = 32, kBK = 32;
 constexpr int kRowPad = 40;  // bf16 per staged row (32 used)
 constexpr int kThreads = 256;
 constexpr int kStages = 2;
-constexpr int kBuckets = kExactLevels + 1;
 constexpr size_t kStageElems = (size_t)kSlices * (kBM + kBN) * kRowPad;  // bf16 per stage
 constexpr size_t kProductSmem = kStages * kStageElems * sizeof(uint16_t);
 
 static_assert(kSlices * kDigitBits <= 56, "digits come from the 56-bit fixed-point magnitude");
-static_assert((kExactLevels + 1) * 127 * 127 * kFlushK < (1 << 24), "exact levels must stay below 2^24 units");
+static_assert(kSlices == 8, "the level folding below assumes eight digits");
+static_assert(kSlices * 127 * 127 * kFlushK < (1 << 24), "every level must stay below 2^24 units per flush");
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -180,29 +182,36 @@ __device__ __forceinline__ double scale_by_pow2(double v, int e)
     return v * pow2(e1) * pow2(e2);
 }
 
-// Stage loader: all digit planes of the A rows [m0, m0+64) and B rows
-// [n0, n0+64) for k in [kt, kt+32).
+// Stage loader: all digit planes of the A rows [m0, m0+kBM) and B rows
+// [n0, n0+kBN) for k in [kt, kt+32).
 __device__ __forceinline__ void load_stage(uint16_t *stage, const uint16_t *__restrict__ Ap, size_t a_plane,
                                            int a_kp, const uint16_t *__restrict__ Bp, size_t b_plane, int b_kp,
                                            int m0, int n0, int kt)
 {
-    // per operand kSlices x 64 rows x 4 chunks of 16 bytes
-    constexpr int kChunks = kSlices * 64 * 4;
+    // kSlices planes x rows x 4 chunks of 16 bytes (32 bf16 of k)
+    constexpr int kChunksA = kSlices * kBM * 4, kChunksB = kSlices * kBN * 4;
+    static_assert((kChunksA + kChunksB) % kThreads == 0, "whole chunks per thread");
 #pragma unroll
-    for (int it = 0; it < 2 * kChunks / kThreads; it++) {
+    for (int it = 0; it < (kChunksA + kChunksB) / kThreads; it++) {
         const int c = threadIdx.x + it * kThreads;
-        const int op = c / kChunks;  // 0 = A, 1 = B
-        const int rem = c - op * kChunks;
-        const int s = rem / 256, row = (rem / 4) % 64, part = rem % 4;
-        const uint16_t *g = op == 0 ? Ap + s * a_plane + (size_t)(m0 + row) * a_kp + kt + part * 8
-                                    : Bp + s * b_plane + (size_t)(n0 + row) * b_kp + kt + part * 8;
-        uint16_t *d = stage + ((size_t)(op * kSlices + s) * 64 + row) * kRowPad + part * 8;
+        const bool isA = c < kChunksA;
+        const int rem = isA ? c : c - kChunksA;
+        const int rows = isA ? kBM : kBN;
+        const int s = rem / (rows * 4), row = (rem / 4) % rows, part = rem % 4;
+        const uint16_t *g = isA ? Ap + s * a_plane + (size_t)(m0 + row) * a_kp + kt + part * 8
+                                : Bp + s * b_plane + (size_t)(n0 + row) * b_kp + kt + part * 8;
+        uint16_t *d = isA ? stage + ((size_t)s * kBM + row) * kRowPad + part * 8
+                          : stage + (size_t)kSlices * kBM * kRowPad + ((size_t)s * kBN + row) * kRowPad + part * 8;
         cp_async16(d, g);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// One 64 x 64 tile of C (or of split z's partial product).
+// One kBM x kBN tile of C (or of split z's partial product).  Warps 4 x 2,
+// each 16 x 16 (two m16n8 tiles); level l = i + j of the digit pairs has its
+// own FP32 accumulator, exact over kFlushK values of k, folded into two
+// 64-bit integers: hi = sum_{l<4} L_l 2^(7(3-l)), lo = sum_{l>=4} L_l
+// 2^(7(7-l)), with L_l the level's sum in units of 2^(-7l).
 __global__ void __launch_bounds__(kThreads, 1)
 sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int a_rp, int a_kp,
                const uint16_t *__restrict__ Bp, const int *__restrict__ eb, int b_rp, int b_kp, int m, int n,
@@ -211,29 +220,29 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
 {
     extern __shared__ __align__(16) uint16_t smem[];
     const int tm = blockIdx.y, tn = blockIdx.x;
-    if (lower && tm < tn) return;  // tile wholly above the diagonal
     const int m0 = tm * kBM, n0 = tn * kBN;
+    if (lower && m0 + kBM - 1 < n0) return;  // tile wholly above the diagonal
     const int kbeg = blockIdx.z * ksplit, kend = min(K, kbeg + ksplit);
     const size_t a_plane = (size_t)a_rp * a_kp, b_plane = (size_t)b_rp * b_kp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp & 3, wn = warp >> 2;
 
-    float acc[kBuckets][4][4];
-    long long T[4][4];
+    float acc[kSlices][2][4];
+    long long hi[2][4], lo[2][4];
 #pragma unroll
-    for (int b = 0; b < kBuckets; b++)
+    for (int l = 0; l < kSlices; l++)
 #pragma unroll
-        for (int t = 0; t < 4; t++)
+        for (int t = 0; t < 2; t++)
 #pragma unroll
-            for (int q = 0; q < 4; q++) acc[b][t][q] = 0.f;
+            for (int q = 0; q < 4; q++) acc[l][t][q] = 0.f;
 #pragma unroll
-    for (int t = 0; t < 4; t++)
+    for (int t = 0; t < 2; t++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) T[t][q] = 0;
+        for (int q = 0; q < 4; q++) hi[t][q] = lo[t][q] = 0;
 
-    // ldmatrix lane offsets (elements within a stage's operand block)
+    // ldmatrix lane offsets within a stage's operand block
     const int a_row = wm * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
-    const int b_row = wn * 32 + (lane & 7) + (lane >> 4) * 8, b_k = ((lane >> 3) & 1) * 8;
+    const int b_row = wn * 16 + (lane & 7) + (lane >> 4) * 8, b_k = ((lane >> 3) & 1) * 8;
 
     int stage = 0;
     if (kbeg < kend) load_stage(smem, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0, kbeg);
@@ -247,58 +256,55 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         const uint16_t *As = smem + (size_t)stage * kStageElems;
-        const uint16_t *Bs = As + (size_t)kSlices * 64 * kRowPad;
+        const uint16_t *Bs = As + (size_t)kSlices * kBM * kRowPad;
 #pragma unroll
         for (int ks = 0; ks < kBK / 16; ks++) {
             unsigned af[kSlices][4];
 #pragma unroll
             for (int s = 0; s < kSlices; s++)
                 ldsm_x4(af[s][0], af[s][1], af[s][2], af[s][3],
-                        As + ((size_t)s * 64 + a_row) * kRowPad + ks * 16 + a_k);
+                        As + ((size_t)s * kBM + a_row) * kRowPad + ks * 16 + a_k);
 #pragma unroll
             for (int j = 0; j < kSlices; j++) {
-                unsigned bf[4][2];
+                unsigned bf[2][2];
+                ldsm_x4(bf[0][0], bf[0][1], bf[1][0], bf[1][1],
+                        Bs + ((size_t)j * kBN + b_row) * kRowPad + ks * 16 + b_k);
 #pragma unroll
-                for (int p = 0; p < 2; p++)
-                    ldsm_x4(bf[2 * p][0], bf[2 * p][1], bf[2 * p + 1][0], bf[2 * p + 1][1],
-                            Bs + ((size_t)j * 64 + b_row + p * 16) * kRowPad + ks * 16 + b_k);
+                for (int i = 0; i + j < kSlices; i++)
 #pragma unroll
-                for (int i = 0; i + j < kSlices; i++) {
-                    constexpr int kLast = kBuckets - 1;
-                    const int bucket = (i + j) < kLast ? (i + j) : kLast;
-#pragma unroll
-                    for (int t = 0; t < 4; t++) mma_bf16(acc[bucket][t], af[i], bf[t][0], bf[t][1]);
-                }
+                    for (int t = 0; t < 2; t++) mma_bf16(acc[i + j][t], af[i], bf[t][0], bf[t][1]);
             }
         }
         __syncthreads();  // this stage's buffer is refilled two steps later
         stage ^= 1;
-        // fold the exact levels into the integer accumulators every kFlushK
+        // fold the levels into the integer accumulators every kFlushK
         if ((steps + 1) % (kFlushK / kBK) == 0 || !more) {
 #pragma unroll
-            for (int b = 0; b < kExactLevels; b++)
+            for (int l = 0; l < kSlices; l++)
 #pragma unroll
-                for (int t = 0; t < 4; t++)
+                for (int t = 0; t < 2; t++)
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
-                        // level b holds an integer multiple of 2^(-7b) below 2^24 units
-                        const int iv = __float2int_rn(acc[b][t][q] * (float)(1 << (kDigitBits * b)));
-                        T[t][q] += (long long)iv << (kDigitBits * (kExactLevels - 1 - b));
-                        acc[b][t][q] = 0.f;
+                        // level l holds an integer multiple of 2^(-7l) below 2^24 units
+                        const long long iv = __float2int_rn(acc[l][t][q] * (float)(1u << (kDigitBits * (l & 3))) *
+                                                            (l >= 4 ? 0x1p28f : 1.0f));
+                        if (l < 4) hi[t][q] += iv << (kDigitBits * (3 - l));
+                        else lo[t][q] += iv << (kDigitBits * (7 - l));
+                        acc[l][t][q] = 0.f;
                     }
         }
     }
 
-    // epilogue: value = (T 2^-28 + low) 2^(ea + eb - 14)
+    // epilogue: value = (hi 2^-21 + lo 2^-49) 2^(ea + eb - 14)
     const int g = lane >> 2, tig = lane & 3;
 #pragma unroll
-    for (int t = 0; t < 4; t++)
+    for (int t = 0; t < 2; t++)
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int r = m0 + wm * 16 + g + (q >> 1) * 8;
-            const int c = n0 + wn * 32 + t * 8 + tig * 2 + (q & 1);
+            const int c = n0 + wn * 16 + t * 8 + tig * 2 + (q & 1);
             if (r >= m || c >= n || (lower && r < c)) continue;
-            double v = (double)T[t][q] * 0x1p-28 + (double)acc[kExactLevels][t][q];
+            double v = (double)hi[t][q] * 0x1p-21 + (double)lo[t][q] * 0x1p-49;
             v = scale_by_pow2(v, ea[r] + eb[c] - 2 * kDigitBits);
             if (part) {
                 part[(size_t)blockIdx.z * m * n + (size_t)c * m + r] = v;
@@ -366,7 +372,11 @@ cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, doub
                                           (int)kProductSmem);
     if (ea != cudaSuccess) return ea;
     const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
-    const long long tiles = lower ? (long long)tiles_m * (tiles_m + 1) / 2 : (long long)tiles_m * tiles_n;
+    long long tiles = (long long)tiles_m * tiles_n;
+    if (lower) {  // tiles not wholly above the diagonal
+        tiles = 0;
+        for (int tm = 0; tm < tiles_m; tm++) tiles += std::min(tiles_n, (tm * kBM + kBM - 1) / kBN + 1);
+    }
     const int Kp = A.Kp;
     // split the reduction when the tiles alone cannot fill the device
     int dev = 0, sms = 148;

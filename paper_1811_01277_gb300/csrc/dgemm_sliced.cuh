@@ -10,12 +10,13 @@
 // bf16 holds exactly.  The product of digit planes i (of A) and j (of B) is
 // an exact multiple of 2^(-7(i+j)) and lands in "level" i+j.  Pairs with
 // i+j < kSlices are formed (the rest lie below FP64's resolution of the
-// scaled row/column maxima).  Levels 0..kExactLevels-1 are accumulated
-// exactly: each level's FP32 tensor-core sum over kFlushK consecutive k is an
-// integer multiple of 2^(-7 level) below 2^24 units, so it is exact, and it
-// is folded into a 64-bit integer per output every kFlushK.  The higher
-// levels, whose weight is below 2^-35 of level 0, share one FP32
-// accumulator.  The result is rounded to FP64 once, at the end.
+// scaled row/column maxima).  Every level has its own FP32 tensor-core
+// accumulator; over kFlushK consecutive k its sum is an integer multiple of
+// 2^(-7 level) below 2^24 units (kSlices * 127^2 * kFlushK < 2^24), so it is
+// exact, and it is folded into two 64-bit integers per output every kFlushK.
+// The result is rounded to FP64 once, at the end.  (A shared FP32
+// accumulator for the low levels is not enough: its truncating additions
+// reach 2^-46 of the result on sums of one sign.)
 //
 // Accuracy is that of an FP64 product measured against the scaled maxima:
 // |C - AB| <~ 2^-53 k max_j|a_ij| max_i|b_ij| per entry.  Inputs must be
@@ -32,7 +33,6 @@ namespace gb {
 
 constexpr int kSlices = 8;
 constexpr int kDigitBits = 7;
-constexpr int kExactLevels = 5;
 constexpr int kFlushK = 128;
 
 // How a slice-row matrix reads a column-major FP64 source `src` (leading

@@ -33,4 +33,13 @@ cudaError_t pipeline_d(int n, int b, int nev, const double *hh_v, const double *
                        long long ldz, int nb, int threads, int column_batch, int lead_tiles, void *ws,
                        size_t ws_bytes, long long spin_polls, long long timeout_ns, int hold_group, cudaStream_t st);
 
+// Tensor-core pipeline (real case, nbw in {16, 32, 64}): same schedule,
+// tiles applied in compact WY form on mma.sync bf16 by exact digit slicing,
+// Z in per-column 64-bit fixed point for the call (converted in place).
+bool pipeline_tc_supported(int b);
+size_t pipeline_tc_workspace_bytes(int n, int b, int nev);
+cudaError_t pipeline_tc_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
+                          int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
+                          int hold_group, cudaStream_t st);
+
 }  // namespace gb

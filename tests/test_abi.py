@@ -36,6 +36,8 @@ def test_every_declared_symbol_is_exported(lib):
     for nm in names:
         assert hasattr(lib, nm), nm
     assert set(names) == set(gb.EXPORTS)
+    # and every export has its binding in the package namespace
+    assert [nm for nm in gb.EXPORTS if not hasattr(gb, nm)] == []
 
 
 @pytest.mark.parametrize("n,b", [(1, 1), (2, 1), (3, 2), (100, 7), (1024, 32), (16384, 64), (1000, 64)])

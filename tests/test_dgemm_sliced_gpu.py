@@ -39,15 +39,28 @@ def ws(nbytes):
     return torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda"), nbytes
 
 
+def ref_hp(opA, opB, alpha, beta, C0):
+    """alpha opA opB + beta C0 in extended precision (np.longdouble: 64- or
+    113-bit significand), so that the reference's own rounding does not
+    enter the comparison."""
+    L = np.longdouble
+    return L(alpha) * (opA.astype(L) @ opB.astype(L)) + L(beta) * C0.astype(L)
+
+
 def bound(opA, opB, alpha, beta, C0):
-    """|C - ref| for the sliced product: k 2^-53 times the row maxima of
-    op(A) and column maxima of op(B) (the scaling the digits are cut
-    against), with a factor 4, plus the final roundings."""
+    """|C - exact| for the sliced product: k 2^-53 times the row maxima of
+    op(A) and the column maxima of op(B) (the scales the digits are cut
+    against), with a factor 4, plus the final FP64 roundings of the result
+    and of the beta C term."""
     k = opA.shape[1]
     amax = np.abs(opA).max(axis=1, initial=0.0)[:, None]
     bmax = np.abs(opB).max(axis=0, initial=0.0)[None, :]
     prod = np.abs(alpha) * (np.abs(opA) @ np.abs(opB))
     return 4 * (k + 2) * U * abs(alpha) * amax * bmax + 4 * U * (prod + abs(beta) * np.abs(C0)) + 1e-300
+
+
+def err(got, ref):
+    return np.abs(got.astype(np.longdouble) - ref).astype(np.float64)
 
 
 SHAPES = [(1, 1, 1), (37, 29, 13), (64, 64, 64), (65, 63, 200), (200, 77, 131), (513, 64, 1000),
@@ -70,9 +83,9 @@ def test_dgemm_sliced(gb, m, n, k, ta, tb):
     gb.gb_dgemm_sliced(ta, tb, m, n, k, alpha, Ad, lda, Bd, ldb, beta, Cd, ldc, w, wsb, torch.cuda.current_stream())
     opA = A.T if ta == "T" else A
     opB = B.T if tb == "T" else B
-    ref = alpha * (opA @ opB) + beta * C0
+    ref = ref_hp(opA, opB, alpha, beta, C0)
     got = host_cm(Cd, m, n)
-    assert np.all(np.abs(got - ref) <= bound(opA, opB, alpha, beta, C0))
+    assert np.all(err(got, ref) <= bound(opA, opB, alpha, beta, C0))
     assert np.all(np.isnan(Cd.cpu().numpy()[:n, m:ldc]))   # padding rows untouched
 
 
@@ -106,8 +119,8 @@ def test_sliced_rows_of_different_magnitude(gb):
     Cd, ldc = dev_cm(np.zeros((m, n)))
     w, wsb = ws(gb.gb_dgemm_sliced_workspace_bytes(m, n, k))
     gb.gb_dgemm_sliced("N", "N", m, n, k, 1.0, Ad, lda, Bd, ldb, 0.0, Cd, ldc, w, wsb, torch.cuda.current_stream())
-    ref = A @ B
-    assert np.all(np.abs(host_cm(Cd, m, n) - ref) <= bound(A, B, 1.0, 0.0, np.zeros((m, n))))
+    ref = ref_hp(A, B, 1.0, 0.0, np.zeros((m, n)))
+    assert np.all(err(host_cm(Cd, m, n), ref) <= bound(A, B, 1.0, 0.0, np.zeros((m, n))))
 
 
 @pytest.mark.parametrize("side", "LR")
@@ -126,8 +139,8 @@ def test_dsymm_sliced_reads_lower_only(gb, side, m, n):
     w, wsb = ws(gb.gb_dsymm_sliced_workspace_bytes(side, m, n))
     gb.gb_dsymm_sliced(side, m, n, -0.5, Sd, lds, Bd, ldb, 2.0, Cd, ldc, w, wsb, torch.cuda.current_stream())
     opA, opB = (S, B) if side == "L" else (B, S)
-    ref = -0.5 * (opA @ opB) + 2.0 * C0
-    assert np.all(np.abs(host_cm(Cd, m, n) - ref) <= bound(opA, opB, -0.5, 2.0, C0))
+    ref = ref_hp(opA, opB, -0.5, 2.0, C0)
+    assert np.all(err(host_cm(Cd, m, n), ref) <= bound(opA, opB, -0.5, 2.0, C0))
 
 
 @pytest.mark.parametrize("n,k", [(1, 1), (50, 3), (64, 64), (129, 64), (300, 200), (1000, 64)])
@@ -144,9 +157,9 @@ def test_dsyr2k_and_dsyrk_sliced_lower_triangle(gb, n, k):
     gb.gb_dsyr2k_sliced(n, k, -1.0, Ad, lda, Bd, ldb, 1.0, Cd, ldc, w, wsb, torch.cuda.current_stream())
     got = host_cm(Cd, n, n)
     AB, BA = np.hstack([A, B]), np.hstack([B, A])
-    ref = C0 - AB @ BA.T
+    ref = ref_hp(AB, BA.T, -1.0, 1.0, C0)
     low = np.tril(np.ones((n, n), dtype=bool))
-    assert np.all((np.abs(got - ref) <= bound(AB, BA.T, -1.0, 1.0, C0))[low])
+    assert np.all((err(got, ref) <= bound(AB, BA.T, -1.0, 1.0, C0))[low])
     assert np.all(got[~low] == sentinel)
     A2 = g.uniform(-1, 1, (k, n))
     A2d, lda2 = dev_cm(A2, k + 3)
@@ -154,8 +167,8 @@ def test_dsyr2k_and_dsyrk_sliced_lower_triangle(gb, n, k):
     w2, wsb2 = ws(gb.gb_dsyrk_sliced_workspace_bytes(n, k))
     gb.gb_dsyrk_sliced(n, k, 1.0, A2d, lda2, 0.0, Cd2, ldc2, w2, wsb2, torch.cuda.current_stream())
     got2 = host_cm(Cd2, n, n)
-    ref2 = A2.T @ A2
-    assert np.all((np.abs(got2 - ref2) <= bound(A2.T, A2, 1.0, 0.0, np.zeros((n, n))))[low])
+    ref2 = ref_hp(A2.T, A2, 1.0, 0.0, np.zeros((n, n)))
+    assert np.all((err(got2, ref2) <= bound(A2.T, A2, 1.0, 0.0, np.zeros((n, n))))[low])
     assert np.all(got2[~low] == sentinel)
 
 
@@ -165,3 +178,24 @@ def test_sliced_argument_errors(gb):
     assert f("N", "N", 4, 1, 1, 1.0, 256, 3, 256, 1, 0.0, 256, 4, 256, 1 << 30, None, check=False) == -8
     assert f("N", "N", 4, 1, 1, 1.0, 256, 4, 256, 1, 0.0, 256, 4, 128, 1 << 30, None, check=False) == -14
     assert f("N", "N", 4, 1, 1, 1.0, 256, 4, 256, 1, 0.0, 256, 4, 256, 16, None, check=False) == -15
+
+
+@pytest.mark.parametrize("k", [128, 1024, 16384])
+def test_sliced_syrk_long_sums_of_one_sign(gb, k):
+    """A^T A with long k: the diagonal sums k squares (all of one sign), the
+    hardest case for exact level accumulation."""
+    n = 256
+    g = np.random.default_rng(k)
+    A = g.uniform(-0.5, 0.5, (k, n))
+    Ad, lda = dev_cm(A)
+    Cd, ldc = dev_cm(np.zeros((n, n)))
+    w, wsb = ws(gb.gb_dsyrk_sliced_workspace_bytes(n, k))
+    gb.gb_dsyrk_sliced(n, k, 1.0, Ad, lda, 0.0, Cd, ldc, w, wsb, torch.cuda.current_stream())
+    got = host_cm(Cd, n, n)
+    ref = ref_hp(A.T, A, 1.0, 0.0, np.zeros((n, n)))
+    low = np.tril(np.ones((n, n), dtype=bool))
+    e = err(got, ref)
+    b = bound(A.T, A, 1.0, 0.0, np.zeros((n, n)))
+    print(f"k={k} diag max err {np.diag(e).max():.3e} (bound {np.diag(b).min():.3e}), "
+          f"offdiag max err {e[np.tril(low, -1)].max() if n > 1 else 0:.3e}")
+    assert np.all((e <= b)[low])

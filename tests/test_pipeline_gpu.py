@@ -42,10 +42,11 @@ def run(gb, n, b, hv, ht, Z, opts):
 
 PIPE = [{"variant": 2, "sweeps_per_tile": 8, "cols_per_block": 64},
         {"variant": 2, "sweeps_per_tile": 16, "cols_per_block": 128},
-        {"variant": 2, "sweeps_per_tile": 16, "cols_per_block": 64}]
+        {"variant": 2, "sweeps_per_tile": 16, "cols_per_block": 64},
+        {"variant": 3}]
 
 
-@pytest.mark.parametrize("opts", PIPE, ids=["nb8t64", "nb16t128", "nb16t64"])
+@pytest.mark.parametrize("opts", PIPE, ids=["nb8t64", "nb16t128", "nb16t64", "tensor_core"])
 @pytest.mark.parametrize("n,b,nev", [(2, 8, 3), (9, 8, 1), (100, 8, 65), (257, 16, 129), (300, 32, 200),
                                      (129, 64, 130), (640, 64, 257), (1000, 64, 64), (65, 64, 31)])
 def test_pipeline_parity(gb, n, b, nev, opts):
