@@ -50,6 +50,7 @@ def algorithmic_flops(n, nev, cplx=False):
 KERNEL_SOURCES = {
     "pipeline_d": ["trans_ev_pipeline.cu", "tile_apply.cuh", "layout.cuh"],
     "wavefront_tile_d": ["trans_ev_wavefront.cu", "tile_apply.cuh", "layout.cuh"],
+    "pipeline_tc": ["trans_ev_tc.cu", "mma_bf16.cuh", "layout.cuh"],
 }
 
 
@@ -272,7 +273,9 @@ def run_ours(args, wl):
                 "cols_per_block": best.cols_per_block}
         tuned = {"level": args.autotune, "chosen": opts, "trials": trials}
     launches_per_call = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
-    variant_name = "pipeline" if launches_per_call == 1 else "wavefront"
+    tc = (opts is not None and (opts.get("variant") if isinstance(opts, dict) else opts.variant) == 3
+          and launches_per_call == 6)
+    variant_name = "pipeline_tc" if tc else ("pipeline" if launches_per_call == 1 else "wavefront")
     wsb = gb.gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts)
     ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -302,7 +305,7 @@ def run_ours(args, wl):
     F = algorithmic_flops(n, nev)
     achieved = F / (ms_per_step / 1e3) / 1e12
     launches = launches_per_call
-    kernel = "pipeline_d" if variant_name == "pipeline" else "wavefront_tile_d"
+    kernel = {"pipeline": "pipeline_d", "pipeline_tc": "pipeline_tc"}.get(variant_name, "wavefront_tile_d")
     sha = kernel_sources_sha1(kernel)
     # the committed ncu figure is for the default configuration only
     traffic = profile_traffic(kernel, args.workload, variant_name, sha) if opts is None else None

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "dgemm_sliced.cuh"
+#include "mma_bf16.cuh"
 
 namespace gb {
 
@@ -34,8 +35,9 @@ constexpr size_t kStageElems = (size_t)kSlices * (kBM + kBN) * kRowPad;  // bf16
 constexpr size_t kProductSmem = kStages * kStageElems * sizeof(uint16_t);
 
 static_assert(kSlices * kDigitBits <= 56, "digits come from the 56-bit fixed-point magnitude");
-static_assert(kSlices == 8, "the level folding below assumes eight digits");
+static_assert(kSlices == 8 && kLevels == 9, "the level folding below assumes eight digits, levels 0..8");
 static_assert(kSlices * 127 * 127 * kFlushK < (1 << 24), "every level must stay below 2^24 units per flush");
+constexpr int kMaxSplitK = 65536;  // keeps lo below 2^61: 512 flushes of at most 2^52
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -101,12 +103,6 @@ __global__ void __launch_bounds__(256) slice_rowmax(int view, const double *__re
     }
 }
 
-// Row exponent e with max|row| < 2^e (0 for an all-zero row).
-__device__ __forceinline__ int row_exponent(unsigned long long maxbits)
-{
-    const int ex = (int)(maxbits >> 52);
-    return ex ? ex - 1022 : 0;
-}
 
 __global__ void __launch_bounds__(256) slice_digits(int view, const double *__restrict__ src, long long ld, int R,
                                                      int K, int Rp, int Kp, const unsigned long long *__restrict__ rmax,
@@ -120,66 +116,17 @@ __global__ void __launch_bounds__(256) slice_digits(int view, const double *__re
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int r = r0 + i, k = k0 + threadIdx.x;
         if (r >= Rp || k >= Kp) continue;
-        const int er = r < R ? row_exponent(rmax[r]) : 0;
+        const int er = r < R ? exponent_above(rmax[r]) : 0;
         if (blockIdx.x == 0 && threadIdx.x == 0) e_out[r] = er;
-        const unsigned long long u = (unsigned long long)__double_as_longlong(t[i][threadIdx.x]);
-        const int ex = (int)((u >> 52) & 0x7ff);
-        // Y = floor(|x| 2^(56 - er)): the 56-bit fixed-point magnitude
-        unsigned long long Y = 0;
-        if (ex != 0) {
-            const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
-            const int sh = ex - 1075 - er + 56;
-            Y = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
-        }
-        const bool neg = (u >> 63) != 0;
+        const double x = t[i][threadIdx.x];
+        const unsigned long long Y = fixed56(x, er);
+        const bool neg = x < 0.0;
 #pragma unroll
         for (int s = 0; s < kSlices; s++) {
-            const int d = (int)((Y >> (kDigitBits * (kSlices - 1 - s))) & 127u);
-            // bf16 of +-d 2^(-7 s): exact (d has at most 7 significant bits)
-            uint16_t h = 0;
-            if (d) {
-                const int p = 31 - __clz(d);                  // d = 1.f x 2^p
-                const unsigned frac = ((unsigned)d << (7 - p)) & 0x7fu;
-                const unsigned expo = (unsigned)(127 + p - kDigitBits * s);
-                h = (uint16_t)((neg ? 0x8000u : 0u) | (expo << 7) | frac);
-            }
+            const uint16_t h = bf16_digit((int)((Y >> (kDigitBits * (kSlices - 1 - s))) & 127u), s, neg);
             planes[s * plane + (size_t)r * Kp + k] = h;
         }
     }
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, const void *p)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
-{
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ double pow2(int e)  // 2^e for -1022 <= e <= 1023
-{
-    return __longlong_as_double((long long)(e + 1023) << 52);
-}
-
-// 2^e for any e the products can produce, as two factors
-__device__ __forceinline__ double scale_by_pow2(double v, int e)
-{
-    const int e1 = e / 2, e2 = e - e1;
-    return v * pow2(e1) * pow2(e2);
 }
 
 // Stage loader: all digit planes of the A rows [m0, m0+kBM) and B rows
@@ -208,10 +155,11 @@ __device__ __forceinline__ void load_stage(uint16_t *stage, const uint16_t *__re
 }
 
 // One kBM x kBN tile of C (or of split z's partial product).  Warps 4 x 2,
-// each 16 x 16 (two m16n8 tiles); level l = i + j of the digit pairs has its
-// own FP32 accumulator, exact over kFlushK values of k, folded into two
-// 64-bit integers: hi = sum_{l<4} L_l 2^(7(3-l)), lo = sum_{l>=4} L_l
-// 2^(7(7-l)), with L_l the level's sum in units of 2^(-7l).
+// each 16 x 16 (two m16n8 tiles); level l = i + j <= kLevels - 1 of the
+// digit pairs has its own FP32 accumulator, exact over kFlushK values of k,
+// folded into two 64-bit integers: hi = sum_{l<4} L_l 2^(7(3-l)),
+// lo = sum_{l>=4} L_l 2^(7(8-l)), with L_l the level's sum in units of
+// 2^(-7l).
 __global__ void __launch_bounds__(kThreads, 1)
 sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int a_rp, int a_kp,
                const uint16_t *__restrict__ Bp, const int *__restrict__ eb, int b_rp, int b_kp, int m, int n,
@@ -227,10 +175,10 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp & 3, wn = warp >> 2;
 
-    float acc[kSlices][2][4];
+    float acc[kLevels][2][4];
     long long hi[2][4], lo[2][4];
 #pragma unroll
-    for (int l = 0; l < kSlices; l++)
+    for (int l = 0; l < kLevels; l++)
 #pragma unroll
         for (int t = 0; t < 2; t++)
 #pragma unroll
@@ -270,9 +218,10 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
                 ldsm_x4(bf[0][0], bf[0][1], bf[1][0], bf[1][1],
                         Bs + ((size_t)j * kBN + b_row) * kRowPad + ks * 16 + b_k);
 #pragma unroll
-                for (int i = 0; i + j < kSlices; i++)
+                for (int i = 0; i < kSlices; i++)
+                    if (i + j < kLevels)
 #pragma unroll
-                    for (int t = 0; t < 2; t++) mma_bf16(acc[i + j][t], af[i], bf[t][0], bf[t][1]);
+                        for (int t = 0; t < 2; t++) mma_bf16(acc[i + j][t], af[i], bf[t][0], bf[t][1]);
             }
         }
         __syncthreads();  // this stage's buffer is refilled two steps later
@@ -280,22 +229,22 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
         // fold the levels into the integer accumulators every kFlushK
         if ((steps + 1) % (kFlushK / kBK) == 0 || !more) {
 #pragma unroll
-            for (int l = 0; l < kSlices; l++)
+            for (int l = 0; l < kLevels; l++)
 #pragma unroll
                 for (int t = 0; t < 2; t++)
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         // level l holds an integer multiple of 2^(-7l) below 2^24 units
-                        const long long iv = __float2int_rn(acc[l][t][q] * (float)(1u << (kDigitBits * (l & 3))) *
-                                                            (l >= 4 ? 0x1p28f : 1.0f));
+                        const float unit = __int_as_float((127 + kDigitBits * l) << 23);  // 2^(7l)
+                        const long long iv = __float2int_rn(acc[l][t][q] * unit);
                         if (l < 4) hi[t][q] += iv << (kDigitBits * (3 - l));
-                        else lo[t][q] += iv << (kDigitBits * (7 - l));
+                        else lo[t][q] += iv << (kDigitBits * (kLevels - 1 - l));
                         acc[l][t][q] = 0.f;
                     }
         }
     }
 
-    // epilogue: value = (hi 2^-21 + lo 2^-49) 2^(ea + eb - 14)
+    // epilogue: value = (hi 2^-21 + lo 2^-56) 2^(ea + eb - 14)
     const int g = lane >> 2, tig = lane & 3;
 #pragma unroll
     for (int t = 0; t < 2; t++)
@@ -304,7 +253,7 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
             const int r = m0 + wm * 16 + g + (q >> 1) * 8;
             const int c = n0 + wn * 16 + t * 8 + tig * 2 + (q & 1);
             if (r >= m || c >= n || (lower && r < c)) continue;
-            double v = (double)hi[t][q] * 0x1p-21 + (double)lo[t][q] * 0x1p-49;
+            double v = (double)hi[t][q] * 0x1p-21 + (double)lo[t][q] * 0x1p-56;
             v = scale_by_pow2(v, ea[r] + eb[c] - 2 * kDigitBits);
             if (part) {
                 part[(size_t)blockIdx.z * m * n + (size_t)c * m + r] = v;
@@ -388,6 +337,10 @@ cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, doub
         const int max_by_k = Kp / (4 * kFlushK);  // keep at least 4 flush chunks per split
         if (splits > max_by_k) splits = max_by_k > 1 ? max_by_k : 1;
         while (splits > 1 && (size_t)splits * m * n > work_elems) splits--;
+    }
+    if (splits < (Kp + kMaxSplitK - 1) / kMaxSplitK) {  // very long sums: split so every part stays exact
+        splits = (Kp + kMaxSplitK - 1) / kMaxSplitK;
+        if (!work || (size_t)splits * m * n > work_elems) return cudaErrorInvalidValue;
     }
     int ksplit = Kp;
     if (splits > 1) {

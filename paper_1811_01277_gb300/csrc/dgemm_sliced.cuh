@@ -9,8 +9,9 @@
 // the entry's sign).  Digit t is stored as the bf16 value d * 2^(-7t), which
 // bf16 holds exactly.  The product of digit planes i (of A) and j (of B) is
 // an exact multiple of 2^(-7(i+j)) and lands in "level" i+j.  Pairs with
-// i+j < kSlices are formed (the rest lie below FP64's resolution of the
-// scaled row/column maxima).  Every level has its own FP32 tensor-core
+// i+j <= 8 are formed; the rest lie 2^-62 below the scaled row/column
+// maxima, and digits are cut from the magnitude rounded to nearest, so the
+// errors stay unbiased and grow like sqrt(k) even in sums of one sign.  Every level has its own FP32 tensor-core
 // accumulator; over kFlushK consecutive k its sum is an integer multiple of
 // 2^(-7 level) below 2^24 units (kSlices * 127^2 * kFlushK < 2^24), so it is
 // exact, and it is folded into two 64-bit integers per output every kFlushK.
@@ -32,6 +33,7 @@
 namespace gb {
 
 constexpr int kSlices = 8;
+constexpr int kLevels = 9;  // digit pairs i + j <= 8 are formed
 constexpr int kDigitBits = 7;
 constexpr int kFlushK = 128;
 

@@ -63,8 +63,10 @@ __device__ __forceinline__ int exponent_above(unsigned long long maxbits)
     return ex ? ex - 1022 : 0;
 }
 
-// Y = floor(|x| 2^(56 - e)) for |x| < 2^e: the 56-bit fixed-point magnitude
-// whose 7-bit groups are the digits (subnormals read as zero).
+// Y = round(|x| 2^(56 - e)) for |x| < 2^e, at most 2^56 - 1: the 56-bit
+// fixed-point magnitude whose 7-bit groups are the digits (subnormals read
+// as zero).  Rounding to nearest keeps the representation error unbiased, so
+// that it grows like sqrt(k) and not like k in sums of one sign.
 __device__ __forceinline__ unsigned long long fixed56(double x, int e)
 {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
@@ -72,7 +74,11 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int e)
     if (ex == 0) return 0ull;
     const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
     const int sh = ex - 1075 - e + 56;
-    return sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ull);
+    unsigned long long Y;
+    if (sh >= 0) Y = M << sh;
+    else if (sh > -54) Y = (M + (1ull << (-sh - 1))) >> -sh;
+    else Y = 0ull;
+    return Y < (1ull << 56) ? Y : (1ull << 56) - 1;
 }
 
 // v * 2^e for -1022 <= e <= 1023, and for wider e as two factors

@@ -41,8 +41,9 @@ constexpr int kNB = 16;      // sweeps per tile
 constexpr int kCols = 64;    // eigenvector columns per work item
 constexpr int kThreads = 256;
 constexpr int kDigits = 8;
+constexpr int kLevels = 9;  // digit pairs i + j <= 8
 constexpr int kColumnBatchTc = 16;
-constexpr int kFlushBound = kDigits * 127 * 127;  // per k value of one level
+constexpr int kFlushBound = kDigits * 127 * 127;  // per k value of one level (at most 8 pairs)
 
 // window rows of a tile, padded to a multiple of 16 (the mma k step)
 template <int B>
@@ -301,18 +302,23 @@ __global__ void __launch_bounds__(128) tc_tile_prep(int n, const double *__restr
 
 // ---- the main kernel ------------------------------------------------------
 
-// Digits of a fixed-point value with |x| < 2^61: bits 60..5 in 7-bit groups.
+// Digits of a fixed-point value with |x| < 2^61: the magnitude rounded to
+// bit 5, then bits 60..5 in 7-bit groups (rounding keeps the error
+// unbiased).
 __device__ __forceinline__ void fixed_digits(long long x, uint16_t (&h)[kDigits])
 {
     const bool neg = x < 0;
     const unsigned long long mag = neg ? (unsigned long long)(-x) : (unsigned long long)x;
+    unsigned long long Y = (mag + 16) >> 5;
+    Y = Y < (1ull << 56) ? Y : (1ull << 56) - 1;
 #pragma unroll
-    for (int s = 0; s < kDigits; s++) h[s] = bf16_digit((int)((mag >> (54 - 7 * s)) & 127u), s, neg);
+    for (int s = 0; s < kDigits; s++) h[s] = bf16_digit((int)((Y >> (49 - 7 * s)) & 127u), s, neg);
 }
 
-// Folds eight exact level accumulators (level l in units of 2^(-7l)) into
-// hi = sum_{l<4} L_l 2^(7(3-l)) and lo = sum_{l>=4} L_l 2^(7(7-l)).
-__device__ __forceinline__ void fold_levels(const float (&acc)[kDigits][4], long long (&hi)[4], long long (&lo)[4])
+// Folds the exact level accumulators (level l in units of 2^(-7l)) into
+// hi = sum_{l<4} L_l 2^(7(3-l)) and lo = sum_{l>=4} L_l 2^(7(8-l)); the
+// sum in level-0 units is hi 2^-21 + lo 2^-56.
+__device__ __forceinline__ void fold_levels(const float (&acc)[kLevels][4], long long (&hi)[4], long long (&lo)[4])
 {
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -320,13 +326,12 @@ __device__ __forceinline__ void fold_levels(const float (&acc)[kDigits][4], long
         lo[q] = 0;
     }
 #pragma unroll
-    for (int l = 0; l < kDigits; l++)
+    for (int l = 0; l < kLevels; l++)
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const long long iv =
-                __float2int_rn(acc[l][q] * (float)(1u << (7 * (l & 3))) * (l >= 4 ? 0x1p28f : 1.0f));
+            const long long iv = __float2int_rn(acc[l][q] * __int_as_float((127 + 7 * l) << 23));
             if (l < 4) hi[q] += iv << (7 * (3 - l));
-            else lo[q] += iv << (7 * (7 - l));
+            else lo[q] += iv << (7 * (8 - l));
         }
 }
 
@@ -452,9 +457,9 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
         __syncthreads();
         // ---- W = V^T Z_win (16 x 64, k = LP): warp w owns columns 8w..8w+7
         {
-            float acc[kDigits][4];
+            float acc[kLevels][4];
 #pragma unroll
-            for (int l = 0; l < kDigits; l++)
+            for (int l = 0; l < kLevels; l++)
 #pragma unroll
                 for (int q = 0; q < 4; q++) acc[l][q] = 0.f;
             const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
@@ -471,18 +476,19 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                     unsigned b0, b1;
                     ldsm_x2(b0, b1, ZP + ((size_t)jd * kCols + b_row) * VROW + ks * 16 + b_k);
 #pragma unroll
-                    for (int i = 0; i + jd < kDigits; i++) mma_bf16(acc[i + jd], af[i], b0, b1);
+                    for (int i = 0; i < kDigits; i++)
+                        if (i + jd < kLevels) mma_bf16(acc[i + jd], af[i], b0, b1);
                 }
             }
             long long hi[4], lo[4];
             fold_levels(acc, hi, lo);
-            // W in the column's fixed point: Wi = S 2^(eV + 47), S = hi 2^-21 + lo 2^-49
+            // W in the column's fixed point: Wi = S 2^(eV + 47), S = hi 2^-21 + lo 2^-56
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int qr = gq + (q >> 1) * 8;          // reflector (row of W)
                 const int cc = warp * 8 + tig * 2 + (q & 1);
                 const int ev = eV[qr];
-                const long long wi = shift_ll(hi[q], ev + 26) + shift_ll(lo[q], ev - 2);
+                const long long wi = shift_ll(hi[q], ev + 26) + shift_ll(lo[q], ev - 9);
                 uint16_t h[kDigits];
                 fixed_digits(wi, h);
 #pragma unroll
@@ -500,9 +506,9 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
             const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
 #pragma unroll 1
             for (int mt = 0; mt < LP / 16; mt++) {
-                float acc[kDigits][4];
+                float acc[kLevels][4];
 #pragma unroll
-                for (int l = 0; l < kDigits; l++)
+                for (int l = 0; l < kLevels; l++)
 #pragma unroll
                     for (int q = 0; q < 4; q++) acc[l][q] = 0.f;
                 unsigned au[kDigits][4];
@@ -513,7 +519,8 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
 #pragma unroll
                 for (int jd = 0; jd < kDigits; jd++)
 #pragma unroll
-                    for (int i = 0; i + jd < kDigits; i++) mma_bf16(acc[i + jd], au[i], bw[jd][0], bw[jd][1]);
+                    for (int i = 0; i < kDigits; i++)
+                        if (i + jd < kLevels) mma_bf16(acc[i + jd], au[i], bw[jd][0], bw[jd][1]);
                 long long hi[4], lo[4];
                 fold_levels(acc, hi, lo);
 #pragma unroll
@@ -522,7 +529,7 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                     const int cc = warp * 8 + tig * 2 + (q & 1);
                     if (j < L) {
                         const int eu = eU[j];
-                        Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 26) + shift_ll(lo[q], eu - 2);
+                        Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 26) + shift_ll(lo[q], eu - 9);
                     }
                 }
             }
