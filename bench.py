@@ -614,7 +614,8 @@ def run_stage_gemm(args):
         ("syrk 4096 k=16384 (Newton-Schulz Z^T Z)", 1.0 * nev * nev * n,
          lambda: gb.gb_dsyrk(nev, n, 1.0, Zt, n, 0.0, G, nev, st),
          lambda: gb.gb_dsyrk_sliced(nev, n, 1.0, Zt, n, 0.0, G2, nev, sws, swb, st),
-         lambda: torch.mm(Zt, Zt.T, out=G), (lambda: G.tril(), lambda: G2.tril())),
+         # the lower triangle of the column-major result is the upper one of the row-major view
+         lambda: torch.mm(Zt, Zt.T, out=G), (lambda: G.triu(), lambda: G2.triu())),
         ("symm_R 16384 x 4096 (Newton-Schulz Z M)", 2.0 * n * nev * nev,
          lambda: gb.gb_dsymm("R", n, nev, 1.0, G2, nev, Zt, n, 0.0, Zo, n, ws, wsb, st),
          lambda: gb.gb_dsymm_sliced("R", n, nev, 1.0, G2, nev, Zt, n, 0.0, Zs, n, sws, swb, st),

@@ -50,24 +50,24 @@ template <int B>
 struct Win {
     static constexpr int L = B + kNB - 1;
     static constexpr int LP = (L + 15) / 16 * 16;
-    static constexpr int VROW = LP + 8;  // staged V^T / Z plane row (bf16): 16-byte rows, distinct banks
-    static constexpr int QROW = kNB + 8; // staged U / W plane row (bf16)
-    static constexpr int ZROW = LP + 1;  // window column stride (int64)
-    // tile record in global memory (unpadded rows), 256-byte multiple
+    // window column stride (int64): 4 mod 16, so that the 64-bit updates of
+    // a warp (rows g, columns 2t) take the minimum two wavefronts, and even
+    // for the 16-byte fragment loads
+    static constexpr int ZROW = (LP + 4) / 16 * 16 + 4 + ((LP + 4) % 16 > 4 ? 16 : 0);
+    // tile record in global memory, 256-byte multiple: V^T planes [8][16][LP],
+    // U planes [8][LP][16] (bf16), exponents eV[16], eU[LP]
     static constexpr size_t VT_BYTES = (size_t)kDigits * kNB * LP * 2;
     static constexpr size_t U_BYTES = (size_t)kDigits * LP * kNB * 2;
     static constexpr size_t E_BYTES = (size_t)(kNB + LP) * 4;
     static constexpr size_t REC = (VT_BYTES + U_BYTES + E_BYTES + 255) / 256 * 256;
-    // shared memory of the main kernel
-    static constexpr size_t S_VT = (size_t)kDigits * kNB * VROW * 2;
-    static constexpr size_t S_U = (size_t)kDigits * LP * QROW * 2;
-    static constexpr size_t S_E = (size_t)(kNB + LP) * 4;
-    static constexpr size_t S_ZP = (size_t)kDigits * kCols * VROW * 2;
-    static constexpr size_t S_WP = (size_t)kDigits * kCols * QROW * 2;
+    // shared memory of the main kernel: the record (same layout, 16-byte
+    // chunks XOR-swizzled), W planes [8][64][16], window [64][ZROW] int64
+    static constexpr size_t S_WP = (size_t)kDigits * kCols * kNB * 2;
     static constexpr size_t S_Z = (size_t)kCols * ZROW * 8;
     static constexpr size_t S_EC = (size_t)kCols * 4;
-    static constexpr size_t SMEM = S_VT + S_U + S_E + S_ZP + S_WP + S_Z + S_EC;
+    static constexpr size_t SMEM = REC + S_WP + S_Z + S_EC;
     static_assert(kFlushBound * LP < (1 << 24), "level sums of one tile product must stay exact in FP32");
+    static_assert((LP / 8) % 2 == 0, "V^T rows hold an even number of 16-byte chunks");
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -302,22 +302,45 @@ __global__ void __launch_bounds__(128) tc_tile_prep(int n, const double *__restr
 
 // ---- the main kernel ------------------------------------------------------
 
-// Digits of a fixed-point value with |x| < 2^61: the magnitude rounded to
-// bit 5, then bits 60..5 in 7-bit groups (rounding keeps the error
-// unbiased).
-__device__ __forceinline__ void fixed_digits(long long x, uint16_t (&h)[kDigits])
+// Exact bf16 of a digit: with eb = the exponent bits of 2^(23 - 7s),
+// float(eb | d) - float(eb) = d 2^(-7s) exactly (Sterbenz), and its upper 16
+// bits are the bf16 (d has at most 7 significant bits).
+template <int S>
+__device__ __forceinline__ float digit_f(unsigned d)
 {
-    const bool neg = x < 0;
-    const unsigned long long mag = neg ? (unsigned long long)(-x) : (unsigned long long)x;
-    unsigned long long Y = (mag + 16) >> 5;
-    Y = Y < (1ull << 56) ? Y : (1ull << 56) - 1;
-#pragma unroll
-    for (int s = 0; s < kDigits; s++) h[s] = bf16_digit((int)((Y >> (49 - 7 * s)) & 127u), s, neg);
+    constexpr unsigned eb = (unsigned)(150 - 7 * S) << 23;
+    return __uint_as_float(eb | d) - __uint_as_float(eb);
 }
 
-// Folds the exact level accumulators (level l in units of 2^(-7l)) into
-// hi = sum_{l<4} L_l 2^(7(3-l)) and lo = sum_{l>=4} L_l 2^(7(8-l)); the
-// sum in level-0 units is hi 2^-21 + lo 2^-56.
+// the two bf16 halves of a and b packed into one register (a low, b high),
+// with the sign words sa, sb (0 or 0x80000000) applied
+__device__ __forceinline__ unsigned pack_bf16(float a, float b, unsigned sa, unsigned sb)
+{
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632) ^ ((sa >> 16) | sb);
+}
+
+// 56-bit rounded magnitude of a fixed-point value |x| < 2^61 (bits 60..5)
+// and its sign word
+__device__ __forceinline__ unsigned long long round56(long long x, unsigned &sign)
+{
+    sign = x < 0 ? 0x80000000u : 0u;
+    const unsigned long long mag = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+    const unsigned long long Y = (mag + 16) >> 5;
+    return Y < (1ull << 56) ? Y : (1ull << 56) - 1;
+}
+
+// digit s (0 = most significant) of a 56-bit magnitude
+__device__ __forceinline__ unsigned digit_of(unsigned long long Y, int s)
+{
+    return (unsigned)(Y >> (49 - 7 * s)) & 127u;
+}
+
+
+// Folds level accumulators (level l in units of 2^(-7l)) into
+// hi = sum_{l<4} L_l 2^(7(3-l)) and lo = sum_{l>=4} L_l 2^(7(8-l)), so the sum
+// in level-0 units is hi 2^-21 + lo 2^-56.  Large: level sums up to 2^24
+// (F2I); otherwise below 2^22 (exact by adding 1.5 2^23 in FP32).
+template <bool Large>
 __device__ __forceinline__ void fold_levels(const float (&acc)[kLevels][4], long long (&hi)[4], long long (&lo)[4])
 {
 #pragma unroll
@@ -329,29 +352,35 @@ __device__ __forceinline__ void fold_levels(const float (&acc)[kLevels][4], long
     for (int l = 0; l < kLevels; l++)
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const long long iv = __float2int_rn(acc[l][q] * __int_as_float((127 + 7 * l) << 23));
-            if (l < 4) hi[q] += iv << (7 * (3 - l));
-            else lo[q] += iv << (7 * (8 - l));
+            const float unit = __uint_as_float((unsigned)(127 + 7 * l) << 23);  // 2^(7l)
+            int iv;
+            if (Large) iv = __float2int_rn(acc[l][q] * unit);
+            else iv = (int)(__float_as_uint(fmaf(acc[l][q], unit, 12582912.0f)) - 0x4B400000u);
+            // one 32 x 32 + 64 multiply-add per level
+            if (l < 4) hi[q] += (long long)iv * (long long)(1 << (7 * (3 - l)));
+            else lo[q] += (long long)iv * (long long)(1 << (7 * (8 - l)));
         }
 }
 
+// swizzled 16-byte chunk of row r: rows r and r + 4 use different banks
+__device__ __forceinline__ int swz(int chunk, int r) { return chunk ^ ((r >> 2) & 1); }
+
 template <int B>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int *__restrict__ Ecol,
             const unsigned char *__restrict__ rec, const long long *__restrict__ off, int G, int C, int CB,
             TcState *state, int *progress, long long spin_polls, long long timeout_ns, int hold_group)
 {
     using W = Win<B>;
-    constexpr int L = W::L, LP = W::LP, VROW = W::VROW, QROW = W::QROW, ZROW = W::ZROW;
+    constexpr int L = W::L, LP = W::LP, ZROW = W::ZROW;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t *VtP = (uint16_t *)smem;                                  // [8][16][VROW]
-    uint16_t *UP = (uint16_t *)(smem + W::S_VT);                       // [8][LP][QROW]
-    int *eV = (int *)(smem + W::S_VT + W::S_U);                        // [16]
-    int *eU = eV + kNB;                                                // [LP]
-    uint16_t *ZP = (uint16_t *)(smem + W::S_VT + W::S_U + W::S_E);     // [8][64][VROW]
-    uint16_t *WP = (uint16_t *)((unsigned char *)ZP + W::S_ZP);        // [8][64][QROW]
-    long long *Zs = (long long *)((unsigned char *)WP + W::S_WP);      // [64][ZROW]
-    int *Es = (int *)((unsigned char *)Zs + W::S_Z);                   // [64]
+    uint16_t *VtP = (uint16_t *)smem;                                  // [8][16][LP]
+    uint16_t *UP = (uint16_t *)(smem + W::VT_BYTES);                   // [8][LP][16]
+    const int *eV = (const int *)(smem + W::VT_BYTES + W::U_BYTES);   // [16]
+    const int *eU = eV + kNB;                                          // [LP]
+    uint16_t *WP = (uint16_t *)(smem + W::REC);                        // [8][64][16]
+    long long *Zs = (long long *)(smem + W::REC + W::S_WP);            // [64][ZROW]
+    int *Es = (int *)(smem + W::REC + W::S_WP + W::S_Z);               // [64]
     __shared__ int s_item, s_abort;
 
     const int b = B;
@@ -369,6 +398,7 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
     const int col0 = c * kCols;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gq = lane >> 2, tig = lane & 3;
+    const int wcol = warp * 8;  // the warp's eight columns of the item
 
     for (int i = threadIdx.x; i < kCols; i += kThreads) Es[i] = (col0 + i < nev) ? Ecol[col0 + i] : 0;
     if (threadIdx.x == 0 && g + 1 != hold_group) st_release(progress + (long long)g * C + c, 0);
@@ -395,24 +425,24 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
             if (!abort && *(volatile int *)&state->abort) abort = 1;
             s_abort = abort;
         }
-        // ---- stage the tile's digit planes (independent of Z)
+        // ---- stage the tile record (independent of Z); chunks swizzled per row
         {
             const unsigned char *r = rec + ((size_t)off[g] + k) * W::REC;
-            constexpr int VT_CH = kDigits * kNB * (LP / 8);   // 16-byte chunks
-            constexpr int U_CH = kDigits * LP * (kNB / 8);
+            constexpr int VT_CH = kDigits * kNB * (LP / 8);
+            constexpr int U_CH = kDigits * LP * 2;
             constexpr int E_CH = (int)((W::E_BYTES + 15) / 16);
             for (int ch = threadIdx.x; ch < VT_CH + U_CH + E_CH; ch += kThreads) {
                 if (ch < VT_CH) {
                     const int row = ch / (LP / 8), part = ch % (LP / 8);  // row = s * 16 + q
-                    cp_async16(VtP + (size_t)row * VROW + part * 8, r + ((size_t)row * LP + part * 8) * 2);
+                    cp_async16(VtP + (size_t)row * LP + swz(part, row & 15) * 8, r + ((size_t)row * LP + part * 8) * 2);
                 } else if (ch < VT_CH + U_CH) {
                     const int c2 = ch - VT_CH;
-                    const int row = c2 / (kNB / 8), part = c2 % (kNB / 8);  // row = s * LP + j
-                    cp_async16(UP + (size_t)row * QROW + part * 8,
+                    const int row = c2 >> 1, part = c2 & 1;  // row = s * LP + j
+                    cp_async16(UP + (size_t)row * kNB + swz(part, row % LP) * 8,
                                r + W::VT_BYTES + ((size_t)row * kNB + part * 8) * 2);
                 } else {
                     const int c3 = ch - VT_CH - U_CH;
-                    cp_async16((unsigned char *)eV + c3 * 16, r + W::VT_BYTES + W::U_BYTES + c3 * 16);
+                    cp_async16(smem + W::VT_BYTES + W::U_BYTES + c3 * 16, r + W::VT_BYTES + W::U_BYTES + c3 * 16);
                 }
             }
             cp_async_commit();
@@ -444,66 +474,73 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
         }
         cp_async_wait_all();
         __syncthreads();
-        // ---- digits of the window: ZP[s][c][j]
-        for (int e = threadIdx.x; e < kCols * (LP / 2); e += kThreads) {
-            const int cc = e / (LP / 2), j = (e % (LP / 2)) * 2;
-            uint16_t h0[kDigits], h1[kDigits];
-            fixed_digits(Zs[cc * ZROW + j], h0);
-            fixed_digits(Zs[cc * ZROW + j + 1], h1);
-#pragma unroll
-            for (int s = 0; s < kDigits; s++)
-                *(unsigned *)(ZP + ((size_t)s * kCols + cc) * VROW + j) = (unsigned)h0[s] | ((unsigned)h1[s] << 16);
-        }
-        __syncthreads();
-        // ---- W = V^T Z_win (16 x 64, k = LP): warp w owns columns 8w..8w+7
+        // ---- W = V^T Z_win (16 x 64, k = LP): warp w owns columns 8w..8w+7.
+        // The B fragments (rows 2t, 2t+1, 2t+8, 2t+9 of column g) are cut
+        // into digits in registers straight from the fixed-point window.
         {
             float acc[kLevels][4];
 #pragma unroll
             for (int l = 0; l < kLevels; l++)
 #pragma unroll
                 for (int q = 0; q < 4; q++) acc[l][q] = 0.f;
-            const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
-            const int b_row = warp * 8 + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
-#pragma unroll
+            const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8;
+            const long long *zcol = Zs + (wcol + gq) * ZROW + 2 * tig;
+#pragma unroll 1
             for (int ks = 0; ks < LP / 16; ks++) {
+                unsigned bf0[kDigits], bf1[kDigits];
+                {
+                    const longlong2 p0 = *(const longlong2 *)(zcol + ks * 16);
+                    const longlong2 p1 = *(const longlong2 *)(zcol + ks * 16 + 8);
+                    unsigned sg0, sg1, sg2, sg3;
+                    const unsigned long long y0 = round56(p0.x, sg0), y1 = round56(p0.y, sg1);
+                    const unsigned long long y2 = round56(p1.x, sg2), y3 = round56(p1.y, sg3);
+#define GB_TC_DIGITS(S)                                                                                 \
+    bf0[S] = pack_bf16(digit_f<S>(digit_of(y0, S)), digit_f<S>(digit_of(y1, S)), sg0, sg1);              \
+    bf1[S] = pack_bf16(digit_f<S>(digit_of(y2, S)), digit_f<S>(digit_of(y3, S)), sg2, sg3);
+                    GB_TC_DIGITS(0) GB_TC_DIGITS(1) GB_TC_DIGITS(2) GB_TC_DIGITS(3)
+                    GB_TC_DIGITS(4) GB_TC_DIGITS(5) GB_TC_DIGITS(6) GB_TC_DIGITS(7)
+#undef GB_TC_DIGITS
+                }
                 unsigned af[kDigits][4];
 #pragma unroll
                 for (int s = 0; s < kDigits; s++)
                     ldsm_x4(af[s][0], af[s][1], af[s][2], af[s][3],
-                            VtP + ((size_t)s * kNB + a_row) * VROW + ks * 16 + a_k);
+                            VtP + ((size_t)s * kNB + a_row) * LP + swz(ks * 2 + (lane >> 4), a_row) * 8);
 #pragma unroll
-                for (int jd = 0; jd < kDigits; jd++) {
-                    unsigned b0, b1;
-                    ldsm_x2(b0, b1, ZP + ((size_t)jd * kCols + b_row) * VROW + ks * 16 + b_k);
+                for (int jd = 0; jd < kDigits; jd++)
 #pragma unroll
                     for (int i = 0; i < kDigits; i++)
-                        if (i + jd < kLevels) mma_bf16(acc[i + jd], af[i], b0, b1);
-                }
+                        if (i + jd < kLevels) mma_bf16(acc[i + jd], af[i], bf0[jd], bf1[jd]);
             }
             long long hi[4], lo[4];
-            fold_levels(acc, hi, lo);
-            // W in the column's fixed point: Wi = S 2^(eV + 47), S = hi 2^-21 + lo 2^-56
+            fold_levels<true>(acc, hi, lo);
+            // W in the column's fixed point (Wi = S 2^(eV + 47)), cut into
+            // digits: WP[s][c][q], chunk of q swizzled by c
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int qr = gq + (q >> 1) * 8;          // reflector (row of W)
-                const int cc = warp * 8 + tig * 2 + (q & 1);
+                const int cc = wcol + tig * 2 + (q & 1);
                 const int ev = eV[qr];
                 const long long wi = shift_ll(hi[q], ev + 26) + shift_ll(lo[q], ev - 9);
-                uint16_t h[kDigits];
-                fixed_digits(wi, h);
-#pragma unroll
-                for (int s = 0; s < kDigits; s++) WP[((size_t)s * kCols + cc) * QROW + qr] = h[s];
+                unsigned sg;
+                const unsigned long long y = round56(wi, sg);
+                uint16_t *wp = WP + (size_t)cc * kNB + swz(qr >> 3, cc) * 8 + (qr & 7);
+                const unsigned sh = sg >> 16;
+#define GB_TC_WDIGIT(S) wp[(size_t)(S) * kCols * kNB] = (uint16_t)((__float_as_uint(digit_f<S>(digit_of(y, S))) >> 16) | sh);
+                GB_TC_WDIGIT(0) GB_TC_WDIGIT(1) GB_TC_WDIGIT(2) GB_TC_WDIGIT(3)
+                GB_TC_WDIGIT(4) GB_TC_WDIGIT(5) GB_TC_WDIGIT(6) GB_TC_WDIGIT(7)
+#undef GB_TC_WDIGIT
             }
         }
         __syncthreads();
         // ---- dZ = U W (LP x 64, k = 16), Zs -= dZ: warp w owns columns 8w..8w+7
         {
             unsigned bw[kDigits][2];
-            const int b_row = warp * 8 + (lane & 7), b_k = ((lane >> 3) & 1) * 8;
+            const int b_row = wcol + (lane & 7);
 #pragma unroll
             for (int jd = 0; jd < kDigits; jd++)
-                ldsm_x2(bw[jd][0], bw[jd][1], WP + ((size_t)jd * kCols + b_row) * QROW + b_k);
-            const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
+                ldsm_x2(bw[jd][0], bw[jd][1], WP + ((size_t)jd * kCols + b_row) * kNB + swz((lane >> 3) & 1, b_row) * 8);
+            const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8;
 #pragma unroll 1
             for (int mt = 0; mt < LP / 16; mt++) {
                 float acc[kLevels][4];
@@ -511,22 +548,23 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                 for (int l = 0; l < kLevels; l++)
 #pragma unroll
                     for (int q = 0; q < 4; q++) acc[l][q] = 0.f;
+                const int j_a = mt * 16 + a_row;
                 unsigned au[kDigits][4];
 #pragma unroll
                 for (int s = 0; s < kDigits; s++)
                     ldsm_x4(au[s][0], au[s][1], au[s][2], au[s][3],
-                            UP + ((size_t)s * LP + mt * 16 + a_row) * QROW + a_k);
+                            UP + ((size_t)s * LP + j_a) * kNB + swz(lane >> 4, j_a) * 8);
 #pragma unroll
                 for (int jd = 0; jd < kDigits; jd++)
 #pragma unroll
                     for (int i = 0; i < kDigits; i++)
                         if (i + jd < kLevels) mma_bf16(acc[i + jd], au[i], bw[jd][0], bw[jd][1]);
                 long long hi[4], lo[4];
-                fold_levels(acc, hi, lo);
+                fold_levels<false>(acc, hi, lo);
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     const int j = mt * 16 + gq + (q >> 1) * 8;  // window row
-                    const int cc = warp * 8 + tig * 2 + (q & 1);
+                    const int cc = wcol + tig * 2 + (q & 1);
                     if (j < L) {
                         const int eu = eU[j];
                         Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 26) + shift_ll(lo[q], eu - 9);
