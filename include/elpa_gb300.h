@@ -30,7 +30,10 @@
  * Ownership: the caller owns every buffer.  Z is updated in place.  The
  * device entry points allocate nothing; the calls are asynchronous on the
  * given CUDA stream (NULL = legacy default stream).  Input buffers must stay
- * valid and unmodified until the stream reaches the end of the call.
+ * valid and unmodified until the stream reaches the end of the call.  While
+ * a call of the tensor-core variant runs, Z holds an intermediate
+ * per-column 64-bit fixed-point form of its values (converted in place
+ * before and after), so Z must not be read on another stream meanwhile.
  *
  * Errors: every entry point returns 0 on success; -i when argument i
  * (1-based) is invalid (nothing is launched); a positive GB_ERR_* code when a
@@ -53,7 +56,9 @@ extern "C" {
 #define GB_ERR_UNSUPPORTED 4 /* valid arguments outside what this build supports */
 
 /* Kernel variants for gb_trans_ev_opts.variant. */
-#define GB_VARIANT_AUTO 0      /* library picks */
+#define GB_VARIANT_AUTO 0      /* library picks: PIPELINE_TC for real data with nbw in
+                                  {16,32,64} and n >= 512, else PIPELINE for real
+                                  data with nbw in {8,16,32,64}, else WAVEFRONT */
 #define GB_VARIANT_WAVEFRONT 1 /* one launch per anti-diagonal of the tile DAG */
 #define GB_VARIANT_PIPELINE 2  /* one persistent launch, tiles ordered by flags */
 #define GB_VARIANT_PIPELINE_TC 3 /* the pipeline's schedule with every tile applied in

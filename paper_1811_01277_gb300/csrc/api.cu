@@ -19,14 +19,16 @@ struct Opts {
     long long spin;
 };
 
+constexpr int kTcMinN = 512;  // below it the tensor-core pipeline's per-call preparation dominates
 constexpr long long kDefaultSpinPolls = 1LL << 40;  // effectively bounded by the timeout
 constexpr long long kTimeoutNs = 10LL * 1000 * 1000 * 1000;
 
 // Returns 0 or -11 (opts is the 11th argument of the device entry points).
-// AUTO picks PIPELINE for real data with nbw in {8,16,32,64} (fastest in the
-// GB300 sweep: nb = 16, 64 columns per block) and WAVEFRONT otherwise;
-// PIPELINE requested for other cases runs as WAVEFRONT.
-int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
+// AUTO picks PIPELINE_TC for real data with nbw in {16,32,64} and n >= 512
+// (2.8x the DFMA pipeline at n = 16384 on GB300), PIPELINE for the other real
+// cases with nbw in {8,16,32,64} (nb = 16, 64 columns per block) and
+// WAVEFRONT otherwise; PIPELINE requested for other cases runs as WAVEFRONT.
+int resolve(const gb_trans_ev_opts *o, int n, int nbw, int is_complex, Opts *r)
 {
     int variant = GB_VARIANT_AUTO, nb = 0, threads = 0;
     r->spin = kDefaultSpinPolls;
@@ -53,7 +55,10 @@ int resolve(const gb_trans_ev_opts *o, int nbw, int is_complex, Opts *r)
     const bool pipe_ok = !is_complex && gb::pipeline_supported(nbw);
     if (variant == GB_VARIANT_PIPELINE_TC && (is_complex || !gb::pipeline_tc_supported(nbw)))
         variant = GB_VARIANT_PIPELINE;
-    if (variant == GB_VARIANT_AUTO) variant = pipe_ok ? GB_VARIANT_PIPELINE : GB_VARIANT_WAVEFRONT;
+    if (variant == GB_VARIANT_AUTO) {
+        if (!is_complex && gb::pipeline_tc_supported(nbw) && n >= kTcMinN) variant = GB_VARIANT_PIPELINE_TC;
+        else variant = pipe_ok ? GB_VARIANT_PIPELINE : GB_VARIANT_WAVEFRONT;
+    }
     if (variant == GB_VARIANT_PIPELINE && !pipe_ok) variant = GB_VARIANT_WAVEFRONT;
     r->variant = variant;
     const bool smem = is_complex || nbw > kMaxRegNbw;
@@ -109,7 +114,7 @@ int gb_max_nbw(void) { return kMaxNbw; }
 size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
 {
     Opts o;
-    if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return 0;
+    if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, n, nbw, is_complex, &o) != 0) return 0;
     if (o.variant == GB_VARIANT_PIPELINE_TC && n > 1 && nev > 0) return gb::pipeline_tc_workspace_bytes(n, nbw, nev);
     if (o.variant == GB_VARIANT_PIPELINE && !is_complex && n > 1 && nev > 0)
         return gb::pipeline_workspace_bytes(n, nev, o.nb, o.threads);
@@ -123,7 +128,7 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, sizeof(double));
     if (rc) return rc;
     Opts o;
-    if ((rc = resolve(opts, nbw, 0, &o)) != 0) return rc;
+    if ((rc = resolve(opts, n, nbw, 0, &o)) != 0) return rc;
     size_t need = gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts);
     if (need > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0)) return -8;
     if (ws_bytes < need) return -9;
@@ -149,7 +154,7 @@ int gb_trans_ev_tridi_to_band_z(int n, int nbw, int nev, const double *hh_v, con
     int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, 2 * sizeof(double));
     if (rc) return rc;
     Opts o;
-    if ((rc = resolve(opts, nbw, 1, &o)) != 0) return rc;
+    if ((rc = resolve(opts, n, nbw, 1, &o)) != 0) return rc;
     (void)workspace;
     (void)ws_bytes;  // the complex kernels need no workspace
     if (n == 1 || nev == 0) return GB_OK;
@@ -174,7 +179,7 @@ int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v
     int rc = check_common(n, nbw, nev, hh_v, hh_tau, Z, ldz, sizeof(double));
     if (rc) return rc;
     Opts o;
-    if ((rc = resolve(opts, nbw, 0, &o)) != 0) return rc;
+    if ((rc = resolve(opts, n, nbw, 0, &o)) != 0) return rc;
     size_t need = gb_trans_ev_host_buffer_bytes(n, nbw, nev, ldz, 0, opts);
     if (!dev_buf || ((uintptr_t)dev_buf % 256) != 0) return -8;
     if (dev_bytes < need) return -9;
@@ -211,7 +216,7 @@ int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream)
 long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
 {
     Opts o;
-    if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, nbw, is_complex, &o) != 0) return -1;
+    if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, n, nbw, is_complex, &o) != 0) return -1;
     if (n == 1 || nev == 0) return 0;
     if (o.variant == GB_VARIANT_PIPELINE) return 1;
     if (o.variant == GB_VARIANT_PIPELINE_TC) return 6;  // scales, to fixed, offsets, tile prep, pipeline, back

@@ -5,8 +5,9 @@
 // end the fastest setting is kept.  The walk can be saved to a text file and
 // resumed, so that it can be spread over the iterations of an application's
 // self-consistency loop (Sec. 5.3).
-//   FAST   : the kernel variant only (wavefront, pipeline)
-//   MEDIUM : the variant and its blocking (sweeps per tile, columns per block)
+//   FAST   : the kernel variant only (wavefront, pipeline, tensor-core pipeline)
+//   MEDIUM : the variant and its blocking (sweeps per tile, columns per block;
+//            column batch for the tensor-core pipeline)
 // Host code only; no device memory is touched.
 #include <stdio.h>
 #include <stdlib.h>
@@ -27,22 +28,25 @@ struct gb_autotune {
 namespace {
 
 bool pipeline_ok(int nbw) { return nbw == 8 || nbw == 16 || nbw == 32 || nbw == 64; }
+bool tc_ok(int nbw) { return nbw == 16 || nbw == 32 || nbw == 64; }
 
 void build_candidates(gb_autotune *t)
 {
     t->cand.clear();
-    auto add = [&](int variant, int nb, int cols) {
+    auto add = [&](int variant, int nb, int cols, int batch = 0) {
         gb_trans_ev_opts o;
         memset(&o, 0, sizeof(o));
         o.variant = variant;
         o.sweeps_per_tile = nb;
         o.cols_per_block = cols;
+        o.column_batch = batch;
         t->cand.push_back(o);
     };
     const bool real_reg = t->nbw <= 64;
     if (t->level == GB_AUTOTUNE_FAST) {
         add(GB_VARIANT_WAVEFRONT, 0, 0);
         if (pipeline_ok(t->nbw)) add(GB_VARIANT_PIPELINE, 0, 0);
+        if (tc_ok(t->nbw)) add(GB_VARIANT_PIPELINE_TC, 0, 0);
     } else {
         const int wnb[3] = {4, 8, 16}, wcols[3] = {32, 64, 128};
         for (int a = 0; a < 3; a++)
@@ -52,6 +56,10 @@ void build_candidates(gb_autotune *t)
             const int pnb[2] = {8, 16}, pcols[2] = {64, 128};
             for (int a = 0; a < 2; a++)
                 for (int c = 0; c < 2; c++) add(GB_VARIANT_PIPELINE, pnb[a], pcols[c]);
+        }
+        if (tc_ok(t->nbw)) {
+            const int tcb[3] = {8, 16, 32};
+            for (int a = 0; a < 3; a++) add(GB_VARIANT_PIPELINE_TC, 0, 0, tcb[a]);
         }
     }
     t->secs.assign(t->cand.size(), -1.0);
@@ -126,11 +134,11 @@ int gb_autotune_save(const gb_autotune *t, const char *path)
     if (!f) return GB_ERR_UNSUPPORTED;
     // a candidate handed out but not reported yet is tried again on resume
     const int next = t->pending >= 0 ? t->pending : t->next;
-    fprintf(f, "gb_autotune 1\nlevel %d\nn %d\nnbw %d\nnev %d\nnext %d\ncandidates %zu\n", t->level, t->n, t->nbw,
+    fprintf(f, "gb_autotune 2\nlevel %d\nn %d\nnbw %d\nnev %d\nnext %d\ncandidates %zu\n", t->level, t->n, t->nbw,
             t->nev, next, t->cand.size());
     for (size_t i = 0; i < t->cand.size(); i++)
-        fprintf(f, "c %d %d %d %.17g\n", t->cand[i].variant, t->cand[i].sweeps_per_tile, t->cand[i].cols_per_block,
-                t->secs[i]);
+        fprintf(f, "c %d %d %d %d %.17g\n", t->cand[i].variant, t->cand[i].sweeps_per_tile, t->cand[i].cols_per_block,
+                t->cand[i].column_batch, t->secs[i]);
     int rc = fclose(f);
     return rc == 0 ? GB_OK : GB_ERR_UNSUPPORTED;
 }
@@ -145,14 +153,15 @@ gb_autotune *gb_autotune_load(const char *path)
     gb_autotune *t = NULL;
     if (fscanf(f, "gb_autotune %d level %d n %d nbw %d nev %d next %d candidates %zu", &ver, &level, &n, &nbw, &nev,
                &next, &ncand) == 7 &&
-        ver == 1) {
+        ver == 2) {
         t = gb_autotune_create(level, n, nbw, nev);
         if (t && ncand == t->cand.size() && next >= 0 && next <= (int)ncand) {
             for (size_t i = 0; i < ncand; i++) {
-                int v, nb, cols;
+                int v, nb, cols, cb;
                 double s;
-                if (fscanf(f, " c %d %d %d %lg", &v, &nb, &cols, &s) != 4 || v != t->cand[i].variant ||
-                    nb != t->cand[i].sweeps_per_tile || cols != t->cand[i].cols_per_block) {
+                if (fscanf(f, " c %d %d %d %d %lg", &v, &nb, &cols, &cb, &s) != 5 || v != t->cand[i].variant ||
+                    nb != t->cand[i].sweeps_per_tile || cols != t->cand[i].cols_per_block ||
+                    cb != t->cand[i].column_batch) {
                     delete t;
                     t = NULL;
                     break;

@@ -18,7 +18,8 @@
 // against per-row powers of two, once per tile, by tc_tile_prep.
 //
 // Z itself is held as 64-bit fixed point per column for the whole call:
-// z = Zi 2^(E_c - 61) with ||z_c||_2 < 2^(E_c - 1).  Householder reflectors
+// z = Zi 2^(E_c - 62) with ||z_c||_2 < 2^(E_c - 1), so |Zi| < 2^61 and every
+// update |dZi| <= 2 ||z|| 2^(62 - E_c) < 2^62.  Householder reflectors
 // are orthogonal, so every entry of every intermediate column stays below
 // its initial 2-norm: one scale per column serves the whole sweep, digits
 // come straight from the integer's bits, each level's tensor-core sum is
@@ -95,10 +96,13 @@ struct TcState {  // head of the workspace (zeroed before every launch)
     int error;
 };
 
-// x * 2^sh for a 64-bit integer (arithmetic shift right, truncating, when sh < 0)
+// x * 2^sh for a 64-bit integer, rounded to nearest when sh < 0 (so that
+// the rescaling adds no bias)
 __device__ __forceinline__ long long shift_ll(long long x, int sh)
 {
-    return sh >= 0 ? (x << sh) : (sh > -64 ? (x >> -sh) : (x < 0 ? -1 : 0));
+    if (sh >= 0) return x << sh;
+    if (sh <= -63) return 0;
+    return (x + (1ll << (-sh - 1))) >> -sh;
 }
 
 // ---- column scales and fixed-point conversion ----------------------------
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(256) tc_col_scale(int n, int nev, const double
     }
 }
 
-// In place: z -> round(z 2^(61 - E_c)) as int64 (to_fixed) or back (from_fixed).
+// In place: z -> round(z 2^(62 - E_c)) as int64 (to_fixed) or back (from_fixed).
 __global__ void __launch_bounds__(256) tc_convert(int n, int nev, double *__restrict__ Z, long long ldz,
                                                   const int *__restrict__ E, int to_fixed)
 {
@@ -150,8 +154,8 @@ __global__ void __launch_bounds__(256) tc_convert(int n, int nev, double *__rest
         double *z = Z + (long long)c * ldz;
         long long *zi = (long long *)z;
         for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-            if (to_fixed) zi[r] = __double2ll_rn(scale_by_pow2(z[r], 61 - e));
-            else z[r] = scale_by_pow2(__ll2double_rn(zi[r]), e - 61);
+            if (to_fixed) zi[r] = __double2ll_rn(scale_by_pow2(z[r], 62 - e));
+            else z[r] = scale_by_pow2(__ll2double_rn(zi[r]), e - 62);
         }
     }
 }
@@ -319,13 +323,13 @@ __device__ __forceinline__ unsigned pack_bf16(float a, float b, unsigned sa, uns
     return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632) ^ ((sa >> 16) | sb);
 }
 
-// 56-bit rounded magnitude of a fixed-point value |x| < 2^61 (bits 60..5)
+// 56-bit rounded magnitude of a fixed-point value |x| < 2^62 (bits 61..6)
 // and its sign word
 __device__ __forceinline__ unsigned long long round56(long long x, unsigned &sign)
 {
     sign = x < 0 ? 0x80000000u : 0u;
     const unsigned long long mag = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
-    const unsigned long long Y = (mag + 16) >> 5;
+    const unsigned long long Y = (mag + 32) >> 6;
     return Y < (1ull << 56) ? Y : (1ull << 56) - 1;
 }
 
@@ -514,14 +518,15 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
             }
             long long hi[4], lo[4];
             fold_levels<true>(acc, hi, lo);
-            // W in the column's fixed point (Wi = S 2^(eV + 47)), cut into
-            // digits: WP[s][c][q], chunk of q swizzled by c
+            // W in the column's fixed point (Wi = W 2^(62 - E_c) = S 2^(eV + 48),
+            // |Wi| < 2^61 since |v_q^T z| <= ||z||), cut into digits: WP[s][c][q],
+            // chunk of q swizzled by c
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int qr = gq + (q >> 1) * 8;          // reflector (row of W)
                 const int cc = wcol + tig * 2 + (q & 1);
                 const int ev = eV[qr];
-                const long long wi = shift_ll(hi[q], ev + 26) + shift_ll(lo[q], ev - 9);
+                const long long wi = shift_ll(hi[q], ev + 27) + shift_ll(lo[q], ev - 8);
                 unsigned sg;
                 const unsigned long long y = round56(wi, sg);
                 uint16_t *wp = WP + (size_t)cc * kNB + swz(qr >> 3, cc) * 8 + (qr & 7);
@@ -567,7 +572,7 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                     const int cc = wcol + tig * 2 + (q & 1);
                     if (j < L) {
                         const int eu = eU[j];
-                        Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 26) + shift_ll(lo[q], eu - 9);
+                        Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 27) + shift_ll(lo[q], eu - 8);
                     }
                 }
             }

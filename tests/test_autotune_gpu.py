@@ -51,10 +51,10 @@ def test_medium_walk_on_gpu(gb):
         sec = e0.elapsed_time(e1) / 1e3
         out = Zt.cpu().numpy().T
         assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
-        times[(o.variant, o.sweeps_per_tile, o.cols_per_block)] = sec
+        times[(o.variant, o.sweeps_per_tile, o.cols_per_block, o.column_batch)] = sec
         assert gb.gb_autotune_report(t, sec) == 0
     best, s = gb.gb_autotune_best(t)
-    assert len(times) == 13
+    assert len(times) == 9 + 4 + 3          # wavefront, pipeline, tensor-core pipeline settings
     assert s == min(times.values())
-    assert times[(best.variant, best.sweeps_per_tile, best.cols_per_block)] == s
+    assert times[(best.variant, best.sweeps_per_tile, best.cols_per_block, best.column_batch)] == s
     gb.gb_autotune_destroy(t)
