@@ -81,6 +81,22 @@ __device__ __forceinline__ unsigned long long fixed56(double x, int e)
     return Y < (1ull << 56) ? Y : (1ull << 56) - 1;
 }
 
+// Y = round(|x| 2^(63 - e)) for |x| < 2^e, at most 2^63 - 1: nine 7-bit
+// digits (exact for entries within 10 binades of the row's largest)
+__device__ __forceinline__ unsigned long long fixed63(double x, int e)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    if (ex == 0) return 0ull;
+    const unsigned long long M = (u & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = ex - 1075 - e + 63;
+    unsigned long long Y;
+    if (sh >= 0) Y = M << sh;
+    else if (sh > -54) Y = (M + (1ull << (-sh - 1))) >> -sh;
+    else Y = 0ull;
+    return Y < (1ull << 63) ? Y : (1ull << 63) - 1;
+}
+
 // v * 2^e for -1022 <= e <= 1023, and for wider e as two factors
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 __device__ __forceinline__ double scale_by_pow2(double v, int e)

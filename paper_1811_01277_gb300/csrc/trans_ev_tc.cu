@@ -41,10 +41,10 @@ namespace {
 constexpr int kNB = 16;      // sweeps per tile
 constexpr int kCols = 64;    // eigenvector columns per work item
 constexpr int kThreads = 256;
-constexpr int kDigits = 8;
-constexpr int kLevels = 9;  // digit pairs i + j <= 8
+constexpr int kDigits = 9;   // 63 bits: the fixed-point Z and W are cut exactly
+constexpr int kLevels = 10;  // digit pairs i + j <= 9
 constexpr int kColumnBatchTc = 16;
-constexpr int kFlushBound = kDigits * 127 * 127;  // per k value of one level (at most 8 pairs)
+constexpr int kFlushBound = kDigits * 127 * 127;  // per k value of one level (at most 9 pairs)
 
 // window rows of a tile, padded to a multiple of 16 (the mma k step)
 template <int B>
@@ -287,20 +287,20 @@ __global__ void __launch_bounds__(128) tc_tile_prep(int n, const double *__restr
     for (int e = threadIdx.x; e < kNB * LP; e += blockDim.x) {
         const int q = e / LP, j = e % LP;
         const double x = V[j][q];
-        const unsigned long long Y = fixed56(x, seV[q]);
+        const unsigned long long Y = fixed63(x, seV[q]);
         const bool neg = x < 0.0;
 #pragma unroll
         for (int s = 0; s < kDigits; s++)
-            vt[((size_t)s * kNB + q) * LP + j] = bf16_digit((int)((Y >> (7 * (kDigits - 1 - s))) & 127u), s, neg);
+            vt[((size_t)s * kNB + q) * LP + j] = bf16_digit((int)((Y >> (56 - 7 * s)) & 127u), s, neg);
     }
     for (int e = threadIdx.x; e < LP * kNB; e += blockDim.x) {
         const int j = e / kNB, q = e % kNB;
         const double x = U[j][q];
-        const unsigned long long Y = fixed56(x, seU[j]);
+        const unsigned long long Y = fixed63(x, seU[j]);
         const bool neg = x < 0.0;
 #pragma unroll
         for (int s = 0; s < kDigits; s++)
-            up[((size_t)s * LP + j) * kNB + q] = bf16_digit((int)((Y >> (7 * (kDigits - 1 - s))) & 127u), s, neg);
+            up[((size_t)s * LP + j) * kNB + q] = bf16_digit((int)((Y >> (56 - 7 * s)) & 127u), s, neg);
     }
 }
 
@@ -323,26 +323,25 @@ __device__ __forceinline__ unsigned pack_bf16(float a, float b, unsigned sa, uns
     return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632) ^ ((sa >> 16) | sb);
 }
 
-// 56-bit rounded magnitude of a fixed-point value |x| < 2^62 (bits 61..6)
-// and its sign word
-__device__ __forceinline__ unsigned long long round56(long long x, unsigned &sign)
+// The 63-bit magnitude of a fixed-point value |x| < 2^61 (bits 60..0, two
+// zero bits appended: exact) and its sign word
+__device__ __forceinline__ unsigned long long mag63(long long x, unsigned &sign)
 {
     sign = x < 0 ? 0x80000000u : 0u;
     const unsigned long long mag = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
-    const unsigned long long Y = (mag + 32) >> 6;
-    return Y < (1ull << 56) ? Y : (1ull << 56) - 1;
+    return mag << 2;
 }
 
-// digit s (0 = most significant) of a 56-bit magnitude
+// digit s (0 = most significant) of a 63-bit magnitude
 __device__ __forceinline__ unsigned digit_of(unsigned long long Y, int s)
 {
-    return (unsigned)(Y >> (49 - 7 * s)) & 127u;
+    return (unsigned)(Y >> (56 - 7 * s)) & 127u;
 }
 
 
 // Folds level accumulators (level l in units of 2^(-7l)) into
-// hi = sum_{l<4} L_l 2^(7(3-l)) and lo = sum_{l>=4} L_l 2^(7(8-l)), so the sum
-// in level-0 units is hi 2^-21 + lo 2^-56.  Large: level sums up to 2^24
+// hi = sum_{l<4} L_l 2^(7(3-l)) and lo = sum_{l>=4} L_l 2^(7(9-l)), so the sum
+// in level-0 units is hi 2^-21 + lo 2^-63.  Large: level sums up to 2^24
 // (F2I); otherwise below 2^22 (exact by adding 1.5 2^23 in FP32).
 template <bool Large>
 __device__ __forceinline__ void fold_levels(const float (&acc)[kLevels][4], long long (&hi)[4], long long (&lo)[4])
@@ -362,7 +361,7 @@ __device__ __forceinline__ void fold_levels(const float (&acc)[kLevels][4], long
             else iv = (int)(__float_as_uint(fmaf(acc[l][q], unit, 12582912.0f)) - 0x4B400000u);
             // one 32 x 32 + 64 multiply-add per level
             if (l < 4) hi[q] += (long long)iv * (long long)(1 << (7 * (3 - l)));
-            else lo[q] += (long long)iv * (long long)(1 << (7 * (8 - l)));
+            else lo[q] += (long long)iv * (1ll << (7 * (9 - l)));
         }
 }
 
@@ -496,13 +495,13 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                     const longlong2 p0 = *(const longlong2 *)(zcol + ks * 16);
                     const longlong2 p1 = *(const longlong2 *)(zcol + ks * 16 + 8);
                     unsigned sg0, sg1, sg2, sg3;
-                    const unsigned long long y0 = round56(p0.x, sg0), y1 = round56(p0.y, sg1);
-                    const unsigned long long y2 = round56(p1.x, sg2), y3 = round56(p1.y, sg3);
+                    const unsigned long long y0 = mag63(p0.x, sg0), y1 = mag63(p0.y, sg1);
+                    const unsigned long long y2 = mag63(p1.x, sg2), y3 = mag63(p1.y, sg3);
 #define GB_TC_DIGITS(S)                                                                                 \
     bf0[S] = pack_bf16(digit_f<S>(digit_of(y0, S)), digit_f<S>(digit_of(y1, S)), sg0, sg1);              \
     bf1[S] = pack_bf16(digit_f<S>(digit_of(y2, S)), digit_f<S>(digit_of(y3, S)), sg2, sg3);
                     GB_TC_DIGITS(0) GB_TC_DIGITS(1) GB_TC_DIGITS(2) GB_TC_DIGITS(3)
-                    GB_TC_DIGITS(4) GB_TC_DIGITS(5) GB_TC_DIGITS(6) GB_TC_DIGITS(7)
+                    GB_TC_DIGITS(4) GB_TC_DIGITS(5) GB_TC_DIGITS(6) GB_TC_DIGITS(7) GB_TC_DIGITS(8)
 #undef GB_TC_DIGITS
                 }
                 unsigned af[kDigits][4];
@@ -518,22 +517,23 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
             }
             long long hi[4], lo[4];
             fold_levels<true>(acc, hi, lo);
-            // W in the column's fixed point (Wi = W 2^(62 - E_c) = S 2^(eV + 48),
-            // |Wi| < 2^61 since |v_q^T z| <= ||z||), cut into digits: WP[s][c][q],
-            // chunk of q swizzled by c
+            // W in the column's fixed point (Wi = W 2^(62 - E_c) = S 2^(eV + 47):
+            // the digits of Z stand for 2^(E_c - 1) sum d_s 2^(-7(s+1)); |Wi| < 2^61
+            // since |v_q^T z| <= ||z||), cut into digits: WP[s][c][q], chunk of
+            // q swizzled by c
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int qr = gq + (q >> 1) * 8;          // reflector (row of W)
                 const int cc = wcol + tig * 2 + (q & 1);
                 const int ev = eV[qr];
-                const long long wi = shift_ll(hi[q], ev + 27) + shift_ll(lo[q], ev - 8);
+                const long long wi = shift_ll(hi[q], ev + 26) + shift_ll(lo[q], ev - 16);
                 unsigned sg;
-                const unsigned long long y = round56(wi, sg);
+                const unsigned long long y = mag63(wi, sg);
                 uint16_t *wp = WP + (size_t)cc * kNB + swz(qr >> 3, cc) * 8 + (qr & 7);
                 const unsigned sh = sg >> 16;
 #define GB_TC_WDIGIT(S) wp[(size_t)(S) * kCols * kNB] = (uint16_t)((__float_as_uint(digit_f<S>(digit_of(y, S))) >> 16) | sh);
                 GB_TC_WDIGIT(0) GB_TC_WDIGIT(1) GB_TC_WDIGIT(2) GB_TC_WDIGIT(3)
-                GB_TC_WDIGIT(4) GB_TC_WDIGIT(5) GB_TC_WDIGIT(6) GB_TC_WDIGIT(7)
+                GB_TC_WDIGIT(4) GB_TC_WDIGIT(5) GB_TC_WDIGIT(6) GB_TC_WDIGIT(7) GB_TC_WDIGIT(8)
 #undef GB_TC_WDIGIT
             }
         }
@@ -572,7 +572,7 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                     const int cc = wcol + tig * 2 + (q & 1);
                     if (j < L) {
                         const int eu = eU[j];
-                        Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 27) + shift_ll(lo[q], eu - 8);
+                        Zs[cc * ZROW + j] -= shift_ll(hi[q], eu + 26) + shift_ll(lo[q], eu - 16);
                     }
                 }
             }
