@@ -359,6 +359,34 @@ size_t gb_dsyrk_sliced_workspace_bytes(int n, int k);
 int gb_dsyrk_sliced(int n, int k, double alpha, const double *A, int lda, double beta, double *C, int ldc,
                     void *workspace, size_t ws_bytes, void *stream);
 
+/* Complex (complex128, interleaved re/im; leading dimensions in complex
+ * elements) forms of the sliced products, real alpha and beta.  The complex
+ * product is computed as the real product of the expanded left operand,
+ * whose entries x + iy become 2 x 2 blocks [x -y; y x], with the right
+ * operand and C in their interleaved storage; same accuracy statement as the
+ * real forms.
+ *   gb_zgemm_sliced : C (m x n) = alpha op(A) B + beta C, transa = 'N' or
+ *                     'C' (conjugate transpose), op(A) m x k, B k x n.
+ *   gb_zhemm_sliced : C (m x n) = alpha S B + beta C, S (m x m) Hermitian,
+ *                     only its lower triangle is read (the diagonal's
+ *                     imaginary parts are read as zero).
+ *   gb_zher2k_sliced: lower triangle of C (n x n) = alpha (X Y^H + Y X^H)
+ *                     + beta C, X, Y n x k; the diagonal's imaginary parts
+ *                     are set to zero; the strict upper triangle is not
+ *                     touched.
+ * Pointers 16-byte aligned, workspace 256-byte aligned and at least the
+ * *_workspace_bytes figure; -i for invalid argument i, GB_ERR_CUDA for a
+ * launch error. */
+size_t gb_zgemm_sliced_workspace_bytes(int m, int n, int k);
+int gb_zgemm_sliced(char transa, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
+                    int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);
+size_t gb_zhemm_sliced_workspace_bytes(int m, int n);
+int gb_zhemm_sliced(int m, int n, double alpha, const double *S, int lds, const double *B, int ldb, double beta,
+                    double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);
+size_t gb_zher2k_sliced_workspace_bytes(int n, int k);
+int gb_zher2k_sliced(int n, int k, double alpha, const double *X, int ldx, const double *Y, int ldy, double beta,
+                     double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);
+
 /* Human-readable text for a status code (never NULL). */
 const char *gb_status_string(int status);
 

@@ -19,7 +19,8 @@ from ._lib import (  # noqa: F401
     gb_dgemm, gb_dgemm_workspace_bytes, gb_dsymm, gb_dsyr2k, gb_dsyrk,
     GB_SOLVE_DFMA_PRODUCTS, gb_dgemm_sliced, gb_dgemm_sliced_workspace_bytes, gb_dsymm_sliced,
     gb_dsymm_sliced_workspace_bytes, gb_dsyr2k_sliced, gb_dsyr2k_sliced_workspace_bytes, gb_dsyrk_sliced,
-    gb_dsyrk_sliced_workspace_bytes,
+    gb_dsyrk_sliced_workspace_bytes, gb_zgemm_sliced, gb_zgemm_sliced_workspace_bytes, gb_zhemm_sliced,
+    gb_zhemm_sliced_workspace_bytes, gb_zher2k_sliced, gb_zher2k_sliced_workspace_bytes,
 )
 
 

@@ -37,6 +37,8 @@ EXPORTS = (
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
     "gb_dgemm_sliced_workspace_bytes", "gb_dgemm_sliced", "gb_dsymm_sliced_workspace_bytes", "gb_dsymm_sliced",
     "gb_dsyr2k_sliced_workspace_bytes", "gb_dsyr2k_sliced", "gb_dsyrk_sliced_workspace_bytes", "gb_dsyrk_sliced",
+    "gb_zgemm_sliced_workspace_bytes", "gb_zgemm_sliced", "gb_zhemm_sliced_workspace_bytes", "gb_zhemm_sliced",
+    "gb_zher2k_sliced_workspace_bytes", "gb_zher2k_sliced",
 )
 GB_SOLVE_RECORD_STAGES = 2
 GB_SOLVE_DFMA_PRODUCTS = 4
@@ -136,6 +138,12 @@ def load(path=None):
     L.gb_dsyr2k_sliced.argtypes = [i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dsyr2k_sliced.restype = i
     L.gb_dsyrk_sliced_workspace_bytes.argtypes = [i, i]; L.gb_dsyrk_sliced_workspace_bytes.restype = sz
     L.gb_dsyrk_sliced.argtypes = [i, i, dd, p, i, dd, p, i, p, sz, p]; L.gb_dsyrk_sliced.restype = i
+    L.gb_zgemm_sliced_workspace_bytes.argtypes = [i, i, i]; L.gb_zgemm_sliced_workspace_bytes.restype = sz
+    L.gb_zgemm_sliced.argtypes = [ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_zgemm_sliced.restype = i
+    L.gb_zhemm_sliced_workspace_bytes.argtypes = [i, i]; L.gb_zhemm_sliced_workspace_bytes.restype = sz
+    L.gb_zhemm_sliced.argtypes = [i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_zhemm_sliced.restype = i
+    L.gb_zher2k_sliced_workspace_bytes.argtypes = [i, i]; L.gb_zher2k_sliced_workspace_bytes.restype = sz
+    L.gb_zher2k_sliced.argtypes = [i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_zher2k_sliced.restype = i
     _lib = L
     return L
 
@@ -472,6 +480,43 @@ def gb_dsyrk_sliced(n, k, alpha, A, lda, beta, C, ldc, workspace, ws_bytes, stre
                                 _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsyrk_sliced")
+    return rc
+
+
+def gb_zgemm_sliced_workspace_bytes(m, n, k):
+    return load().gb_zgemm_sliced_workspace_bytes(m, n, k)
+
+
+def gb_zgemm_sliced(transa, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None,
+                    check=True):
+    rc = load().gb_zgemm_sliced(_c(transa), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc,
+                                _p(workspace), ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_zgemm_sliced")
+    return rc
+
+
+def gb_zhemm_sliced_workspace_bytes(m, n):
+    return load().gb_zhemm_sliced_workspace_bytes(m, n)
+
+
+def gb_zhemm_sliced(m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_zhemm_sliced(m, n, alpha, _p(S), lds, _p(B), ldb, beta, _p(C), ldc, _p(workspace), ws_bytes,
+                                _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_zhemm_sliced")
+    return rc
+
+
+def gb_zher2k_sliced_workspace_bytes(n, k):
+    return load().gb_zher2k_sliced_workspace_bytes(n, k)
+
+
+def gb_zher2k_sliced(n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_zher2k_sliced(n, k, alpha, _p(X), ldx, _p(Y), ldy, beta, _p(C), ldc, _p(workspace), ws_bytes,
+                                 _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_zher2k_sliced")
     return rc
 
 

@@ -57,12 +57,38 @@ SliceLayout slice_layout(int R, int K)
     return L;
 }
 
+// entry (a, b) of the 2 x 2 real block [x -y; y x] of x + iy
+__device__ __forceinline__ double zblock(double x, double y, int a, int b) { return a == b ? x : (a ? y : -y); }
+
 // element (r, k) of the view (r < R, k < K)
 __device__ __forceinline__ double view_at(int view, const double *__restrict__ src, long long ld, int r, int k)
 {
-    if (view == kViewRow) return src[r + (long long)k * ld];
-    if (view == kViewCol) return src[k + (long long)r * ld];
-    return r >= k ? src[r + (long long)k * ld] : src[k + (long long)r * ld];
+    switch (view) {
+    case kViewRow: return src[r + (long long)k * ld];
+    case kViewCol: return src[k + (long long)r * ld];
+    case kViewSym: return r >= k ? src[r + (long long)k * ld] : src[k + (long long)r * ld];
+    case kViewZExpandN: {
+        const double *p = src + 2 * ((r >> 1) + (long long)(k >> 1) * ld);
+        return zblock(p[0], p[1], r & 1, k & 1);
+    }
+    case kViewZExpandC: {  // A^H(i, j) = conj(A(j, i))
+        const double *p = src + 2 * ((k >> 1) + (long long)(r >> 1) * ld);
+        return zblock(p[0], -p[1], r & 1, k & 1);
+    }
+    case kViewZHermExpand: {
+        const int i = r >> 1, j = k >> 1;
+        if (i > j) {
+            const double *p = src + 2 * (i + (long long)j * ld);
+            return zblock(p[0], p[1], r & 1, k & 1);
+        }
+        const double *p = src + 2 * (j + (long long)i * ld);
+        return zblock(p[0], i == j ? 0.0 : -p[1], r & 1, k & 1);
+    }
+    default: {  // kViewZRowConj
+        const double *p = src + 2 * (r + (long long)(k >> 1) * ld);
+        return (k & 1) ? -p[1] : p[0];
+    }
+    }
 }
 
 // Loads the 32 x 32 tile at (r0, k0) into t[r][k] (zero outside R x K), with
@@ -73,8 +99,8 @@ __device__ __forceinline__ void load_tile(int view, const double *__restrict__ s
     const int tx = threadIdx.x, ty = threadIdx.y;
     // which index is contiguous in memory for this tile
     bool along_r;
-    if (view == kViewRow) along_r = true;
-    else if (view == kViewCol) along_r = false;
+    if (view == kViewRow || view == kViewZExpandN || view == kViewZRowConj) along_r = true;
+    else if (view == kViewCol || view == kViewZExpandC) along_r = false;
     else along_r = (r0 >= k0 + 31) || !(r0 + 31 < k0);  // lower or diagonal tiles: read src[r + k ld]
     for (int i = ty; i < 32; i += 8) {
         const int a = along_r ? i : tx, bb = along_r ? tx : i;  // a: k offset, bb: r offset
@@ -163,13 +189,14 @@ __device__ __forceinline__ void load_stage(uint16_t *stage, const uint16_t *__re
 __global__ void __launch_bounds__(kThreads, 1)
 sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int a_rp, int a_kp,
                const uint16_t *__restrict__ Bp, const int *__restrict__ eb, int b_rp, int b_kp, int m, int n,
-               int ksplit, int K, double alpha, double beta, double *__restrict__ C, long long ldc, int lower,
+               int ksplit, int K, double alpha, double beta, double *__restrict__ C, long long ldc, int fill,
                double *__restrict__ part)
 {
     extern __shared__ __align__(16) uint16_t smem[];
     const int tm = blockIdx.y, tn = blockIdx.x;
     const int m0 = tm * kBM, n0 = tn * kBN;
-    if (lower && m0 + kBM - 1 < n0) return;  // tile wholly above the diagonal
+    if (fill == kFillLower && m0 + kBM - 1 < n0) return;          // tile wholly above the diagonal
+    if (fill == kFillZLower && ((m0 + kBM - 1) >> 1) < n0) return;
     const int kbeg = blockIdx.z * ksplit, kend = min(K, kbeg + ksplit);
     const size_t a_plane = (size_t)a_rp * a_kp, b_plane = (size_t)b_rp * b_kp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -252,9 +279,15 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
         for (int q = 0; q < 4; q++) {
             const int r = m0 + wm * 16 + g + (q >> 1) * 8;
             const int c = n0 + wn * 16 + t * 8 + tig * 2 + (q & 1);
-            if (r >= m || c >= n || (lower && r < c)) continue;
+            if (r >= m || c >= n || (fill == kFillLower && r < c) || (fill == kFillZLower && (r >> 1) < c))
+                continue;
             double v = (double)hi[t][q] * 0x1p-21 + (double)lo[t][q] * 0x1p-56;
             v = scale_by_pow2(v, ea[r] + eb[c] - 2 * kDigitBits);
+            if (fill == kFillZLower && (r >> 1) == c && (r & 1)) {  // Hermitian diagonal: real
+                if (part) part[(size_t)blockIdx.z * m * n + (size_t)c * m + r] = 0.0;
+                else C[r + (long long)c * ldc] = 0.0;
+                continue;
+            }
             if (part) {
                 part[(size_t)blockIdx.z * m * n + (size_t)c * m + r] = v;
             } else {
@@ -266,12 +299,16 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
 
 __global__ void __launch_bounds__(256) sliced_reduce(int m, int n, int splits, const double *__restrict__ part,
                                                       double alpha, double beta, double *__restrict__ C,
-                                                      long long ldc, int lower)
+                                                      long long ldc, int fill)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)m * n) return;
     const int r = (int)(idx % m), c = (int)(idx / m);
-    if (lower && r < c) return;
+    if ((fill == kFillLower && r < c) || (fill == kFillZLower && (r >> 1) < c)) return;
+    if (fill == kFillZLower && (r >> 1) == c && (r & 1)) {
+        C[r + (long long)c * ldc] = 0.0;
+        return;
+    }
     double s = 0.0;
     for (int z = 0; z < splits; z++) s += part[(size_t)z * m * n + idx];
     double *cp = C + r + (long long)c * ldc;
@@ -312,7 +349,7 @@ cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long l
 }
 
 cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, double alpha, double beta, double *C,
-                        long long ldc, bool lower, double *work, size_t work_elems, cudaStream_t st)
+                        long long ldc, int fill, double *work, size_t work_elems, cudaStream_t st)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (A.K != B.K || A.Kp != B.Kp || m > A.R || n > B.R) return cudaErrorInvalidValue;
@@ -322,9 +359,12 @@ cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, doub
     if (ea != cudaSuccess) return ea;
     const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
     long long tiles = (long long)tiles_m * tiles_n;
-    if (lower) {  // tiles not wholly above the diagonal
+    if (fill != kFillAll) {  // tiles not wholly above the diagonal
         tiles = 0;
-        for (int tm = 0; tm < tiles_m; tm++) tiles += std::min(tiles_n, (tm * kBM + kBM - 1) / kBN + 1);
+        for (int tm = 0; tm < tiles_m; tm++) {
+            const int top = fill == kFillZLower ? (tm * kBM + kBM - 1) >> 1 : tm * kBM + kBM - 1;
+            tiles += std::min(tiles_n, top / kBN + 1);
+        }
     }
     const int Kp = A.Kp;
     // split the reduction when the tiles alone cannot fill the device
@@ -349,13 +389,12 @@ cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, doub
     }
     const dim3 grid(tiles_n, tiles_m, splits);
     sliced_product<<<grid, kThreads, kProductSmem, st>>>(A.planes, A.e, A.Rp, A.Kp, B.planes, B.e, B.Rp, B.Kp, m, n,
-                                                         ksplit, Kp, alpha, beta, C, ldc, lower ? 1 : 0,
+                                                         ksplit, Kp, alpha, beta, C, ldc, fill,
                                                          splits > 1 ? work : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     const long long total = (long long)m * n;
-    sliced_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(m, n, splits, work, alpha, beta, C, ldc,
-                                                                    lower ? 1 : 0);
+    sliced_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(m, n, splits, work, alpha, beta, C, ldc, fill);
     return cudaGetLastError();
 }
 
@@ -415,7 +454,7 @@ cudaError_t sliced_dgemm(char transa, char transb, int m, int n, int k, double a
     cudaError_t e = slice_matrix(transa == 'N' ? kViewRow : kViewCol, m, k, A, lda, w.a, &a, st);
     if (e != cudaSuccess) return e;
     if ((e = slice_matrix(transb == 'N' ? kViewCol : kViewRow, n, k, B, ldb, w.b, &b, st)) != cudaSuccess) return e;
-    return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, false, w.part, kPartialElems, st);
+    return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, kFillAll, w.part, kPartialElems, st);
 }
 
 cudaError_t sliced_dsymm(char side, int m, int n, double alpha, const double *S, long long lds, const double *B,
@@ -432,7 +471,7 @@ cudaError_t sliced_dsymm(char side, int m, int n, double alpha, const double *S,
         if ((e = slice_matrix(kViewRow, m, n, B, ldb, w.a, &a, st)) != cudaSuccess) return e;
         if ((e = slice_matrix(kViewSym, n, n, S, lds, w.b, &b, st)) != cudaSuccess) return e;
     }
-    return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, false, w.part, kPartialElems, st);
+    return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, kFillAll, w.part, kPartialElems, st);
 }
 
 cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, long long lda, const double *B,
@@ -455,7 +494,7 @@ cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, lon
     SlicedOp a, b;
     if ((e = slice_matrix(kViewRow, n, 2 * k, AB, n, w.a, &a, st)) != cudaSuccess) return e;
     if ((e = slice_matrix(kViewRow, n, 2 * k, BA, n, w.b, &b, st)) != cudaSuccess) return e;
-    return sliced_gemm(a, b, n, n, alpha, beta, C, ldc, true, w.part, kPartialElems, st);
+    return sliced_gemm(a, b, n, n, alpha, beta, C, ldc, kFillLower, w.part, kPartialElems, st);
 }
 
 cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
@@ -466,7 +505,63 @@ cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, lo
     SlicedOp a;
     cudaError_t e = slice_matrix(kViewCol, n, k, A, lda, w.a, &a, st);
     if (e != cudaSuccess) return e;
-    return sliced_gemm(a, a, n, n, alpha, beta, C, ldc, true, w.part, kPartialElems, st);
+    return sliced_gemm(a, a, n, n, alpha, beta, C, ldc, kFillLower, w.part, kPartialElems, st);
+}
+
+// ---- complex products (interleaved storage; real alpha, beta) ----
+
+size_t sliced_zgemm_ws_bytes(int m, int n, int k) { return sliced_ws(2 * m, n, 2 * k, 0, 0, nullptr).total; }
+size_t sliced_zhemm_ws_bytes(int m, int n) { return sliced_ws(2 * m, n, 2 * m, 0, 0, nullptr).total; }
+size_t sliced_zher2k_ws_bytes(int n, int k)
+{
+    // two n x 2k complex concatenations = n x 4k doubles each
+    return sliced_ws(2 * n, n, 4 * k, n, 4 * k, nullptr).total;
+}
+
+cudaError_t sliced_zgemm(char transa, int m, int n, int k, double alpha, const double *A, long long lda,
+                         const double *B, long long ldb, double beta, double *C, long long ldc, void *ws,
+                         cudaStream_t st)
+{
+    SlicedWs w = sliced_ws(2 * m, n, 2 * k, 0, 0, ws);
+    SlicedOp a, b;
+    cudaError_t e = slice_matrix(transa == 'N' ? kViewZExpandN : kViewZExpandC, 2 * m, 2 * k, A, lda, w.a, &a, st);
+    if (e != cudaSuccess) return e;
+    if ((e = slice_matrix(kViewCol, n, 2 * k, B, 2 * ldb, w.b, &b, st)) != cudaSuccess) return e;
+    return sliced_gemm(a, b, 2 * m, n, alpha, beta, C, 2 * ldc, kFillAll, w.part, kPartialElems, st);
+}
+
+cudaError_t sliced_zhemm_left(int m, int n, double alpha, const double *S, long long lds, const double *B,
+                              long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st)
+{
+    SlicedWs w = sliced_ws(2 * m, n, 2 * m, 0, 0, ws);
+    SlicedOp a, b;
+    cudaError_t e = slice_matrix(kViewZHermExpand, 2 * m, 2 * m, S, lds, w.a, &a, st);
+    if (e != cudaSuccess) return e;
+    if ((e = slice_matrix(kViewCol, n, 2 * m, B, 2 * ldb, w.b, &b, st)) != cudaSuccess) return e;
+    return sliced_gemm(a, b, 2 * m, n, alpha, beta, C, 2 * ldc, kFillAll, w.part, kPartialElems, st);
+}
+
+cudaError_t sliced_zher2k_lower(int n, int k, double alpha, const double *X, long long ldx, const double *Y,
+                                long long ldy, double beta, double *C, long long ldc, void *ws, cudaStream_t st)
+{
+    // X Y^H + Y X^H = [X Y] [Y X]^H
+    SlicedWs w = sliced_ws(2 * n, n, 4 * k, n, 4 * k, ws);
+    double *XY = (double *)w.cat1, *YX = (double *)w.cat2;
+    const size_t row = (size_t)n * 16;
+    cudaError_t e;
+    if (k > 0) {
+        if ((e = cudaMemcpy2DAsync(XY, row, X, ldx * 16, row, k, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(XY + (size_t)2 * n * k, row, Y, ldy * 16, row, k, cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy2DAsync(YX, row, Y, ldy * 16, row, k, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(YX + (size_t)2 * n * k, row, X, ldx * 16, row, k, cudaMemcpyDeviceToDevice, st)) !=
+                cudaSuccess)
+            return e;
+    }
+    SlicedOp a, b;
+    if ((e = slice_matrix(kViewZExpandN, 2 * n, 4 * k, XY, n, w.a, &a, st)) != cudaSuccess) return e;
+    if ((e = slice_matrix(kViewZRowConj, n, 4 * k, YX, n, w.b, &b, st)) != cudaSuccess) return e;
+    return sliced_gemm(a, b, 2 * n, n, alpha, beta, C, 2 * ldc, kFillZLower, w.part, kPartialElems, st);
 }
 
 }  // namespace gb
@@ -580,6 +675,84 @@ int gb_dsyrk_sliced(int n, int k, double alpha, const double *A, int lda, double
     if (sl_bad_ws(workspace)) return -9;
     if (ws_bytes < gb::sliced_syrk_ws_bytes(n, k)) return -10;
     cudaError_t e = gb::sliced_dsyrk_lower_t(n, k, alpha, A, lda, beta, C, ldc, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+size_t gb_zgemm_sliced_workspace_bytes(int m, int n, int k)
+{
+    if (m < 0 || n < 0 || k < 0) return 0;
+    return gb::sliced_zgemm_ws_bytes(m, n, k);
+}
+
+static bool sl_bad_z(const void *p) { return !p || ((uintptr_t)p % 16) != 0; }
+
+int gb_zgemm_sliced(char transa, int m, int n, int k, double alpha, const double *A, int lda, const double *B,
+                    int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream)
+{
+    const bool ta = transa == 'C' || transa == 'c';
+    if (!ta && transa != 'N' && transa != 'n') return -1;
+    if (m < 0) return -2;
+    if (n < 0) return -3;
+    if (k < 0) return -4;
+    if (m == 0 || n == 0) return GB_OK;
+    if (k > 0 && sl_bad_z(A)) return -6;
+    if (lda < (ta ? (k > 1 ? k : 1) : m)) return -7;
+    if (k > 0 && sl_bad_z(B)) return -8;
+    if (ldb < (k > 1 ? k : 1)) return -9;
+    if (sl_bad_z(C)) return -11;
+    if (ldc < m) return -12;
+    if (sl_bad_ws(workspace)) return -13;
+    if (ws_bytes < gb::sliced_zgemm_ws_bytes(m, n, k)) return -14;
+    cudaError_t e = gb::sliced_zgemm(ta ? 'C' : 'N', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace,
+                                     (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+size_t gb_zhemm_sliced_workspace_bytes(int m, int n)
+{
+    if (m < 0 || n < 0) return 0;
+    return gb::sliced_zhemm_ws_bytes(m, n);
+}
+
+int gb_zhemm_sliced(int m, int n, double alpha, const double *S, int lds, const double *B, int ldb, double beta,
+                    double *C, int ldc, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (m == 0 || n == 0) return GB_OK;
+    if (sl_bad_z(S)) return -4;
+    if (lds < m) return -5;
+    if (sl_bad_z(B)) return -6;
+    if (ldb < m) return -7;
+    if (sl_bad_z(C)) return -9;
+    if (ldc < m) return -10;
+    if (sl_bad_ws(workspace)) return -11;
+    if (ws_bytes < gb::sliced_zhemm_ws_bytes(m, n)) return -12;
+    cudaError_t e = gb::sliced_zhemm_left(m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace, (cudaStream_t)stream);
+    return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+size_t gb_zher2k_sliced_workspace_bytes(int n, int k)
+{
+    if (n < 0 || k < 0) return 0;
+    return gb::sliced_zher2k_ws_bytes(n, k);
+}
+
+int gb_zher2k_sliced(int n, int k, double alpha, const double *X, int ldx, const double *Y, int ldy, double beta,
+                     double *C, int ldc, void *workspace, size_t ws_bytes, void *stream)
+{
+    if (n < 0) return -1;
+    if (k < 0) return -2;
+    if (n == 0) return GB_OK;
+    if (k > 0 && sl_bad_z(X)) return -4;
+    if (ldx < n) return -5;
+    if (k > 0 && sl_bad_z(Y)) return -6;
+    if (ldy < n) return -7;
+    if (sl_bad_z(C)) return -9;
+    if (ldc < n) return -10;
+    if (sl_bad_ws(workspace)) return -11;
+    if (ws_bytes < gb::sliced_zher2k_ws_bytes(n, k)) return -12;
+    cudaError_t e = gb::sliced_zher2k_lower(n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, workspace, (cudaStream_t)stream);
     return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 

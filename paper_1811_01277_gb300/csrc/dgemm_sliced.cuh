@@ -42,7 +42,25 @@ constexpr int kFlushK = 128;
 //   kViewRow: src[r + k ld]     (slice rows are the source's rows)
 //   kViewCol: src[k + r ld]     (slice rows are the source's columns)
 //   kViewSym: the symmetric matrix whose lower triangle src holds.
-enum SliceView { kViewRow = 0, kViewCol = 1, kViewSym = 2 };
+// Complex sources (interleaved re, im; ld in complex elements).  A complex
+// product C = op(A) B is the real product of the expanded op(A), whose
+// entry a = x + iy becomes the 2 x 2 block [x -y; y x], with B and C read
+// as real matrices of twice the rows (their interleaved storage as is):
+//   kViewZExpandN:   expanded A (2 rows x 2 columns per complex entry)
+//   kViewZExpandC:   expanded A^H
+//   kViewZHermExpand: expanded Hermitian matrix whose lower triangle src
+//                    holds (the diagonal's imaginary part read as zero)
+//   kViewZRowConj:   row r of the real form of B^H for a complex B with
+//                    rows r: element (r, 2k + c) = c ? -Im B(r, k) : Re B(r, k)
+enum SliceView {
+    kViewRow = 0,
+    kViewCol = 1,
+    kViewSym = 2,
+    kViewZExpandN = 3,
+    kViewZExpandC = 4,
+    kViewZHermExpand = 5,
+    kViewZRowConj = 6
+};
 
 struct SlicedOp {
     const uint16_t *planes;  // kSlices planes of Rp x Kp bf16, row-major (k fastest)
@@ -59,12 +77,20 @@ size_t sliced_bytes(int R, int K);
 cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long long ld, void *buf, SlicedOp *out,
                          cudaStream_t st);
 
+// Which part of C a product writes.
+enum SlicedFill {
+    kFillAll = 0,
+    kFillLower = 1,       // entries r >= c
+    kFillZLower = 2,      // C is the real form of a complex matrix (rows 2r, 2r+1 = re, im of
+                          // complex row r): complex entries r >= c, diagonal imaginary parts zeroed
+};
+
 // C (m x n, column-major) = alpha A B^T + beta C where A, B are sliced
-// (A.R >= m, B.R >= n, A.K == B.K): row r of A times row c of B.  lower:
-// only C's lower triangle (r >= c) is written.  `work` (doubles) holds
-// split-K partials; the reduction splits while splits * m * n <= work_elems.
+// (A.R >= m, B.R >= n, A.K == B.K): row r of A times row c of B; `fill`
+// selects the entries written.  `work` (doubles) holds split-K partials; the
+// reduction splits while splits * m * n <= work_elems.
 cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, double alpha, double beta, double *C,
-                        long long ldc, bool lower, double *work, size_t work_elems, cudaStream_t st);
+                        long long ldc, int fill, double *work, size_t work_elems, cudaStream_t st);
 
 // Whole products (slice both operands into ws, multiply), with the DFMA
 // forms' conventions (dgemm_dfma.cuh); ws must hold the matching *_ws_bytes.
@@ -81,5 +107,21 @@ cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, lon
                                 long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
 cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
                                  long long ldc, void *ws, cudaStream_t st);
+
+// Complex (interleaved) products with real alpha, beta; lda etc. in complex
+// elements.  C (m x n) = alpha op(A) B + beta C, op = 'N' or 'C'.
+size_t sliced_zgemm_ws_bytes(int m, int n, int k);
+cudaError_t sliced_zgemm(char transa, int m, int n, int k, double alpha, const double *A, long long lda,
+                         const double *B, long long ldb, double beta, double *C, long long ldc, void *ws,
+                         cudaStream_t st);
+// C (m x n) = alpha S B + beta C, S Hermitian (lower triangle stored).
+size_t sliced_zhemm_ws_bytes(int m, int n);
+cudaError_t sliced_zhemm_left(int m, int n, double alpha, const double *S, long long lds, const double *B,
+                              long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
+// Lower triangle of C (n x n) = alpha (X Y^H + Y X^H) + beta C, X, Y n x k;
+// the diagonal's imaginary parts are set to zero.
+size_t sliced_zher2k_ws_bytes(int n, int k);
+cudaError_t sliced_zher2k_lower(int n, int k, double alpha, const double *X, long long ldx, const double *Y,
+                                long long ldy, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
 
 }  // namespace gb

@@ -217,9 +217,23 @@ SolveWs carve(int n, int nev, int b, char *base)
 // Complex workspace: complex pieces hold 2 doubles per entry.
 struct SolveWsZ {
     double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Zre, *Gns, *Zns, *S, *S2, *gw;
-    void *chase, *eig;
-    size_t chase_bytes, gw_elems, total;
+    void *chase, *eig, *sl;
+    size_t chase_bytes, gw_elems, sl_bytes, total;
 };
+
+// complex products: 8 real flops per complex multiply-add
+bool zsliced_pays(double m, double n, double k) { return 8.0 * m * n * k >= kSlicedMinFlops; }
+
+size_t zsliced_region_bytes(int n, int nev, int b)
+{
+    if (!zsliced_pays(n, b, n)) return 0;
+    size_t s = std::max(gb::sliced_zhemm_ws_bytes(n, b), gb::sliced_zher2k_ws_bytes(n, b));
+    s = std::max(s, gb::sliced_zgemm_ws_bytes(b, nev, n));
+    s = std::max(s, gb::sliced_zgemm_ws_bytes(n, nev, b));
+    s = std::max(s, gb::sliced_syrk_ws_bytes(nev, n));            // the real Newton-Schulz step
+    s = std::max(s, gb::sliced_symm_ws_bytes('R', n, nev));
+    return s;
+}
 
 SolveWsZ carve_z(int n, int nev, int b, char *base)
 {
@@ -258,6 +272,8 @@ SolveWsZ carve_z(int n, int nev, int b, char *base)
     w.chase_bytes = gb::band_to_tridi_workspace_bytes_z(n, b);
     w.chase = take(w.chase_bytes);
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
+    w.sl_bytes = zsliced_region_bytes(n, nev, b);
+    w.sl = w.sl_bytes ? take(w.sl_bytes) : nullptr;
     w.total = off;
     return w;
 }
@@ -466,7 +482,10 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     const int b = nbw;
     SolveWsZ w = carve_z(n, nev, b, (char *)workspace);
     if (ws_bytes < w.total) return -10;
-    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES)) return -12;
+    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS)) return -12;
+    // large products sliced on the tensor cores unless the caller asks for the FP64 path (cuBLAS here)
+    const bool zslice_ok = w.sl && !(flags & GB_SOLVE_DFMA_PRODUCTS);
+    auto use_zsliced = [&](double m_, double n_, double k_) { return zslice_ok && zsliced_pays(m_, n_, k_); };
     cudaStream_t st = (cudaStream_t)stream;
     cublasHandle_t h = blas_handle(st);
     if (!h) return GB_ERR_CUDA;
@@ -492,12 +511,20 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, m, &one, Y, m, Y, m, &zero, G, b));
         GB_CU(gb::zpanel_t(b, (const double *)G, b, tau, (double *)T, b, st));
         GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &one, Y, m, T, b, &zero, YT, m));
-        GB_BL(cublasZhemm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, m, b, &one, A2, ldw, YT, m, &zero, X, m));
+        if (use_zsliced(m, b, m))
+            GB_CU(gb::sliced_zhemm_left(m, b, 1.0, (const double *)A2, ldw, (const double *)YT, m, 0.0, (double *)X, m,
+                                        w.sl, st));
+        else
+            GB_BL(cublasZhemm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, m, b, &one, A2, ldw, YT, m, &zero, X, m));
         GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, m, &one, Y, m, X, m, &zero, Pm, b));
         GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, b, &one, T, b, Pm, b, &zero, M, b));
         GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &mhalf, Y, m, M, b, &one, X, m));
         const double rone = 1.0;  // ZHER2K: C = alpha A B^H + conj(alpha) B A^H + beta C, beta real
-        GB_BL(cublasZher2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, m, b, &mone, X, m, Y, m, &rone, A2, ldw));
+        if (use_zsliced(m, m, b))
+            GB_CU(gb::sliced_zher2k_lower(m, b, -1.0, (const double *)X, m, (const double *)Y, m, 1.0, (double *)A2,
+                                          ldw, w.sl, st));
+        else
+            GB_BL(cublasZher2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, m, b, &mone, X, m, Y, m, &rone, A2, ldw));
     }
     GB_CU(gb::zband_from_full(n, b, (const double *)Aw, ldw, w.AB, b + 1, st));
 
@@ -506,9 +533,15 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
 
     // ---- real tridiagonal eigenpairs, Newton-Schulz, promote to complex Z
     GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Zre, n, w.eig, st));
-    GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, st));
+    if (zslice_ok && sliced_pays(nev, nev, n))
+        GB_CU(gb::sliced_dsyrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, w.sl, st));
+    else
+        GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, st));
     GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.gw, w.gw_elems, st));
+    if (zslice_ok && sliced_pays(n, nev, nev))
+        GB_CU(gb::sliced_dsymm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.sl, st));
+    else
+        GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.gw, w.gw_elems, st));
     GB_CU(gb::promote_real(n, nev, w.Zns, n, Z, ldz, st));
 
     // ---- tridiagonal -> band (complex back-transformation)
@@ -522,9 +555,17 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         const C *T = (const C *)(w.Tall + (long long)p * b * b * 2);
         C *Zr = Zc + (j + b);
         GB_CU(gb::zpanel_y(m, b, (const double *)panel, ldw, (double *)Y, m, st));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, nev, m, &one, Y, m, Zr, ldz, &zero, S, b));
+        if (use_zsliced(b, nev, m))
+            GB_CU(gb::sliced_zgemm('C', b, nev, m, 1.0, (const double *)Y, m, (const double *)Zr, ldz, 0.0,
+                                   (double *)S, b, w.sl, st));
+        else
+            GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, nev, m, &one, Y, m, Zr, ldz, &zero, S, b));
         GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, S, b, &zero, S2, b));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, Y, m, S2, b, &one, Zr, ldz));
+        if (use_zsliced(m, nev, b))
+            GB_CU(gb::sliced_zgemm('N', m, nev, b, -1.0, (const double *)Y, m, (const double *)S2, b, 1.0,
+                                   (double *)Zr, ldz, w.sl, st));
+        else
+            GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, Y, m, S2, b, &one, Zr, ldz));
     }
     GB_CU(cudaGetLastError());
     return GB_OK;

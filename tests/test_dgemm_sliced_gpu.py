@@ -199,3 +199,96 @@ def test_sliced_syrk_long_sums_of_one_sign(gb, k):
     print(f"k={k} diag max err {np.diag(e).max():.3e} (bound {np.diag(b).min():.3e}), "
           f"offdiag max err {e[np.tril(low, -1)].max() if n > 1 else 0:.3e}")
     assert np.all((e <= b)[low])
+
+
+# ---- complex forms ---------------------------------------------------------
+
+def zdev_cm(X, ld=None):
+    """Column-major complex128 device copy (interleaved), leading dimension ld,
+    padding rows NaN."""
+    r, c = X.shape
+    ld = ld or max(r, 1)
+    buf = np.full((max(c, 1), ld), np.nan + 1j * np.nan)
+    buf[:c, :r] = X.T
+    return torch.from_numpy(buf).cuda(), ld
+
+
+def zbound(opA, opB, alpha, beta, C0):
+    """Complex analogue of bound(): the expanded real product has 2k terms,
+    scaled by the maxima of |Re| and |Im| of the rows and columns."""
+    k = opA.shape[1]
+    amax = np.maximum(np.abs(opA.real), np.abs(opA.imag)).max(axis=1, initial=0.0)[:, None]
+    bmax = np.maximum(np.abs(opB.real), np.abs(opB.imag)).max(axis=0, initial=0.0)[None, :]
+    prod = abs(alpha) * (np.abs(opA) @ np.abs(opB))
+    return 8 * (2 * k + 2) * U * abs(alpha) * amax * bmax + 4 * U * (prod + abs(beta) * np.abs(C0)) + 1e-300
+
+
+def zref(opA, opB, alpha, beta, C0):
+    L = np.clongdouble
+    return L(alpha) * (opA.astype(L) @ opB.astype(L)) + L(beta) * C0.astype(L)
+
+
+def zerr(got, ref):
+    return np.abs(got.astype(np.clongdouble) - ref).astype(np.float64)
+
+
+def crandn(g, shape):
+    return g.uniform(-1, 1, shape) + 1j * g.uniform(-1, 1, shape)
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (37, 29, 13), (64, 64, 64), (130, 70, 200), (64, 300, 2500)])
+@pytest.mark.parametrize("ta", "NC")
+def test_zgemm_sliced(gb, m, n, k, ta):
+    g = np.random.default_rng(m * 7 + n * 3 + k)
+    A = crandn(g, (k, m) if ta == "C" else (m, k))
+    B = crandn(g, (k, n))
+    C0 = crandn(g, (m, n))
+    Ad, lda = zdev_cm(A, A.shape[0] + 2)
+    Bd, ldb = zdev_cm(B, k + 1)
+    Cd, ldc = zdev_cm(C0, m + 3)
+    w, wsb = ws(gb.gb_zgemm_sliced_workspace_bytes(m, n, k))
+    gb.gb_zgemm_sliced(ta, m, n, k, -0.5, Ad, lda, Bd, ldb, 1.5, Cd, ldc, w, wsb, torch.cuda.current_stream())
+    opA = A.conj().T if ta == "C" else A
+    got = Cd.cpu().numpy()[:n, :m].T
+    assert np.all(zerr(got, zref(opA, B, -0.5, 1.5, C0)) <= zbound(opA, B, -0.5, 1.5, C0))
+    assert np.all(np.isnan(Cd.cpu().numpy()[:n, m:ldc].real))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (45, 17), (130, 64), (600, 64)])
+def test_zhemm_sliced_reads_lower_only(gb, m, n):
+    g = np.random.default_rng(m + n)
+    S = crandn(g, (m, m))
+    S = S + S.conj().T                                    # Hermitian, real diagonal
+    S_low = np.tril(S) + np.triu(np.full((m, m), np.nan + 1j * np.nan), 1)
+    S_low[np.diag_indices(m)] += 1j * 7.0                 # the diagonal's imaginary part must be ignored
+    B = crandn(g, (m, n))
+    C0 = crandn(g, (m, n))
+    Sd, lds = zdev_cm(S_low, m + 1)
+    Bd, ldb = zdev_cm(B, m)
+    Cd, ldc = zdev_cm(C0, m + 2)
+    w, wsb = ws(gb.gb_zhemm_sliced_workspace_bytes(m, n))
+    gb.gb_zhemm_sliced(m, n, 1.0, Sd, lds, Bd, ldb, 0.0, Cd, ldc, w, wsb, torch.cuda.current_stream())
+    got = Cd.cpu().numpy()[:n, :m].T
+    assert np.all(zerr(got, zref(S, B, 1.0, 0.0, C0)) <= zbound(S, B, 1.0, 0.0, C0))
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (50, 3), (129, 64), (500, 64)])
+def test_zher2k_sliced_lower_triangle(gb, n, k):
+    g = np.random.default_rng(n * 5 + k)
+    X, Y = crandn(g, (n, k)), crandn(g, (n, k))
+    C0 = crandn(g, (n, n))
+    C0 = C0 + C0.conj().T
+    sentinel = 12345.0 + 0j
+    C0u = np.tril(C0) + np.triu(np.full((n, n), sentinel), 1)
+    Xd, ldx = zdev_cm(X, n + 1)
+    Yd, ldy = zdev_cm(Y, n)
+    Cd, ldc = zdev_cm(C0u, n + 2)
+    w, wsb = ws(gb.gb_zher2k_sliced_workspace_bytes(n, k))
+    gb.gb_zher2k_sliced(n, k, -1.0, Xd, ldx, Yd, ldy, 1.0, Cd, ldc, w, wsb, torch.cuda.current_stream())
+    got = Cd.cpu().numpy()[:n, :n].T
+    XY, YX = np.hstack([X, Y]), np.hstack([Y, X])
+    ref = zref(XY, YX.conj().T, -1.0, 1.0, C0)
+    low = np.tril(np.ones((n, n), dtype=bool))
+    assert np.all((zerr(got, ref) <= zbound(XY, YX.conj().T, -1.0, 1.0, C0))[low])
+    assert np.all(got.imag[np.diag_indices(n)] == 0.0)
+    assert np.all(got[~low] == sentinel)

@@ -23,7 +23,7 @@ def gb():
     return m
 
 
-def solve_z(gb, A, nev, nbw):
+def solve_z(gb, A, nev, nbw, flags=0):
     n = A.shape[0]
     dev = torch.device("cuda")
     A_d = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev)
@@ -32,7 +32,7 @@ def solve_z(gb, A, nev, nbw):
     wsb = gb.gb_solve_workspace_bytes_z(n, nev, nbw)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream()
-    gb.gb_solve_z(n, nev, nbw, A_d, n, ev, Z, n, ws, wsb, st, 0)
+    gb.gb_solve_z(n, nev, nbw, A_d, n, ev, Z, n, ws, wsb, st, flags)
     assert gb.gb_solve_query_z(ws, n, nev, nbw, st) == 0
     return ev.cpu().numpy(), Z.cpu().numpy().T
 
@@ -57,5 +57,19 @@ def test_solve_hermitian_clustered(gb):
     lam = inputs.clustered_spectrum(n, seed=11)
     A = inputs.symmetric_with_spectrum(lam, seed=12, cplx=True)
     w, Z = solve_z(gb, A, nev, 32)
+    assert np.abs(w - lam[:nev]).max() / np.abs(lam).max() <= 1e-11
+    check(A, w, Z, nev)
+
+
+@pytest.mark.parametrize("flags", [0, 4], ids=["sliced_products", "cublas_products"])
+def test_solve_hermitian_large_products_both_paths(gb, flags):
+    """n = 1200: the complex solve's large products (ZHEMM, ZHER2K, the
+    band->full products, the real Newton-Schulz step) take the sliced
+    tensor-core path by default and cuBLAS / DFMA with
+    GB_SOLVE_DFMA_PRODUCTS; both meet the bounds."""
+    n, nev = 1200, 300
+    lam = inputs.clustered_spectrum(n, seed=31)
+    A = inputs.symmetric_with_spectrum(lam, seed=32, cplx=True)
+    w, Z = solve_z(gb, A, nev, 64, flags)
     assert np.abs(w - lam[:nev]).max() / np.abs(lam).max() <= 1e-11
     check(A, w, Z, nev)
