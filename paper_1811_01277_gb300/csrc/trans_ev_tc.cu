@@ -455,23 +455,38 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
             cp_async_wait_all();
             return;
         }
-        // ---- window: carry NB-1 rows, load the rest (rows past n are zero)
+        // ---- window: load the new rows (all of a warp's loads in flight at
+        // once), carry NB-1 rows meanwhile, then store (rows past n are zero)
         const long long row0 = (long long)s0 + (long long)k * b;
-        if (k > 0) {
-            for (int e = threadIdx.x; e < kCols * (kNB - 1); e += kThreads) {
-                const int cc = e / (kNB - 1), j = e % (kNB - 1);
-                Zs[cc * ZROW + j] = Zs[cc * ZROW + j + b];
-            }
-            __syncthreads();
-        }
         {
+            constexpr int H = (LP + 31) / 32;        // row strides of 32 per column
+            constexpr int CW = kCols / (kThreads / 32);  // columns per warp
             const int jlo = (k == 0) ? 0 : kNB - 1;
-            for (int cc = warp; cc < kCols; cc += kThreads / 32) {
-                const int col = col0 + cc;
+            long long v[CW][H];
+#pragma unroll
+            for (int i = 0; i < CW; i++) {
+                const int col = col0 + warp + i * (kThreads / 32);
                 const long long *zc = Zi + (long long)(col < nev ? col : 0) * ldz;
-                for (int j = jlo + lane; j < LP; j += 32) {
-                    const long long r = row0 + j;
-                    Zs[cc * ZROW + j] = (col < nev && j < L && r < n) ? __ldcg(zc + r) : 0ll;
+#pragma unroll
+                for (int h = 0; h < H; h++) {
+                    const int j = jlo + lane + 32 * h;
+                    v[i][h] = (col < nev && j < L && row0 + j < n) ? __ldcg(zc + row0 + j) : 0ll;
+                }
+            }
+            if (k > 0) {
+                for (int e = threadIdx.x; e < kCols * (kNB - 1); e += kThreads) {
+                    const int cc = e / (kNB - 1), j = e % (kNB - 1);
+                    Zs[cc * ZROW + j] = Zs[cc * ZROW + j + b];
+                }
+                __syncthreads();  // carried rows read before the new rows overwrite them
+            }
+#pragma unroll
+            for (int i = 0; i < CW; i++) {
+                const int cc = warp + i * (kThreads / 32);
+#pragma unroll
+                for (int h = 0; h < H; h++) {
+                    const int j = jlo + lane + 32 * h;
+                    if (j < LP) Zs[cc * ZROW + j] = v[i][h];
                 }
             }
         }
