@@ -81,8 +81,9 @@ typedef struct gb_trans_ev_opts {
     int test_hold_group; /* fault-injection hook for tests: when g+1 > 0, sweep
                             group g never publishes its progress so that the
                             next group's wait must give up; 0 = off */
-    int column_batch;    /* PIPELINE only: column blocks per ticket batch,
-                            1..1024 (0 = default 16).  Items of one batch run
+    int column_batch;    /* PIPELINE and PIPELINE_TC: column blocks per ticket
+                            batch, 1..1024 (0 = default: 16, and 8 for
+                            PIPELINE_TC).  Items of one batch run
                             group after group; smaller batches keep fewer
                             eigenvector rows live in L2, larger ones read the
                             reflectors fewer times. */
