@@ -740,6 +740,24 @@ def run_stage_batched(args):
     el = time.perf_counter() - t0
     clocks = sampler.stop()
     per = np.array([a.elapsed_time(b) for a, b in zip(es, ee)])   # last batch, ms
+    # the plain solve on the same problems, one after another on one stream
+    # (every 8th problem: the rate, not the whole batch's time, is compared)
+    sample = list(range(0, len(sizes), 8))
+    pst = torch.cuda.Stream(device=dev)
+    pmax = max(gb.gb_solve_workspace_bytes(sizes[i], sizes[i], gb.gb_solve_default_nbw(sizes[i])) for i in sample)
+    pws = torch.empty(pmax, dtype=torch.uint8, device=dev)
+
+    def plain(i):
+        n_, b_ = sizes[i], gb.gb_solve_default_nbw(sizes[i])
+        gb.gb_solve_d(n_, n_, b_, A[i], n_, ev[i], Z[i], n_, pws, pmax, pst, 0)
+
+    plain(sample[0])
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for i in sample:
+        plain(i)
+    torch.cuda.synchronize(dev)
+    plain_rate = len(sample) / (time.perf_counter() - t1)
     # accuracy on a few problems
     worst = 0.0
     for i in range(0, len(sizes), max(1, len(sizes) // 8)):
@@ -754,6 +772,8 @@ def run_stage_batched(args):
         "host_issue_seconds_per_batch": issue / args.steps,
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "streams": len(streams), "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+        "plain_solve_one_at_a_time": {"value": plain_rate, "unit": "solves/s", "sample": f"every 8th problem ({len(sample)})",
+                                      "speedup_of_batched": (args.steps * len(sizes) / el) / plain_rate},
         "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks}))
     return 0
 
@@ -800,12 +820,27 @@ def run_stage_serve(args):
     done = srv.run(reqs)
     clocks = sampler.stop()
     summ = serve.latency_summary(done)
+    # the plain solve on the same requests, one after another on one stream
+    pst = torch.cuda.Stream(device=dev)
+    pmax = max(gb.gb_solve_workspace_bytes_z(r.n, r.nev, gb.gb_solve_default_nbw(r.n)) for r in reqs)
+    pws = torch.empty(pmax, dtype=torch.uint8, device=dev)
+    pev = torch.empty(max(r.nev for r in reqs), dtype=torch.float64, device=dev)
+    pZ = torch.empty(max(r.n * r.nev for r in reqs), dtype=torch.complex128, device=dev)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for r in reqs:
+        b_ = gb.gb_solve_default_nbw(r.n)
+        gb.gb_solve_z(r.n, r.nev, b_, r.A, r.n, pev, pZ, r.n, pws, pmax, pst, 0)
+    torch.cuda.synchronize(dev)
+    plain_rate = len(reqs) / (time.perf_counter() - t1)
     print(json.dumps({
         "stage": "serve", "metric": "served complex Hermitian eigensolves: solves/s and latency",
         "value": summ["solves_per_s"], "unit": "solves/s", "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
         "max_ms": summ["max_ms"], "requests": summ["requests"], "arrival_rate_per_s": args.serve_rate,
         "sizes": sizes, "systems": args.serve_systems, "repeats": args.serve_repeats, "slots": args.serve_slots,
         "hbm_budget_gb": args.serve_budget_gb, "failed": sum(1 for r in done if r.status != 0),
+        "plain_solve_one_at_a_time": {"value": plain_rate, "unit": "solves/s", "sample": "the same requests",
+                                      "speedup_of_served": summ["solves_per_s"] / plain_rate},
         "dtype": "complex128", "data": "synthetic Hermitian, A <- A + 1e-3 E per re-submission",
         "clocks": clocks}))
     return 0
