@@ -537,7 +537,8 @@ def run_stage_solve(args):
     n, nev, nbw = args.solve_n, args.solve_nev, args.solve_nbw
     cplx = args.complex
     dev = torch.device("cuda", 0)
-    lam = torch.from_numpy(inputs.clustered_spectrum(n, seed=n)).to(dev)
+    spec = inputs.gapped_uniform_spectrum if args.spectrum == "uniform-gapped" else inputs.clustered_spectrum
+    lam = torch.from_numpy(spec(n, seed=n)).to(dev)
     A = prescribed_symmetric_gpu(lam, 256, seed=n + 1, dev=dev, cplx=cplx)
     Acm = A.T.contiguous() if cplx else A       # column-major storage (A Hermitian: A^T = conj(A))
     ev = torch.zeros(nev, dtype=torch.float64, device=dev)
@@ -572,7 +573,7 @@ def run_stage_solve(args):
     ms = e0.elapsed_time(e1) / args.steps
     F, Fst = solve_flops(n, nev, nbw, cplx)
     stages = None
-    if not cplx:
+    if not cplx and not args.no_stages:
         step(gb.GB_SOLVE_RECORD_STAGES)        # one more solve, outside the timed region
         stages = gb.gb_solve_stage_ms(st)
     # accuracy: eigenvalues against the prescribed ones, residual and
@@ -590,7 +591,9 @@ def run_stage_solve(args):
                                     f"{'complex128 Hermitian' if cplx else 'real FP64'}",
         "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "seconds_per_solve": ms / 1e3,
         "steps": args.steps, "warmup": args.warmup, "status": status, "dtype": "f64",
-        "data": "synthetic: A = Q diag(clustered spectrum) Q^T, Q a product of 256 seeded Householders",
+        "data": ("synthetic: A = Q diag(uniform [-1,1] spectrum, 10% in clusters with 1e-6 gaps) Q^T"
+                 if args.spectrum == "uniform-gapped" else "synthetic: A = Q diag(clustered spectrum) Q^T")
+                + ", Q a product of 256 seeded Householders",
         "stage_ms": stages,
         "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12,
@@ -895,6 +898,9 @@ def main():
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
     ap.add_argument("--complex", action="store_true", help="solve stage: complex128 Hermitian")
+    ap.add_argument("--spectrum", choices=["clustered", "uniform-gapped"], default="clustered",
+                    help="solve stage: clustered in [-50, 50] (1e-8 clusters), or uniform in [-1, 1] with 1e-6 gaps")
+    ap.add_argument("--no-stages", action="store_true", help="solve stage: skip the extra stage-timing solve")
     ap.add_argument("--dfma-products", action="store_true",
                     help="solve stage: run the real solve's products on the FP64 FMA pipe (not sliced)")
     ap.add_argument("--emulated-gemm", action="store_true",

@@ -121,6 +121,20 @@ def clustered_spectrum(n, seed, lo_exp=-3.0, hi=50.0, cluster_frac=0.1, cluster_
     return np.sort(np.array(lam[:n]))
 
 
+def gapped_uniform_spectrum(n, seed, cluster_frac=0.1, cluster_size=8, gap=1e-6):
+    """Eigenvalues uniform in [-1, 1], with cluster_frac of them in groups of
+    cluster_size whose consecutive members are `gap` apart (eigenvector
+    clusters of condition ~1/gap).  Sorted ascending."""
+    g = _rng(seed + 16180)
+    ncl = int(round(n * cluster_frac / cluster_size))
+    nfree = n - ncl * cluster_size
+    lam = list(g.uniform(-1.0, 1.0, nfree))
+    span = (cluster_size - 1) * gap
+    for c in g.uniform(-1.0, 1.0 - span, ncl):
+        lam.extend(c + gap * np.arange(cluster_size))
+    return np.sort(np.array(lam[:n]))
+
+
 def symmetric_with_spectrum(lam, seed, cplx=False):
     """A = Q diag(lam) Q^H with Q Haar-distributed (QR of a Gaussian matrix,
     phases fixed by R's diagonal); exactly symmetric (Hermitian)."""

@@ -313,3 +313,14 @@ def test_two_stage_toeplitz_closed_form():
     k = np.arange(1, n + 1)
     assert np.abs(w - np.sort(2 - 2 * np.cos(k * np.pi / (n + 1)))).max() <= 50 * n * U * 4
     assert np.linalg.norm(B @ Z - Z * w) / np.linalg.norm(B) <= 50 * n * U
+
+
+def test_gapped_uniform_spectrum():
+    """The n = 32768 workload's spectrum: in [-1, 1], sorted, n values, and
+    10% of them in runs of 8 whose neighbours are 1e-6 apart."""
+    lam = inputs.gapped_uniform_spectrum(4096, seed=3)
+    assert lam.shape == (4096,) and np.all(np.diff(lam) >= 0)
+    assert lam.min() >= -1.0 and lam.max() <= 1.0
+    gaps = np.diff(lam)
+    close = np.isclose(gaps, 1e-6, rtol=1e-6, atol=0)
+    assert close.sum() >= 51 * 7 * 0.95   # 51 clusters x 7 inner gaps (a few may merge with free values)
