@@ -893,7 +893,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-lo", type=int, default=128)
     ap.add_argument("--batch-hi", type=int, default=2048)
-    ap.add_argument("--batch-streams", type=int, default=8)
+    ap.add_argument("--batch-streams", type=int, default=16)
     ap.add_argument("--solve-n", type=int, default=16384)
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
