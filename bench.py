@@ -909,7 +909,7 @@ def main():
     ap.add_argument("--serve-sizes", default="512,1024,2048")
     ap.add_argument("--serve-systems", type=int, default=6)
     ap.add_argument("--serve-repeats", type=int, default=10)
-    ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--serve-slots", type=int, default=12)
     ap.add_argument("--serve-budget-gb", type=int, default=64)
     ap.add_argument("--chase-n", type=int, default=16384)
     ap.add_argument("--chase-b", type=int, default=64)
