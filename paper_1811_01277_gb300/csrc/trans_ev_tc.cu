@@ -14,7 +14,7 @@
 // by the inverse factors),
 //     Z_win <- Z_win - U (V^T Z_win).
 // Both products run on mma.sync bf16 by exact digit slicing (see
-// dgemm_sliced.cuh): V^T and U are cut into eight 7-bit digits per entry
+// dgemm_sliced.cuh): V^T and U are cut into nine 7-bit digits per entry
 // against per-row powers of two, once per tile, by tc_tile_prep.
 //
 // Z itself is held as 64-bit fixed point per column for the whole call:
@@ -58,14 +58,14 @@ struct Win {
     // a warp (rows g, columns 2t) take the minimum two wavefronts, and even
     // for the 16-byte fragment loads
     static constexpr int ZROW = (LP + 4) / 16 * 16 + 4 + ((LP + 4) % 16 > 4 ? 16 : 0);
-    // tile record in global memory, 256-byte multiple: V^T planes [8][16][LP],
-    // U planes [8][LP][16] (bf16), exponents eV[16], eU[LP]
+    // tile record in global memory, 256-byte multiple: V^T planes [9][16][LP],
+    // U planes [9][LP][16] (bf16), exponents eV[16], eU[LP]
     static constexpr size_t VT_BYTES = (size_t)kDigits * kNB * LP * 2;
     static constexpr size_t U_BYTES = (size_t)kDigits * LP * kNB * 2;
     static constexpr size_t E_BYTES = (size_t)(kNB + LP) * 4;
     static constexpr size_t REC = (VT_BYTES + U_BYTES + E_BYTES + 255) / 256 * 256;
     // shared memory of the main kernel: the record (same layout, 16-byte
-    // chunks XOR-swizzled), W planes [8][64][16], window [64][ZROW] int64
+    // chunks XOR-swizzled), W planes [9][64][16], window [64][ZROW] int64
     static constexpr size_t S_WP = (size_t)kDigits * kCols * kNB * 2;
     static constexpr size_t S_Z = (size_t)kCols * ZROW * 8;
     static constexpr size_t S_EC = (size_t)kCols * 4;
@@ -380,11 +380,11 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
     using W = Win<B>;
     constexpr int L = W::L, LP = W::LP, ZROW = W::ZROW;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint16_t *VtP = (uint16_t *)smem;                                  // [8][16][LP]
-    uint16_t *UP = (uint16_t *)(smem + W::VT_BYTES);                   // [8][LP][16]
+    uint16_t *VtP = (uint16_t *)smem;                                  // [9][16][LP]
+    uint16_t *UP = (uint16_t *)(smem + W::VT_BYTES);                   // [9][LP][16]
     const int *eV = (const int *)(smem + W::VT_BYTES + W::U_BYTES);   // [16]
     const int *eU = eV + kNB;                                          // [LP]
-    uint16_t *WP = (uint16_t *)(smem + W::REC);                        // [8][64][16]
+    uint16_t *WP = (uint16_t *)(smem + W::REC);                        // [9][64][16]
     long long *Zs = (long long *)(smem + W::REC + W::S_WP);            // [64][ZROW]
     int *Es = (int *)(smem + W::REC + W::S_WP + W::S_Z);               // [64]
     __shared__ int s_item, s_abort;
