@@ -601,7 +601,8 @@ def run_stage_solve(args):
                      "note": "algorithmic FP64 flops of the whole solve against the FP64 DFMA peak; real "
                              "solve: large products on the bf16 tensor cores by exact digit slicing (FP64 "
                              "accuracy; the DFMA kernels with --dfma-products), the rest in DFMA kernels; "
-                             "complex solve: cuBLAS ZGEMM/ZHEMM/ZHER2K for the complex products"},
+                             "complex solve: the large complex products sliced the same way (2 x 2 real "
+                             "blocks), the b x b ones in cuBLAS ZGEMM"},
         "accuracy": {"max_dlambda_over_norm": dlam, "residual_rel_fro": resid, "orth_max": orth,
                      "bound_50nu": 50 * n * u, "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
         "clocks": clocks}))
@@ -781,6 +782,60 @@ def run_stage_batched(args):
     return 0
 
 
+def run_stage_trans_ev_z(args):
+    """The complex128 back-transformation alone: synthetic unitary reflectors
+    (the bulge chase's layout) applied to Gaussian Z, timed with CUDA events
+    on the launching stream; FP64 TFLOP/s on the algorithmic flops
+    (16 nev per reflector element: one complex dot and one complex update)."""
+    import numpy as np
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    from paper_1811_01277_gb300 import inputs
+    gbuild.build()
+    gb.load()
+    n, nev, nbw = args.zn, args.znev, args.solve_nbw
+    dev = torch.device("cuda", 0)
+    hv, ht = inputs.synthetic_reflectors(n, nbw, seed=n, cplx=True)
+    Z = inputs.z_gaussian(n, nev, seed=nev, cplx=True)
+    hv_d = torch.from_numpy(np.ascontiguousarray(hv)).to(dev)
+    ht_d = torch.from_numpy(np.ascontiguousarray(ht)).to(dev)
+    Zt = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)     # column-major n x nev data
+    wsb = gb.gb_trans_ev_workspace_bytes(n, nbw, nev, 1, None)
+    ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        gb.gb_trans_ev_tridi_to_band_z(n, nbw, nev, hv_d, ht_d, Zt, n, ws if wsb else None, wsb, st, None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    status = gb.gb_trans_ev_query(ws if wsb else None, wsb, st)
+    ms = e0.elapsed_time(e1) / args.steps
+    F = algorithmic_flops(n, nev, cplx=True)
+    # unitary reflectors keep every column's norm
+    norms = torch.linalg.norm(Zt, dim=1).cpu().numpy()
+    drift = float(np.max(np.abs(norms / np.linalg.norm(Z, axis=0) - 1.0)))
+    print(json.dumps({
+        "stage": "trans_ev_z", "metric": f"complex128 trans_ev_tridi_to_band s at n={n}, nev={nev}, nbw={nbw}",
+        "value": 1e3 / ms, "unit": "back-transforms/s", "ms_per_step": ms, "steps": args.steps,
+        "warmup": args.warmup, "status": status, "dtype": "complex128", "variant": "library default",
+        "data": "synthetic unitary reflectors (v0 = 1, v U[-1,1]/sqrt(len), tau = (1 - e^{i theta})/|v|^2), Z iid N(0,1/n)",
+        "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12},
+        "column_norm_drift_max": drift, "clocks": clocks}))
+    return 0
+
+
 def run_stage_serve(args):
     """Poisson stream of complex Hermitian requests through the
     continuous-batching server: `systems` systems with sizes drawn from
@@ -888,7 +943,7 @@ def main():
     ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
                     help="walk the autotuner first and time its fastest setting")
     ap.add_argument("--measure-fp64-peak", action="store_true")
-    ap.add_argument("--stage", choices=["trans_ev", "band_to_tridi", "solve", "batched", "serve", "gemm"],
+    ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm"],
                     default="trans_ev")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-lo", type=int, default=128)
@@ -898,6 +953,8 @@ def main():
     ap.add_argument("--solve-nev", type=int, default=4096)
     ap.add_argument("--solve-nbw", type=int, default=64)
     ap.add_argument("--complex", action="store_true", help="solve stage: complex128 Hermitian")
+    ap.add_argument("--zn", type=int, default=8192, help="trans_ev_z stage: n")
+    ap.add_argument("--znev", type=int, default=2048, help="trans_ev_z stage: nev")
     ap.add_argument("--spectrum", choices=["clustered", "uniform-gapped"], default="clustered",
                     help="solve stage: clustered in [-50, 50] (1e-8 clusters), or uniform in [-1, 1] with 1e-6 gaps")
     ap.add_argument("--no-stages", action="store_true", help="solve stage: skip the extra stage-timing solve")
@@ -922,6 +979,8 @@ def main():
         return run_stage_gemm(args)
     if args.stage == "batched":
         return run_stage_batched(args)
+    if args.stage == "trans_ev_z":
+        return run_stage_trans_ev_z(args)
     if args.stage == "serve":
         return run_stage_serve(args)
     if args.measure_fp64_peak:
