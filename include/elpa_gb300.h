@@ -251,6 +251,16 @@ int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *strea
  * band->full) of the last gb_solve_d on this stream that had
  * GB_SOLVE_RECORD_STAGES set; ms has 7 entries.  Synchronises the stream. */
 int gb_solve_stage_ms(void *stream, float *ms);
+/* The solvers cache per (device, stream) a cuBLAS handle (complex solve),
+ * a look-ahead helper stream with its events (n >= 4096) and the stage
+ * events; they are created on first use and otherwise kept until the
+ * process exits.  gb_solve_release frees those of `stream` on the current
+ * device, or of every stream on every device if all_streams is nonzero.
+ * Call it only when no solve is in flight on the streams concerned (it
+ * waits for the helper streams).  A later solve on such a stream creates
+ * them again.  Returns GB_OK, or GB_ERR_CUDA if a CUDA or cuBLAS call
+ * failed (the cache entries are dropped either way). */
+int gb_solve_release(void *stream, int all_streams);
 /* Convenience form with host-side defaults: nbw = min(64, n-1), legacy
  * default stream, and a workspace it allocates with cudaMalloc and frees
  * before returning (synchronous).  All pointers are device pointers. */

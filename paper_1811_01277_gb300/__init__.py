@@ -15,7 +15,7 @@ from ._lib import (  # noqa: F401
     GB_AUTOTUNE_FAST, GB_AUTOTUNE_MEDIUM, elpa_b200_solve, gb_autotune_best, gb_autotune_create,
     gb_autotune_destroy, gb_autotune_load, gb_autotune_progress, gb_autotune_report, gb_autotune_save,
     gb_autotune_step, gb_solve_batched_d, gb_solve_batched_workspace_bytes, gb_solve_d,
-    gb_solve_default_nbw, gb_solve_stage_ms, gb_solve_workspace_bytes_z, gb_solve_z, gb_solve_query_z, GB_SOLVE_RECORD_STAGES, SOLVE_STAGES, gb_solve_query, gb_solve_workspace_bytes, load,
+    gb_solve_default_nbw, gb_solve_stage_ms, gb_solve_release, gb_solve_workspace_bytes_z, gb_solve_z, gb_solve_query_z, GB_SOLVE_RECORD_STAGES, SOLVE_STAGES, gb_solve_query, gb_solve_workspace_bytes, load,
     gb_dgemm, gb_dgemm_workspace_bytes, gb_dsymm, gb_dsyr2k, gb_dsyrk,
     GB_SOLVE_DFMA_PRODUCTS, gb_dgemm_sliced, gb_dgemm_sliced_workspace_bytes, gb_dsymm_sliced,
     gb_dsymm_sliced_workspace_bytes, gb_dsyr2k_sliced, gb_dsyr2k_sliced_workspace_bytes, gb_dsyrk_sliced,

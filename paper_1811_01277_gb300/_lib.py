@@ -32,6 +32,7 @@ EXPORTS = (
     "gb_autotune_create", "gb_autotune_destroy", "gb_autotune_step", "gb_autotune_report",
     "gb_autotune_best", "gb_autotune_progress", "gb_autotune_save", "gb_autotune_load",
     "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d", "gb_solve_stage_ms",
+    "gb_solve_release",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
@@ -112,6 +113,7 @@ def load(path=None):
     L.gb_autotune_load.argtypes = [ctypes.c_char_p]; L.gb_autotune_load.restype = p
     L.gb_solve_default_nbw.argtypes = [i]; L.gb_solve_default_nbw.restype = i
     L.gb_solve_stage_ms.argtypes = [p, ctypes.POINTER(ctypes.c_float)]; L.gb_solve_stage_ms.restype = i
+    L.gb_solve_release.argtypes = [p, i]; L.gb_solve_release.restype = i
     L.gb_band_to_tridi_workspace_bytes_z.argtypes = [i, i]; L.gb_band_to_tridi_workspace_bytes_z.restype = sz
     L.gb_band_to_tridi_z.argtypes = [i, i, p, i, p, p, p, p, p, sz, p]; L.gb_band_to_tridi_z.restype = i
     L.gb_solve_workspace_bytes_z.argtypes = [i, i, i]; L.gb_solve_workspace_bytes_z.restype = sz
@@ -353,6 +355,13 @@ def gb_solve_stage_ms(stream=None):
     if rc != GB_OK:
         raise GbError(rc, "gb_solve_stage_ms")
     return dict(zip(SOLVE_STAGES, [float(x) for x in ms]))
+
+
+def gb_solve_release(stream=None, all_streams=False, check=True):
+    rc = load().gb_solve_release(_stream(stream), int(bool(all_streams)))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_release")
+    return rc
 
 
 def gb_solve_default_nbw(n):

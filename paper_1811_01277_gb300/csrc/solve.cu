@@ -578,6 +578,56 @@ int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *strea
     return gb_trans_ev_query(w.chase, w.chase_bytes, stream);
 }
 
+int gb_solve_release(void *stream, int all_streams)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    const cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    auto match = [&](const std::pair<int, cudaStream_t> &k) {
+        return all_streams || (k.first == dev && k.second == st);
+    };
+    int rc = GB_OK;
+    auto on_device = [&](int d) {  // resources are destroyed with their own device current
+        if (cudaSetDevice(d) != cudaSuccess) rc = GB_ERR_CUDA;
+    };
+    for (auto it = g_blas.begin(); it != g_blas.end();) {
+        if (!match(it->first)) {
+            ++it;
+            continue;
+        }
+        on_device(it->first.first);
+        if (cublasDestroy(it->second) != CUBLAS_STATUS_SUCCESS) rc = GB_ERR_CUDA;
+        it = g_blas.erase(it);
+    }
+    for (auto it = g_lookahead.begin(); it != g_lookahead.end();) {
+        if (!match(it->first)) {
+            ++it;
+            continue;
+        }
+        on_device(it->first.first);
+        const Lookahead &la = it->second;
+        if (cudaStreamSynchronize(la.side) != cudaSuccess) rc = GB_ERR_CUDA;
+        cudaEventDestroy(la.start);
+        cudaEventDestroy(la.ready);
+        cudaEventDestroy(la.factored);
+        if (cudaStreamDestroy(la.side) != cudaSuccess) rc = GB_ERR_CUDA;
+        it = g_lookahead.erase(it);
+    }
+    for (auto it = g_stage_events.begin(); it != g_stage_events.end();) {
+        if (!match(it->first)) {
+            ++it;
+            continue;
+        }
+        on_device(it->first.first);
+        for (int i = 0; i <= kStages; i++) cudaEventDestroy(it->second[i]);
+        delete[] it->second;
+        it = g_stage_events.erase(it);
+    }
+    if (cudaSetDevice(dev) != cudaSuccess) rc = GB_ERR_CUDA;
+    return rc;
+}
+
 int gb_solve_stage_ms(void *stream, float *ms)
 {
     if (!ms) return -2;
