@@ -162,6 +162,18 @@ def _p(x):
     raise TypeError(f"cannot take a pointer of {type(x)}")
 
 
+
+def _dp(x):
+    """Pointer of an argument the library dereferences on the device: a CUDA
+    tensor, a raw integer address or None.  Host tensors and arrays are
+    refused here, before a kernel could read them."""
+    if hasattr(x, "is_cuda") and not x.is_cuda:
+        raise TypeError("expected a CUDA tensor (device memory), got a host tensor")
+    if hasattr(x, "ctypes") and not hasattr(x, "data_ptr"):
+        raise TypeError("expected device memory, got a host array")
+    return _p(x)
+
+
 def _opts(o):
     if o is None:
         return None
@@ -196,8 +208,8 @@ def gb_trans_ev_workspace_bytes(n, nbw, nev, is_complex=0, opts=None):
 
 def gb_trans_ev_tridi_to_band_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, workspace=None, ws_bytes=0,
                                 stream=None, opts=None, check=True):
-    rc = load().gb_trans_ev_tridi_to_band_d(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
-                                            _p(workspace), ws_bytes, _stream(stream), _opts(opts))
+    rc = load().gb_trans_ev_tridi_to_band_d(n, nbw, nev, _dp(hh_v), _dp(hh_tau), _dp(Z), ldz,
+                                            _dp(workspace), ws_bytes, _stream(stream), _opts(opts))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_trans_ev_tridi_to_band_d")
     return rc
@@ -205,8 +217,8 @@ def gb_trans_ev_tridi_to_band_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, workspace=Non
 
 def gb_trans_ev_tridi_to_band_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, workspace=None, ws_bytes=0,
                                 stream=None, opts=None, check=True):
-    rc = load().gb_trans_ev_tridi_to_band_z(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
-                                            _p(workspace), ws_bytes, _stream(stream), _opts(opts))
+    rc = load().gb_trans_ev_tridi_to_band_z(n, nbw, nev, _dp(hh_v), _dp(hh_tau), _dp(Z), ldz,
+                                            _dp(workspace), ws_bytes, _stream(stream), _opts(opts))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_trans_ev_tridi_to_band_z")
     return rc
@@ -219,7 +231,7 @@ def gb_trans_ev_host_buffer_bytes(n, nbw, nev, ldz, is_complex=0, opts=None):
 def gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, hh_v, hh_tau, Z, ldz, dev_buf, dev_bytes,
                                      stream=None, opts=None, check=True):
     rc = load().gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
-                                                 _p(dev_buf), dev_bytes, _stream(stream), _opts(opts))
+                                                 _dp(dev_buf), dev_bytes, _stream(stream), _opts(opts))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_trans_ev_tridi_to_band_d_host")
     return rc
@@ -230,14 +242,14 @@ def gb_trans_ev_launch_count(n, nbw, nev, is_complex=0, opts=None):
 
 
 def gb_trans_ev_query(workspace=None, ws_bytes=0, stream=None):
-    return load().gb_trans_ev_query(_p(workspace), ws_bytes, _stream(stream))
+    return load().gb_trans_ev_query(_dp(workspace), ws_bytes, _stream(stream))
 
 
 def gb_trans_ev_tridi_to_band_d_noalloc(n, nbw, nev, hh_v, hh_tau, Z, ldz, status=None, stream=None,
                                         check=True):
     """No-allocation form for callers that cannot allocate device memory
     (scratch in a fixed device array of GB_NOALLOC_SCRATCH_BYTES)."""
-    rc = load().gb_trans_ev_tridi_to_band_d_noalloc(n, nbw, nev, _p(hh_v), _p(hh_tau), _p(Z), ldz,
+    rc = load().gb_trans_ev_tridi_to_band_d_noalloc(n, nbw, nev, _dp(hh_v), _dp(hh_tau), _dp(Z), ldz,
                                                     _p(status), _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_trans_ev_tridi_to_band_d_noalloc")
@@ -249,7 +261,7 @@ def gb_band_to_tridi_workspace_bytes(n, nbw):
 
 
 def gb_band_to_tridi_d(n, nbw, AB, ldab, d, e, hh_v, hh_tau, workspace, ws_bytes, stream=None, check=True):
-    rc = load().gb_band_to_tridi_d(n, nbw, _p(AB), ldab, _p(d), _p(e), _p(hh_v), _p(hh_tau), _p(workspace),
+    rc = load().gb_band_to_tridi_d(n, nbw, _dp(AB), ldab, _dp(d), _dp(e), _dp(hh_v), _dp(hh_tau), _dp(workspace),
                                    ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_band_to_tridi_d")
@@ -261,7 +273,7 @@ def gb_solve_workspace_bytes(n, nev, nbw):
 
 
 def gb_solve_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream=None, flags=0, check=True):
-    rc = load().gb_solve_d(n, nev, nbw, _p(A), lda, _p(ev), _p(Z), ldz, _p(workspace), ws_bytes,
+    rc = load().gb_solve_d(n, nev, nbw, _dp(A), lda, _dp(ev), _dp(Z), ldz, _dp(workspace), ws_bytes,
                            _stream(stream), flags)
     if check and rc != GB_OK:
         raise GbError(rc, "gb_solve_d")
@@ -269,11 +281,11 @@ def gb_solve_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream=None
 
 
 def gb_solve_query(workspace, n, nev, nbw, stream=None):
-    return load().gb_solve_query(_p(workspace), n, nev, nbw, _stream(stream))
+    return load().gb_solve_query(_dp(workspace), n, nev, nbw, _stream(stream))
 
 
 def elpa_b200_solve(n, nev, A, lda, ev, Z, ldz, check=True):
-    rc = load().elpa_b200_solve(n, nev, _p(A), lda, _p(ev), _p(Z), ldz)
+    rc = load().elpa_b200_solve(n, nev, _dp(A), lda, _dp(ev), _dp(Z), ldz)
     if check and rc != GB_OK:
         raise GbError(rc, "elpa_b200_solve")
     return rc
@@ -326,7 +338,7 @@ def gb_band_to_tridi_workspace_bytes_z(n, nbw):
 
 
 def gb_band_to_tridi_z(n, nbw, AB, ldab, d, e, hh_v, hh_tau, workspace, ws_bytes, stream=None, check=True):
-    rc = load().gb_band_to_tridi_z(n, nbw, _p(AB), ldab, _p(d), _p(e), _p(hh_v), _p(hh_tau), _p(workspace),
+    rc = load().gb_band_to_tridi_z(n, nbw, _dp(AB), ldab, _dp(d), _dp(e), _dp(hh_v), _dp(hh_tau), _dp(workspace),
                                    ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_band_to_tridi_z")
@@ -338,7 +350,7 @@ def gb_solve_workspace_bytes_z(n, nev, nbw):
 
 
 def gb_solve_z(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream=None, flags=0, check=True):
-    rc = load().gb_solve_z(n, nev, nbw, _p(A), lda, _p(ev), _p(Z), ldz, _p(workspace), ws_bytes,
+    rc = load().gb_solve_z(n, nev, nbw, _dp(A), lda, _dp(ev), _dp(Z), ldz, _dp(workspace), ws_bytes,
                            _stream(stream), flags)
     if check and rc != GB_OK:
         raise GbError(rc, "gb_solve_z")
@@ -346,7 +358,7 @@ def gb_solve_z(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream=None
 
 
 def gb_solve_query_z(workspace, n, nev, nbw, stream=None):
-    return load().gb_solve_query_z(_p(workspace), n, nev, nbw, _stream(stream))
+    return load().gb_solve_query_z(_dp(workspace), n, nev, nbw, _stream(stream))
 
 
 def gb_solve_stage_ms(stream=None):
@@ -373,7 +385,7 @@ def _iarr(xs):
 
 
 def _parr(xs):
-    return (ctypes.c_void_p * len(xs))(*[_p(x) if x is not None else None for x in xs])
+    return (ctypes.c_void_p * len(xs))(*[_dp(x) if x is not None else None for x in xs])
 
 
 def gb_solve_batched_workspace_bytes(n, nev, nslots):
@@ -396,7 +408,7 @@ def gb_solve_batched_d(n, nev, A, lda, ev, Z, ldz, workspace, ws_bytes, streams,
     es = (ctypes.c_void_p * len(ev_start))(*[handle(e) for e in ev_start]) if ev_start else None
     ee = (ctypes.c_void_p * len(ev_end))(*[handle(e) for e in ev_end]) if ev_end else None
     rc = load().gb_solve_batched_d(len(n), _iarr(n), _iarr(nev), _parr(A), _iarr(lda), _parr(ev), _parr(Z),
-                                   _iarr(ldz), _p(workspace), ws_bytes, len(streams), st, es, ee)
+                                   _iarr(ldz), _dp(workspace), ws_bytes, len(streams), st, es, ee)
     if check and rc != GB_OK:
         raise GbError(rc, "gb_solve_batched_d")
     return rc
@@ -412,8 +424,8 @@ def _c(ch):
 
 def gb_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace=None, ws_bytes=0,
              stream=None, check=True):
-    rc = load().gb_dgemm(_c(transa), _c(transb), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc,
-                         _p(workspace), ws_bytes, _stream(stream))
+    rc = load().gb_dgemm(_c(transa), _c(transb), m, n, k, alpha, _dp(A), lda, _dp(B), ldb, beta, _dp(C), ldc,
+                         _dp(workspace), ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dgemm")
     return rc
@@ -421,7 +433,7 @@ def gb_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, works
 
 def gb_dsymm(side, m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace=None, ws_bytes=0, stream=None,
              check=True):
-    rc = load().gb_dsymm(_c(side), m, n, alpha, _p(S), lds, _p(B), ldb, beta, _p(C), ldc, _p(workspace),
+    rc = load().gb_dsymm(_c(side), m, n, alpha, _dp(S), lds, _dp(B), ldb, beta, _dp(C), ldc, _dp(workspace),
                          ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsymm")
@@ -429,14 +441,14 @@ def gb_dsymm(side, m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace=None, ws
 
 
 def gb_dsyr2k(n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None, check=True):
-    rc = load().gb_dsyr2k(n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc, _stream(stream))
+    rc = load().gb_dsyr2k(n, k, alpha, _dp(A), lda, _dp(B), ldb, beta, _dp(C), ldc, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsyr2k")
     return rc
 
 
 def gb_dsyrk(n, k, alpha, A, lda, beta, C, ldc, stream=None, check=True):
-    rc = load().gb_dsyrk(n, k, alpha, _p(A), lda, beta, _p(C), ldc, _stream(stream))
+    rc = load().gb_dsyrk(n, k, alpha, _dp(A), lda, beta, _dp(C), ldc, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsyrk")
     return rc
@@ -448,8 +460,8 @@ def gb_dgemm_sliced_workspace_bytes(m, n, k):
 
 def gb_dgemm_sliced(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes,
                     stream=None, check=True):
-    rc = load().gb_dgemm_sliced(_c(transa), _c(transb), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc,
-                                _p(workspace), ws_bytes, _stream(stream))
+    rc = load().gb_dgemm_sliced(_c(transa), _c(transb), m, n, k, alpha, _dp(A), lda, _dp(B), ldb, beta, _dp(C), ldc,
+                                _dp(workspace), ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dgemm_sliced")
     return rc
@@ -461,7 +473,7 @@ def gb_dsymm_sliced_workspace_bytes(side, m, n):
 
 def gb_dsymm_sliced(side, m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None,
                     check=True):
-    rc = load().gb_dsymm_sliced(_c(side), m, n, alpha, _p(S), lds, _p(B), ldb, beta, _p(C), ldc, _p(workspace),
+    rc = load().gb_dsymm_sliced(_c(side), m, n, alpha, _dp(S), lds, _dp(B), ldb, beta, _dp(C), ldc, _dp(workspace),
                                 ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsymm_sliced")
@@ -473,7 +485,7 @@ def gb_dsyr2k_sliced_workspace_bytes(n, k):
 
 
 def gb_dsyr2k_sliced(n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
-    rc = load().gb_dsyr2k_sliced(n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc, _p(workspace), ws_bytes,
+    rc = load().gb_dsyr2k_sliced(n, k, alpha, _dp(A), lda, _dp(B), ldb, beta, _dp(C), ldc, _dp(workspace), ws_bytes,
                                  _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsyr2k_sliced")
@@ -485,7 +497,7 @@ def gb_dsyrk_sliced_workspace_bytes(n, k):
 
 
 def gb_dsyrk_sliced(n, k, alpha, A, lda, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
-    rc = load().gb_dsyrk_sliced(n, k, alpha, _p(A), lda, beta, _p(C), ldc, _p(workspace), ws_bytes,
+    rc = load().gb_dsyrk_sliced(n, k, alpha, _dp(A), lda, beta, _dp(C), ldc, _dp(workspace), ws_bytes,
                                 _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dsyrk_sliced")
@@ -498,8 +510,8 @@ def gb_zgemm_sliced_workspace_bytes(m, n, k):
 
 def gb_zgemm_sliced(transa, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None,
                     check=True):
-    rc = load().gb_zgemm_sliced(_c(transa), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta, _p(C), ldc,
-                                _p(workspace), ws_bytes, _stream(stream))
+    rc = load().gb_zgemm_sliced(_c(transa), m, n, k, alpha, _dp(A), lda, _dp(B), ldb, beta, _dp(C), ldc,
+                                _dp(workspace), ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_zgemm_sliced")
     return rc
@@ -510,7 +522,7 @@ def gb_zhemm_sliced_workspace_bytes(m, n):
 
 
 def gb_zhemm_sliced(m, n, alpha, S, lds, B, ldb, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
-    rc = load().gb_zhemm_sliced(m, n, alpha, _p(S), lds, _p(B), ldb, beta, _p(C), ldc, _p(workspace), ws_bytes,
+    rc = load().gb_zhemm_sliced(m, n, alpha, _dp(S), lds, _dp(B), ldb, beta, _dp(C), ldc, _dp(workspace), ws_bytes,
                                 _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_zhemm_sliced")
@@ -522,7 +534,7 @@ def gb_zher2k_sliced_workspace_bytes(n, k):
 
 
 def gb_zher2k_sliced(n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, workspace, ws_bytes, stream=None, check=True):
-    rc = load().gb_zher2k_sliced(n, k, alpha, _p(X), ldx, _p(Y), ldy, beta, _p(C), ldc, _p(workspace), ws_bytes,
+    rc = load().gb_zher2k_sliced(n, k, alpha, _dp(X), ldx, _dp(Y), ldy, beta, _dp(C), ldc, _dp(workspace), ws_bytes,
                                  _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_zher2k_sliced")

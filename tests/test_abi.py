@@ -4,6 +4,7 @@ oracle; invalid arguments are rejected before anything touches a GPU."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle
@@ -89,3 +90,21 @@ def test_launch_count_is_host_only(lib):
     c = gb.gb_trans_ev_launch_count(n, b, 1024, opts={"variant": 1, "sweeps_per_tile": 16})
     G = (n - 1 + 15) // 16
     assert G <= c <= G + (n + b - 1) // b
+
+
+def test_device_arguments_refuse_host_memory(lib):
+    """The binding refuses host tensors and arrays where the library reads
+    device memory, before anything is called; raw addresses and None pass."""
+    torch = pytest.importorskip("torch")
+    h = torch.zeros(16, dtype=torch.float64)
+    a = np.zeros(16)
+    with pytest.raises(TypeError):
+        gb.gb_trans_ev_tridi_to_band_d(10, 3, 2, h, h, h, 10, check=False)
+    with pytest.raises(TypeError):
+        gb.gb_solve_d(4, 4, 2, a, 4, a, a, 4, None, 0, None, 0, check=False)
+    with pytest.raises(TypeError):
+        gb.gb_dgemm_sliced("N", "N", 2, 2, 2, 1.0, h, 2, h, 2, 0.0, h, 2, None, 0, None, check=False)
+    with pytest.raises(TypeError):
+        gb.gb_solve_batched_d([4], [4], [h], [4], [h], [h], [4], None, 0, [0], check=False)
+    # argument checks on raw addresses still reach the library
+    assert gb.gb_trans_ev_tridi_to_band_d(10, 3, 2, 256, 256, 256, 9, check=False) == -7
