@@ -58,13 +58,14 @@ def measured_peaks():
 def tc_executed_flops(n, nbw, nev):
     """bf16 tensor-core flops one pipeline_tc call executes: per tile (16
     sweeps) and 64-column item, W = V^T Z (16 x LP x 64) and dZ = U W
-    (LP x 16 x 64), each over the 43 digit-plane pairs (i + j <= 8 of 8 x 8),
-    LP = nbw + 15 rounded up to 16."""
+    (LP x 16 x 64), each over the 53 digit-plane pairs (i + j <= 9 of nine
+    digits per operand), LP = nbw + 15 rounded up to 16."""
     lp = (nbw + 15 + 15) // 16 * 16
     G = (n - 1 + 15) // 16
     tiles = sum((n - (1 + 16 * g) + nbw - 1) // nbw for g in range(G))
     items = tiles * ((nev + 63) // 64)
-    return items * 43 * 2 * (2 * 16 * lp * 64)
+    pairs = sum(min(9, 10 - i) for i in range(9))     # 53
+    return items * pairs * 2 * (2 * 16 * lp * 64)
 
 
 def algorithmic_flops(n, nev, cplx=False):
