@@ -89,6 +89,25 @@ def test_tc_columns_of_different_norms(gb):
     assert colwise_err(out, ref, Z) <= 50 * n * U
 
 
+def test_tc_columns_at_the_fixed_point_edge(gb):
+    """Columns whose one entry holds the whole norm and sits just below a
+    power of two (the tightest column scale), and columns of identity: each
+    stays within 50 n u of the oracle and keeps its norm."""
+    n, b, nev = 700, 64, 12
+    hv, ht = inputs.synthetic_reflectors(n, b, seed=41)
+    Z = np.zeros((n, nev), order="F")
+    below = np.nextafter(1.0, 0.0)                      # 1 - 2^-53
+    for c in range(nev):
+        Z[(37 * c + 5) % n, c] = below * (2.0 ** (c - 6)) * (-1) ** c
+    Z[:, 11] = 0.0
+    Z[0, 11] = 1.0
+    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    assert rc == 0 and q == 0
+    ref = oracle.trans_ev(n, b, hv, ht, Z)
+    assert colwise_err(out, ref, Z) <= 50 * n * U
+    assert np.abs(np.linalg.norm(out, axis=0) / np.linalg.norm(Z, axis=0) - 1.0).max() <= 50 * n * U
+
+
 def test_tc_eigenvectors_residual(gb):
     """Z_in = tridiagonal eigenvectors from the oracle's chase + QL: the
     output satisfies B Z = Z Lambda and Z^T Z = I to 50 n u."""
