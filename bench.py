@@ -24,7 +24,7 @@ import sys
 import time
 
 # Solves overlapping on many streams (batched and serve stages) need as many
-# hardware work queues; the driver reads this before the CUDA context exists.
+# hardware work queues; the CUDA driver reads this before the context exists.
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -38,13 +38,13 @@ WORKLOADS = {
 # FP64 DFMA: 2 lanes per clock per SM on GB300 (1.25 TFLOP/s nominal at the
 # 2070 MHz maximum SM clock over 152 SMs: 152 * 2 * 2 flop * 2.07e9).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FP64_DFMA_MEASURED_TFLOPS = 1.256  # DFMA microbenchmark on this machine's GB300 (profiles/)
+FP64_DFMA_MEASURED_TFLOPS = 1.256  # DFMA microbenchmark on a GB300 (profiles/)
 MMA_SYNC_BF16_TFLOPS = 606.0       # bf16 mma.sync m16n8k16 microbenchmark, same part (profiles/)
 
 
 def measured_peaks():
-    """The measured peaks (MEASURED_PEAKS.json), or the profiling
-    recipe's fallback figures when the file is absent."""
+    """The measured copy bandwidth and cuBLAS bf16 rates (MEASURED_PEAKS.json),
+    or fallback figures from an earlier GB300 measurement when the file is absent."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
