@@ -18,10 +18,9 @@
 // against per-row powers of two, once per tile, by tc_tile_prep.
 //
 // Z itself is held as 64-bit fixed point per column for the whole call:
-// z = Zi 2^(E_c - 62) with ||z_c||_2 < 2^(E_c - 2), so |Zi| < 2^60 (a factor
-// of two below the 2^61 the digits cut exactly, so that rounding can never
-// carry an entry that holds nearly all of its column's norm past it) and
-// every update |dZi| <= 2 ||z|| 2^(62 - E_c) < 2^61.  Householder reflectors
+// z = Zi 2^(E_c - 62) with ||z_c||_2 < 2^(E_c - 1) (and a margin of at least
+// 2^-30 of that bound, see tc_col_scale), so |Zi| < 2^61 and every update
+// |dZi| <= 2 ||z|| 2^(62 - E_c) < 2^62.  Householder reflectors
 // are orthogonal, so every entry of every intermediate column stays below
 // its initial 2-norm: one scale per column serves the whole sweep, digits
 // come straight from the integer's bits, each level's tensor-core sum is
@@ -112,10 +111,14 @@ __device__ __forceinline__ long long shift_ll(long long x, int sh)
 
 // ---- column scales and fixed-point conversion ----------------------------
 
-// E_c with ||z_c||_2 < 2^(E_c - 2), one warp per column.  The sum of squares
+// E_c with ||z_c||_2 < 2^(E_c - 1), one warp per column.  The sum of squares
 // is taken on the column scaled by 2^-em (max|z| < 2^em, an exact scaling),
 // so it neither overflows nor underflows: ||z||^2 < 2^(e2 + 2 em) gives
-// E_c = ceil(e2 / 2) + em + 2 (0 for a zero column).
+// E_c = ceil(e2 / 2) + em + 1 (0 for a zero column).  For even e2 the bound
+// is tight, and where ||z|| sits within 2^-30 of it, E_c takes one more bit.
+// Rounding (of s, and of the fixed-point updates) can then never carry an
+// entry past 2^61, even if the whole norm gathers in it: digit 0 stays
+// below 128.
 __global__ void __launch_bounds__(256) tc_col_scale(int n, int nev, const double *__restrict__ Z, long long ldz,
                                                     int *__restrict__ E)
 {
@@ -146,7 +149,9 @@ __global__ void __launch_bounds__(256) tc_col_scale(int n, int nev, const double
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int e2 = exponent_above((unsigned long long)__double_as_longlong(s));
-        E[c] = ((e2 + 1) >> 1) + em + 2;
+        int ec = ((e2 + 1) >> 1) + em + 1;
+        if (!(e2 & 1) && s > scale_by_pow2(1.0 - 0x1p-29, e2)) ec += 1;  // 1/4 <= s < n: -1 <= e2 <= 32
+        E[c] = ec;
     }
 }
 
@@ -538,7 +543,7 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
             long long hi[4], lo[4];
             fold_levels<true>(acc, hi, lo);
             // W in the column's fixed point (Wi = W 2^(62 - E_c) = S 2^(eV + 47):
-            // the digits of Z stand for 2^(E_c - 1) sum d_s 2^(-7(s+1)); |Wi| < 2^60
+            // the digits of Z stand for 2^(E_c - 1) sum d_s 2^(-7(s+1)); |Wi| < 2^61
             // since |v_q^T z| <= ||z||), cut into digits: WP[s][c][q], chunk of
             // q swizzled by c
 #pragma unroll
