@@ -38,8 +38,11 @@ WORKLOADS = {
 # FP64 DFMA: 2 lanes per clock per SM on GB300 (1.25 TFLOP/s nominal at the
 # 2070 MHz maximum SM clock over 152 SMs: 152 * 2 * 2 flop * 2.07e9).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FP64_DFMA_MEASURED_TFLOPS = 1.256  # DFMA microbenchmark on a GB300 (profiles/)
-MMA_SYNC_BF16_TFLOPS = 606.0       # bf16 mma.sync m16n8k16 microbenchmark, same part (profiles/)
+# measured constants of this part (one GB300, SM clock 2070 MHz throughout;
+# profiles/fp64_peak_and_variant_sweep.md): the DFMA pipe and the legacy
+# warp-level bf16 mma.sync m16n8k16 path
+FP64_DFMA_MEASURED_TFLOPS = 1.256
+MMA_SYNC_BF16_TFLOPS = 606.0
 
 
 def measured_peaks():
@@ -238,7 +241,9 @@ def run_reference(args, wl):
     return 0
 
 
-METRIC = "trans_ev_tridi_to_band throughput at n=16384, nev=4096 (25% vecs), nbw=64 (1/value = solve s)"
+METRIC = ("solve s at n=16384 (25% vecs); trans_ev % of FP64 peak; batched solves/s, p99 -- value: "
+          "trans_ev_tridi_to_band back-transforms/s at n=16384, nev=4096, nbw=64 (FP64 accuracy); "
+          "keys solve (full two-stage solve at that size) and batched (512 problems) carry the rest")
 
 
 def config_of(wl):
@@ -406,6 +411,24 @@ def run_ours(args, wl):
                 f: getattr(opts, f) for f, _ in gb.gb_trans_ev_opts._fields_}
         if tuned:
             line["autotune"] = tuned
+        if world == 1 and not args.no_extra:
+            # the rest of the metric: the full solve at the same size (one
+            # warm-up, one timed solve) and the 512-problem batch (one warm-up
+            # batch, one timed batch), after the back-transformation's buffers
+            # are released
+            del Z_d, hv_d, ht_d, ws
+            if e2e is not None:
+                del buf, hv_h, ht_h, Z_h
+            torch.cuda.empty_cache()
+            sv = measure_solve(n, nev, nbw, steps=1, warmup=1, record_stages=False)
+            line["solve"] = {"seconds_per_solve": sv["seconds_per_solve"], "n": n, "nev": nev, "nbw": nbw,
+                             "status": sv["status"], "accuracy": sv["accuracy"], "roofline": sv["roofline"],
+                             "steps": 1, "warmup": 1, "data": sv["data"], "clocks": sv["clocks"]}
+            bt = measure_batched(512, 128, 2048, 16, steps=1, warmup=1)
+            line["batched"] = {k_: bt[k_] for k_ in ("solves_per_s", "p50_ms", "p99_ms", "seconds_per_batch",
+                                                     "streams", "plain_solve_one_at_a_time",
+                                                     "accuracy_worst_over_50nu", "data", "clocks", "metric")}
+            line["batched"].update(steps=1, warmup=1)
         print(json.dumps(line))
     return 0
 
@@ -525,20 +548,19 @@ def prescribed_symmetric_gpu(lam, k, seed, dev, cplx=False):
     return 0.5 * (A + A.conj().T)
 
 
-def run_stage_solve(args):
-    """Time gb_solve_d (full two-stage solve) on A = Q L Q^T with a clustered
-    spectrum L; checks the eigenvalues against L and reports one JSON line."""
-    import numpy as np
+def measure_solve(n, nev, nbw, cplx=False, spectrum="clustered", steps=1, warmup=1, dfma_products=False,
+                  emulated_gemm=False, record_stages=True):
+    """Time gb_solve_d / gb_solve_z (the full two-stage solve) on A = Q L Q^T
+    with a prescribed spectrum L, and check the eigenvalues against L and the
+    residual and orthogonality on all nev columns.  Returns a dict."""
     import torch
     import paper_1811_01277_gb300 as gb
     from paper_1811_01277_gb300 import build as gbuild
     from paper_1811_01277_gb300 import inputs
     gbuild.build()
     gb.load()
-    n, nev, nbw = args.solve_n, args.solve_nev, args.solve_nbw
-    cplx = args.complex
-    dev = torch.device("cuda", 0)
-    spec = inputs.gapped_uniform_spectrum if args.spectrum == "uniform-gapped" else inputs.clustered_spectrum
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = inputs.gapped_uniform_spectrum if spectrum == "uniform-gapped" else inputs.clustered_spectrum
     lam = torch.from_numpy(spec(n, seed=n)).to(dev)
     A = prescribed_symmetric_gpu(lam, 256, seed=n + 1, dev=dev, cplx=cplx)
     Acm = A.T.contiguous() if cplx else A       # column-major storage (A Hermitian: A^T = conj(A))
@@ -548,8 +570,8 @@ def run_stage_solve(args):
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream(dev)
 
-    base_flags = gb.GB_SOLVE_FP64_EMULATED_GEMM if args.emulated_gemm else 0
-    if args.dfma_products:
+    base_flags = gb.GB_SOLVE_FP64_EMULATED_GEMM if emulated_gemm else 0
+    if dfma_products:
         base_flags |= gb.GB_SOLVE_DFMA_PRODUCTS
 
     def step(flags=0):
@@ -559,22 +581,22 @@ def run_stage_solve(args):
         else:
             gb.gb_solve_d(n, nev, nbw, Acm, n, ev, Z, n, ws, wsb, st, flags)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(st)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     status = (gb.gb_solve_query_z if cplx else gb.gb_solve_query)(ws, n, nev, nbw, st)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     F, Fst = solve_flops(n, nev, nbw, cplx)
     stages = None
-    if not cplx and not args.no_stages:
+    if not cplx and record_stages:
         step(gb.GB_SOLVE_RECORD_STAGES)        # one more solve, outside the timed region
         stages = gb.gb_solve_stage_ms(st)
     # accuracy: eigenvalues against the prescribed ones, residual and
@@ -584,29 +606,45 @@ def run_stage_solve(args):
     dlam = (ev - lam[:nev]).abs().max().item() / anorm
     R = A @ Zc - Zc * ev[None, :].to(Zc.dtype)
     resid = (torch.linalg.norm(R) / torch.linalg.norm(A)).item()
+    del R
     orth = (Zc.conj().T @ Zc - torch.eye(nev, dtype=Zc.dtype, device=dev)).abs().max().item()
     u = 2.0 ** -53
-    print(json.dumps({
-        "emulated_gemm": bool(args.emulated_gemm), "products": "dfma" if args.dfma_products else "sliced",
-        "stage": "solve", "metric": f"two-stage eigensolve s at n={n} ({100 * nev // n}% vecs), nbw={nbw}, "
-                                    f"{'complex128 Hermitian' if cplx else 'real FP64'}",
+    out = {
+        "emulated_gemm": bool(emulated_gemm), "products": "dfma" if dfma_products else "sliced",
+        "metric": f"two-stage eigensolve s at n={n} ({100 * nev // n}% vecs), nbw={nbw}, "
+                  f"{'complex128 Hermitian' if cplx else 'real FP64'}",
+        "n": n, "nev": nev, "nbw": nbw,
         "value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "seconds_per_solve": ms / 1e3,
-        "steps": args.steps, "warmup": args.warmup, "status": status, "dtype": "f64",
+        "steps": steps, "warmup": warmup, "status": status, "dtype": "f64",
         "data": ("synthetic: A = Q diag(uniform [-1,1] spectrum, 10% in clusters with 1e-6 gaps) Q^T"
-                 if args.spectrum == "uniform-gapped" else "synthetic: A = Q diag(clustered spectrum) Q^T")
+                 if spectrum == "uniform-gapped" else "synthetic: A = Q diag(clustered spectrum) Q^T")
                 + ", Q a product of 256 seeded Householders",
         "stage_ms": stages,
         "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12,
                      "by_stage_tflop": {k_: v_ / 1e12 for k_, v_ in Fst.items()},
-                     "note": "algorithmic FP64 flops of the whole solve against the FP64 DFMA peak; real "
-                             "solve: large products on the bf16 tensor cores by exact digit slicing (FP64 "
-                             "accuracy; the DFMA kernels with --dfma-products), the rest in DFMA kernels; "
-                             "complex solve: the large complex products sliced the same way (2 x 2 real "
-                             "blocks), the b x b ones in cuBLAS ZGEMM"},
+                     "note": "algorithmic FP64 flops of the whole solve against the FP64 DFMA peak; "
+                             "large products on the bf16 tensor cores by exact digit slicing (FP64 "
+                             "accuracy; the DFMA kernels with --dfma-products), the rest in DFMA kernels"},
         "accuracy": {"max_dlambda_over_norm": dlam, "residual_rel_fro": resid, "orth_max": orth,
-                     "bound_50nu": 50 * n * u, "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
-        "clocks": clocks}))
+                     "bound_50nu": 50 * n * u,
+                     "within": bool(dlam <= 1e-11 and resid <= 50 * n * u and orth <= 50 * n * u)},
+        "clocks": clocks}
+    del A, Acm, Z, ws, ev
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_stage_solve(args):
+    """Time gb_solve_d (full two-stage solve) on A = Q L Q^T with a clustered
+    spectrum L; checks the eigenvalues against L and reports one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    r = measure_solve(args.solve_n, args.solve_nev, args.solve_nbw, cplx=args.complex, spectrum=args.spectrum,
+                      steps=args.steps, warmup=args.warmup, dfma_products=args.dfma_products,
+                      emulated_gemm=args.emulated_gemm, record_stages=not args.no_stages)
+    r = dict(stage="solve", **r)
+    print(json.dumps(r))
     return 0
 
 
@@ -703,19 +741,21 @@ def run_stage_gemm(args):
     return 0
 
 
-def run_stage_batched(args):
+def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
     """Many independent problems (sizes U[lo, hi], N(0,1) entries symmetrised,
     all eigenpairs) through gb_solve_batched_d on several streams: solves/s
-    over the whole batch and p50/p99 of the per-solve times."""
+    over the whole batch, p50/p99 of the per-solve times, and the plain
+    gb_solve_d one problem at a time on every `plain_every`-th problem for
+    comparison.  Returns a dict."""
     import numpy as np
     import torch
     import paper_1811_01277_gb300 as gb
     from paper_1811_01277_gb300 import build as gbuild
     gbuild.build()
     gb.load()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     g = np.random.default_rng(512)
-    sizes = [int(x) for x in g.integers(args.batch_lo, args.batch_hi + 1, args.batch_count)]
+    sizes = [int(x) for x in g.integers(lo, hi + 1, count)]
     gen = torch.Generator(device=dev).manual_seed(513)
     A = []
     for n in sizes:
@@ -723,7 +763,7 @@ def run_stage_batched(args):
         A.append(0.5 * (R + R.T))
     ev = [torch.zeros(n, dtype=torch.float64, device=dev) for n in sizes]
     Z = [torch.zeros((n, n), dtype=torch.float64, device=dev) for n in sizes]
-    streams = [torch.cuda.Stream(device=dev) for _ in range(args.batch_streams)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(nstreams)]
     wsb = gb.gb_solve_batched_workspace_bytes(sizes, sizes, len(streams))
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     es = [torch.cuda.Event(enable_timing=True) for _ in sizes]
@@ -733,12 +773,12 @@ def run_stage_batched(args):
         gb.gb_solve_batched_d(sizes, sizes, A, sizes, ev, Z, sizes, ws, wsb, streams,
                               es if events else None, ee if events else None)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch(False)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         batch(True)
     issue = time.perf_counter() - t0          # host time to issue the work
     torch.cuda.synchronize(dev)
@@ -746,8 +786,8 @@ def run_stage_batched(args):
     clocks = sampler.stop()
     per = np.array([a.elapsed_time(b) for a, b in zip(es, ee)])   # last batch, ms
     # the plain solve on the same problems, one after another on one stream
-    # (every 8th problem: the rate, not the whole batch's time, is compared)
-    sample = list(range(0, len(sizes), 8))
+    # (every plain_every-th problem: the rate, not the whole batch's time, is compared)
+    sample = list(range(0, len(sizes), plain_every))
     pst = torch.cuda.Stream(device=dev)
     pmax = max(gb.gb_solve_workspace_bytes(sizes[i], sizes[i], gb.gb_solve_default_nbw(sizes[i])) for i in sample)
     pws = torch.empty(pmax, dtype=torch.uint8, device=dev)
@@ -771,15 +811,28 @@ def run_stage_batched(args):
         r = torch.linalg.norm(A[i] @ Zi - Zi * ev[i][None, :]) / torch.linalg.norm(A[i])
         o = (Zi.T @ Zi - torch.eye(n, dtype=torch.float64, device=dev)).abs().max()
         worst = max(worst, float(r) / (50 * n * 2.0 ** -53), float(o) / (50 * n * 2.0 ** -53))
-    print(json.dumps({
-        "stage": "batched", "metric": f"batched eigensolves/s, {len(sizes)} problems n~U[{args.batch_lo},{args.batch_hi}], all eigenpairs",
-        "value": args.steps * len(sizes) / el, "unit": "solves/s", "seconds_per_batch": el / args.steps,
-        "host_issue_seconds_per_batch": issue / args.steps,
+    rate = steps * len(sizes) / el
+    out = {
+        "metric": f"batched eigensolves/s, {len(sizes)} problems n~U[{lo},{hi}], all eigenpairs",
+        "value": rate, "unit": "solves/s", "solves_per_s": rate, "seconds_per_batch": el / steps,
+        "host_issue_seconds_per_batch": issue / steps,
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
-        "streams": len(streams), "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
-        "plain_solve_one_at_a_time": {"value": plain_rate, "unit": "solves/s", "sample": f"every 8th problem ({len(sample)})",
-                                      "speedup_of_batched": (args.steps * len(sizes) / el) / plain_rate},
-        "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks}))
+        "streams": len(streams), "steps": steps, "warmup": warmup, "dtype": "f64",
+        "plain_solve_one_at_a_time": {"value": plain_rate, "unit": "solves/s",
+                                      "sample": f"every {plain_every}th problem ({len(sample)})",
+                                      "speedup_of_batched": rate / plain_rate},
+        "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks}
+    del A, Z, ev, ws, pws
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_stage_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = measure_batched(args.batch_count, args.batch_lo, args.batch_hi, args.batch_streams, steps=args.steps,
+                        warmup=args.warmup)
+    print(json.dumps(dict(stage="batched", **r)))
     return 0
 
 
@@ -905,28 +958,6 @@ def run_stage_serve(args):
     return 0
 
 
-def measure_fp64_peak():
-    """Build and run the FP64 microbenchmark (DFMA and f64 mma.sync) with the
-    SM clock sampled, and print one JSON line."""
-    src = os.path.join(ROOT, "paper_1811_01277_gb300", "microbench", "fp64_peak.cu")
-    exe = os.path.join(ROOT, "paper_1811_01277_gb300", "_build", "fp64_peak")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True)
-    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-    out = subprocess.run([exe, "2.0"], capture_output=True, text=True, check=True).stdout
-    clocks = sampler.stop()
-    res = {}
-    for line in out.splitlines():
-        parts = line.split()
-        res[parts[0]] = {"tflops": float(parts[1]), "seconds": float(parts[2])}
-    mhz = clocks["sm_mhz"] if clocks else None
-    if mhz:
-        for v in res.values():
-            v["flop_per_clk_per_sm"] = v["tflops"] * 1e12 / (152 * mhz * 1e6)
-    print(json.dumps({"fp64_peak": res, "clocks": clocks}))
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -943,7 +974,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
                     help="walk the autotuner first and time its fastest setting")
-    ap.add_argument("--measure-fp64-peak", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default stage: skip the solve and batched measurements that complete the metric")
     ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm"],
                     default="trans_ev")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -984,8 +1016,6 @@ def main():
         return run_stage_trans_ev_z(args)
     if args.stage == "serve":
         return run_stage_serve(args)
-    if args.measure_fp64_peak:
-        return measure_fp64_peak()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)

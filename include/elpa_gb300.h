@@ -54,6 +54,10 @@ extern "C" {
 #define GB_ERR_TIMEOUT 2     /* a device-side dependency wait exceeded its bound */
 #define GB_ERR_WORKSPACE 3   /* workspace pointer NULL/misaligned or too small */
 #define GB_ERR_UNSUPPORTED 4 /* valid arguments outside what this build supports */
+#define GB_ERR_NONFINITE 5   /* Z held NaN or Inf (tensor-core variants): those columns come back
+                                as all NaN, the other columns are exact results */
+#define GB_ERR_RANGE 6       /* a column left its fixed-point range (tensor-core variants): the
+                                reflectors were not orthogonal / unitary; Z is unspecified but finite */
 
 /* Kernel variants for gb_trans_ev_opts.variant. */
 #define GB_VARIANT_AUTO 0      /* library picks: PIPELINE_TC for real data with nbw in
@@ -141,7 +145,11 @@ int gb_trans_ev_tridi_to_band_d_host(int n, int nbw, int nev, const double *hh_v
 
 /* Completion status of the device work of earlier calls that used this
  * workspace: synchronises the stream, then returns GB_OK, GB_ERR_TIMEOUT (a
- * PIPELINE dependency wait gave up; Z is then unspecified) or GB_ERR_CUDA.
+ * PIPELINE dependency wait gave up; Z is then unspecified), GB_ERR_NONFINITE
+ * (tensor-core variants: Z held NaN or Inf; those columns are returned as
+ * all NaN, the others are exact), GB_ERR_RANGE (tensor-core variants: a
+ * column left its fixed-point range because the reflectors were not
+ * orthogonal; Z is unspecified but finite) or GB_ERR_CUDA.
  * workspace may be NULL (WAVEFRONT calls need none): then only the stream is
  * synchronised. */
 int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream);
@@ -163,8 +171,10 @@ long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex,
  * a problem needing more (gb_trans_ev_workspace_bytes with variant PIPELINE,
  * sweeps_per_tile 16, cols_per_block 64) is rejected with GB_ERR_WORKSPACE
  * before anything is launched (n = 16384, nev = 4096 needs 256.25 KiB).
- * The first call on a device looks the array's address up on that device
- * (make it before any stream capture).  All calls share the array and it
+ * Every call looks the array's address up on the current device (this
+ * allocates nothing, and stays right if the context is re-created); the
+ * first call on a device loads the array there, so make it before any
+ * stream capture.  All calls share the array and it
  * keeps the last call's contents; each call clears what must start at zero,
  * and calls whose device work overlaps on the GPU race on it.
  * status (argument 8) may be NULL, or a device or pinned-host int that

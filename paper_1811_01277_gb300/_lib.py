@@ -17,6 +17,8 @@ GB_ERR_CUDA = 1
 GB_ERR_TIMEOUT = 2
 GB_ERR_WORKSPACE = 3
 GB_ERR_UNSUPPORTED = 4
+GB_ERR_NONFINITE = 5
+GB_ERR_RANGE = 6
 GB_VARIANT_AUTO = 0
 GB_VARIANT_WAVEFRONT = 1
 GB_VARIANT_PIPELINE = 2

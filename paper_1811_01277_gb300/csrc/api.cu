@@ -280,6 +280,8 @@ const char *gb_status_string(int status)
     case GB_ERR_TIMEOUT: return "a device-side dependency wait exceeded its bound";
     case GB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case GB_ERR_UNSUPPORTED: return "arguments valid but not supported by this build";
+    case GB_ERR_NONFINITE: return "Z held NaN or Inf; those columns were returned as NaN";
+    case GB_ERR_RANGE: return "a column left its fixed-point range (reflectors not orthogonal); Z unspecified";
     default: break;
     }
     if (status < 0) return "invalid argument (status -i names argument i)";

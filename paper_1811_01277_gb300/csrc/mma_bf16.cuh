@@ -56,11 +56,14 @@ __device__ __forceinline__ uint16_t bf16_digit(int d, int s, bool neg)
 }
 
 // Row exponent e with max|row| < 2^e from the bit pattern of the row's
-// largest magnitude (0 for an all-zero row).
+// largest magnitude (0 for an all-zero row).  A subnormal maximum m 2^-1074
+// with m < 2^L gives e = L - 1074.
 __device__ __forceinline__ int exponent_above(unsigned long long maxbits)
 {
     const int ex = (int)(maxbits >> 52) & 0x7ff;
-    return ex ? ex - 1022 : 0;
+    if (ex) return ex - 1022;
+    if (!maxbits) return 0;
+    return (64 - __clzll((long long)maxbits)) - 1074;
 }
 
 // Y = round(|x| 2^(56 - e)) for |x| < 2^e, at most 2^56 - 1: the 56-bit

@@ -11,18 +11,20 @@
 // the library's module is loaded on a device and held until the process
 // exits.
 //
-// In host code the array's name is only a host-side stand-in, so the device
-// address is looked up with cudaGetSymbolAddress, once per device, with that
-// device current, on the first call made on it.  That first call should come
-// before any stream capture.  Every call then reuses the same array: the
-// pipeline launcher clears it (cudaMemsetAsync, no allocation) before each
-// launch, and calls whose device work overlaps on the GPU race on it.  The
-// device-side status word is copied (cudaMemcpyAsync, no allocation) to the
-// caller's optional status int after the kernel, in stream order.
+// In host code the array's name is only a host-side stand-in, so every call
+// looks up the device address with cudaGetSymbolAddress, with the call's
+// device current (the lookup allocates nothing).  Looking it up each time,
+// rather than caching it per device, keeps the address right after a
+// cudaDeviceReset or any other re-creation of the device's primary context,
+// which loads the module again and may place the array elsewhere.  The first
+// call on a device loads the module there, so it should come before any
+// stream capture.  Every call reuses the same array: the pipeline launcher
+// clears it (cudaMemsetAsync, no allocation) before each launch, and calls
+// whose device work overlaps on the GPU race on it.  The device-side status
+// word is copied (cudaMemcpyAsync, no allocation) to the caller's optional
+// status int after the kernel, in stream order.
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include <mutex>
 
 #include "elpa_gb300.h"
 #include "layout.cuh"
@@ -32,30 +34,19 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GB_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
 constexpr long long kNoallocSpinPolls = 1LL << 40;
 constexpr long long kNoallocTimeoutNs = 10LL * 1000 * 1000 * 1000;
 constexpr int kNoallocNb = 16;       // same tiling as the library default
 constexpr int kNoallocThreads = 64;
 
-std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up on
+// every call (no cache that could outlive the context).
 cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -33,6 +33,7 @@
 #include "elpa_gb300.h"
 #include "layout.cuh"
 #include "mma_bf16.cuh"
+#include "tc_fixed.cuh"
 #include "trans_ev_kernels.cuh"
 
 namespace gb {
@@ -75,112 +76,7 @@ struct Win {
     static_assert((LP / 8) % 2 == 0, "V^T rows hold an even number of 16-byte chunks");
 };
 
-__device__ __forceinline__ int ld_acquire(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int *p, int v)
-{
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long now_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-struct TcState {  // head of the workspace (zeroed before every launch)
-    int ticket;
-    int abort;
-    int error;
-};
-
-// x * 2^sh for a 64-bit integer, rounded to nearest when sh < 0 (so that
-// the rescaling adds no bias)
-__device__ __forceinline__ long long shift_ll(long long x, int sh)
-{
-    if (sh >= 0) return x << sh;
-    if (sh <= -63) return 0;
-    return (x + (1ll << (-sh - 1))) >> -sh;
-}
-
-// ---- column scales and fixed-point conversion ----------------------------
-
-// E_c with ||z_c||_2 < 2^(E_c - 1), one warp per column.  The sum of squares
-// is taken on the column scaled by 2^-em (max|z| < 2^em, an exact scaling),
-// so it neither overflows nor underflows: ||z||^2 < 2^(e2 + 2 em) gives
-// E_c = ceil(e2 / 2) + em + 1 (0 for a zero column).  For even e2 the bound
-// is tight, and where ||z|| sits within 2^-30 of it, E_c takes one more bit.
-// Rounding (of s, and of the fixed-point updates) can then never carry an
-// entry past 2^61, even if the whole norm gathers in it: digit 0 stays
-// below 128.
-__global__ void __launch_bounds__(256) tc_col_scale(int n, int nev, const double *__restrict__ Z, long long ldz,
-                                                    int *__restrict__ E)
-{
-    const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (c >= nev) return;
-    const double *z = Z + (long long)c * ldz;
-    unsigned long long m = 0;
-    for (int r = lane; r < n; r += 32) {
-        const unsigned long long u = (unsigned long long)__double_as_longlong(z[r]) & ~(1ull << 63);
-        m = u > m ? u : m;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
-        m = u > m ? u : m;
-    }
-    if (m == 0) {
-        if (lane == 0) E[c] = 0;
-        return;
-    }
-    const int em = exponent_above(m);
-    double s = 0.0;
-    for (int r = lane; r < n; r += 32) {
-        const double x = scale_by_pow2(z[r], -em);
-        s = fma(x, x, s);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-        const int e2 = exponent_above((unsigned long long)__double_as_longlong(s));
-        int ec = ((e2 + 1) >> 1) + em + 1;
-        if (!(e2 & 1) && s > scale_by_pow2(1.0 - 0x1p-29, e2)) ec += 1;  // 1/4 <= s < n: -1 <= e2 <= 32
-        E[c] = ec;
-    }
-}
-
-// In place: z -> round(z 2^(62 - E_c)) as int64 (to_fixed) or back (from_fixed).
-__global__ void __launch_bounds__(256) tc_convert(int n, int nev, double *__restrict__ Z, long long ldz,
-                                                  const int *__restrict__ E, int to_fixed)
-{
-    for (int c = blockIdx.y; c < nev; c += gridDim.y) {
-        const int e = E[c];
-        double *z = Z + (long long)c * ldz;
-        long long *zi = (long long *)z;
-        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-            if (to_fixed) zi[r] = __double2ll_rn(scale_by_pow2(z[r], 62 - e));
-            else z[r] = scale_by_pow2(__ll2double_rn(zi[r]), e - 62);
-        }
-    }
-}
-
 // ---- per-tile V^T and U digit planes ---------------------------------------
-
-__global__ void tc_tile_offsets(int n, int b, int G, long long *__restrict__ off)
-{
-    long long acc = 0;
-    for (int g = 0; g < G; g++) {
-        off[g] = acc;
-        acc += group_tiles(n, b, kNB, g);
-    }
-    off[G] = acc;
-}
 
 template <int B>
 __global__ void __launch_bounds__(128) tc_tile_prep(int n, const double *__restrict__ hh_v,
@@ -612,7 +508,11 @@ pipeline_tc(int n, int nev, long long *__restrict__ Zi, long long ldz, const int
                 long long *zc = Zi + (long long)col * ldz;
                 for (int j = lane; j < jhi; j += 32) {
                     const long long r = row0 + j;
-                    if (r < n) zc[r] = Zs[cc * ZROW + j];
+                    if (r < n) {
+                        const long long v = Zs[cc * ZROW + j];
+                        if (tc_out_of_range(v)) tc_set_error(state, GB_ERR_RANGE);
+                        zc[r] = v;
+                    }
                 }
             }
         }
@@ -662,9 +562,9 @@ cudaError_t run_tc(int n, int nev, const double *hh_v, const double *hh_tau, dou
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(progress, 0xff, (size_t)G * C * 4, st)) != cudaSuccess) return e;
     const dim3 conv_grid((n + 255) / 256 < 64 ? (n + 255) / 256 : 64, nev < 65535 ? nev : 65535);
-    tc_col_scale<<<(nev + 7) / 8, 256, 0, st>>>(n, nev, Z, ldz, E);
+    tc_col_scale<<<(nev + 7) / 8, 256, 0, st>>>(n, nev, Z, ldz, E, state);
     tc_convert<<<conv_grid, 256, 0, st>>>(n, nev, Z, ldz, E, 1);
-    tc_tile_offsets<<<1, 1, 0, st>>>(n, B, G, toff);
+    tc_tile_offsets<<<1, 1, 0, st>>>(n, B, kNB, G, toff);
     tc_tile_prep<B><<<dim3(group_tiles(n, B, kNB, 0), G), 128, 0, st>>>(n, hh_v, hh_tau, toff, rec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pipeline_tc<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W::SMEM)) !=

@@ -34,6 +34,7 @@ class Request:
     done: float = None
     status: int = None
     _ws: torch.Tensor = None
+    _ready: torch.cuda.Event = None   # recorded on the submitting stream: A is written
     _end: torch.cuda.Event = None
     _slot: int = None
     _bytes: int = 0
@@ -71,9 +72,15 @@ class EigenServer:
     def now(self):
         return time.perf_counter() - self.t0
 
-    def submit(self, req):
+    def submit(self, req, stream=None):
+        """Queue a request.  `stream` is the stream whose work produces req.A
+        (default: the device's current stream); the solve is ordered after
+        everything already issued on it, so A may be computed on the device
+        right before submit (e.g. A_{k+1} = A_k + 1e-3 E)."""
         if not req.nbw:
             req.nbw = gb.gb_solve_default_nbw(req.n)
+        req._ready = torch.cuda.Event()
+        req._ready.record(stream if stream is not None else torch.cuda.current_stream(self.device))
         self.waiting.append(req)
 
     def _admit(self):
@@ -92,6 +99,10 @@ class EigenServer:
                 req.ev = torch.empty(req.nev, dtype=torch.float64, device=self.device)
                 req.Z = torch.empty((req.nev, req.n), dtype=req.A.dtype, device=self.device)
             f = gb.gb_solve_z if req.complex else gb.gb_solve_d
+            # the slot stream waits for the writer of A, and A's memory is not
+            # handed to another tensor before the slot stream is done with it
+            st.wait_event(req._ready)
+            req.A.record_stream(st)
             req.start = self.now()
             req.status = f(req.n, req.nev, req.nbw, req.A, req.n, req.ev, req.Z, req.n, req._ws, wsb, st, 0,
                            check=False)

@@ -1,5 +1,8 @@
 """Complex Hermitian back-transformation and real band widths above 64
-(shared-memory window kernels) against the oracle, through the C ABI."""
+(shared-memory window kernels) against the oracle, through the C ABI.
+
+Parity: ||Z_gpu - Z_oracle||_F / ||Z_in||_F <= 1e-12 on the whole block and
+on every column (the map is deterministic and column-wise)."""
 import numpy as np
 import pytest
 
@@ -10,6 +13,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 U = 2.0 ** -53
+PARITY = 1e-12
+
+
+def assert_parity(out, ref, Z):
+    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= PARITY
+    nz = np.linalg.norm(Z, axis=0)
+    assert np.max(np.linalg.norm(out - ref, axis=0) / nz) <= PARITY
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +61,7 @@ def test_complex_parity_bulge_chase(gb, n, b, nev, opts):
     Z = inputs.z_gaussian(n, nev, seed=nev, cplx=True)
     out = run(gb, n, b, hv, ht, Z, opts)
     ref = oracle.trans_ev(n, b, hv, ht, Z)
-    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
+    assert_parity(out, ref, Z)
 
 
 def test_complex_eigenvectors_residual(gb):
@@ -66,15 +76,16 @@ def test_complex_eigenvectors_residual(gb):
 
 
 def test_complex_config_size_sampled(gb):
-    """complex128 Hermitian n = 8192, nev = 2048 (25%), nbw = 64; 16 seeded
-    columns against the oracle, all columns for norm preservation."""
+    """complex128 Hermitian n = 8192, nev = 2048 (25%), nbw = 64; 64 seeded
+    columns against the oracle element by element, all columns for norm
+    preservation."""
     n, b, nev = 8192, 64, 2048
     hv, ht = inputs.synthetic_reflectors(n, b, seed=81, cplx=True)
     Z = inputs.z_gaussian(n, nev, seed=82, cplx=True)
     out = run(gb, n, b, hv, ht, Z)
-    cols = np.sort(np.random.default_rng(3).choice(nev, 16, replace=False))
+    cols = np.sort(np.random.default_rng(3).choice(nev, 64, replace=False))
     ref = oracle.trans_ev(n, b, hv, ht, np.asfortranarray(Z[:, cols]))
-    assert np.linalg.norm(out[:, cols] - ref) / np.linalg.norm(Z[:, cols]) <= 50 * n * U
+    assert_parity(out[:, cols], ref, Z[:, cols])
     nr = np.linalg.norm(out, axis=0) / np.linalg.norm(Z, axis=0)
     assert np.abs(nr - 1).max() <= 50 * n * U
 
@@ -89,4 +100,4 @@ def test_real_wide_band_parity(gb, n, b, nev):
     Z = inputs.z_gaussian(n, nev, seed=5)
     out = run(gb, n, b, hv, ht, Z)
     ref = oracle.trans_ev(n, b, hv, ht, Z)
-    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= 50 * n * U
+    assert_parity(out, ref, Z)

@@ -1,11 +1,12 @@
 """Parity of the CUDA back-transformation with the CPU oracle, through the C ABI.
 
 Tolerance: the two sides apply the same reflectors in the same order per
-column; they differ only in rounding (the kernel fuses multiply-adds).  We
-check ||Z_gpu - Z_oracle||_F / ||Z_in||_F <= 50 n u (u = 2^-53), the form of
-the eigen-residual bounds the method is held to; on the eigenvector inputs the
-GPU result must also satisfy ||B Z - Z L||_F/||B||_F <= 50 n u and
-||Z^H Z - I||_max <= 50 n u.
+column; they differ only in rounding (the kernel fuses multiply-adds).  The
+map is deterministic and acts on each column alone, so it is compared
+element by element: ||Z_gpu - Z_oracle||_F / ||Z_in||_F <= 1e-12 on the whole
+block and on every column (measured ~5e-15).  On eigenvector inputs the GPU
+result must also satisfy ||B Z - Z L||_F/||B||_F <= 50 n u and
+||Z^H Z - I||_max <= 50 n u (u = 2^-53).
 """
 import numpy as np
 import pytest
@@ -17,6 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 U = 2.0 ** -53
+PARITY = 1e-12   # ||Z_gpu - Z_oracle||_F / ||Z_in||_F, whole block and per column
 
 
 @pytest.fixture(scope="module")
@@ -51,6 +53,19 @@ def rel_err(A, B, Zin):
     return np.linalg.norm(A - B) / max(np.linalg.norm(Zin), 1e-300)
 
 
+def col_err(A, B, Zin):
+    """max over columns of ||A_c - B_c|| / ||Zin_c|| (zero columns must match exactly)."""
+    nz = np.linalg.norm(Zin, axis=0)
+    d = np.linalg.norm(A - B, axis=0)
+    assert np.all(d[nz == 0] == 0)
+    return float(np.max(d[nz > 0] / nz[nz > 0])) if np.any(nz > 0) else 0.0
+
+
+def assert_parity(out, ref, Z):
+    assert rel_err(out, ref, Z) <= PARITY
+    assert col_err(out, ref, Z) <= PARITY
+
+
 VARIANTS = [
     None,
     {"variant": 1, "sweeps_per_tile": 4, "cols_per_block": 32},
@@ -70,7 +85,7 @@ def test_parity_bulge_chase_reflectors(gb, n, b, nev, opts):
     Z = inputs.z_gaussian(n, nev, seed=n + nev)
     ref = oracle.trans_ev(n, b, hv, ht, Z)
     out = run_gpu(gb, n, b, hv, ht, Z, opts)
-    assert rel_err(out, ref, Z) <= 50 * n * U
+    assert_parity(out, ref, Z)
 
 
 @pytest.mark.parametrize("opts", VARIANTS, ids=["default", "nb4t32", "nb8t64", "nb16t128"])
@@ -80,7 +95,7 @@ def test_parity_synthetic_reflectors(gb, n, b, nev, opts):
     Z = inputs.z_gaussian(n, nev, seed=11)
     ref = oracle.trans_ev(n, b, hv, ht, Z)
     out = run_gpu(gb, n, b, hv, ht, Z, opts)
-    assert rel_err(out, ref, Z) <= 50 * n * U
+    assert_parity(out, ref, Z)
 
 
 def test_parity_ldz_padding(gb):
@@ -89,7 +104,7 @@ def test_parity_ldz_padding(gb):
     Z = inputs.z_gaussian(n, nev, seed=6, ldz=n + 13)
     ref = oracle.trans_ev(n, b, hv, ht, Z)
     out = run_gpu(gb, n, b, hv, ht, Z)
-    assert rel_err(out[:n], ref[:n], Z[:n]) <= 50 * n * U
+    assert_parity(out[:n], ref[:n], Z[:n])
     assert np.array_equal(out[n:], Z[n:])  # padding rows untouched
 
 
@@ -126,22 +141,24 @@ def test_config1_eigenvectors(gb, config1, opts):
     n, b, B, hv, ht, w, V = config1
     ref = oracle.trans_ev(n, b, hv, ht, V)
     out = run_gpu(gb, n, b, hv, ht, V, opts)
-    assert rel_err(out, ref, V) <= 50 * n * U
+    assert_parity(out, ref, V)
     assert np.linalg.norm(B @ out - out * w) / np.linalg.norm(B) <= 50 * n * U
     assert np.abs(out.T @ out - np.eye(n)).max() <= 50 * n * U
 
 
 def test_full_size_sampled_columns(gb):
-    """n = 16384, nev = 4096, nbw = 64 in the default launch configuration;
-    32 seeded columns checked against the oracle (columns are independent),
-    every column checked for norm preservation (Q2 is orthogonal)."""
+    """n = 16384, nev = 4096, nbw = 64 in the default launch configuration
+    (the bench's inputs and call); 64 seeded columns checked against the
+    oracle element by element (columns are independent, so a subset is an
+    exact check), every column checked for norm preservation (Q2 is
+    orthogonal)."""
     n, b, nev = 16384, 64, 4096
     hv, ht = inputs.synthetic_reflectors(n, b, seed=2024)
     Z = inputs.z_gaussian(n, nev, seed=2025)
     out = run_gpu(gb, n, b, hv, ht, Z)
-    cols = np.sort(np.random.default_rng(7).choice(nev, 32, replace=False))
+    cols = np.sort(np.random.default_rng(7).choice(nev, 64, replace=False))
     ref = oracle.trans_ev(n, b, hv, ht, np.asfortranarray(Z[:, cols]))
-    assert rel_err(out[:, cols], ref, Z[:, cols]) <= 50 * n * U
+    assert_parity(out[:, cols], ref, Z[:, cols])
     nin = np.linalg.norm(Z, axis=0)
     nout = np.linalg.norm(out, axis=0)
     assert np.abs(nout / nin - 1.0).max() <= 50 * n * U

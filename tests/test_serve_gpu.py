@@ -1,7 +1,11 @@
 """Continuous-batching service (paper_1811_01277_gb300.serve): requests that
 run concurrently in the mix give the same results as each run alone (within
-the tolerances), every result passes the LAPACK checks, and the HBM budget
-limits how many requests are admitted at once."""
+the tolerances), every result matches its prescribed spectrum, and the HBM
+budget limits how many requests are admitted at once.
+
+Each system is A = Q diag(lam) Q^H and its re-submissions A + 1e-3 j E with
+E = Q diag(mu) Q^H (same Q, ||E||_2 = 1), so the expected eigenvalues are
+lam + 1e-3 j mu in closed form (LAPACK only as a secondary check)."""
 import numpy as np
 import pytest
 
@@ -27,31 +31,36 @@ def serve():
 
 def make_requests(serve):
     dev = torch.device("cuda")
-    reqs, mats = [], []
+    reqs, mats, spectra = [], [], []
     rid = 0
     for k, n in enumerate([256, 384, 512]):
-        A = inputs.band_symmetric(n, n, seed=40 + k, cplx=True)
-        E = inputs.band_symmetric(n, n, seed=80 + k, cplx=True)
-        E /= np.linalg.norm(E, 2)
+        g = np.random.default_rng(40 + k)
+        lam = g.uniform(-1.0, 1.0, n)
+        mu = g.uniform(-1.0, 1.0, n)
+        mu[np.argmax(np.abs(mu))] = 1.0
+        A = inputs.symmetric_with_spectrum(lam, seed=40 + k, cplx=True)
+        E = inputs.symmetric_with_spectrum(mu, seed=40 + k, cplx=True)   # same Q
         for j in range(2):        # the system re-submitted with a perturbed matrix
             M = A + 1e-3 * j * E
             mats.append(M)
+            spectra.append(np.sort(lam + 1e-3 * j * mu))
             Ad = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev)   # column-major data
             reqs.append(serve.Request(rid=rid, A=Ad, nev=int(0.3 * n), arrival=0.0))
             rid += 1
-    return reqs, mats
+    return reqs, (mats, spectra)
 
 
-def check(M, w, Z):
+def check(M, w, Z, lam):
     n, nev = M.shape[0], len(w)
     nrm = np.linalg.norm(M, 2)
-    assert np.abs(w - np.linalg.eigvalsh(M)[:nev]).max() / nrm <= 1e-11
+    assert np.abs(w - lam[:nev]).max() / nrm <= 1e-11
+    assert np.abs(w - np.linalg.eigvalsh(M)[:nev]).max() / nrm <= 1e-11   # secondary (LAPACK)
     assert np.linalg.norm(M @ Z - Z * w) / np.linalg.norm(M) <= 50 * n * U
     assert np.abs(Z.conj().T @ Z - np.eye(nev)).max() <= 50 * n * U
 
 
 def test_mix_equals_alone(serve):
-    reqs, mats = make_requests(serve)
+    reqs, (mats, spectra) = make_requests(serve)
     srv = serve.EigenServer(slots=3)
     done = srv.run(reqs)
     assert len(done) == len(reqs) and all(r.status == 0 for r in done)
@@ -63,7 +72,7 @@ def test_mix_equals_alone(serve):
         wa, Za = d.ev.cpu().numpy(), d.Z.cpu().numpy().T
         wm, Zm = mix[r.rid]
         M = mats[r.rid]
-        check(M, wm, Zm)
+        check(M, wm, Zm, spectra[r.rid])
         assert np.abs(wa - wm).max() / np.linalg.norm(M, 2) <= 1e-11
         gaps = np.minimum(np.diff(np.concatenate([[-np.inf], wa])), np.diff(np.concatenate([wa, [np.inf]])))
         simple = gaps > 1e-6 * np.linalg.norm(M, 2)
@@ -73,7 +82,7 @@ def test_mix_equals_alone(serve):
 
 
 def test_hbm_budget_limits_admission(serve):
-    reqs, mats = make_requests(serve)
+    reqs, (mats, spectra) = make_requests(serve)
     # any two requests together exceed the smallest footprint: one at a time
     # (a request larger than the budget is still admitted when nothing runs)
     need = min(serve.request_bytes(r.n, r.nev, True, 32) for r in reqs)
@@ -89,4 +98,33 @@ def test_hbm_budget_limits_admission(serve):
     done = srv.run(reqs)
     assert peak == 1
     for r in done:
-        check(mats[r.rid], r.ev.cpu().numpy(), r.Z.cpu().numpy().T)
+        check(mats[r.rid], r.ev.cpu().numpy(), r.Z.cpu().numpy().T, spectra[r.rid])
+
+
+def test_matrix_built_on_the_device_right_before_submit(serve):
+    """A_{k+1} = A_k + 1e-3 E computed on the current stream (not synchronised)
+    just before submit: the served result equals the one-at-a-time result, and
+    the source tensors may be dropped right after submit."""
+    dev = torch.device("cuda")
+    n = 384
+    g = np.random.default_rng(7)
+    lam = g.uniform(-1.0, 1.0, n)
+    mu = g.uniform(-1.0, 1.0, n)
+    mu[np.argmax(np.abs(mu))] = 1.0
+    A0 = torch.from_numpy(np.ascontiguousarray(inputs.symmetric_with_spectrum(lam, seed=7, cplx=True).T)).to(dev)
+    E = torch.from_numpy(np.ascontiguousarray(inputs.symmetric_with_spectrum(mu, seed=7, cplx=True).T)).to(dev)
+    torch.cuda.synchronize()
+    srv = serve.EigenServer(slots=2)
+    reqs = []
+    for j in range(1, 4):
+        big = torch.randn(4096, 4096, dtype=torch.float64, device=dev)   # keeps the stream busy
+        big = big @ big
+        Aj = A0 + (1e-3 * j) * E                                         # written on the current stream
+        reqs.append(serve.Request(rid=j, A=Aj, nev=100, arrival=0.0))
+        del big
+    done = srv.run(reqs)
+    assert all(r.status == 0 for r in done)
+    for r in done:
+        lamj = np.sort(lam + 1e-3 * r.rid * mu)
+        M = (A0 + (1e-3 * r.rid) * E).cpu().numpy().T
+        check(M, r.ev.cpu().numpy(), r.Z.cpu().numpy().T, lamj)
