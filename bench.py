@@ -71,6 +71,19 @@ def tc_executed_flops(n, nbw, nev):
     return items * pairs * 2 * (2 * 16 * lp * 64)
 
 
+def tc5_executed_flops(n, nbw, nev):
+    """FP16 tensor-core flops one pipeline_tc5 call executes: per tile (16
+    sweeps) and 128-column item, W^T = Z^T V (128 x LP x 16) and
+    dZ^T = W^T U^T (128 x 16 x LP), each over the 43 digit-plane pairs
+    (s + t <= 8 of eight digits per operand), LP = nbw + 15 rounded up to 16."""
+    lp = (nbw + 15 + 15) // 16 * 16
+    G = (n - 1 + 15) // 16
+    tiles = sum((n - (1 + 16 * g) + nbw - 1) // nbw for g in range(G))
+    items = tiles * ((nev + 127) // 128)
+    pairs = sum(1 for s_ in range(8) for t_ in range(8) if s_ + t_ <= 8)     # 43
+    return items * pairs * 2 * (2 * 128 * 16 * lp)
+
+
 def algorithmic_flops(n, nev, cplx=False):
     """4 flops per reflector element and column (16 for complex); the
     reflectors of a sweep s cover n-s rows, so sum len = n(n-1)/2."""
@@ -81,6 +94,7 @@ KERNEL_SOURCES = {
     "pipeline_d": ["trans_ev_pipeline.cu", "tile_apply.cuh", "layout.cuh"],
     "wavefront_tile_d": ["trans_ev_wavefront.cu", "tile_apply.cuh", "layout.cuh"],
     "pipeline_tc": ["trans_ev_tc.cu", "mma_bf16.cuh", "layout.cuh"],
+    "pipeline_tc5": ["trans_ev_tc5.cu", "tcgen05.cuh", "tc_fixed.cuh", "mma_bf16.cuh", "layout.cuh"],
 }
 
 
@@ -246,13 +260,16 @@ METRIC = ("solve s at n=16384 (25% vecs); trans_ev % of FP64 peak; batched solve
           "keys solve (full two-stage solve at that size) and batched (512 problems) carry the rest")
 
 
-def config_of(wl):
+def config_of(wl, shards=1):
     n, nev, nbw = wl["n"], wl["nev"], wl["nbw"]
     count = sum((n - s + nbw - 1) // nbw for s in range(1, n))
-    return {"workload": f"trans_ev_tridi_to_band n={n} nev={nev} nbw={nbw} real FP64",
-            "n": n, "nev": nev, "nbw": nbw,
-            "l2": "inputs larger than L2 (Z %.2f GB, reflectors %.2f GB); no flush" % (
-                8 * n * nev / 1e9, 8 * nbw * count / 1e9)}
+    c = {"workload": f"trans_ev_tridi_to_band n={n} nev={nev} nbw={nbw} real FP64",
+         "n": n, "nev": nev, "nbw": nbw,
+         "l2": "inputs larger than L2 (Z %.2f GB, reflectors %.2f GB); no flush" % (
+             8 * n * nev / 1e9, 8 * nbw * count / 1e9)}
+    c["parallelism"] = (f"one problem, columns sharded over {shards} GPUs (reflectors replicated, no exchange "
+                        f"during the step)") if shards > 1 else "one independent problem per GPU"
+    return c
 
 
 def run_ours(args, wl):
@@ -273,8 +290,19 @@ def run_ours(args, wl):
     if args.variant == 0 and args.nb == 0 and args.threads == 0 and args.column_batch == 0 and args.lead_tiles == 0:
         opts = None  # the library's default choice
 
-    hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024 + 1000 * rank)
-    Z = inputs.z_gaussian(n, nev, seed=2025 + 1000 * rank)
+    shard = args.shard and world > 1
+    if shard:
+        # one problem for the whole job: every rank builds the same reflectors
+        # (the replicated set; sharded.broadcast_reflectors would send them
+        # from one rank instead) and back-transforms its own column block
+        from paper_1811_01277_gb300.sharded import column_shard
+        hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024)
+        c0, nev_loc = column_shard(nev, world, rank)
+        Z = np.asfortranarray(inputs.z_gaussian(n, nev, seed=2025)[:, c0:c0 + nev_loc])
+        nev_job, nev = nev, nev_loc
+    else:
+        hv, ht = inputs.synthetic_reflectors(n, nbw, seed=2024 + 1000 * rank)
+        Z = inputs.z_gaussian(n, nev, seed=2025 + 1000 * rank)
     hv_d = torch.from_numpy(hv).to(dev)
     ht_d = torch.from_numpy(ht).to(dev)
     Z_d = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)  # (nev, n) row-major = column-major Z
@@ -306,10 +334,10 @@ def run_ours(args, wl):
                 "cols_per_block": best.cols_per_block, "column_batch": best.column_batch}
         tuned = {"level": args.autotune, "chosen": opts, "trials": trials}
     launches_per_call = gb.gb_trans_ev_launch_count(n, nbw, nev, 0, opts)
-    # the tensor-core pipeline is six launches (scales, to fixed point, tile
+    # the tensor-core pipelines are six launches (scales, to fixed point, tile
     # offsets, tile prep, pipeline, back); the DFMA pipeline one
-    tc = launches_per_call == 6 and nbw in (16, 32, 64)
-    variant_name = "pipeline_tc" if tc else ("pipeline" if launches_per_call == 1 else "wavefront")
+    variant_name = {gb.GB_VARIANT_PIPELINE_TC5: "pipeline_tc5", gb.GB_VARIANT_PIPELINE_TC: "pipeline_tc",
+                    gb.GB_VARIANT_PIPELINE: "pipeline"}.get(gb.gb_trans_ev_variant(n, nbw, nev, 0, opts), "wavefront")
     wsb = gb.gb_trans_ev_workspace_bytes(n, nbw, nev, 0, opts)
     ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -335,11 +363,14 @@ def run_ours(args, wl):
     el_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     clocks = sampler.stop() if sampler else None
     ms_per_step = el_ms / args.steps
-    value = aggregate(world, args.steps, el_ms / 1e3)
+    # replicas: every rank finished its own problem per step; shard: the
+    # ranks together finished one problem per step
+    value = args.steps / (el_ms / 1e3) if shard else aggregate(world, args.steps, el_ms / 1e3)
     F = algorithmic_flops(n, nev)
     achieved = F / (ms_per_step / 1e3) / 1e12
     launches = launches_per_call
-    kernel = {"pipeline": "pipeline_d", "pipeline_tc": "pipeline_tc"}.get(variant_name, "wavefront_tile_d")
+    kernel = {"pipeline": "pipeline_d", "pipeline_tc": "pipeline_tc",
+              "pipeline_tc5": "pipeline_tc5"}.get(variant_name, "wavefront_tile_d")
     sha = kernel_sources_sha1(kernel)
     # the committed ncu figure is for the default configuration only
     traffic = profile_traffic(kernel, args.workload, variant_name, sha) if opts is None else None
@@ -365,7 +396,7 @@ def run_ours(args, wl):
             hstep()
         el = max_over_ranks(time.perf_counter() - t0, world, dev)
         h2d = hv.nbytes + ht.nbytes + Z.nbytes
-        e2e = {"value": aggregate(world, args.steps, el), "unit": "back-transforms/s",
+        e2e = {"value": args.steps / el if shard else aggregate(world, args.steps, el), "unit": "back-transforms/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(Z.nbytes),
                "api": "gb_trans_ev_tridi_to_band_d_host (pinned host buffers)"}
 
@@ -373,7 +404,25 @@ def run_ours(args, wl):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(n, nev, nbw, hv, ht, Z)
 
-    if variant_name == "pipeline_tc":
+    if variant_name == "pipeline_tc5":
+        # tcgen05 MMAs on FP16 digit planes (same dense rate as bf16): executed
+        # tensor flops against the measured bf16 peak (cuBLAS, tcgen05 path);
+        # the bench loops the call for seconds, so the sustained figure is the
+        # denominator, the burst one beside it
+        pk = measured_peaks()
+        Ft = tc5_executed_flops(n, nbw, nev)
+        tc_ach = Ft / (ms_per_step / 1e3) / 1e12
+        peak = pk["bf16_tflops_sustained"] or pk["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": tc_ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": tc_ach / peak, "traffic": traffic,
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained ({pk['source']}; cuBLAS bf16 on the "
+                               f"tcgen05 path, FP16 runs at the same dense rate)",
+                "frac_of_burst_peak": tc_ach / pk["bf16_tflops"],
+                "kernel": kernel, "per": "step", "executed_fp16_tflop_per_step": Ft / 1e12,
+                "fp64_equivalent": {"achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": achieved / FP64_PEAK_TFLOPS,
+                                    "algorithmic_tflop_per_step": F / 1e12}}
+    elif variant_name == "pipeline_tc":
         # the dominant kernel runs on the bf16 tensor pipe: executed tensor
         # flops against the measured bf16 peak; the FP64-equivalent rate of
         # the algorithmic work beside it
@@ -400,8 +449,8 @@ def run_ours(args, wl):
         line = {
             "metric": METRIC, "value": value, "unit": "back-transforms/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(wl), "variant": variant_name,
+            "higher_is_better": True, "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl, world if shard else 1), "variant": variant_name,
             "roofline": roof,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches) * args.steps,
             "clocks": clocks, "kernel_sources_sha1": sha,
@@ -974,6 +1023,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--autotune", choices=["fast", "medium"], default=None,
                     help="walk the autotuner first and time its fastest setting")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1 ranks: split one problem's columns over the ranks (strong scaling) "
+                         "instead of one independent problem per rank")
     ap.add_argument("--no-extra", action="store_true",
                     help="default stage: skip the solve and batched measurements that complete the metric")
     ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm"],

@@ -60,7 +60,7 @@ extern "C" {
                                 reflectors were not orthogonal / unitary; Z is unspecified but finite */
 
 /* Kernel variants for gb_trans_ev_opts.variant. */
-#define GB_VARIANT_AUTO 0      /* library picks: PIPELINE_TC for real data with nbw in
+#define GB_VARIANT_AUTO 0      /* library picks: PIPELINE_TC5 for real data with nbw in
                                   {16,32,64} and n >= 512, else PIPELINE for real
                                   data with nbw in {8,16,32,64}, else WAVEFRONT */
 #define GB_VARIANT_WAVEFRONT 1 /* one launch per anti-diagonal of the tile DAG */
@@ -68,8 +68,15 @@ extern "C" {
 #define GB_VARIANT_PIPELINE_TC 3 /* the pipeline's schedule with every tile applied in
                                     compact WY form on the bf16 tensor cores (exact
                                     digit slicing, Z in per-column 64-bit fixed point
-                                    during the call); real data, nbw in {16,32,64},
-                                    otherwise runs as PIPELINE */
+                                    during the call) issued as warp-level mma.sync;
+                                    real data, nbw in {16,32,64}, otherwise runs as
+                                    PIPELINE */
+#define GB_VARIANT_PIPELINE_TC5 4 /* the same compact WY tiles on the tcgen05 tensor
+                                     cores: 128 eigenvector columns per work item as
+                                     the MMA's M, FP16 digit planes of Z and W in
+                                     tensor memory, FP32 level accumulators in tensor
+                                     memory, tile records by bulk copy; real data,
+                                     nbw in {16,32,64}, otherwise runs as PIPELINE */
 
 /* Tuning knobs (the paper's MEDIUM autotuning level tunes the blocking of the
  * back transformation, Sec. 4.3 and Sec. 5.3).  Zero fields mean "default". */
@@ -85,9 +92,10 @@ typedef struct gb_trans_ev_opts {
     int test_hold_group; /* fault-injection hook for tests: when g+1 > 0, sweep
                             group g never publishes its progress so that the
                             next group's wait must give up; 0 = off */
-    int column_batch;    /* PIPELINE and PIPELINE_TC: column blocks per ticket
-                            batch, 1..1024 (0 = default: 16, and 8 for
-                            PIPELINE_TC).  Items of one batch run
+    int column_batch;    /* PIPELINE, PIPELINE_TC and PIPELINE_TC5: column blocks
+                            per ticket batch, 1..1024 (0 = default: 16, 8 for
+                            PIPELINE_TC (64-column blocks), 4 for PIPELINE_TC5
+                            (128-column blocks)).  Items of one batch run
                             group after group; smaller batches keep fewer
                             eigenvector rows live in L2, larger ones read the
                             reflectors fewer times. */
@@ -157,6 +165,11 @@ int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream);
 /* Number of kernel launches one call with these arguments issues. */
 long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex,
                                    const gb_trans_ev_opts *opts);
+
+/* The kernel variant (GB_VARIANT_WAVEFRONT, _PIPELINE, _PIPELINE_TC or
+ * _PIPELINE_TC5) a call with these arguments runs, after AUTO and the
+ * fallbacks are resolved; -1 for invalid arguments.  Host only. */
+int gb_trans_ev_variant(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts);
 
 /* No-allocation form of the real case, for callers that cannot call
  * cudaMalloc (code running inside a memory pool or arena that owns all

@@ -7,8 +7,9 @@ The computation runs in ``libelpa_gb300.so`` (CUDA C++, C ABI declared in
 seeded input generators; PyTorch only provides device memory and streams.
 """
 from ._lib import (  # noqa: F401
-    EXPORTS, GB_ERR_CUDA, GB_ERR_TIMEOUT, GB_ERR_UNSUPPORTED, GB_ERR_WORKSPACE, GB_OK,
-    GB_NOALLOC_SCRATCH_BYTES, GB_SOLVE_FP64_EMULATED_GEMM, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_PIPELINE_TC, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH,
+    EXPORTS, GB_ERR_CUDA, GB_ERR_TIMEOUT, GB_ERR_UNSUPPORTED, GB_ERR_WORKSPACE, GB_ERR_NONFINITE, GB_ERR_RANGE, GB_OK,
+    GB_NOALLOC_SCRATCH_BYTES, GB_SOLVE_FP64_EMULATED_GEMM, GB_VARIANT_AUTO, GB_VARIANT_PIPELINE, GB_VARIANT_PIPELINE_TC,
+    GB_VARIANT_PIPELINE_TC5, GB_VARIANT_WAVEFRONT, GbError, LIB_PATH, gb_trans_ev_variant,
     gb_band_to_tridi_d, gb_band_to_tridi_workspace_bytes, gb_band_to_tridi_workspace_bytes_z, gb_band_to_tridi_z, gb_hh_count, gb_hh_index, gb_max_nbw, gb_status_string, gb_trans_ev_host_buffer_bytes,
     gb_trans_ev_launch_count, gb_trans_ev_opts, gb_trans_ev_query, gb_trans_ev_tridi_to_band_d,
     gb_trans_ev_tridi_to_band_d_host, gb_trans_ev_tridi_to_band_d_noalloc, gb_trans_ev_tridi_to_band_z, gb_trans_ev_workspace_bytes,

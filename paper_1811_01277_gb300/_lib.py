@@ -23,12 +23,13 @@ GB_VARIANT_AUTO = 0
 GB_VARIANT_WAVEFRONT = 1
 GB_VARIANT_PIPELINE = 2
 GB_VARIANT_PIPELINE_TC = 3
+GB_VARIANT_PIPELINE_TC5 = 4
 
 EXPORTS = (
     "gb_hh_count", "gb_hh_index", "gb_max_nbw", "gb_trans_ev_workspace_bytes",
     "gb_trans_ev_tridi_to_band_d", "gb_trans_ev_tridi_to_band_z",
     "gb_trans_ev_host_buffer_bytes", "gb_trans_ev_tridi_to_band_d_host",
-    "gb_trans_ev_launch_count", "gb_status_string", "gb_trans_ev_query",
+    "gb_trans_ev_launch_count", "gb_trans_ev_variant", "gb_status_string", "gb_trans_ev_query",
     "gb_trans_ev_tridi_to_band_d_noalloc", "gb_band_to_tridi_workspace_bytes", "gb_band_to_tridi_d",
     "gb_solve_workspace_bytes", "gb_solve_d", "gb_solve_query", "elpa_b200_solve",
     "gb_autotune_create", "gb_autotune_destroy", "gb_autotune_step", "gb_autotune_report",
@@ -94,6 +95,7 @@ def load(path=None):
     L.gb_trans_ev_tridi_to_band_d_host.argtypes = [i, i, i, p, p, p, i, p, sz, p, po]
     L.gb_trans_ev_tridi_to_band_d_host.restype = i
     L.gb_trans_ev_launch_count.argtypes = [i, i, i, i, po]; L.gb_trans_ev_launch_count.restype = ll
+    L.gb_trans_ev_variant.argtypes = [i, i, i, i, po]; L.gb_trans_ev_variant.restype = i
     L.gb_status_string.argtypes = [i]; L.gb_status_string.restype = ctypes.c_char_p
     L.gb_trans_ev_query.argtypes = [p, sz, p]; L.gb_trans_ev_query.restype = i
     L.gb_trans_ev_tridi_to_band_d_noalloc.argtypes = [i, i, i, p, p, p, i, p, p]
@@ -241,6 +243,10 @@ def gb_trans_ev_tridi_to_band_d_host(n, nbw, nev, hh_v, hh_tau, Z, ldz, dev_buf,
 
 def gb_trans_ev_launch_count(n, nbw, nev, is_complex=0, opts=None):
     return load().gb_trans_ev_launch_count(n, nbw, nev, int(is_complex), _opts(opts))
+
+
+def gb_trans_ev_variant(n, nbw, nev, is_complex=0, opts=None):
+    return load().gb_trans_ev_variant(n, nbw, nev, int(is_complex), _opts(opts))
 
 
 def gb_trans_ev_query(workspace=None, ws_bytes=0, stream=None):

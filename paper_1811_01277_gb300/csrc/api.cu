@@ -24,10 +24,11 @@ constexpr long long kDefaultSpinPolls = 1LL << 40;  // effectively bounded by th
 constexpr long long kTimeoutNs = 10LL * 1000 * 1000 * 1000;
 
 // Returns 0 or -11 (opts is the 11th argument of the device entry points).
-// AUTO picks PIPELINE_TC for real data with nbw in {16,32,64} and n >= 512
-// (2.8x the DFMA pipeline at n = 16384 on GB300), PIPELINE for the other real
-// cases with nbw in {8,16,32,64} (nb = 16, 64 columns per block) and
-// WAVEFRONT otherwise; PIPELINE requested for other cases runs as WAVEFRONT.
+// AUTO picks PIPELINE_TC5 (tcgen05) for real data with nbw in {16,32,64} and
+// n >= 512, PIPELINE for the other real cases with nbw in {8,16,32,64}
+// (nb = 16, 64 columns per block) and WAVEFRONT otherwise; PIPELINE requested
+// for other cases runs as WAVEFRONT, and either tensor-core variant requested
+// for unsupported cases runs as PIPELINE.
 int resolve(const gb_trans_ev_opts *o, int n, int nbw, int is_complex, Opts *r)
 {
     int variant = GB_VARIANT_AUTO, nb = 0, threads = 0;
@@ -36,7 +37,7 @@ int resolve(const gb_trans_ev_opts *o, int n, int nbw, int is_complex, Opts *r)
     r->column_batch = 0;
     r->lead_tiles = 0;
     if (o) {
-        if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE_TC) return -11;
+        if (o->variant < 0 || o->variant > GB_VARIANT_PIPELINE_TC5) return -11;
         if (o->sweeps_per_tile < 0 || o->sweeps_per_tile > 32) return -11;
         if (o->cols_per_block != 0 && o->cols_per_block != 32 && o->cols_per_block != 64 &&
             o->cols_per_block != 128)
@@ -55,8 +56,10 @@ int resolve(const gb_trans_ev_opts *o, int n, int nbw, int is_complex, Opts *r)
     const bool pipe_ok = !is_complex && gb::pipeline_supported(nbw);
     if (variant == GB_VARIANT_PIPELINE_TC && (is_complex || !gb::pipeline_tc_supported(nbw)))
         variant = GB_VARIANT_PIPELINE;
+    if (variant == GB_VARIANT_PIPELINE_TC5 && (is_complex || !gb::pipeline_tc5_supported(nbw)))
+        variant = GB_VARIANT_PIPELINE;
     if (variant == GB_VARIANT_AUTO) {
-        if (!is_complex && gb::pipeline_tc_supported(nbw) && n >= kTcMinN) variant = GB_VARIANT_PIPELINE_TC;
+        if (!is_complex && gb::pipeline_tc5_supported(nbw) && n >= kTcMinN) variant = GB_VARIANT_PIPELINE_TC5;
         else variant = pipe_ok ? GB_VARIANT_PIPELINE : GB_VARIANT_WAVEFRONT;
     }
     if (variant == GB_VARIANT_PIPELINE && !pipe_ok) variant = GB_VARIANT_WAVEFRONT;
@@ -116,6 +119,7 @@ size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, cons
     Opts o;
     if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, n, nbw, is_complex, &o) != 0) return 0;
     if (o.variant == GB_VARIANT_PIPELINE_TC && n > 1 && nev > 0) return gb::pipeline_tc_workspace_bytes(n, nbw, nev);
+    if (o.variant == GB_VARIANT_PIPELINE_TC5 && n > 1 && nev > 0) return gb::pipeline_tc5_workspace_bytes(n, nbw, nev);
     if (o.variant == GB_VARIANT_PIPELINE && !is_complex && n > 1 && nev > 0)
         return gb::pipeline_workspace_bytes(n, nev, o.nb, o.threads);
     return 0;  // the wavefront variant needs no workspace
@@ -134,7 +138,10 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     if (ws_bytes < need) return -9;
     if (n == 1 || nev == 0) return GB_OK;
     cudaError_t e;
-    if (o.variant == GB_VARIANT_PIPELINE_TC)
+    if (o.variant == GB_VARIANT_PIPELINE_TC5)
+        e = gb::pipeline_tc5_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.column_batch, workspace, need, o.spin, kTimeoutNs,
+                               o.hold, (cudaStream_t)stream);
+    else if (o.variant == GB_VARIANT_PIPELINE_TC)
         e = gb::pipeline_tc_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.column_batch, workspace, need, o.spin, kTimeoutNs,
                               o.hold, (cudaStream_t)stream);
     else if (o.variant == GB_VARIANT_PIPELINE)
@@ -213,13 +220,21 @@ int gb_trans_ev_query(const void *workspace, size_t ws_bytes, void *stream)
     return head[2] ? head[2] : GB_OK;
 }
 
+int gb_trans_ev_variant(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
+{
+    Opts o;
+    if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, n, nbw, is_complex, &o) != 0) return -1;
+    return o.variant;
+}
+
 long long gb_trans_ev_launch_count(int n, int nbw, int nev, int is_complex, const gb_trans_ev_opts *opts)
 {
     Opts o;
     if (n < 1 || nbw < 1 || nbw > kMaxNbw || nev < 0 || resolve(opts, n, nbw, is_complex, &o) != 0) return -1;
     if (n == 1 || nev == 0) return 0;
     if (o.variant == GB_VARIANT_PIPELINE) return 1;
-    if (o.variant == GB_VARIANT_PIPELINE_TC) return 6;  // scales, to fixed, offsets, tile prep, pipeline, back
+    if (o.variant == GB_VARIANT_PIPELINE_TC || o.variant == GB_VARIANT_PIPELINE_TC5)
+        return 6;  // scales, to fixed, offsets, tile prep, pipeline, back
     return gb::wavefront_launch_count(n, nbw, o.nb);
 }
 

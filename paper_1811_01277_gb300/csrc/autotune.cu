@@ -47,6 +47,7 @@ void build_candidates(gb_autotune *t)
         add(GB_VARIANT_WAVEFRONT, 0, 0);
         if (pipeline_ok(t->nbw)) add(GB_VARIANT_PIPELINE, 0, 0);
         if (tc_ok(t->nbw)) add(GB_VARIANT_PIPELINE_TC, 0, 0);
+        if (tc_ok(t->nbw)) add(GB_VARIANT_PIPELINE_TC5, 0, 0);
     } else {
         const int wnb[3] = {4, 8, 16}, wcols[3] = {32, 64, 128};
         for (int a = 0; a < 3; a++)
@@ -60,6 +61,8 @@ void build_candidates(gb_autotune *t)
         if (tc_ok(t->nbw)) {
             const int tcb[3] = {8, 16, 32};
             for (int a = 0; a < 3; a++) add(GB_VARIANT_PIPELINE_TC, 0, 0, tcb[a]);
+            const int tc5b[3] = {2, 4, 8};  // 128-column blocks per batch
+            for (int a = 0; a < 3; a++) add(GB_VARIANT_PIPELINE_TC5, 0, 0, tc5b[a]);
         }
     }
     t->secs.assign(t->cand.size(), -1.0);

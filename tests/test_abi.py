@@ -83,6 +83,31 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert gb.gb_status_string(gb.GB_ERR_TIMEOUT).startswith("a device-side")
 
 
+def test_variant_resolution_is_host_only(lib):
+    """AUTO resolves to the tcgen05 pipeline for real nbw in {16, 32, 64} and
+    n >= 512, the DFMA pipeline for the other real pipeline band widths,
+    the wavefront otherwise; tensor-core requests fall back to the pipeline."""
+    v = gb.gb_trans_ev_variant
+    assert v(16384, 64, 4096) == gb.GB_VARIANT_PIPELINE_TC5
+    assert v(1024, 32, 1024) == gb.GB_VARIANT_PIPELINE_TC5
+    assert v(600, 16, 10) == gb.GB_VARIANT_PIPELINE_TC5
+    assert v(500, 64, 10) == gb.GB_VARIANT_PIPELINE
+    assert v(4096, 8, 100) == gb.GB_VARIANT_PIPELINE
+    assert v(4096, 13, 100) == gb.GB_VARIANT_WAVEFRONT
+    assert v(4096, 64, 100, 1) == gb.GB_VARIANT_WAVEFRONT          # complex
+    assert v(4096, 64, 100, 0, {"variant": 3}) == gb.GB_VARIANT_PIPELINE_TC
+    assert v(4096, 8, 100, 0, {"variant": 4}) == gb.GB_VARIANT_PIPELINE
+    assert v(4096, 64, 100, 1, {"variant": 4}) == gb.GB_VARIANT_WAVEFRONT
+    assert v(4096, 64, 100, 0, {"variant": 5}) == -1
+    assert gb.gb_trans_ev_launch_count(4096, 64, 100, 0, {"variant": 4}) == 6
+    # the tcgen05 workspace: head, flags, scales, offsets and one 41344-byte
+    # record per tile (b = 64)
+    n, b, nev = 4096, 64, 300
+    G = (n - 1 + 15) // 16
+    tiles = sum((n - (1 + 16 * g) + b - 1) // b for g in range(G))
+    assert gb.gb_trans_ev_workspace_bytes(n, b, nev) >= tiles * 41344
+
+
 def test_launch_count_is_host_only(lib):
     # one launch per anti-diagonal of the tile graph
     assert gb.gb_trans_ev_launch_count(1, 4, 10) == 0

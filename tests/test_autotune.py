@@ -28,10 +28,10 @@ def walk(t, cost):
 
 def test_fast_level_tries_each_variant_once():
     t = gb.gb_autotune_create(gb.GB_AUTOTUNE_FAST, 4096, 64, 1024)
-    seen = walk(t, lambda k: {1: 2.0, 2: 1.5, 3: 0.7}[k[0]])
-    assert sorted(seen) == [(1, 0, 0, 0), (2, 0, 0, 0), (3, 0, 0, 0)]
+    seen = walk(t, lambda k: {1: 2.0, 2: 1.5, 3: 0.7, 4: 0.3}[k[0]])
+    assert sorted(seen) == [(1, 0, 0, 0), (2, 0, 0, 0), (3, 0, 0, 0), (4, 0, 0, 0)]
     best, s = gb.gb_autotune_best(t)
-    assert (best.variant, s) == (3, 0.7)
+    assert (best.variant, s) == (4, 0.3)
     gb.gb_autotune_destroy(t)
     t = gb.gb_autotune_create(gb.GB_AUTOTUNE_FAST, 4096, 13, 1024)   # no pipeline for nbw = 13
     assert walk(t, lambda k: 1.0) == [(1, 0, 0, 0)]
@@ -42,7 +42,7 @@ def test_medium_level_finds_minimum():
     t = gb.gb_autotune_create(gb.GB_AUTOTUNE_MEDIUM, 16384, 64, 4096)
     cost = lambda k: 1.0 + 0.01 * k[1] + (0.5 if k[0] == 1 else 0.0) + 0.001 * k[2] + 0.0001 * k[3]
     seen = walk(t, cost)
-    assert len(seen) == 9 + 4 + 3 and len(set(seen)) == len(seen)
+    assert len(seen) == 9 + 4 + 3 + 3 and len(set(seen)) == len(seen)
     best, s = gb.gb_autotune_best(t)
     assert (best.variant, best.sweeps_per_tile, best.cols_per_block, best.column_batch) == min(seen, key=cost)
     assert s == min(cost(k) for k in seen)
@@ -75,7 +75,7 @@ def test_save_and_resume_mid_walk(tmp_path):
     gb.gb_autotune_destroy(t)
     t2 = gb.gb_autotune_load(path)
     assert t2
-    assert gb.gb_autotune_progress(t2) == (5, 16)
+    assert gb.gb_autotune_progress(t2) == (5, 19)
     rest = walk(t2, cost)
     assert rest[0] == (pending.variant, pending.sweeps_per_tile, pending.cols_per_block, pending.column_batch)
     best, s = gb.gb_autotune_best(t2)

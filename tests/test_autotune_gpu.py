@@ -54,7 +54,7 @@ def test_medium_walk_on_gpu(gb):
         times[(o.variant, o.sweeps_per_tile, o.cols_per_block, o.column_batch)] = sec
         assert gb.gb_autotune_report(t, sec) == 0
     best, s = gb.gb_autotune_best(t)
-    assert len(times) == 9 + 4 + 3          # wavefront, pipeline, tensor-core pipeline settings
+    assert len(times) == 9 + 4 + 3 + 3      # wavefront, pipeline, mma.sync and tcgen05 pipeline settings
     assert s == min(times.values())
     assert times[(best.variant, best.sweeps_per_tile, best.cols_per_block, best.column_batch)] == s
     gb.gb_autotune_destroy(t)

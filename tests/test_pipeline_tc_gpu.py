@@ -1,6 +1,9 @@
-"""The tensor-core pipeline (GB_VARIANT_PIPELINE_TC: tiles in compact WY form
-on mma.sync bf16 by exact digit slicing, Z in per-column 64-bit fixed point)
-through the C ABI, against the oracle: every supported band width, ragged
+"""The tensor-core pipelines through the C ABI, against the oracle:
+GB_VARIANT_PIPELINE_TC5 (the default: tcgen05 MMAs with FP16 digit planes
+and FP32 level sums in tensor memory, 128-column items) and
+GB_VARIANT_PIPELINE_TC (warp-level mma.sync on bf16 digits, 64-column
+items); both apply every tile in compact WY form by exact digit slicing with
+Z in per-column 64-bit fixed point.  Covered: every supported band width, ragged
 and tiny shapes, reflectors from real bulge chases at the sizes where this
 kernel is the default (the oracle's chase of the n = 1024, nbw = 32 config
 and the device chase at n = 2048, nbw = 64), columns of wildly different
@@ -23,6 +26,8 @@ pytestmark = pytest.mark.gpu
 U = 2.0 ** -53
 PARITY = 1e-12
 TC = {"variant": 3}
+TC5 = {"variant": 4}
+BOTH = pytest.mark.parametrize("opts", [TC5, TC], ids=["tcgen05", "mma_sync"])
 
 
 @pytest.fixture(scope="module")
@@ -60,18 +65,21 @@ def colwise_err(out, ref, Z):
     return np.max(np.linalg.norm((out - ref) / s, axis=0) / nz)
 
 
+@BOTH
 @pytest.mark.parametrize("n,b,nev", [(2, 16, 3), (17, 16, 1), (100, 16, 65), (257, 16, 129), (300, 32, 200),
                                      (129, 64, 130), (640, 64, 257), (1000, 64, 64), (65, 64, 31),
-                                     (1500, 32, 100), (2049, 64, 70), (4096, 64, 96)])
-def test_tc_parity(gb, n, b, nev):
+                                     (1500, 32, 100), (2049, 64, 70), (4096, 64, 96), (700, 16, 300),
+                                     (1200, 32, 385), (3000, 64, 513)])
+def test_tc_parity(gb, n, b, nev, opts):
     if n <= 400:
         B = inputs.band_symmetric(n, b, seed=n + b)
         _, _, hv, ht, _ = oracle.bulge_chase(B, b)
     else:
         hv, ht = inputs.synthetic_reflectors(n, b, seed=n)
     Z = inputs.z_gaussian(n, nev, seed=nev)
-    assert gb.gb_trans_ev_launch_count(n, b, nev, 0, TC) == (6 if n > 1 else 0)
-    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    assert gb.gb_trans_ev_launch_count(n, b, nev, 0, opts) == (6 if n > 1 else 0)
+    assert gb.gb_trans_ev_variant(n, b, nev, 0, opts) == opts["variant"]
+    rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     ref = oracle.trans_ev(n, b, hv, ht, Z)
     assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= PARITY
@@ -89,14 +97,16 @@ def config1():
     return n, b, B, hv, ht, w, V
 
 
-def test_tc_config1_bulge_chase_reflectors(gb, config1):
-    """The default kernel on the n = 1024 config's own reflectors (tau = 0
-    runs included) and all 1024 eigenvectors: every column against the
-    oracle, plus residual and orthogonality."""
+@pytest.mark.parametrize("opts", [None, TC], ids=["default", "mma_sync"])
+def test_tc_config1_bulge_chase_reflectors(gb, config1, opts):
+    """The default kernel (tcgen05) and the mma.sync one on the n = 1024
+    config's own reflectors (tau = 0 runs included) and all 1024
+    eigenvectors: every column against the oracle, plus residual and
+    orthogonality."""
     n, b, B, hv, ht, w, V = config1
-    assert gb.gb_trans_ev_launch_count(n, b, n, 0, None) == 6   # the library default is this kernel
+    assert gb.gb_trans_ev_variant(n, b, n, 0, None) == gb.GB_VARIANT_PIPELINE_TC5   # the library default
     assert np.any(ht == 0) and np.any(ht != 0)
-    rc, q, out = run(gb, n, b, hv, ht, V, None)
+    rc, q, out = run(gb, n, b, hv, ht, V, opts)
     assert rc == 0 and q == 0
     ref = oracle.trans_ev(n, b, hv, ht, V)
     assert np.linalg.norm(out - ref) / np.linalg.norm(V) <= PARITY
@@ -134,15 +144,17 @@ def test_tc_device_chase_reflectors_n2048(gb):
     hv, ht = hv_d.cpu().numpy(), ht_d.cpu().numpy()
     assert np.any(ht != 0)
     Z = inputs.z_gaussian(n, nev, seed=2049)
-    assert gb.gb_trans_ev_launch_count(n, b, nev, 0, None) == 6
-    rc, q, out = run(gb, n, b, hv, ht, Z, None)
-    assert rc == 0 and q == 0
-    ref = oracle.trans_ev(n, b, hv, ht, Z)
-    assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= PARITY
-    assert colwise_err(out, ref, Z) <= PARITY
+    assert gb.gb_trans_ev_variant(n, b, nev, 0, None) == gb.GB_VARIANT_PIPELINE_TC5
+    for opts in (None, TC):
+        rc, q, out = run(gb, n, b, hv, ht, Z, opts)
+        assert rc == 0 and q == 0
+        ref = oracle.trans_ev(n, b, hv, ht, Z)
+        assert np.linalg.norm(out - ref) / np.linalg.norm(Z) <= PARITY
+        assert colwise_err(out, ref, Z) <= PARITY
 
 
-def test_tc_columns_of_different_norms(gb):
+@BOTH
+def test_tc_columns_of_different_norms(gb, opts):
     """Column scales 1e-200 .. 1e200, a zero column and a column with one
     dominant entry: each column is accurate relative to its own norm."""
     n, b, nev = 500, 64, 9
@@ -154,14 +166,14 @@ def test_tc_columns_of_different_norms(gb):
     Z[:, 3] = 0.0
     Z[7, 3] = 3.0
     Z[:, 4] *= 2.0 ** 500
-    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     ref = oracle.trans_ev(n, b, hv, ht, Z)
     assert np.all(out[:, 2] == 0.0)
     assert colwise_err(out, ref, Z) <= PARITY
 
 
-@pytest.mark.parametrize("opts", [None, TC], ids=["default", "mma_sync"])
+@BOTH
 def test_tc_subnormal_columns(gb, opts):
     """A column whose largest entry is subnormal is scaled like any other
     (not flushed to zero): it matches the oracle run on the same column
@@ -183,7 +195,7 @@ def test_tc_subnormal_columns(gb, opts):
     assert np.any(out[:, 1] != 0.0)        # not flushed to zero
 
 
-@pytest.mark.parametrize("opts", [None, TC], ids=["default", "mma_sync"])
+@BOTH
 def test_tc_nonfinite_columns_reported(gb, opts):
     """NaN / +Inf / -Inf entries: the call reports GB_ERR_NONFINITE, those
     columns come back all NaN, every other column is the exact result."""
@@ -207,7 +219,7 @@ def test_tc_nonfinite_columns_reported(gb, opts):
     assert rc == 0 and q == 0 and np.all(np.isfinite(out2))
 
 
-@pytest.mark.parametrize("opts", [None, TC], ids=["default", "mma_sync"])
+@BOTH
 def test_tc_non_orthogonal_reflectors_reported(gb, opts):
     """tau three times the orthogonal value (I - tau v v^T then stretches by
     5 along v): the columns leave the fixed-point range, and the call
@@ -220,7 +232,8 @@ def test_tc_non_orthogonal_reflectors_reported(gb, opts):
     assert gb.gb_status_string(q)
 
 
-def test_tc_columns_at_the_fixed_point_edge(gb):
+@BOTH
+def test_tc_columns_at_the_fixed_point_edge(gb, opts):
     """Columns whose one entry holds the whole norm and sits just below a
     power of two (the tightest column scale), and columns of identity: each
     stays within 50 n u of the oracle and keeps its norm."""
@@ -232,14 +245,15 @@ def test_tc_columns_at_the_fixed_point_edge(gb):
         Z[(37 * c + 5) % n, c] = below * (2.0 ** (c - 6)) * (-1) ** c
     Z[:, 11] = 0.0
     Z[0, 11] = 1.0
-    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     ref = oracle.trans_ev(n, b, hv, ht, Z)
     assert colwise_err(out, ref, Z) <= PARITY
     assert np.abs(np.linalg.norm(out, axis=0) / np.linalg.norm(Z, axis=0) - 1.0).max() <= 50 * n * U
 
 
-def test_tc_eigenvectors_residual(gb):
+@BOTH
+def test_tc_eigenvectors_residual(gb, opts):
     """Z_in = tridiagonal eigenvectors from the oracle's chase + QL: the
     output satisfies B Z = Z Lambda and Z^T Z = I to 50 n u."""
     n, b = 400, 32
@@ -247,41 +261,45 @@ def test_tc_eigenvectors_residual(gb):
     d, e, hv, ht, _ = oracle.bulge_chase(B, b)
     w, V = oracle.tridiag_ql(d, e)
     Z = np.asfortranarray(V[:, :200])
-    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     assert np.linalg.norm(B @ out - out * w[:200]) / np.linalg.norm(B) <= 50 * n * U
     assert np.abs(out.T @ out - np.eye(200)).max() <= 50 * n * U
 
 
+@BOTH
 @pytest.mark.parametrize("cb", [1, 3, 1024])
-def test_tc_schedule_bit_identical(gb, cb):
+def test_tc_schedule_bit_identical(gb, cb, opts):
     n, b, nev = 900, 64, 300
     hv, ht = inputs.synthetic_reflectors(n, b, seed=31)
     Z = inputs.z_gaussian(n, nev, seed=32)
-    rc0, q0, out0 = run(gb, n, b, hv, ht, Z, TC)
-    rc, q, out = run(gb, n, b, hv, ht, Z, dict(TC, column_batch=cb))
+    rc0, q0, out0 = run(gb, n, b, hv, ht, Z, opts)
+    rc, q, out = run(gb, n, b, hv, ht, Z, dict(opts, column_batch=cb))
     assert rc0 == 0 and q0 == 0 and rc == 0 and q == 0
     assert np.array_equal(out, out0)
 
 
-def test_tc_unsupported_band_width_runs_as_pipeline(gb):
+@BOTH
+def test_tc_unsupported_band_width_runs_as_pipeline(gb, opts):
     n, b, nev = 200, 8, 40
-    assert gb.gb_trans_ev_launch_count(n, b, nev, 0, TC) == 1
+    assert gb.gb_trans_ev_launch_count(n, b, nev, 0, opts) == 1
+    assert gb.gb_trans_ev_variant(n, b, nev, 0, opts) == gb.GB_VARIANT_PIPELINE
     hv, ht = inputs.synthetic_reflectors(n, b, seed=1)
     Z = inputs.z_gaussian(n, nev, seed=2)
-    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     assert np.linalg.norm(out - oracle.trans_ev(n, b, hv, ht, Z)) / np.linalg.norm(Z) <= PARITY
 
 
-def test_tc_wait_gives_up_and_context_survives(gb):
+@BOTH
+def test_tc_wait_gives_up_and_context_survives(gb, opts):
     n, b, nev = 600, 32, 128
     hv, ht = inputs.synthetic_reflectors(n, b, seed=3)
     Z = inputs.z_gaussian(n, nev, seed=4)
     G = (n - 1 + 15) // 16
-    rc, q, _ = run(gb, n, b, hv, ht, Z, dict(TC, spin_limit=20000, test_hold_group=G))
+    rc, q, _ = run(gb, n, b, hv, ht, Z, dict(opts, spin_limit=20000, test_hold_group=G))
     assert rc == 0
     assert q == gb.GB_ERR_TIMEOUT
-    rc, q, out = run(gb, n, b, hv, ht, Z, TC)
+    rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     assert np.linalg.norm(out - oracle.trans_ev(n, b, hv, ht, Z)) / np.linalg.norm(Z) <= PARITY
