@@ -62,7 +62,7 @@ namespace {
 
 constexpr int kNB5 = 16;          // sweeps per tile
 constexpr int kCols5 = 128;       // eigenvector columns per work item (the MMA's M)
-constexpr int kThreads5 = 256;    // 8 warps: two per TMEM lane quarter
+constexpr int kThreads5 = 512;    // 16 warps: four per TMEM lane quarter (and per SM sub-partition)
 constexpr int kPlanes = 8;        // balanced base-256 digits of a 64-bit value
 constexpr int kLevels5 = 9;       // digit-pair levels 0..8
 constexpr int kColumnBatch5 = 4;  // 128-column blocks per ticket batch
@@ -85,9 +85,11 @@ struct Geo {
     // window: [128 columns][ZROW] int64, ZROW = 2 mod 4 so that a warp's
     // 16-byte accesses to one row pair of 32 columns are conflict-free
     static constexpr int ZROW = LP + 2;
-    // dZ row chunks: 9 levels x N columns of TMEM each
-    static constexpr int N0 = LP >= 48 ? 48 : LP;
-    static constexpr int N1 = LP - N0;
+    // dZ row chunks of up to 32 rows (an MMA's N = 32 rows x up to 8 U
+    // planes <= 256); the U^T record is laid out chunk by chunk, the planes
+    // of a chunk contiguous along N
+    static constexpr int NCH = 32;
+    static constexpr int CHUNKS = (LP + NCH - 1) / NCH;
     // TMEM columns
     static constexpr int T_ZD = 0;
     static constexpr int T_WACC = 64 * KSTEPS;
@@ -99,9 +101,10 @@ struct Geo {
     static constexpr int S_BAR = S_Z + kCols5 * ZROW * 8;    // 3 mbarriers + TMEM base
     static constexpr int SMEM = S_BAR + 64;
     static_assert(T_WACC + 16 * kLevels5 <= kTmemCols, "Z digits and W levels fit in TMEM");
-    static_assert(T_DZ + kLevels5 * N0 <= kTmemCols && T_DZ + kLevels5 * N1 <= kTmemCols, "dZ levels fit");
+    static_assert(T_DZ + kLevels5 * NCH <= kTmemCols, "dZ levels fit");
     static_assert(8 * LP * 128 * 128 < (1 << 24), "W level sums stay exact in FP32");
-    static_assert(N0 % 16 == 0 && N1 % 16 == 0 && (N0 / 2) % 8 == 0 && (N1 / 2) % 8 == 0, "row chunks");
+    static_assert(LP % 16 == 0 && (NCH / 4) % 4 == 0, "row chunks (the last one 16 or 32 rows)");
+    static_assert((LP / 8) * 8 == LP, "cut units of 8 rows");
     static_assert(REC % 128 == 0 && SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -142,10 +145,30 @@ __device__ __forceinline__ long long fold9(const int (&Lv)[kLevels5], int e)
     return (long long)((unsigned long long)shift_ll(hi, 26 + e) + (unsigned long long)shift_ll(lo, e - 14));
 }
 
-// exact integer of an FP32 level sum below 2^22 in magnitude
-__device__ __forceinline__ int small_int(uint32_t bits)
+// An FP32 level sum x (an integer, |x| < 2^22) plus 1.5 2^23 has the bit
+// pattern 0x4B400000 + x.  Two such patterns combine into the int32
+// L_a 2^8 + L_b with one multiply-add and one subtraction of the combined
+// offset (257 * 0x4B400000 mod 2^32), exact whenever |L_a 2^8 + L_b| < 2^31.
+constexpr uint32_t kMagicBits = 0x4B400000u;
+constexpr uint32_t kPairBias = 0x4B400000u * 257u;
+
+__device__ __forceinline__ uint32_t magic_bits(uint32_t f)
 {
-    return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
+    return __float_as_uint(__fadd_rn(__uint_as_float(f), 12582912.0f));
+}
+
+__device__ __forceinline__ int pair_from_bits(uint32_t a, uint32_t b) { return (int)(a * 256u + b - kPairBias); }
+
+// fold9 for level sums below 2^22 given as magic bit patterns (the dZ
+// product: K = 16, at most 8 pairs of magnitude <= 2^14 per level)
+__device__ __forceinline__ long long fold9_bits(const uint32_t (&b)[kLevels5], int e)
+{
+    const int p0 = pair_from_bits(b[0], b[1]), p1 = pair_from_bits(b[2], b[3]);
+    const int p2 = pair_from_bits(b[4], b[5]), p3 = pair_from_bits(b[6], b[7]);
+    const int l8 = (int)(b[8] - kMagicBits);
+    const long long hi = (long long)p0 * 65536 + p1;
+    const long long lo = ((long long)p2 * 65536 + p3) * 256 + l8;
+    return (long long)((unsigned long long)shift_ll(hi, 26 + e) + (unsigned long long)shift_ll(lo, e - 14));
 }
 
 // round(x 2^(62 - e)) for |x| < 2^e: the row's fixed point (|result| <= 2^62)
@@ -258,8 +281,12 @@ __global__ void __launch_bounds__(128) tc5_tile_prep(int n, const double *__rest
     }
     __syncthreads();
     // digit planes in the canonical K-major layout of the B operands:
-    // V (N = q, K = j): byte (q/8) 16 LP + (j/8) 128 + (q%8) 16 + (j%8) 2;
-    // U^T (N = j, K = q): byte (j/8) 256 + (q/8) 128 + (j%8) 16 + (q%8) 2
+    // V (N = q, K = j), plane t: byte t 32 LP + (q/8) 16 LP + (j/8) 128 +
+    // (q%8) 16 + (j%8) 2, so the planes follow each other along N at the same
+    // 8-row stride (an MMA's B may span planes t0, t0+1, ...);
+    // U^T (N = j, K = q), by chunks of 32 rows: chunk c = j/32 at c 8192,
+    // within it plane t at t (rows of the chunk / 8) 256, then (j%32/8) 256 +
+    // (q/8) 128 + (j%8) 16 + (q%8) 2 (again the planes contiguous along N)
     for (int e = threadIdx.x; e < kNB5 * LP; e += blockDim.x) {
         const int q = e / LP, j = e % LP;
         const unsigned long long y = (unsigned long long)fixed_row(V[j][q], seV[q]) + kDigitBias;
@@ -272,10 +299,11 @@ __global__ void __launch_bounds__(128) tc5_tile_prep(int n, const double *__rest
     for (int e = threadIdx.x; e < LP * kNB5; e += blockDim.x) {
         const int j = e / kNB5, q = e % kNB5;
         const unsigned long long y = (unsigned long long)fixed_row(U[j][q], seU[j]) + kDigitBias;
-        const int o = (j >> 3) * 256 + (q >> 3) * 128 + (j & 7) * 16 + (q & 7) * 2;
+        const int ch = j / Gm::NCH, rows = min(Gm::NCH, LP - ch * Gm::NCH);
+        const int o = ch * Gm::NCH * 256 + ((j % Gm::NCH) >> 3) * 256 + (q >> 3) * 128 + (j & 7) * 16 + (q & 7) * 2;
 #pragma unroll
         for (int t = 0; t < kPlanes; t++)
-            *(__half *)(r + Gm::R_U + t * Gm::PLANE + o) =
+            *(__half *)(r + Gm::R_U + t * (rows / 8) * 256 + o) =
                 __float2half_rn((float)((int)((y >> (56 - 8 * t)) & 0xff) - 128));
     }
 }
@@ -303,7 +331,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     __shared__ Tc5Shared sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, wq = warp >> 2;            // lane quarter, and which of its four warps
     const int col = quarter * 32 + lane;                    // this thread's column of the item (its TMEM lane)
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int b = B;
@@ -418,22 +446,23 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         }
         __syncthreads();
         // ---- Z^T digit planes into TMEM: K step kk, plane s at columns
-        // kk*64 + s*8 .. +7 (pairs of rows); the two warps of a lane quarter
-        // take alternate K steps
+        // kk*64 + s*8 .. +7 (pairs of rows); units of 8 rows (half a K
+        // step) go round-robin to the four warps of the lane quarter
         {
             const long long *zc = Zs + col * ZROW;
-            for (int kk = half; kk < KSTEPS; kk += 2) {
-                uint32_t w[kPlanes][8];
+            for (int u = wq; u < LP / 8; u += 4) {
+                uint32_t w[kPlanes][4];
 #pragma unroll
-                for (int p = 0; p < 8; p++) {
-                    const longlong2 z2 = *(const longlong2 *)(zc + kk * 16 + 2 * p);
+                for (int p = 0; p < 4; p++) {
+                    const longlong2 z2 = *(const longlong2 *)(zc + u * 8 + 2 * p);
                     uint32_t d[kPlanes];
                     cut_pair(z2.x, z2.y, d);
 #pragma unroll
                     for (int s = 0; s < kPlanes; s++) w[s][p] = d[s];
                 }
 #pragma unroll
-                for (int s = 0; s < kPlanes; s++) tc5::st_x8(tmem + lane_off + Gm::T_ZD + kk * 64 + s * 8, w[s]);
+                for (int s = 0; s < kPlanes; s++)
+                    tc5::st_x4(tmem + lane_off + Gm::T_ZD + (u >> 1) * 64 + s * 8 + (u & 1) * 4, w[s]);
             }
             tc5::wait_st();
         }
@@ -449,22 +478,36 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         // ---- W^T = Z^T V: 43 digit pairs x KSTEPS MMAs (M 128, N 16, K 16)
         if (tid == 0) {
             tc5::fence_after_sync();
+            // one MMA per Z digit plane s and K step: B spans V planes
+            // 0 .. 8-s along N, so plane t lands in level s+t (D columns
+            // T_WACC + 16 (s+t)); in the first K step level 8 is first
+            // written by its own MMA (s = 1, t = 7), every other level by s = 0
             const uint32_t sbase = tc5::smem_addr(srec);
             const uint64_t vdesc = tc5::smem_desc(sbase + Gm::R_V, 128, 16 * LP);
-            constexpr uint32_t idw = tc5::idesc_f16_f32(128, 16);
-#pragma unroll 1
+#pragma unroll
             for (int kk = 0; kk < KSTEPS; kk++)
 #pragma unroll
-                for (int s = 0; s < kPlanes; s++)
-#pragma unroll
-                    for (int t = 0; t < kPlanes; t++) {
-                        const int l = s + t;
-                        if (l >= kLevels5) continue;
-                        const uint32_t acc = (kk > 0 || s > (l > 7 ? l - 7 : 0)) ? 1u : 0u;
-                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16 * l, tmem + Gm::T_ZD + kk * 64 + s * 8,
-                                        vdesc + (uint64_t)((t * Gm::PLANE + kk * 256) >> 4), idw, acc);
+                for (int s = 0; s < kPlanes; s++) {
+                    const uint32_t a_t = tmem + Gm::T_ZD + kk * 64 + s * 8;
+                    const uint64_t b0 = vdesc + (uint64_t)((kk * 256) >> 4);
+                    const int nt = s == 0 ? kPlanes : kLevels5 - s;          // planes t = 0 .. nt-1
+                    if (kk == 0 && s == 1) {
+                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16 * 8, a_t, b0 + (uint64_t)((7 * Gm::PLANE) >> 4),
+                                        tc5::idesc_f16_f32(128, 16), 0u);
+                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16, a_t, b0, tc5::idesc_f16_f32(128, 16 * 7), 1u);
+                    } else {
+                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16 * s, a_t, b0, tc5::idesc_f16_f32(128, 16 * nt),
+                                        (kk > 0 || s > 0) ? 1u : 0u);
                     }
+                }
             tc5::commit(bar_mma);
+            // publish the previous tile while the products run: its stores
+            // happened before the barriers since, and the fence and release
+            // here make them visible at GPU scope before the flag
+            if (k > 0 && g + 1 != hold_group) {
+                __threadfence();
+                st_release(progress + (long long)g * C + c, k);
+            }
         }
         mma_pending = true;
         if (!tc5::mbar_wait(bar_mma, mma_phase & 1, kMbarTimeoutNs)) {
@@ -476,16 +519,16 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         }
         mma_phase++;
         tc5::fence_after_sync();
-        // ---- fold W's levels (reflectors 8*half .. +7 of this column), cut
-        // W into digit planes (TMEM columns s*8 + 4*half .. +3)
+        // ---- fold W's levels (reflectors 4*wq .. +3 of this column), cut
+        // W into digit planes (TMEM columns s*8 + 2*wq .. +1)
         {
-            uint32_t a[kLevels5][8];
+            uint32_t a[kLevels5][4];
 #pragma unroll
-            for (int l = 0; l < kLevels5; l++) tc5::ld_x8(tmem + lane_off + Gm::T_WACC + 16 * l + 8 * half, a[l]);
+            for (int l = 0; l < kLevels5; l++) tc5::ld_x4(tmem + lane_off + Gm::T_WACC + 16 * l + 4 * wq, a[l]);
             tc5::wait_ld();
-            uint32_t wd[kPlanes][4];
+            uint32_t wd[kPlanes][2];
 #pragma unroll
-            for (int p = 0; p < 4; p++) {
+            for (int p = 0; p < 2; p++) {
                 long long wi[2];
 #pragma unroll
                 for (int u = 0; u < 2; u++) {
@@ -493,7 +536,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                     int Lv[kLevels5];
 #pragma unroll
                     for (int l = 0; l < kLevels5; l++) Lv[l] = __float2int_rn(__uint_as_float(a[l][i]));
-                    wi[u] = fold9(Lv, eV[8 * half + i]);
+                    wi[u] = fold9(Lv, eV[4 * wq + i]);
                 }
                 uint32_t d[kPlanes];
                 cut_pair(wi[0], wi[1], d);
@@ -504,7 +547,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             // products completed; the W levels stay untouched until the dZ
             // products, issued after the barrier below)
 #pragma unroll
-            for (int s = 0; s < kPlanes; s++) tc5::st_x4(tmem + lane_off + Gm::T_WD + s * 8 + 4 * half, wd[s]);
+            for (int s = 0; s < kPlanes; s++) tc5::st_x2(tmem + lane_off + Gm::T_WD + s * 8 + 2 * wq, wd[s]);
             tc5::wait_st();
         }
         tc5::fence_before_sync();
@@ -513,10 +556,9 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         // ---- dZ^T = W^T U^T by row chunks (M 128, N = chunk, K 16), fold
         // into the window: Zs -= dZ
 #pragma unroll
-        for (int ch = 0; ch < (Gm::N1 ? 2 : 1); ch++) {
-            constexpr int NN0 = Gm::N0;
-            const int N = ch ? Gm::N1 : Gm::N0;
-            const int j0 = ch ? NN0 : 0;
+        for (int ch = 0; ch < Gm::CHUNKS; ch++) {
+            const int j0 = ch * Gm::NCH;
+            const int N = (LP - j0) < Gm::NCH ? (LP - j0) : Gm::NCH;
             if (ch) {
                 tc5::fence_before_sync();
                 __syncthreads();  // the previous chunk's levels are read before they are overwritten
@@ -524,19 +566,25 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             }
             if (tid == 0) {
                 tc5::fence_after_sync();
+                // per W digit plane s one MMA whose B spans the chunk's U
+                // planes 0 .. 8-s along N (level l = s+t at D columns
+                // T_DZ + l N); level 8 first written alone (s = 1, t = 7)
                 const uint32_t sbase = tc5::smem_addr(srec);
-                const uint64_t udesc = tc5::smem_desc(sbase + Gm::R_U + (j0 >> 3) * 256, 128, 256);
-                const uint32_t idz = tc5::idesc_f16_f32(128, N);
+                const uint64_t udesc = tc5::smem_desc(sbase + Gm::R_U + j0 * 256, 128, 256);
+                const uint32_t pstride = (uint32_t)(N / 8) * 256;   // bytes between the chunk's planes
 #pragma unroll
-                for (int s = 0; s < kPlanes; s++)
-#pragma unroll
-                    for (int t = 0; t < kPlanes; t++) {
-                        const int l = s + t;
-                        if (l >= kLevels5) continue;
-                        const uint32_t acc = (s > (l > 7 ? l - 7 : 0)) ? 1u : 0u;
-                        tc5::mma_tmem_a(tmem + Gm::T_DZ + l * N, tmem + Gm::T_WD + s * 8,
-                                        udesc + (uint64_t)((t * Gm::PLANE) >> 4), idz, acc);
+                for (int s = 0; s < kPlanes; s++) {
+                    const uint32_t a_t = tmem + Gm::T_WD + s * 8;
+                    const int nt = s == 0 ? kPlanes : kLevels5 - s;
+                    if (s == 1) {
+                        tc5::mma_tmem_a(tmem + Gm::T_DZ + 8 * N, a_t, udesc + (uint64_t)((7 * pstride) >> 4),
+                                        tc5::idesc_f16_f32(128, N), 0u);
+                        tc5::mma_tmem_a(tmem + Gm::T_DZ + N, a_t, udesc, tc5::idesc_f16_f32(128, 7 * N), 1u);
+                    } else {
+                        tc5::mma_tmem_a(tmem + Gm::T_DZ + s * N, a_t, udesc, tc5::idesc_f16_f32(128, nt * N),
+                                        s > 0 ? 1u : 0u);
                     }
+                }
                 tc5::commit(bar_mma);
             }
             mma_pending = true;
@@ -549,24 +597,44 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             }
             mma_phase++;
             tc5::fence_after_sync();
-            // this thread: rows j0 + half*N/2 .. +N/2 of its column, 8 at a time
+            // this thread: rows j0 + wq*N/4 .. +N/4 of its column (8 or 4),
+            // all levels fetched in one round of TMEM loads
             long long *zc = Zs + col * ZROW;
-            for (int jj = half * (N / 2); jj < (half + 1) * (N / 2); jj += 8) {
-                uint32_t a[kLevels5][8];
+            const int jb = wq * (N / 4);
+            uint32_t a8[kLevels5][8];
+            if (N == 32) {
 #pragma unroll
-                for (int l = 0; l < kLevels5; l++) tc5::ld_x8(tmem + lane_off + Gm::T_DZ + l * N + jj, a[l]);
-                tc5::wait_ld();
+                for (int l = 0; l < kLevels5; l++) tc5::ld_x8(tmem + lane_off + Gm::T_DZ + l * N + jb, a8[l]);
+            } else {
 #pragma unroll
-                for (int p = 0; p < 4; p++) {
+                for (int l = 0; l < kLevels5; l++) {
+                    uint32_t a4[4];
+                    tc5::ld_x4(tmem + lane_off + Gm::T_DZ + l * N + jb, a4);
+#pragma unroll
+                    for (int i = 0; i < 4; i++) a8[l][i] = a4[i];
+                }
+            }
+            tc5::wait_ld();
+#pragma unroll
+            for (int blk = 0; blk < 2; blk++) {
+                if (blk * 4 >= N / 4) break;
+                const int jj = jb + blk * 4;
+                uint32_t a[kLevels5][4];
+#pragma unroll
+                for (int l = 0; l < kLevels5; l++)
+#pragma unroll
+                    for (int i = 0; i < 4; i++) a[l][i] = a8[l][blk * 4 + i];
+#pragma unroll
+                for (int p = 0; p < 2; p++) {
                     const int j = j0 + jj + 2 * p;
                     if (j >= L) continue;
                     long long dz[2];
 #pragma unroll
                     for (int u = 0; u < 2; u++) {
-                        int Lv[kLevels5];
+                        uint32_t bits[kLevels5];
 #pragma unroll
-                        for (int l = 0; l < kLevels5; l++) Lv[l] = small_int(a[l][2 * p + u]);
-                        dz[u] = fold9(Lv, eU[j + u]);
+                        for (int l = 0; l < kLevels5; l++) bits[l] = magic_bits(a[l][2 * p + u]);
+                        dz[u] = fold9_bits(bits, eU[j + u]);
                     }
                     longlong2 *zp = (longlong2 *)(zc + j);
                     longlong2 z2 = *zp;
@@ -596,9 +664,15 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                 }
             }
         }
-        __threadfence();
+        // every thread's stores happen before thread 0's fence and release
+        // (barrier, then a cumulative release at GPU scope); the release of
+        // tile k is issued during tile k+1 (after its products are issued),
+        // that of the item's last tile right here
         __syncthreads();
-        if (tid == 0 && g + 1 != hold_group) st_release(progress + (long long)g * C + c, k + 1);
+        if (tid == 0 && k == K - 1 && g + 1 != hold_group) {
+            __threadfence();
+            st_release(progress + (long long)g * C + c, k + 1);
+        }
     }
     // ---- leave: no copy or MMA of this CTA may still be in flight when its
     // TMEM is released (bounded waits; a timeout was already recorded)
