@@ -72,16 +72,18 @@ def tc_executed_flops(n, nbw, nev):
 
 
 def tc5_executed_flops(n, nbw, nev):
-    """FP16 tensor-core flops one pipeline_tc5 call executes: per tile (16
-    sweeps) and 128-column item, W^T = Z^T V (128 x LP x 16) and
-    dZ^T = W^T U^T (128 x 16 x LP), each over the 43 digit-plane pairs
-    (s + t <= 8 of eight digits per operand), LP = nbw + 15 rounded up to 16."""
-    lp = (nbw + 15 + 15) // 16 * 16
-    G = (n - 1 + 15) // 16
-    tiles = sum((n - (1 + 16 * g) + nbw - 1) // nbw for g in range(G))
+    """FP16 tensor-core flops one pipeline_tc5 call executes: per tile (NB
+    sweeps: 32 for nbw = 64, else 16) and 128-column item, W^T = Z^T V
+    (128 x LP x NB) and dZ^T = W^T U^T (128 x NB x LP), each over the 43
+    digit-plane pairs (s + t <= 8 of eight digits per operand),
+    LP = nbw + NB - 1 rounded up to 16."""
+    nb = 32 if nbw == 64 else 16
+    lp = (nbw + nb - 1 + 15) // 16 * 16
+    G = (n - 1 + nb - 1) // nb
+    tiles = sum((n - (1 + nb * g) + nbw - 1) // nbw for g in range(G))
     items = tiles * ((nev + 127) // 128)
     pairs = sum(1 for s_ in range(8) for t_ in range(8) if s_ + t_ <= 8)     # 43
-    return items * pairs * 2 * (2 * 128 * 16 * lp)
+    return items * pairs * 2 * (2 * 128 * nb * lp)
 
 
 def algorithmic_flops(n, nev, cplx=False):

@@ -46,6 +46,7 @@ cudaError_t pipeline_tc_d(int n, int b, int nev, const double *hh_v, const doubl
 // tiles with 128-column items, FP16 digit planes and FP32 level sums in
 // tensor memory.
 bool pipeline_tc5_supported(int b);
+int pipeline_tc5_sweeps_per_tile(int b);
 size_t pipeline_tc5_workspace_bytes(int n, int b, int nev);
 cudaError_t pipeline_tc5_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
                            int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,

@@ -2,21 +2,21 @@
 // data with nbw in {16, 32, 64}).
 //
 // Schedule (as in the other pipelines): work item (g, c) = all tiles of
-// sweep group g (NB = 16 sweeps) for column block c (128 columns); items
-// take tickets in batches of column blocks, groups descending, so every
-// dependency wait targets an item that is already running; tile k of group
-// g waits until group g+1 has published min(k+1, K_{g+1}) tiles.  All waits
-// are bounded.
+// sweep group g (NB sweeps: 32 for nbw = 64, else 16) for column block c
+// (128 columns); items take tickets in batches of column blocks, groups
+// descending, so every dependency wait targets an item that is already
+// running; tile k of group g waits until group g+1 has published
+// min(k+1, K_{g+1}) tiles.  All waits are bounded.
 //
-// Tile algebra (Sec. 3.1's blocked Householder aggregation): the tile's 16
+// Tile algebra (Sec. 3.1's blocked Householder aggregation): the tile's NB
 // reflectors, applied last sweep first, multiply to I - V T V^T, with V the
-// (b+15) x 16 parallelogram of reflectors and T upper triangular; with
+// (b+NB-1) x NB parallelogram of reflectors and T upper triangular; with
 // U = V T (V's columns scaled to unit length, U's by the inverse factors),
 //     Z_win <- Z_win - U (V^T Z_win).
 // Both products run on the tensor cores, transposed so that the 128
 // eigenvector columns are the MMA's M dimension:
-//     W^T  (128 x 16)  = Z_win^T (128 x LP) . V   (LP x 16)
-//     dZ^T (128 x LP)  = W^T     (128 x 16) . U^T (16 x LP)
+//     W^T  (128 x NB)  = Z_win^T (128 x LP) . V   (LP x NB)
+//     dZ^T (128 x LP)  = W^T     (128 x NB) . U^T (NB x LP)
 //
 // Exact FP64-accurate arithmetic from FP16 digits:
 //  * Z is per-column 64-bit fixed point for the whole call (tc_fixed.cuh),
@@ -28,23 +28,32 @@
 //    x = sum_s d_s 256^(7-s).  Each digit is exact in FP16.
 //  * Digit products of level l = s + t <= 8 (43 pairs) accumulate in FP32 in
 //    TMEM, one accumulator per level.  A level sums at most 8 pairs x K
-//    products of magnitude <= 2^14; for K = 80 that is < 2^23.4, so every
-//    level sum is an exact integer.  The dropped levels (>= 9) are below
-//    2^-69 of the products' scale.
+//    products of magnitude <= 2^14: for the first product K = LP <= 96,
+//    below 2^24 (exact); for the second K = NB <= 32, and because the top
+//    digits are bounded by 32 (W) and 64 (U), below 2^22 (exact, and
+//    convertible by one floating-point addition).  The dropped levels
+//    (>= 9) are below 2^-69 of the products' scale.
+//  * One MMA per digit plane s of the A operand: its B operand spans the
+//    other operand's planes t = 0 .. 8-s along N (the planes follow each
+//    other in shared memory at the same 8-row stride), so plane t's product
+//    lands in the accumulator of level s+t.  9 MMAs per K step instead of 43.
 //  * Levels are folded into 64-bit integers (one rounding per entry) and the
 //    update Zi -= dZi is an integer subtraction.
 //
-// Data movement per tile (b = 64, LP = 80):
-//  * the tile record (V and U^T digit planes in the MMA's canonical
-//    K-major layout, row exponents; 41 KB, built once per tile by
-//    tc5_tile_prep) arrives by cp.async.bulk on an mbarrier, one tile ahead;
-//  * the window (LP rows x 128 columns, int64) lives in shared memory;
-//    the 64 new rows come from global memory through L2, 15 rows carry over;
+// Data movement per tile (b = 64, NB = 32, LP = 96):
+//  * the tile record is a V part (V digit planes in the MMA's canonical
+//    K-major layout, 48 KB) and a U part (U^T digit planes by 32-row
+//    chunks, the row exponents of V and U; 48.5 KB), built once per tile by
+//    tc5_tile_prep; each part arrives by cp.async.bulk on its own mbarrier,
+//    requested as soon as the previous tile no longer needs the buffer;
+//  * the window (LP rows x 128 columns, int64) lives in shared memory; the
+//    64 new rows come from global memory through L2, NB-1 rows carry over;
 //  * Z's digit planes are cut by the threads straight into TMEM (tcgen05.st)
-//    and are the A operand of the first product (A from TMEM); W's digit
-//    planes are the A operand of the second.
-// TMEM (512 columns): Z digits [0, 64 KSTEPS), W levels [64 KSTEPS, +144);
-// then W digits [0, 64) and the dZ levels of a row chunk [64, 64 + 9 N).
+//    and are the A operand of the first product, W's digit planes the A
+//    operand of the second.
+// TMEM (512 columns): Z digits of up to ZR K steps [0, 64 ZR) (two rounds
+// when all K steps do not fit), W levels [64 ZR, + 9 NB); then W digits
+// [0, 64 NB/16) and the dZ levels of a 32-row chunk [64 NB/16, + 9 32).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -60,7 +69,6 @@ namespace gb {
 
 namespace {
 
-constexpr int kNB5 = 16;          // sweeps per tile
 constexpr int kCols5 = 128;       // eigenvector columns per work item (the MMA's M)
 constexpr int kThreads5 = 512;    // 16 warps: four per TMEM lane quarter (and per SM sub-partition)
 constexpr int kPlanes = 8;        // balanced base-256 digits of a 64-bit value
@@ -72,40 +80,49 @@ constexpr long long kMbarTimeoutNs = 2000000000ll;  // an MMA batch or a record 
 
 template <int B>
 struct Geo {
-    static constexpr int L = B + kNB5 - 1;             // window rows
-    static constexpr int LP = (L + 15) / 16 * 16;      // padded to the MMA's K step
-    static constexpr int KSTEPS = LP / 16;
-    static constexpr int PLANE = 32 * LP;              // bytes of one V (16 x LP) or U^T (LP x 16) digit plane
-    // tile record (global and shared): V planes, U^T planes, eV[16], eU[LP]
-    static constexpr int R_V = 0;
-    static constexpr int R_U = kPlanes * PLANE;
-    static constexpr int R_EV = 2 * kPlanes * PLANE;
-    static constexpr int R_EU = R_EV + 16 * 4;
-    static constexpr int REC = (R_EU + LP * 4 + 127) / 128 * 128;
+    static constexpr int NB = B == 64 ? 32 : 16;        // sweeps per tile
+    static constexpr int L = B + NB - 1;                // window rows
+    static constexpr int LP = (L + 15) / 16 * 16;       // padded to the MMA's K step
+    static constexpr int KSTEPS = LP / 16;              // K steps of the first product
+    static constexpr int KD = NB / 16;                  // K steps of the second
+    // tile record: V part [8 planes][NB rows q][LP] and U part [chunks of 32
+    // rows][8 planes][rows][NB] + eV[NB] + eU[LP], canonical K-major
+    static constexpr int VPLANE = NB * LP * 2;
+    static constexpr int VBYTES = kPlanes * VPLANE;
+    static constexpr int UBYTES = kPlanes * LP * NB * 2;
+    static constexpr int U_EV = UBYTES;
+    static constexpr int U_EU = UBYTES + NB * 4;
+    static constexpr int UPART = (UBYTES + (NB + LP) * 4 + 127) / 128 * 128;
+    static constexpr int REC = VBYTES + UPART;
+    static constexpr int SBO_V = 16 * LP;               // bytes between 8-row groups of V (N = q)
+    static constexpr int SBO_U = 16 * NB;               // bytes between 8-row groups of U^T (N = j)
     // window: [128 columns][ZROW] int64, ZROW = 2 mod 4 so that a warp's
     // 16-byte accesses to one row pair of 32 columns are conflict-free
     static constexpr int ZROW = LP + 2;
-    // dZ row chunks of up to 32 rows (an MMA's N = 32 rows x up to 8 U
-    // planes <= 256); the U^T record is laid out chunk by chunk, the planes
-    // of a chunk contiguous along N
+    // dZ row chunks of up to 32 rows (N = 32 rows x up to 8 U planes <= 256)
     static constexpr int NCH = 32;
     static constexpr int CHUNKS = (LP + NCH - 1) / NCH;
     // TMEM columns
+    static constexpr int WLEV = kLevels5 * NB;                      // W level accumulators
+    static constexpr int ZR = (kTmemCols - WLEV) / 64 < KSTEPS ? (kTmemCols - WLEV) / 64 : KSTEPS;
+    static constexpr int ROUNDS = (KSTEPS + ZR - 1) / ZR;
     static constexpr int T_ZD = 0;
-    static constexpr int T_WACC = 64 * KSTEPS;
+    static constexpr int T_WACC = 64 * ZR;
     static constexpr int T_WD = 0;
-    static constexpr int T_DZ = 64;
+    static constexpr int T_DZ = 64 * KD;
     // shared memory
-    static constexpr int S_REC = 0;                          // two record buffers
-    static constexpr int S_Z = 2 * REC;
+    static constexpr int S_V = 0;
+    static constexpr int S_U = VBYTES;
+    static constexpr int S_Z = REC;
     static constexpr int S_BAR = S_Z + kCols5 * ZROW * 8;    // 3 mbarriers + TMEM base
     static constexpr int SMEM = S_BAR + 64;
-    static_assert(T_WACC + 16 * kLevels5 <= kTmemCols, "Z digits and W levels fit in TMEM");
-    static_assert(T_DZ + kLevels5 * NCH <= kTmemCols, "dZ levels fit");
+    static_assert(ZR >= 1 && T_WACC + WLEV <= kTmemCols, "Z digits and W levels fit in TMEM");
+    static_assert(T_DZ + kLevels5 * NCH <= kTmemCols, "W digits and dZ levels fit in TMEM");
     static_assert(8 * LP * 128 * 128 < (1 << 24), "W level sums stay exact in FP32");
-    static_assert(LP % 16 == 0 && (NCH / 4) % 4 == 0, "row chunks (the last one 16 or 32 rows)");
-    static_assert((LP / 8) * 8 == LP, "cut units of 8 rows");
-    static_assert(REC % 128 == 0 && SMEM <= 227 * 1024, "shared memory");
+    static_assert(NB * (7 * 128 * 128) < (1 << 22), "dZ level sums stay below 2^22");
+    static_assert(LP % 16 == 0 && NB % 16 == 0 && NB <= B, "tile shape");
+    static_assert(VBYTES % 128 == 0 && REC % 128 == 0 && S_Z % 16 == 0, "record alignment");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 // ---- digits ----------------------------------------------------------------
@@ -159,8 +176,7 @@ __device__ __forceinline__ uint32_t magic_bits(uint32_t f)
 
 __device__ __forceinline__ int pair_from_bits(uint32_t a, uint32_t b) { return (int)(a * 256u + b - kPairBias); }
 
-// fold9 for level sums below 2^22 given as magic bit patterns (the dZ
-// product: K = 16, at most 8 pairs of magnitude <= 2^14 per level)
+// fold9 for level sums below 2^22 given as magic bit patterns (the dZ product)
 __device__ __forceinline__ long long fold9_bits(const uint32_t (&b)[kLevels5], int e)
 {
     const int p0 = pair_from_bits(b[0], b[1]), p1 = pair_from_bits(b[2], b[3]);
@@ -177,27 +193,37 @@ __device__ __forceinline__ long long fixed_row(double x, int e) { return __doubl
 // ---- per-tile records ------------------------------------------------------
 
 template <int B>
-__global__ void __launch_bounds__(128) tc5_tile_prep(int n, const double *__restrict__ hh_v,
+constexpr size_t prep_smem_bytes()
+{
+    using Gm = Geo<B>;
+    return (size_t)(2 * Gm::LP * (Gm::NB + 1) + 2 * Gm::NB * (Gm::NB + 1) + 2 * Gm::NB) * 8 +
+           (size_t)(Gm::NB + Gm::LP) * 4;
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) tc5_tile_prep(int n, const double *__restrict__ hh_v,
                                                      const double *__restrict__ hh_tau,
                                                      const long long *__restrict__ off,
                                                      unsigned char *__restrict__ rec)
 {
     using Gm = Geo<B>;
-    constexpr int L = Gm::L, LP = Gm::LP;
+    constexpr int L = Gm::L, LP = Gm::LP, NB = Gm::NB, NB1 = NB + 1;
     const int k = blockIdx.x, g = blockIdx.y;
     const int b = B;
-    if (k >= group_tiles(n, b, kNB5, g)) return;
-    __shared__ double V[LP][kNB5 + 1];
-    __shared__ double U[LP][kNB5 + 1];
-    __shared__ double T[kNB5][kNB5 + 1];
-    __shared__ double Gr[kNB5][kNB5 + 1];
-    __shared__ double tau[kNB5];
-    __shared__ double nv[kNB5];
-    __shared__ int seV[kNB5], seU[LP];
-    const int s0 = 1 + g * kNB5;
+    if (k >= group_tiles(n, b, NB, g)) return;
+    extern __shared__ double psm[];
+    double *V = psm;                      // [LP][NB1]
+    double *U = V + LP * NB1;             // [LP][NB1]
+    double *T = U + LP * NB1;             // [NB][NB1]
+    double *Gr = T + NB * NB1;            // [NB][NB1]
+    double *tau = Gr + NB * NB1;          // [NB]
+    double *nv = tau + NB;                // [NB]
+    int *seV = (int *)(nv + NB);          // [NB]
+    int *seU = seV + NB;                  // [LP]
+    const int s0 = 1 + g * NB;
     // reflector q of the tile occupies window rows q .. q+len-1 of column q
-    for (int e = threadIdx.x; e < LP * kNB5; e += blockDim.x) {
-        const int j = e / kNB5, q = e % kNB5;
+    for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
         const int s = s0 + q;
         double val = 0.0;
         if (s <= n - 1 && s + k * b < n && j - q >= 0 && j - q < b && j < L) {
@@ -207,103 +233,105 @@ __global__ void __launch_bounds__(128) tc5_tile_prep(int n, const double *__rest
             const int i = j - q;
             if (t != 0.0 && i < len) val = (i == 0) ? 1.0 : hh_v[idx * b + i];
         }
-        V[j][q] = val;
+        V[j * NB1 + q] = val;
     }
-    if (threadIdx.x < kNB5) {
+    if (threadIdx.x < NB) {
         const int s = s0 + threadIdx.x;
         tau[threadIdx.x] = (s <= n - 1 && s + k * b < n) ? hh_tau[sweep_first(n, b, s) + k] : 0.0;
     }
     __syncthreads();
     // Gram matrix (upper triangle), T by the forward recurrence
     // T(q,q) = tau_q, T(0:q,q) = -tau_q T(0:q,0:q) V(:,0:q)^T v_q
-    for (int e = threadIdx.x; e < kNB5 * kNB5; e += blockDim.x) {
-        const int p = e / kNB5, q = e % kNB5;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int p = e / NB, q = e % NB;
         double a = 0.0;
         if (p < q)
-            for (int j = q; j < min(p + b, LP); j++) a = fma(V[j][p], V[j][q], a);
-        Gr[p][q] = a;
+            for (int j = q; j < min(p + b, LP); j++) a = fma(V[j * NB1 + p], V[j * NB1 + q], a);
+        Gr[p * NB1 + q] = a;
     }
     __syncthreads();
-    for (int q = 0; q < kNB5; q++) {
-        if (threadIdx.x < kNB5) {
+    for (int q = 0; q < NB; q++) {
+        if (threadIdx.x < NB) {
             const int i = threadIdx.x;
             double t = 0.0;
             if (i < q) {
-                for (int p = i; p < q; p++) t = fma(T[i][p], Gr[p][q], t);
+                for (int p = i; p < q; p++) t = fma(T[i * NB1 + p], Gr[p * NB1 + q], t);
                 t = -tau[q] * t;
             } else if (i == q) {
                 t = tau[q];
             }
-            T[i][q] = t;
+            T[i * NB1 + q] = t;
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < LP * kNB5; e += blockDim.x) {
-        const int j = e / kNB5, q = e % kNB5;
+    for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
         double a = 0.0;
-        for (int p = 0; p <= q; p++) a = fma(V[j][p], T[p][q], a);
-        U[j][q] = a;
+        for (int p = 0; p <= q; p++) a = fma(V[j * NB1 + p], T[p * NB1 + q], a);
+        U[j * NB1 + q] = a;
     }
     // unit columns of V (U rescaled to keep U V^T): |v_q^T z| <= ||z||, so W
     // stays inside the column's fixed-point range whatever tau is
-    if (threadIdx.x < kNB5) {
+    if (threadIdx.x < NB) {
         double a = 0.0;
-        for (int j = 0; j < LP; j++) a = fma(V[j][threadIdx.x], V[j][threadIdx.x], a);
+        for (int j = 0; j < LP; j++) a = fma(V[j * NB1 + threadIdx.x], V[j * NB1 + threadIdx.x], a);
         nv[threadIdx.x] = sqrt(a);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < LP * kNB5; e += blockDim.x) {
-        const int j = e / kNB5, q = e % kNB5;
+    for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
         if (nv[q] > 0.0) {
-            V[j][q] = V[j][q] / nv[q];
-            U[j][q] = U[j][q] * nv[q];
+            V[j * NB1 + q] = V[j * NB1 + q] / nv[q];
+            U[j * NB1 + q] = U[j * NB1 + q] * nv[q];
         }
     }
     __syncthreads();
     unsigned char *r = rec + ((size_t)off[g] + k) * Gm::REC;
-    if (threadIdx.x < kNB5) {
+    unsigned char *ru = r + Gm::VBYTES;
+    if (threadIdx.x < NB) {
         unsigned long long m = 0;
         for (int j = 0; j < LP; j++) {
-            const unsigned long long u = (unsigned long long)__double_as_longlong(V[j][threadIdx.x]) & ~(1ull << 63);
+            const unsigned long long u = (unsigned long long)__double_as_longlong(V[j * NB1 + threadIdx.x]) & ~(1ull << 63);
             m = u > m ? u : m;
         }
         seV[threadIdx.x] = exponent_above(m);
-        ((int *)(r + Gm::R_EV))[threadIdx.x] = seV[threadIdx.x];
+        ((int *)(ru + Gm::U_EV))[threadIdx.x] = seV[threadIdx.x];
     }
     for (int j = threadIdx.x; j < LP; j += blockDim.x) {
         unsigned long long m = 0;
-        for (int q = 0; q < kNB5; q++) {
-            const unsigned long long u = (unsigned long long)__double_as_longlong(U[j][q]) & ~(1ull << 63);
+        for (int q = 0; q < NB; q++) {
+            const unsigned long long u = (unsigned long long)__double_as_longlong(U[j * NB1 + q]) & ~(1ull << 63);
             m = u > m ? u : m;
         }
         seU[j] = exponent_above(m);
-        ((int *)(r + Gm::R_EU))[j] = seU[j];
+        ((int *)(ru + Gm::U_EU))[j] = seU[j];
     }
     __syncthreads();
     // digit planes in the canonical K-major layout of the B operands:
-    // V (N = q, K = j), plane t: byte t 32 LP + (q/8) 16 LP + (j/8) 128 +
+    // V (N = q, K = j), plane t: byte t VPLANE + (q/8) SBO_V + (j/8) 128 +
     // (q%8) 16 + (j%8) 2, so the planes follow each other along N at the same
     // 8-row stride (an MMA's B may span planes t0, t0+1, ...);
-    // U^T (N = j, K = q), by chunks of 32 rows: chunk c = j/32 at c 8192,
-    // within it plane t at t (rows of the chunk / 8) 256, then (j%32/8) 256 +
-    // (q/8) 128 + (j%8) 16 + (q%8) 2 (again the planes contiguous along N)
-    for (int e = threadIdx.x; e < kNB5 * LP; e += blockDim.x) {
+    // U^T (N = j, K = q), by chunks of 32 rows: chunk c = j/32 at c 32 SBO_U,
+    // within it plane t at t (rows of the chunk / 8) SBO_U, then
+    // (j%32/8) SBO_U + (q/8) 128 + (j%8) 16 + (q%8) 2 (again the planes of a
+    // chunk contiguous along N)
+    for (int e = threadIdx.x; e < NB * LP; e += blockDim.x) {
         const int q = e / LP, j = e % LP;
-        const unsigned long long y = (unsigned long long)fixed_row(V[j][q], seV[q]) + kDigitBias;
-        const int o = (q >> 3) * 16 * LP + (j >> 3) * 128 + (q & 7) * 16 + (j & 7) * 2;
+        const unsigned long long y = (unsigned long long)fixed_row(V[j * NB1 + q], seV[q]) + kDigitBias;
+        const int o = (q >> 3) * Gm::SBO_V + (j >> 3) * 128 + (q & 7) * 16 + (j & 7) * 2;
 #pragma unroll
         for (int t = 0; t < kPlanes; t++)
-            *(__half *)(r + Gm::R_V + t * Gm::PLANE + o) =
-                __float2half_rn((float)((int)((y >> (56 - 8 * t)) & 0xff) - 128));
+            *(__half *)(r + t * Gm::VPLANE + o) = __float2half_rn((float)((int)((y >> (56 - 8 * t)) & 0xff) - 128));
     }
-    for (int e = threadIdx.x; e < LP * kNB5; e += blockDim.x) {
-        const int j = e / kNB5, q = e % kNB5;
-        const unsigned long long y = (unsigned long long)fixed_row(U[j][q], seU[j]) + kDigitBias;
+    for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
+        const unsigned long long y = (unsigned long long)fixed_row(U[j * NB1 + q], seU[j]) + kDigitBias;
         const int ch = j / Gm::NCH, rows = min(Gm::NCH, LP - ch * Gm::NCH);
-        const int o = ch * Gm::NCH * 256 + ((j % Gm::NCH) >> 3) * 256 + (q >> 3) * 128 + (j & 7) * 16 + (q & 7) * 2;
+        const int o = ch * Gm::NCH * Gm::SBO_U + ((j % Gm::NCH) >> 3) * Gm::SBO_U + (q >> 3) * 128 + (j & 7) * 16 +
+                      (q & 7) * 2;
 #pragma unroll
         for (int t = 0; t < kPlanes; t++)
-            *(__half *)(r + Gm::R_U + t * (rows / 8) * 256 + o) =
+            *(__half *)(ru + t * (rows / 8) * Gm::SBO_U + o) =
                 __float2half_rn((float)((int)((y >> (56 - 8 * t)) & 0xff) - 128));
     }
 }
@@ -315,6 +343,16 @@ struct Tc5Shared {
     int abort;
 };
 
+// every thread: wait for an mbarrier phase; on giving up record the timeout
+__device__ __forceinline__ bool tc5_wait(uint32_t bar, uint32_t parity, TcState *state, Tc5Shared &sh)
+{
+    if (tc5::mbar_wait(bar, parity, kMbarTimeoutNs)) return true;
+    tc_set_error(state, GB_ERR_TIMEOUT);
+    atomicExch(&state->abort, 1);
+    sh.abort = 1;
+    return false;
+}
+
 template <int B>
 __global__ void __launch_bounds__(kThreads5, 1)
 pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const unsigned char *__restrict__ rec,
@@ -322,12 +360,16 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
              long long spin_polls, long long timeout_ns, int hold_group)
 {
     using Gm = Geo<B>;
-    constexpr int L = Gm::L, LP = Gm::LP, ZROW = Gm::ZROW, KSTEPS = Gm::KSTEPS;
+    constexpr int L = Gm::L, LP = Gm::LP, ZROW = Gm::ZROW, KSTEPS = Gm::KSTEPS, NB = Gm::NB;
+    constexpr int ZR = Gm::ZR, KD = Gm::KD;
     extern __shared__ __align__(1024) unsigned char smem[];
     long long *Zs = (long long *)(smem + Gm::S_Z);
-    const uint32_t bar_rec0 = tc5::smem_addr(smem + Gm::S_BAR);
-    const uint32_t bar_mma = bar_rec0 + 16;
+    const uint32_t bar_v = tc5::smem_addr(smem + Gm::S_BAR);
+    const uint32_t bar_u = bar_v + 8;
+    const uint32_t bar_mma = bar_v + 16;
     uint32_t *tmem_slot = (uint32_t *)(smem + Gm::S_BAR + 32);
+    const int *eV = (const int *)(smem + Gm::S_U + Gm::U_EV);
+    const int *eU = (const int *)(smem + Gm::S_U + Gm::U_EU);
     __shared__ Tc5Shared sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -339,8 +381,8 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     if (tid == 0) {
         sh.item = atomicAdd(&state->ticket, 1);
         sh.abort = 0;
-        tc5::mbar_init(bar_rec0, 1);
-        tc5::mbar_init(bar_rec0 + 8, 1);
+        tc5::mbar_init(bar_v, 1);
+        tc5::mbar_init(bar_u, 1);
         tc5::mbar_init(bar_mma, 1);
         tc5::mbar_init_fence();
     }
@@ -356,31 +398,27 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     const int cb = min(CB, C - batch * CB);
     const int g = G - 1 - rem / cb;
     const int c = batch * CB + rem % cb;
-    const int s0 = 1 + g * kNB5;
-    const int K = group_tiles(n, b, kNB5, g);
-    const int Knext = (g + 1 < G) ? group_tiles(n, b, kNB5, g + 1) : 0;
+    const int s0 = 1 + g * NB;
+    const int K = group_tiles(n, b, NB, g);
+    const int Knext = (g + 1 < G) ? group_tiles(n, b, NB, g + 1) : 0;
     const int col0 = c * kCols5;
     const unsigned char *rec_g = rec + (size_t)off[g] * Gm::REC;
 
-    int issued = 0;        // records requested so far (thread 0)
     uint32_t mma_phase = 0;
     bool mma_pending = false;
+    int v_issued = 0, u_issued = 0;   // record parts requested so far (thread 0)
 
     if (tid == 0) {
         if (g + 1 != hold_group) st_release(progress + (long long)g * C + c, 0);
-        tc5::fence_proxy_async_smem();
-        tc5::bulk_load(tc5::smem_addr(smem + Gm::S_REC), rec_g, Gm::REC, bar_rec0);
-        issued = 1;
+        tc5::bulk_load(tc5::smem_addr(smem + Gm::S_V), rec_g, Gm::VBYTES, bar_v);
+        tc5::bulk_load(tc5::smem_addr(smem + Gm::S_U), rec_g + Gm::VBYTES, Gm::UPART, bar_u);
+        v_issued = u_issued = 1;
     }
     // window padding rows stay zero for the whole item
     for (int e = tid; e < kCols5 * (LP - L); e += kThreads5) Zs[(e / (LP - L)) * ZROW + L + e % (LP - L)] = 0;
 
     for (int k = 0; k < K; k++) {
-        const int buf = k & 1;
-        const unsigned char *srec = smem + Gm::S_REC + buf * Gm::REC;
-        const int *eV = (const int *)(srec + Gm::R_EV);
-        const int *eU = (const int *)(srec + Gm::R_EU);
-        // ---- dependency wait; then request the next tile's record
+        // ---- dependency wait
         if (tid == 0) {
             int abort = 0;
             const int need = (g + 1 < G) ? min(k + 1, Knext) : 0;
@@ -400,21 +438,15 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             }
             if (!abort && *(volatile int *)&state->abort) abort = 1;
             if (abort) sh.abort = 1;
-            if (!abort && k + 1 < K) {
-                tc5::fence_proxy_async_smem();
-                tc5::bulk_load(tc5::smem_addr(smem + Gm::S_REC + (buf ^ 1) * Gm::REC), rec_g + (size_t)(k + 1) * Gm::REC,
-                               Gm::REC, bar_rec0 + 8 * (buf ^ 1));
-                issued = k + 2;
-            }
         }
         __syncthreads();
         if (sh.abort) break;
         // ---- window: new rows from global memory (through L2: rows written
-        // by other SMs), the 15 rows shared with the previous tile carried
+        // by other SMs), the NB-1 rows shared with the previous tile carried
         const long long row0 = (long long)s0 + (long long)k * b;
-        const int jlo = (k == 0) ? 0 : kNB5 - 1;
+        const int jlo = (k == 0) ? 0 : NB - 1;
         {
-            constexpr int H = (L + 31) / 32;           // passes of 32 rows per column
+            constexpr int H = (L + 31) / 32;               // passes of 32 rows per column
             constexpr int CW = kCols5 / (kThreads5 / 32);  // columns per warp
             long long v[CW][H];
 #pragma unroll
@@ -428,8 +460,8 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                 }
             }
             if (k > 0) {
-                for (int e = tid; e < kCols5 * (kNB5 - 1); e += kThreads5) {
-                    const int cc = e / (kNB5 - 1), j = e % (kNB5 - 1);
+                for (int e = tid; e < kCols5 * (NB - 1); e += kThreads5) {
+                    const int cc = e / (NB - 1), j = e % (NB - 1);
                     Zs[cc * ZROW + j] = Zs[cc * ZROW + j + b];
                 }
                 __syncthreads();  // carried rows read before the new rows overwrite them
@@ -445,12 +477,20 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             }
         }
         __syncthreads();
-        // ---- Z^T digit planes into TMEM: K step kk, plane s at columns
-        // kk*64 + s*8 .. +7 (pairs of rows); units of 8 rows (half a K
-        // step) go round-robin to the four warps of the lane quarter
-        {
-            const long long *zc = Zs + col * ZROW;
-            for (int u = wq; u < LP / 8; u += 4) {
+        // ---- W^T = Z^T V, in rounds of ZR K steps (Z digit planes cut into
+        // TMEM, K step kk of the round at columns (kk - r ZR) 64 + s 8 + pair;
+        // units of 8 rows go round-robin to the four warps of a lane quarter)
+        const long long *zc = Zs + col * ZROW;
+#pragma unroll 1
+        for (int r = 0; r < Gm::ROUNDS; r++) {
+            const int kk0 = r * ZR, kk1 = (kk0 + ZR < KSTEPS) ? kk0 + ZR : KSTEPS;
+            if (r > 0) {   // the previous round's MMAs read the Z-digit columns
+                mma_pending = true;
+                if (tc5_wait(bar_mma, mma_phase & 1, state, sh)) mma_pending = false;
+                mma_phase++;
+                tc5::fence_after_sync();
+            }
+            for (int u = 2 * kk0 + wq; u < 2 * kk1; u += 4) {
                 uint32_t w[kPlanes][4];
 #pragma unroll
                 for (int p = 0; p < 4; p++) {
@@ -462,73 +502,74 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                 }
 #pragma unroll
                 for (int s = 0; s < kPlanes; s++)
-                    tc5::st_x4(tmem + lane_off + Gm::T_ZD + (u >> 1) * 64 + s * 8 + (u & 1) * 4, w[s]);
+                    tc5::st_x4(tmem + lane_off + Gm::T_ZD + ((u >> 1) - kk0) * 64 + s * 8 + (u & 1) * 4, w[s]);
             }
             tc5::wait_st();
-        }
-        // every thread sees the record land (its row exponents are read below)
-        if (!tc5::mbar_wait(bar_rec0 + 8 * buf, (uint32_t)((k >> 1) & 1), kMbarTimeoutNs)) {
-            tc_set_error(state, GB_ERR_TIMEOUT);
-            atomicExch(&state->abort, 1);
-            sh.abort = 1;
-        }
-        tc5::fence_before_sync();
-        __syncthreads();
-        if (sh.abort) break;
-        // ---- W^T = Z^T V: 43 digit pairs x KSTEPS MMAs (M 128, N 16, K 16)
-        if (tid == 0) {
-            tc5::fence_after_sync();
-            // one MMA per Z digit plane s and K step: B spans V planes
-            // 0 .. 8-s along N, so plane t lands in level s+t (D columns
-            // T_WACC + 16 (s+t)); in the first K step level 8 is first
-            // written by its own MMA (s = 1, t = 7), every other level by s = 0
-            const uint32_t sbase = tc5::smem_addr(srec);
-            const uint64_t vdesc = tc5::smem_desc(sbase + Gm::R_V, 128, 16 * LP);
+            if (r == 0) tc5_wait(bar_v, (uint32_t)(k & 1), state, sh);   // this tile's V planes
+            tc5::fence_before_sync();
+            __syncthreads();
+            if (sh.abort) break;
+            if (tid == 0) {
+                // one MMA per Z digit plane s and K step: B spans V planes
+                // 0 .. 8-s along N, so plane t lands in level s+t (D columns
+                // T_WACC + NB (s+t)); in the first K step level 8 is first
+                // written by its own MMA (s = 1, t = 7), every other level by s = 0
+                tc5::fence_after_sync();
+                const uint64_t vdesc = tc5::smem_desc(tc5::smem_addr(smem + Gm::S_V), 128, Gm::SBO_V);
+                for (int kk = kk0; kk < kk1; kk++)
 #pragma unroll
-            for (int kk = 0; kk < KSTEPS; kk++)
-#pragma unroll
-                for (int s = 0; s < kPlanes; s++) {
-                    const uint32_t a_t = tmem + Gm::T_ZD + kk * 64 + s * 8;
-                    const uint64_t b0 = vdesc + (uint64_t)((kk * 256) >> 4);
-                    const int nt = s == 0 ? kPlanes : kLevels5 - s;          // planes t = 0 .. nt-1
-                    if (kk == 0 && s == 1) {
-                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16 * 8, a_t, b0 + (uint64_t)((7 * Gm::PLANE) >> 4),
-                                        tc5::idesc_f16_f32(128, 16), 0u);
-                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16, a_t, b0, tc5::idesc_f16_f32(128, 16 * 7), 1u);
-                    } else {
-                        tc5::mma_tmem_a(tmem + Gm::T_WACC + 16 * s, a_t, b0, tc5::idesc_f16_f32(128, 16 * nt),
-                                        (kk > 0 || s > 0) ? 1u : 0u);
+                    for (int s = 0; s < kPlanes; s++) {
+                        const uint32_t a_t = tmem + Gm::T_ZD + (kk - kk0) * 64 + s * 8;
+                        const uint64_t b0 = vdesc + (uint64_t)((kk * 256) >> 4);
+                        const int nt = s == 0 ? kPlanes : kLevels5 - s;          // planes t = 0 .. nt-1
+                        if (kk == 0 && s == 1) {
+                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NB * 8, a_t, b0 + (uint64_t)((7 * Gm::VPLANE) >> 4),
+                                            tc5::idesc_f16_f32(128, NB), 0u);
+                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NB, a_t, b0, tc5::idesc_f16_f32(128, NB * 7), 1u);
+                        } else {
+                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NB * s, a_t, b0, tc5::idesc_f16_f32(128, NB * nt),
+                                            (kk > 0 || s > 0) ? 1u : 0u);
+                        }
                     }
+                tc5::commit(bar_mma);
+                // publish the previous tile while the products run: its stores
+                // happened before the barriers since, and the fence and release
+                // here make them visible at GPU scope before the flag
+                if (r == 0 && k > 0 && g + 1 != hold_group) {
+                    __threadfence();
+                    st_release(progress + (long long)g * C + c, k);
                 }
-            tc5::commit(bar_mma);
-            // publish the previous tile while the products run: its stores
-            // happened before the barriers since, and the fence and release
-            // here make them visible at GPU scope before the flag
-            if (k > 0 && g + 1 != hold_group) {
-                __threadfence();
-                st_release(progress + (long long)g * C + c, k);
             }
         }
+        if (sh.abort) break;
         mma_pending = true;
-        if (!tc5::mbar_wait(bar_mma, mma_phase & 1, kMbarTimeoutNs)) {
-            tc_set_error(state, GB_ERR_TIMEOUT);
-            atomicExch(&state->abort, 1);
-            sh.abort = 1;
-        } else {
-            mma_pending = false;
-        }
+        if (tc5_wait(bar_mma, mma_phase & 1, state, sh)) mma_pending = false;
         mma_phase++;
         tc5::fence_after_sync();
-        // ---- fold W's levels (reflectors 4*wq .. +3 of this column), cut
-        // W into digit planes (TMEM columns s*8 + 2*wq .. +1)
+        // the V buffer is free: request the next tile's V planes
+        if (tid == 0 && k + 1 < K) {
+            tc5::bulk_load(tc5::smem_addr(smem + Gm::S_V), rec_g + (size_t)(k + 1) * Gm::REC, Gm::VBYTES, bar_v);
+            v_issued = k + 2;
+        }
+        // ---- fold W's levels (reflectors q0 .. q0+NB/4-1 of this column), cut
+        // W into digit planes (TMEM: K step q/16, columns s*8 + (q%16)/2)
+        tc5_wait(bar_u, (uint32_t)(k & 1), state, sh);   // this tile's U part (row exponents)
         {
-            uint32_t a[kLevels5][4];
+            constexpr int QW = NB / 4;
+            const int q0 = wq * QW;
+            uint32_t a[kLevels5][QW];
 #pragma unroll
-            for (int l = 0; l < kLevels5; l++) tc5::ld_x4(tmem + lane_off + Gm::T_WACC + 16 * l + 4 * wq, a[l]);
+            for (int l = 0; l < kLevels5; l++) {
+                if constexpr (QW == 8) {
+                    tc5::ld_x8(tmem + lane_off + Gm::T_WACC + NB * l + q0, a[l]);
+                } else {
+                    tc5::ld_x4(tmem + lane_off + Gm::T_WACC + NB * l + q0, a[l]);
+                }
+            }
             tc5::wait_ld();
-            uint32_t wd[kPlanes][2];
+            uint32_t wd[kPlanes][QW / 2];
 #pragma unroll
-            for (int p = 0; p < 2; p++) {
+            for (int p = 0; p < QW / 2; p++) {
                 long long wi[2];
 #pragma unroll
                 for (int u = 0; u < 2; u++) {
@@ -536,7 +577,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                     int Lv[kLevels5];
 #pragma unroll
                     for (int l = 0; l < kLevels5; l++) Lv[l] = __float2int_rn(__uint_as_float(a[l][i]));
-                    wi[u] = fold9(Lv, eV[4 * wq + i]);
+                    wi[u] = fold9(Lv, eV[q0 + i]);
                 }
                 uint32_t d[kPlanes];
                 cut_pair(wi[0], wi[1], d);
@@ -546,15 +587,22 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             // (the W digits go to the Z-digit columns, dead since the W
             // products completed; the W levels stay untouched until the dZ
             // products, issued after the barrier below)
+            const uint32_t wcol = Gm::T_WD + (q0 >> 4) * 64 + (q0 & 15) / 2;
 #pragma unroll
-            for (int s = 0; s < kPlanes; s++) tc5::st_x2(tmem + lane_off + Gm::T_WD + s * 8 + 2 * wq, wd[s]);
+            for (int s = 0; s < kPlanes; s++) {
+                if constexpr (QW == 8) {
+                    tc5::st_x4(tmem + lane_off + wcol + s * 8, wd[s]);
+                } else {
+                    tc5::st_x2(tmem + lane_off + wcol + s * 8, wd[s]);
+                }
+            }
             tc5::wait_st();
         }
         tc5::fence_before_sync();
         __syncthreads();
         if (sh.abort) break;
-        // ---- dZ^T = W^T U^T by row chunks (M 128, N = chunk, K 16), fold
-        // into the window: Zs -= dZ
+        // ---- dZ^T = W^T U^T by row chunks (M 128, N = rows x planes, K NB),
+        // folded into the window: Zs -= dZ
 #pragma unroll
         for (int ch = 0; ch < Gm::CHUNKS; ch++) {
             const int j0 = ch * Gm::NCH;
@@ -565,41 +613,38 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                 if (sh.abort) break;
             }
             if (tid == 0) {
+                // per W digit plane s and K step one MMA whose B spans the
+                // chunk's U planes 0 .. 8-s along N (level l = s+t at D
+                // columns T_DZ + l N); level 8 first written alone (s = 1, t = 7)
                 tc5::fence_after_sync();
-                // per W digit plane s one MMA whose B spans the chunk's U
-                // planes 0 .. 8-s along N (level l = s+t at D columns
-                // T_DZ + l N); level 8 first written alone (s = 1, t = 7)
-                const uint32_t sbase = tc5::smem_addr(srec);
-                const uint64_t udesc = tc5::smem_desc(sbase + Gm::R_U + j0 * 256, 128, 256);
-                const uint32_t pstride = (uint32_t)(N / 8) * 256;   // bytes between the chunk's planes
+                const uint64_t udesc =
+                    tc5::smem_desc(tc5::smem_addr(smem + Gm::S_U) + (uint32_t)j0 * Gm::SBO_U, 128, Gm::SBO_U);
+                const uint32_t pstride = (uint32_t)(N / 8) * Gm::SBO_U;   // bytes between the chunk's planes
 #pragma unroll
-                for (int s = 0; s < kPlanes; s++) {
-                    const uint32_t a_t = tmem + Gm::T_WD + s * 8;
-                    const int nt = s == 0 ? kPlanes : kLevels5 - s;
-                    if (s == 1) {
-                        tc5::mma_tmem_a(tmem + Gm::T_DZ + 8 * N, a_t, udesc + (uint64_t)((7 * pstride) >> 4),
-                                        tc5::idesc_f16_f32(128, N), 0u);
-                        tc5::mma_tmem_a(tmem + Gm::T_DZ + N, a_t, udesc, tc5::idesc_f16_f32(128, 7 * N), 1u);
-                    } else {
-                        tc5::mma_tmem_a(tmem + Gm::T_DZ + s * N, a_t, udesc, tc5::idesc_f16_f32(128, nt * N),
-                                        s > 0 ? 1u : 0u);
+                for (int kd = 0; kd < KD; kd++)
+#pragma unroll
+                    for (int s = 0; s < kPlanes; s++) {
+                        const uint32_t a_t = tmem + Gm::T_WD + kd * 64 + s * 8;
+                        const uint64_t b0 = udesc + (uint64_t)((kd * 256) >> 4);
+                        const int nt = s == 0 ? kPlanes : kLevels5 - s;
+                        if (kd == 0 && s == 1) {
+                            tc5::mma_tmem_a(tmem + Gm::T_DZ + 8 * N, a_t, b0 + (uint64_t)((7 * pstride) >> 4),
+                                            tc5::idesc_f16_f32(128, N), 0u);
+                            tc5::mma_tmem_a(tmem + Gm::T_DZ + N, a_t, b0, tc5::idesc_f16_f32(128, 7 * N), 1u);
+                        } else {
+                            tc5::mma_tmem_a(tmem + Gm::T_DZ + s * N, a_t, b0, tc5::idesc_f16_f32(128, nt * N),
+                                            (kd > 0 || s > 0) ? 1u : 0u);
+                        }
                     }
-                }
                 tc5::commit(bar_mma);
             }
             mma_pending = true;
-            if (!tc5::mbar_wait(bar_mma, mma_phase & 1, kMbarTimeoutNs)) {
-                tc_set_error(state, GB_ERR_TIMEOUT);
-                atomicExch(&state->abort, 1);
-                sh.abort = 1;
-            } else {
-                mma_pending = false;
-            }
+            if (tc5_wait(bar_mma, mma_phase & 1, state, sh)) mma_pending = false;
             mma_phase++;
             tc5::fence_after_sync();
             // this thread: rows j0 + wq*N/4 .. +N/4 of its column (8 or 4),
             // all levels fetched in one round of TMEM loads
-            long long *zc = Zs + col * ZROW;
+            long long *zw = Zs + col * ZROW;
             const int jb = wq * (N / 4);
             uint32_t a8[kLevels5][8];
             if (N == 32) {
@@ -616,38 +661,37 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
             }
             tc5::wait_ld();
 #pragma unroll
-            for (int blk = 0; blk < 2; blk++) {
-                if (blk * 4 >= N / 4) break;
-                const int jj = jb + blk * 4;
-                uint32_t a[kLevels5][4];
+            for (int p = 0; p < 4; p++) {
+                if (2 * p >= N / 4) break;
+                const int j = j0 + jb + 2 * p;
+                if (j >= L) continue;
+                long long dz[2];
 #pragma unroll
-                for (int l = 0; l < kLevels5; l++)
+                for (int u = 0; u < 2; u++) {
+                    uint32_t bits[kLevels5];
 #pragma unroll
-                    for (int i = 0; i < 4; i++) a[l][i] = a8[l][blk * 4 + i];
-#pragma unroll
-                for (int p = 0; p < 2; p++) {
-                    const int j = j0 + jj + 2 * p;
-                    if (j >= L) continue;
-                    long long dz[2];
-#pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        uint32_t bits[kLevels5];
-#pragma unroll
-                        for (int l = 0; l < kLevels5; l++) bits[l] = magic_bits(a[l][2 * p + u]);
-                        dz[u] = fold9_bits(bits, eU[j + u]);
-                    }
-                    longlong2 *zp = (longlong2 *)(zc + j);
-                    longlong2 z2 = *zp;
-                    z2.x -= dz[0];
-                    if (j + 1 < L) z2.y -= dz[1];
-                    *zp = z2;
+                    for (int l = 0; l < kLevels5; l++) bits[l] = magic_bits(a8[l][2 * p + u]);
+                    dz[u] = fold9_bits(bits, eU[j + u]);
                 }
+                longlong2 *zp = (longlong2 *)(zw + j);
+                longlong2 z2 = *zp;
+                z2.x -= dz[0];
+                if (j + 1 < L) z2.y -= dz[1];
+                *zp = z2;
             }
         }
         tc5::fence_before_sync();   // this tile's TMEM reads precede the next tile's TMEM writes
         __syncthreads();
         tc5::fence_after_sync();
         if (sh.abort) break;
+        // the U part is consumed (planes by the MMAs, exponents by the folds
+        // above): request the next tile's
+        if (tid == 0 && k + 1 < K) {
+            tc5::fence_proxy_async_smem();
+            tc5::bulk_load(tc5::smem_addr(smem + Gm::S_U), rec_g + (size_t)(k + 1) * Gm::REC + Gm::VBYTES, Gm::UPART,
+                           bar_u);
+            u_issued = k + 2;
+        }
         // ---- store the rows final for this group (all rows after the last tile)
         {
             const int jhi = (k == K - 1) ? L : b;
@@ -655,11 +699,11 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                 if (col0 + cc >= nev) continue;
                 long long *zg = Zi + (long long)(col0 + cc) * ldz;
                 for (int j = lane; j < jhi; j += 32) {
-                    const long long r = row0 + j;
-                    if (r < n) {
-                        const long long v = Zs[cc * ZROW + j];
-                        if (tc_out_of_range(v)) tc_set_error(state, GB_ERR_RANGE);
-                        zg[r] = v;
+                    const long long rr = row0 + j;
+                    if (rr < n) {
+                        const long long val = Zs[cc * ZROW + j];
+                        if (tc_out_of_range(val)) tc_set_error(state, GB_ERR_RANGE);
+                        zg[rr] = val;
                     }
                 }
             }
@@ -677,8 +721,8 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     // ---- leave: no copy or MMA of this CTA may still be in flight when its
     // TMEM is released (bounded waits; a timeout was already recorded)
     if (tid == 0) {
-        for (int r = issued - 2; r < issued; r++)
-            if (r >= 0) tc5::mbar_wait(bar_rec0 + 8 * (r & 1), (uint32_t)((r >> 1) & 1), kMbarTimeoutNs);
+        if (v_issued > 0) tc5::mbar_wait(bar_v, (uint32_t)((v_issued - 1) & 1), kMbarTimeoutNs);
+        if (u_issued > 0) tc5::mbar_wait(bar_u, (uint32_t)((u_issued - 1) & 1), kMbarTimeoutNs);
     }
     if (mma_pending) tc5::mbar_wait(bar_mma, (mma_phase - 1) & 1, kMbarTimeoutNs);
     tc5::fence_before_sync();
@@ -693,10 +737,10 @@ template <int B>
 size_t tc5_bytes(int n, int nev)
 {
     using Gm = Geo<B>;
-    const long long G = group_count(n, kNB5);
+    const long long G = group_count(n, Gm::NB);
     const long long C = (nev + kCols5 - 1) / kCols5;
     long long tiles = 0;
-    for (long long g = 0; g < G; g++) tiles += group_tiles(n, B, kNB5, (int)g);
+    for (long long g = 0; g < G; g++) tiles += group_tiles(n, B, Gm::NB, (int)g);
     size_t o = 256 + (size_t)(G * C) * 4;                   // head + progress
     o = (o + 255) & ~(size_t)255;
     o += ((size_t)nev * 4 + 255) & ~(size_t)255;            // column scales
@@ -711,7 +755,7 @@ cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, do
                     int hold_group, cudaStream_t st)
 {
     using Gm = Geo<B>;
-    const int G = group_count(n, kNB5);
+    const int G = group_count(n, Gm::NB);
     const int C = (nev + kCols5 - 1) / kCols5;
     if (G <= 0 || nev <= 0) return cudaSuccess;
     if (ws_bytes < tc5_bytes<B>(n, nev)) return cudaErrorInvalidValue;
@@ -731,8 +775,12 @@ cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, do
     const dim3 conv_grid((n + 255) / 256 < 64 ? (n + 255) / 256 : 64, nev < 65535 ? nev : 65535);
     tc_col_scale<<<(nev + 7) / 8, 256, 0, st>>>(n, nev, Z, ldz, E, state);
     tc_convert<<<conv_grid, 256, 0, st>>>(n, nev, Z, ldz, E, 1);
-    tc_tile_offsets<<<1, 1, 0, st>>>(n, B, kNB5, G, toff);
-    tc5_tile_prep<B><<<dim3(group_tiles(n, B, kNB5, 0), G), 128, 0, st>>>(n, hh_v, hh_tau, toff, rec);
+    tc_tile_offsets<<<1, 1, 0, st>>>(n, B, Gm::NB, G, toff);
+    constexpr size_t prep_smem = prep_smem_bytes<B>();
+    if ((e = cudaFuncSetAttribute(tc5_tile_prep<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem)) !=
+        cudaSuccess)
+        return e;
+    tc5_tile_prep<B><<<dim3(group_tiles(n, B, Gm::NB, 0), G), 256, prep_smem, st>>>(n, hh_v, hh_tau, toff, rec);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(pipeline_tc5<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM)) !=
         cudaSuccess)
@@ -749,6 +797,8 @@ cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, do
 }  // namespace
 
 bool pipeline_tc5_supported(int b) { return b == 16 || b == 32 || b == 64; }
+
+int pipeline_tc5_sweeps_per_tile(int b) { return b == 64 ? Geo<64>::NB : 16; }
 
 size_t pipeline_tc5_workspace_bytes(int n, int b, int nev)
 {

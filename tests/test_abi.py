@@ -100,12 +100,13 @@ def test_variant_resolution_is_host_only(lib):
     assert v(4096, 64, 100, 1, {"variant": 4}) == gb.GB_VARIANT_WAVEFRONT
     assert v(4096, 64, 100, 0, {"variant": 5}) == -1
     assert gb.gb_trans_ev_launch_count(4096, 64, 100, 0, {"variant": 4}) == 6
-    # the tcgen05 workspace: head, flags, scales, offsets and one 41344-byte
-    # record per tile (b = 64)
+    # the tcgen05 workspace: head, flags, scales, offsets and one 98816-byte
+    # record per tile (b = 64: tiles of 32 sweeps, window 95 rows padded to 96)
     n, b, nev = 4096, 64, 300
-    G = (n - 1 + 15) // 16
-    tiles = sum((n - (1 + 16 * g) + b - 1) // b for g in range(G))
-    assert gb.gb_trans_ev_workspace_bytes(n, b, nev) >= tiles * 41344
+    G = (n - 1 + 31) // 32
+    tiles = sum((n - (1 + 32 * g) + b - 1) // b for g in range(G))
+    wsb = gb.gb_trans_ev_workspace_bytes(n, b, nev)
+    assert tiles * 98816 <= wsb <= tiles * 98816 + (1 << 20)
 
 
 def test_launch_count_is_host_only(lib):
