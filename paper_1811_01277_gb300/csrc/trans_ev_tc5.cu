@@ -120,6 +120,7 @@ struct Geo {
     static_assert(T_DZ + kLevels5 * NCH <= kTmemCols, "W digits and dZ levels fit in TMEM");
     static_assert(8 * LP * 128 * 128 < (1 << 24), "W level sums stay exact in FP32");
     static_assert(NB * (7 * 128 * 128) < (1 << 22), "dZ level sums stay below 2^22");
+    static_assert(LP * (32 * 128 + 128 * 128 + 128 * 64) < (1 << 22), "W levels 0..2 stay below 2^22");
     static_assert(LP % 16 == 0 && NB % 16 == 0 && NB <= B, "tile shape");
     static_assert(VBYTES % 128 == 0 && REC % 128 == 0 && S_Z % 16 == 0, "record alignment");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -341,6 +342,7 @@ __global__ void __launch_bounds__(256) tc5_tile_prep(int n, const double *__rest
 struct Tc5Shared {
     int item;
     int abort;
+    int u_issued;   // U parts requested so far (written by the thread that requests them)
 };
 
 // every thread: wait for an mbarrier phase; on giving up record the timeout
@@ -381,6 +383,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     if (tid == 0) {
         sh.item = atomicAdd(&state->ticket, 1);
         sh.abort = 0;
+        sh.u_issued = 1;
         tc5::mbar_init(bar_v, 1);
         tc5::mbar_init(bar_u, 1);
         tc5::mbar_init(bar_mma, 1);
@@ -406,13 +409,13 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
 
     uint32_t mma_phase = 0;
     bool mma_pending = false;
-    int v_issued = 0, u_issued = 0;   // record parts requested so far (thread 0)
+    int v_issued = 0;   // V parts requested so far (thread 0)
 
     if (tid == 0) {
         if (g + 1 != hold_group) st_release(progress + (long long)g * C + c, 0);
         tc5::bulk_load(tc5::smem_addr(smem + Gm::S_V), rec_g, Gm::VBYTES, bar_v);
         tc5::bulk_load(tc5::smem_addr(smem + Gm::S_U), rec_g + Gm::VBYTES, Gm::UPART, bar_u);
-        v_issued = u_issued = 1;
+        v_issued = 1;
     }
     // window padding rows stay zero for the whole item
     for (int e = tid; e < kCols5 * (LP - L); e += kThreads5) Zs[(e / (LP - L)) * ZROW + L + e % (LP - L)] = 0;
@@ -575,8 +578,12 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                 for (int u = 0; u < 2; u++) {
                     const int i = 2 * p + u;
                     int Lv[kLevels5];
+                    // levels 0..2 stay below 2^22 (at most 3 pairs, the top
+                    // digits bounded by 32 and 64): one addition converts them
 #pragma unroll
-                    for (int l = 0; l < kLevels5; l++) Lv[l] = __float2int_rn(__uint_as_float(a[l][i]));
+                    for (int l = 0; l < 3; l++) Lv[l] = (int)(magic_bits(a[l][i]) - kMagicBits);
+#pragma unroll
+                    for (int l = 3; l < kLevels5; l++) Lv[l] = __float2int_rn(__uint_as_float(a[l][i]));
                     wi[u] = fold9(Lv, eV[q0 + i]);
                 }
                 uint32_t d[kPlanes];
@@ -685,28 +692,44 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         tc5::fence_after_sync();
         if (sh.abort) break;
         // the U part is consumed (planes by the MMAs, exponents by the folds
-        // above): request the next tile's
-        if (tid == 0 && k + 1 < K) {
+        // above): request the next tile's (a thread other than the one that
+        // polls the dependency flags and issues the MMAs)
+        if (tid == 32 && k + 1 < K) {
             tc5::fence_proxy_async_smem();
             tc5::bulk_load(tc5::smem_addr(smem + Gm::S_U), rec_g + (size_t)(k + 1) * Gm::REC + Gm::VBYTES, Gm::UPART,
                            bar_u);
-            u_issued = k + 2;
+            sh.u_issued = k + 2;
         }
-        // ---- store the rows final for this group (all rows after the last tile)
+        // ---- store the rows final for this group (all rows after the last
+        // tile): all of a warp's shared-memory reads first, then the stores
         {
+            constexpr int CW = kCols5 / (kThreads5 / 32);
+            constexpr int H = (L + 31) / 32;
             const int jhi = (k == K - 1) ? L : b;
-            for (int cc = warp; cc < kCols5; cc += kThreads5 / 32) {
+            long long v[CW][H];
+#pragma unroll
+            for (int i = 0; i < CW; i++)
+#pragma unroll
+                for (int h = 0; h < H; h++) {
+                    const int j = lane + 32 * h;
+                    v[i][h] = (j < jhi) ? Zs[(warp * CW + i) * ZROW + j] : 0ll;
+                }
+            bool bad = false;
+#pragma unroll
+            for (int i = 0; i < CW; i++) {
+                const int cc = warp * CW + i;
                 if (col0 + cc >= nev) continue;
                 long long *zg = Zi + (long long)(col0 + cc) * ldz;
-                for (int j = lane; j < jhi; j += 32) {
-                    const long long rr = row0 + j;
-                    if (rr < n) {
-                        const long long val = Zs[cc * ZROW + j];
-                        if (tc_out_of_range(val)) tc_set_error(state, GB_ERR_RANGE);
-                        zg[rr] = val;
+#pragma unroll
+                for (int h = 0; h < H; h++) {
+                    const int j = lane + 32 * h;
+                    if (j < jhi && row0 + j < n) {
+                        bad |= tc_out_of_range(v[i][h]);
+                        zg[row0 + j] = v[i][h];
                     }
                 }
             }
+            if (bad) tc_set_error(state, GB_ERR_RANGE);
         }
         // every thread's stores happen before thread 0's fence and release
         // (barrier, then a cumulative release at GPU scope); the release of
@@ -720,9 +743,10 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     }
     // ---- leave: no copy or MMA of this CTA may still be in flight when its
     // TMEM is released (bounded waits; a timeout was already recorded)
+    __syncthreads();
     if (tid == 0) {
         if (v_issued > 0) tc5::mbar_wait(bar_v, (uint32_t)((v_issued - 1) & 1), kMbarTimeoutNs);
-        if (u_issued > 0) tc5::mbar_wait(bar_u, (uint32_t)((u_issued - 1) & 1), kMbarTimeoutNs);
+        if (sh.u_issued > 0) tc5::mbar_wait(bar_u, (uint32_t)((sh.u_issued - 1) & 1), kMbarTimeoutNs);
     }
     if (mma_pending) tc5::mbar_wait(bar_mma, (mma_phase - 1) & 1, kMbarTimeoutNs);
     tc5::fence_before_sync();
