@@ -71,6 +71,17 @@ def tc_executed_flops(n, nbw, nev):
     return items * pairs * 2 * (2 * 16 * lp * 64)
 
 
+def tc5_executed_flops_z(n, nbw, nev):
+    """pipeline_tc5 on complex data (the real 2 x 2-block form): per tile of
+    8 sweeps and 128-column item, W'^T (128 x LP x 16) and dZ'^T
+    (128 x 16 x LP) over 43 digit pairs, LP = 2 (nbw + 7) rounded up to 16."""
+    lp = (2 * (nbw + 7) + 15) // 16 * 16
+    G = (n - 1 + 7) // 8
+    tiles = sum((n - (1 + 8 * g) + nbw - 1) // nbw for g in range(G))
+    items = tiles * ((nev + 127) // 128)
+    return items * 43 * 2 * (2 * 128 * 16 * lp)
+
+
 def tc5_executed_flops(n, nbw, nev):
     """FP16 tensor-core flops one pipeline_tc5 call executes: per tile (NB
     sweeps: 32 for nbw = 64, else 16) and 128-column item, W^T = Z^T V
@@ -930,14 +941,26 @@ def run_stage_trans_ev_z(args):
     # unitary reflectors keep every column's norm
     norms = torch.linalg.norm(Zt, dim=1).cpu().numpy()
     drift = float(np.max(np.abs(norms / np.linalg.norm(Z, axis=0) - 1.0)))
+    variant = gb.gb_trans_ev_variant(n, nbw, nev, 1, None)
+    fp64 = {"achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12}
+    if variant == gb.GB_VARIANT_PIPELINE_TC5:
+        pk = measured_peaks()
+        Ft = tc5_executed_flops_z(n, nbw, nev)
+        ach = Ft / (ms / 1e3) / 1e12
+        peak = pk["bf16_tflops_sustained"] or pk["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "kernel": "pipeline_tc5 (complex, real 2x2-block form)", "executed_fp16_tflop_per_step": Ft / 1e12,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained", "fp64_equivalent": fp64}
+    else:
+        roof = dict(bound="alu", **fp64)
     print(json.dumps({
         "stage": "trans_ev_z", "metric": f"complex128 trans_ev_tridi_to_band s at n={n}, nev={nev}, nbw={nbw}",
         "value": 1e3 / ms, "unit": "back-transforms/s", "ms_per_step": ms, "steps": args.steps,
-        "warmup": args.warmup, "status": status, "dtype": "complex128", "variant": "library default",
+        "warmup": args.warmup, "status": status, "dtype": "complex128",
+        "variant": {gb.GB_VARIANT_PIPELINE_TC5: "pipeline_tc5", gb.GB_VARIANT_WAVEFRONT: "wavefront_smem"}.get(variant, variant),
         "data": "synthetic unitary reflectors (v0 = 1, v U[-1,1]/sqrt(len), tau = (1 - e^{i theta})/|v|^2), Z iid N(0,1/n)",
-        "roofline": {"bound": "alu", "achieved": F / (ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": F / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_tflop": F / 1e12},
-        "column_norm_drift_max": drift, "clocks": clocks}))
+        "roofline": roof, "column_norm_drift_max": drift, "clocks": clocks}))
     return 0
 
 

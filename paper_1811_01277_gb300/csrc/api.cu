@@ -24,11 +24,13 @@ constexpr long long kDefaultSpinPolls = 1LL << 40;  // effectively bounded by th
 constexpr long long kTimeoutNs = 10LL * 1000 * 1000 * 1000;
 
 // Returns 0 or -11 (opts is the 11th argument of the device entry points).
-// AUTO picks PIPELINE_TC5 (tcgen05) for real data with nbw in {16,32,64} and
-// n >= 512, PIPELINE for the other real cases with nbw in {8,16,32,64}
-// (nb = 16, 64 columns per block) and WAVEFRONT otherwise; PIPELINE requested
-// for other cases runs as WAVEFRONT, and either tensor-core variant requested
-// for unsupported cases runs as PIPELINE.
+// AUTO picks PIPELINE_TC5 (tcgen05) for real or complex data with nbw in
+// {16,32,64} and n >= 512, PIPELINE for the other real cases with nbw in
+// {8,16,32,64} (nb = 16, 64 columns per block) and WAVEFRONT otherwise;
+// PIPELINE requested for other cases runs as WAVEFRONT, either tensor-core
+// variant requested for unsupported real cases runs as PIPELINE, and for
+// complex data PIPELINE_TC (real only) and an unsupported PIPELINE_TC5 run as
+// WAVEFRONT.
 int resolve(const gb_trans_ev_opts *o, int n, int nbw, int is_complex, Opts *r)
 {
     int variant = GB_VARIANT_AUTO, nb = 0, threads = 0;
@@ -56,10 +58,10 @@ int resolve(const gb_trans_ev_opts *o, int n, int nbw, int is_complex, Opts *r)
     const bool pipe_ok = !is_complex && gb::pipeline_supported(nbw);
     if (variant == GB_VARIANT_PIPELINE_TC && (is_complex || !gb::pipeline_tc_supported(nbw)))
         variant = GB_VARIANT_PIPELINE;
-    if (variant == GB_VARIANT_PIPELINE_TC5 && (is_complex || !gb::pipeline_tc5_supported(nbw)))
+    if (variant == GB_VARIANT_PIPELINE_TC5 && !gb::pipeline_tc5_supported(nbw))
         variant = GB_VARIANT_PIPELINE;
     if (variant == GB_VARIANT_AUTO) {
-        if (!is_complex && gb::pipeline_tc5_supported(nbw) && n >= kTcMinN) variant = GB_VARIANT_PIPELINE_TC5;
+        if (gb::pipeline_tc5_supported(nbw) && n >= kTcMinN) variant = GB_VARIANT_PIPELINE_TC5;
         else variant = pipe_ok ? GB_VARIANT_PIPELINE : GB_VARIANT_WAVEFRONT;
     }
     if (variant == GB_VARIANT_PIPELINE && !pipe_ok) variant = GB_VARIANT_WAVEFRONT;
@@ -119,7 +121,8 @@ size_t gb_trans_ev_workspace_bytes(int n, int nbw, int nev, int is_complex, cons
     Opts o;
     if (n < 1 || nbw < 1 || nev < 0 || resolve(opts, n, nbw, is_complex, &o) != 0) return 0;
     if (o.variant == GB_VARIANT_PIPELINE_TC && n > 1 && nev > 0) return gb::pipeline_tc_workspace_bytes(n, nbw, nev);
-    if (o.variant == GB_VARIANT_PIPELINE_TC5 && n > 1 && nev > 0) return gb::pipeline_tc5_workspace_bytes(n, nbw, nev);
+    if (o.variant == GB_VARIANT_PIPELINE_TC5 && n > 1 && nev > 0)
+        return gb::pipeline_tc5_workspace_bytes(n, nbw, nev, is_complex);
     if (o.variant == GB_VARIANT_PIPELINE && !is_complex && n > 1 && nev > 0)
         return gb::pipeline_workspace_bytes(n, nev, o.nb, o.threads);
     return 0;  // the wavefront variant needs no workspace
@@ -162,10 +165,16 @@ int gb_trans_ev_tridi_to_band_z(int n, int nbw, int nev, const double *hh_v, con
     if (rc) return rc;
     Opts o;
     if ((rc = resolve(opts, n, nbw, 1, &o)) != 0) return rc;
-    (void)workspace;
-    (void)ws_bytes;  // the complex kernels need no workspace
+    const size_t need = gb_trans_ev_workspace_bytes(n, nbw, nev, 1, opts);
+    if (need > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0)) return -8;
+    if (ws_bytes < need) return -9;
     if (n == 1 || nev == 0) return GB_OK;
-    cudaError_t e = gb::wavefront_smem_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
+    cudaError_t e;
+    if (o.variant == GB_VARIANT_PIPELINE_TC5)
+        e = gb::pipeline_tc5_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.column_batch, workspace, need, o.spin, kTimeoutNs,
+                               o.hold, (cudaStream_t)stream);
+    else  // the shared-memory wavefront kernel, which needs no workspace
+        e = gb::wavefront_smem_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.nb, o.threads, (cudaStream_t)stream);
     return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
 }
 

@@ -217,8 +217,8 @@ SolveWs carve(int n, int nev, int b, char *base)
 // Complex workspace: complex pieces hold 2 doubles per entry.
 struct SolveWsZ {
     double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Zre, *Gns, *Zns, *S, *S2, *gw;
-    void *chase, *eig, *sl;
-    size_t chase_bytes, gw_elems, sl_bytes, total;
+    void *chase, *eig, *sl, *tev;
+    size_t chase_bytes, gw_elems, sl_bytes, tev_bytes, total;
 };
 
 // complex products: 8 real flops per complex multiply-add
@@ -274,6 +274,8 @@ SolveWsZ carve_z(int n, int nev, int b, char *base)
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
     w.sl_bytes = zsliced_region_bytes(n, nev, b);
     w.sl = w.sl_bytes ? take(w.sl_bytes) : nullptr;
+    w.tev_bytes = gb_trans_ev_workspace_bytes(n, b, nev, 1, nullptr);
+    w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
     w.total = off;
     return w;
 }
@@ -545,7 +547,7 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_CU(gb::promote_real(n, nev, w.Zns, n, Z, ldz, st));
 
     // ---- tridiagonal -> band (complex back-transformation)
-    int rc = gb_trans_ev_tridi_to_band_z(n, b, nev, w.hv, w.ht, Z, ldz, nullptr, 0, stream, nullptr);
+    int rc = gb_trans_ev_tridi_to_band_z(n, b, nev, w.hv, w.ht, Z, ldz, w.tev, w.tev_bytes, stream, nullptr);
     if (rc != GB_OK) return rc;
 
     // ---- band -> full: Z_p -= Y (T (Y^H Z_p)), last panel first
@@ -575,7 +577,9 @@ int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *strea
 {
     if (!workspace) return -1;
     SolveWsZ w = carve_z(n, nev, nbw, (char *)workspace);
-    return gb_trans_ev_query(w.chase, w.chase_bytes, stream);
+    int rc = gb_trans_ev_query(w.chase, w.chase_bytes, stream);
+    if (rc != GB_OK) return rc;
+    return gb_trans_ev_query(w.tev, w.tev_bytes, stream);
 }
 
 int gb_solve_release(void *stream, int all_streams)

@@ -42,13 +42,17 @@ cudaError_t pipeline_tc_d(int n, int b, int nev, const double *hh_v, const doubl
                           int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
                           int hold_group, cudaStream_t st);
 
-// tcgen05 pipeline (real case, nbw in {16, 32, 64}): the same compact WY
-// tiles with 128-column items, FP16 digit planes and FP32 level sums in
-// tensor memory.
+// tcgen05 pipeline (nbw in {16, 32, 64}; real data, and complex data in its
+// real 2 x 2-block form): compact WY tiles with 128-column items, FP16 digit
+// planes and FP32 level sums in tensor memory.
 bool pipeline_tc5_supported(int b);
-int pipeline_tc5_sweeps_per_tile(int b);
-size_t pipeline_tc5_workspace_bytes(int n, int b, int nev);
+int pipeline_tc5_sweeps_per_tile(int b, int is_complex);
+size_t pipeline_tc5_workspace_bytes(int n, int b, int nev, int is_complex);
 cudaError_t pipeline_tc5_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
+                           int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
+                           int hold_group, cudaStream_t st);
+// complex128 data: hh_v, hh_tau and Z interleaved (re, im), ldz in complex entries
+cudaError_t pipeline_tc5_z(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
                            int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
                            int hold_group, cudaStream_t st);
 

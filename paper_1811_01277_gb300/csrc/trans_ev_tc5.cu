@@ -78,24 +78,32 @@ constexpr int kTmemCols = 512;
 constexpr unsigned long long kDigitBias = 0x8080808080808080ull;
 constexpr long long kMbarTimeoutNs = 2000000000ll;  // an MMA batch or a record copy takes microseconds
 
-template <int B>
+// RF = 1: real data.  RF = 2: complex data in its real form (interleaved
+// re/im storage of Z read as a real column of 2n rows; every complex entry
+// of V and U expanded to a 2 x 2 real block), so the tile is a real tile of
+// 2 NB reflector columns over a window of 2 (b + NB - 1) rows.
+template <int B, int RF>
 struct Geo {
-    static constexpr int NB = B == 64 ? 32 : 16;        // sweeps per tile
-    static constexpr int L = B + NB - 1;                // window rows
+    static constexpr int NB = RF == 2 ? 8 : (B == 64 ? 32 : 16);  // sweeps per tile
+    static constexpr int NBC = RF * NB;                 // reflector columns of the real form (W's N)
+    static constexpr int ADV = RF * B;                  // window rows advanced per tile
+    static constexpr int LC = B + NB - 1;               // window rows of the data (complex rows for RF = 2)
+    static constexpr int L = RF * LC;                   // window rows of the real form
+    static constexpr int CARRY = L - ADV;               // rows carried from tile to tile
     static constexpr int LP = (L + 15) / 16 * 16;       // padded to the MMA's K step
     static constexpr int KSTEPS = LP / 16;              // K steps of the first product
-    static constexpr int KD = NB / 16;                  // K steps of the second
-    // tile record: V part [8 planes][NB rows q][LP] and U part [chunks of 32
-    // rows][8 planes][rows][NB] + eV[NB] + eU[LP], canonical K-major
-    static constexpr int VPLANE = NB * LP * 2;
+    static constexpr int KD = NBC / 16;                 // K steps of the second
+    // tile record: V part [8 planes][NBC rows q][LP] and U part [chunks of
+    // 32 rows][8 planes][rows][NBC] + eV[NBC] + eU[LP], canonical K-major
+    static constexpr int VPLANE = NBC * LP * 2;
     static constexpr int VBYTES = kPlanes * VPLANE;
-    static constexpr int UBYTES = kPlanes * LP * NB * 2;
+    static constexpr int UBYTES = kPlanes * LP * NBC * 2;
     static constexpr int U_EV = UBYTES;
-    static constexpr int U_EU = UBYTES + NB * 4;
-    static constexpr int UPART = (UBYTES + (NB + LP) * 4 + 127) / 128 * 128;
+    static constexpr int U_EU = UBYTES + NBC * 4;
+    static constexpr int UPART = (UBYTES + (NBC + LP) * 4 + 127) / 128 * 128;
     static constexpr int REC = VBYTES + UPART;
     static constexpr int SBO_V = 16 * LP;               // bytes between 8-row groups of V (N = q)
-    static constexpr int SBO_U = 16 * NB;               // bytes between 8-row groups of U^T (N = j)
+    static constexpr int SBO_U = 16 * NBC;              // bytes between 8-row groups of U^T (N = j)
     // window: [128 columns][ZROW] int64, ZROW = 2 mod 4 so that a warp's
     // 16-byte accesses to one row pair of 32 columns are conflict-free
     static constexpr int ZROW = LP + 2;
@@ -103,7 +111,7 @@ struct Geo {
     static constexpr int NCH = 32;
     static constexpr int CHUNKS = (LP + NCH - 1) / NCH;
     // TMEM columns
-    static constexpr int WLEV = kLevels5 * NB;                      // W level accumulators
+    static constexpr int WLEV = kLevels5 * NBC;                     // W level accumulators
     static constexpr int ZR = (kTmemCols - WLEV) / 64 < KSTEPS ? (kTmemCols - WLEV) / 64 : KSTEPS;
     static constexpr int ROUNDS = (KSTEPS + ZR - 1) / ZR;
     static constexpr int T_ZD = 0;
@@ -118,10 +126,12 @@ struct Geo {
     static constexpr int SMEM = S_BAR + 64;
     static_assert(ZR >= 1 && T_WACC + WLEV <= kTmemCols, "Z digits and W levels fit in TMEM");
     static_assert(T_DZ + kLevels5 * NCH <= kTmemCols, "W digits and dZ levels fit in TMEM");
-    static_assert(8 * LP * 128 * 128 < (1 << 24), "W level sums stay exact in FP32");
-    static_assert(NB * (7 * 128 * 128) < (1 << 22), "dZ level sums stay below 2^22");
+    // level bounds per K with the top digits bounded by 32 (Z, W) and 64
+    // (V, U): at most 7 x 2^14 + 32 128 + 128 64 (level 7) or 7 x 2^14 (level 8)
+    static_assert(LP * (7 * 128 * 128) < (1 << 24), "W level sums stay exact in FP32");
+    static_assert(NBC * (7 * 128 * 128) < (1 << 22), "dZ level sums stay below 2^22");
     static_assert(LP * (32 * 128 + 128 * 128 + 128 * 64) < (1 << 22), "W levels 0..2 stay below 2^22");
-    static_assert(LP % 16 == 0 && NB % 16 == 0 && NB <= B, "tile shape");
+    static_assert(LP % 16 == 0 && NBC % 16 == 0 && NB <= B && CARRY <= ADV, "tile shape");
     static_assert(VBYTES % 128 == 0 && REC % 128 == 0 && S_Z % 16 == 0, "record alignment");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -196,9 +206,17 @@ __device__ __forceinline__ long long fixed_row(double x, int e) { return __doubl
 template <int B>
 constexpr size_t prep_smem_bytes()
 {
-    using Gm = Geo<B>;
+    using Gm = Geo<B, 1>;
     return (size_t)(2 * Gm::LP * (Gm::NB + 1) + 2 * Gm::NB * (Gm::NB + 1) + 2 * Gm::NB) * 8 +
            (size_t)(Gm::NB + Gm::LP) * 4;
+}
+
+template <int B>
+constexpr size_t prep_smem_bytes_z()
+{
+    using Gm = Geo<B, 2>;
+    return (size_t)(2 * Gm::LC * (Gm::NB + 1) + 2 * Gm::NB * (Gm::NB + 1) + Gm::NB) * 16 + (size_t)Gm::NB * 8 +
+           (size_t)(Gm::NB + Gm::LC) * 4;
 }
 
 template <int B>
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(256) tc5_tile_prep(int n, const double *__rest
                                                      const long long *__restrict__ off,
                                                      unsigned char *__restrict__ rec)
 {
-    using Gm = Geo<B>;
+    using Gm = Geo<B, 1>;
     constexpr int L = Gm::L, LP = Gm::LP, NB = Gm::NB, NB1 = NB + 1;
     const int k = blockIdx.x, g = blockIdx.y;
     const int b = B;
@@ -337,6 +355,176 @@ __global__ void __launch_bounds__(256) tc5_tile_prep(int n, const double *__rest
     }
 }
 
+// Complex tile record: the complex V, T, U of the tile (the same forward
+// recurrence with V^H), then their real forms: V's entry v at (row j,
+// column q) becomes the 2 x 2 block [[re v, -im v], [im v, re v]] of
+// V' (rows 2j+p, columns 2q+p'), so that (z^T V')_(2q+p') are the real and
+// imaginary parts of (z^T conj(V))_q; U's entry u becomes, in the B operand
+// of the second product (rows 2q+p', columns 2j+p), [[re u, im u],
+// [-im u, re u]], so that (w'^T B)_(2j+p) are the parts of (w^T U^T)_j.
+// Row exponents are shared by the two real rows of a complex row.
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// conj(a) b + c
+__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+
+template <int B>
+__global__ void __launch_bounds__(256) tc5_tile_prep_z(int n, const double2 *__restrict__ hh_v,
+                                                       const double2 *__restrict__ hh_tau,
+                                                       const long long *__restrict__ off,
+                                                       unsigned char *__restrict__ rec)
+{
+    using Gm = Geo<B, 2>;
+    constexpr int LC = Gm::LC, LP = Gm::LP, NB = Gm::NB, NB1 = NB + 1, NBC = Gm::NBC;
+    const int k = blockIdx.x, g = blockIdx.y;
+    const int b = B;
+    if (k >= group_tiles(n, b, NB, g)) return;
+    extern __shared__ double2 zsm[];
+    double2 *V = zsm;                     // [LC][NB1]
+    double2 *U = V + LC * NB1;            // [LC][NB1]
+    double2 *T = U + LC * NB1;            // [NB][NB1]
+    double2 *Gr = T + NB * NB1;           // [NB][NB1]
+    double2 *tau = Gr + NB * NB1;         // [NB]
+    double *nv = (double *)(tau + NB);    // [NB]
+    int *seV = (int *)(nv + NB);          // [NB]
+    int *seU = seV + NB;                  // [LC]
+    const int s0 = 1 + g * NB;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int e = threadIdx.x; e < LC * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
+        const int s = s0 + q;
+        double2 val = zero;
+        if (s <= n - 1 && s + k * b < n && j - q >= 0 && j - q < b) {
+            const long long idx = sweep_first(n, b, s) + k;
+            const int len = min(b, n - s - k * b);
+            const double2 t = hh_tau[idx];
+            const int i = j - q;
+            if ((t.x != 0.0 || t.y != 0.0) && i < len) val = (i == 0) ? make_double2(1.0, 0.0) : hh_v[idx * b + i];
+        }
+        V[j * NB1 + q] = val;
+    }
+    if (threadIdx.x < NB) {
+        const int s = s0 + threadIdx.x;
+        tau[threadIdx.x] = (s <= n - 1 && s + k * b < n) ? hh_tau[sweep_first(n, b, s) + k] : zero;
+    }
+    __syncthreads();
+    // Gram matrix v_p^H v_q (p < q), T by T(q,q) = tau_q,
+    // T(0:q,q) = -tau_q T(0:q,0:q) V(:,0:q)^H v_q
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int p = e / NB, q = e % NB;
+        double2 a = zero;
+        if (p < q)
+            for (int j = q; j < min(p + b, LC); j++) a = cfma_conj(V[j * NB1 + p], V[j * NB1 + q], a);
+        Gr[p * NB1 + q] = a;
+    }
+    __syncthreads();
+    for (int q = 0; q < NB; q++) {
+        if (threadIdx.x < NB) {
+            const int i = threadIdx.x;
+            double2 t = zero;
+            if (i < q) {
+                for (int p = i; p < q; p++) t = cfma(T[i * NB1 + p], Gr[p * NB1 + q], t);
+                t = cmul(make_double2(-tau[q].x, -tau[q].y), t);
+            } else if (i == q) {
+                t = tau[q];
+            }
+            T[i * NB1 + q] = t;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < LC * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
+        double2 a = zero;
+        for (int p = 0; p <= q; p++) a = cfma(V[j * NB1 + p], T[p * NB1 + q], a);
+        U[j * NB1 + q] = a;
+    }
+    if (threadIdx.x < NB) {
+        double a = 0.0;
+        for (int j = 0; j < LC; j++) {
+            const double2 v = V[j * NB1 + threadIdx.x];
+            a = fma(v.x, v.x, fma(v.y, v.y, a));
+        }
+        nv[threadIdx.x] = sqrt(a);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < LC * NB; e += blockDim.x) {
+        const int j = e / NB, q = e % NB;
+        if (nv[q] > 0.0) {
+            const double2 v = V[j * NB1 + q], u = U[j * NB1 + q];
+            V[j * NB1 + q] = make_double2(v.x / nv[q], v.y / nv[q]);
+            U[j * NB1 + q] = make_double2(u.x * nv[q], u.y * nv[q]);
+        }
+    }
+    __syncthreads();
+    unsigned char *r = rec + ((size_t)off[g] + k) * Gm::REC;
+    unsigned char *ru = r + Gm::VBYTES;
+    auto absbits = [](double x) { return (unsigned long long)__double_as_longlong(x) & ~(1ull << 63); };
+    if (threadIdx.x < NB) {
+        unsigned long long m = 0;
+        for (int j = 0; j < LC; j++) {
+            const double2 v = V[j * NB1 + threadIdx.x];
+            m = max(m, max(absbits(v.x), absbits(v.y)));
+        }
+        seV[threadIdx.x] = exponent_above(m);
+        ((int *)(ru + Gm::U_EV))[2 * threadIdx.x] = seV[threadIdx.x];
+        ((int *)(ru + Gm::U_EV))[2 * threadIdx.x + 1] = seV[threadIdx.x];
+    }
+    for (int j = threadIdx.x; j < LP / 2; j += blockDim.x) {
+        unsigned long long m = 0;
+        if (j < LC)
+            for (int q = 0; q < NB; q++) {
+                const double2 u = U[j * NB1 + q];
+                m = max(m, max(absbits(u.x), absbits(u.y)));
+            }
+        const int ev = exponent_above(m);
+        if (j < LC) seU[j] = ev;
+        ((int *)(ru + Gm::U_EU))[2 * j] = ev;
+        ((int *)(ru + Gm::U_EU))[2 * j + 1] = ev;
+    }
+    __syncthreads();
+    // V' (N = q' = 2q+p', K = j' = 2j+p) and the second product's B
+    // (N = j', K = q'), in the layouts of the real record
+    for (int e = threadIdx.x; e < NBC * LP; e += blockDim.x) {
+        const int qq = e / LP, jj = e % LP;
+        const int q = qq >> 1, pq = qq & 1, j = jj >> 1, pj = jj & 1;
+        double x = 0.0;
+        if (j < LC) {
+            const double2 v = V[j * NB1 + q];
+            x = (pj == pq) ? v.x : (pj ? v.y : -v.y);
+        }
+        const unsigned long long y = (unsigned long long)fixed_row(x, seV[q]) + kDigitBias;
+        const int o = (qq >> 3) * Gm::SBO_V + (jj >> 3) * 128 + (qq & 7) * 16 + (jj & 7) * 2;
+#pragma unroll
+        for (int t = 0; t < kPlanes; t++)
+            *(__half *)(r + t * Gm::VPLANE + o) = __float2half_rn((float)((int)((y >> (56 - 8 * t)) & 0xff) - 128));
+    }
+    for (int e = threadIdx.x; e < LP * NBC; e += blockDim.x) {
+        const int jj = e / NBC, qq = e % NBC;
+        const int q = qq >> 1, pq = qq & 1, j = jj >> 1, pj = jj & 1;
+        double x = 0.0;
+        int ev = 0;
+        if (j < LC) {
+            const double2 u = U[j * NB1 + q];
+            x = (pj == pq) ? u.x : (pq ? -u.y : u.y);
+            ev = seU[j];
+        }
+        const unsigned long long y = (unsigned long long)fixed_row(x, ev) + kDigitBias;
+        const int ch = jj / Gm::NCH, rows = min(Gm::NCH, LP - ch * Gm::NCH);
+        const int o = ch * Gm::NCH * Gm::SBO_U + ((jj % Gm::NCH) >> 3) * Gm::SBO_U + (qq >> 3) * 128 + (jj & 7) * 16 +
+                      (qq & 7) * 2;
+#pragma unroll
+        for (int t = 0; t < kPlanes; t++)
+            *(__half *)(ru + t * (rows / 8) * Gm::SBO_U + o) =
+                __float2half_rn((float)((int)((y >> (56 - 8 * t)) & 0xff) - 128));
+    }
+}
+
 // ---- the main kernel ------------------------------------------------------
 
 struct Tc5Shared {
@@ -355,15 +543,18 @@ __device__ __forceinline__ bool tc5_wait(uint32_t bar, uint32_t parity, TcState 
     return false;
 }
 
-template <int B>
+// n: the data's order (complex rows for RF = 2); Zi, ldz: the real form
+// (ldz in 64-bit words, RF times the data's leading dimension)
+template <int B, int RF>
 __global__ void __launch_bounds__(kThreads5, 1)
 pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const unsigned char *__restrict__ rec,
              const long long *__restrict__ off, int G, int C, int CB, TcState *state, int *progress,
              long long spin_polls, long long timeout_ns, int hold_group)
 {
-    using Gm = Geo<B>;
-    constexpr int L = Gm::L, LP = Gm::LP, ZROW = Gm::ZROW, KSTEPS = Gm::KSTEPS, NB = Gm::NB;
-    constexpr int ZR = Gm::ZR, KD = Gm::KD;
+    using Gm = Geo<B, RF>;
+    constexpr int L = Gm::L, LP = Gm::LP, ZROW = Gm::ZROW, KSTEPS = Gm::KSTEPS, NB = Gm::NB, NBC = Gm::NBC;
+    constexpr int ZR = Gm::ZR, KD = Gm::KD, ADV = Gm::ADV, CARRY = Gm::CARRY;
+    const long long nrows = (long long)RF * n;             // rows of the real form
     extern __shared__ __align__(1024) unsigned char smem[];
     long long *Zs = (long long *)(smem + Gm::S_Z);
     const uint32_t bar_v = tc5::smem_addr(smem + Gm::S_BAR);
@@ -446,8 +637,8 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         if (sh.abort) break;
         // ---- window: new rows from global memory (through L2: rows written
         // by other SMs), the NB-1 rows shared with the previous tile carried
-        const long long row0 = (long long)s0 + (long long)k * b;
-        const int jlo = (k == 0) ? 0 : NB - 1;
+        const long long row0 = (long long)RF * ((long long)s0 + (long long)k * b);
+        const int jlo = (k == 0) ? 0 : CARRY;
         {
             constexpr int H = (L + 31) / 32;               // passes of 32 rows per column
             constexpr int CW = kCols5 / (kThreads5 / 32);  // columns per warp
@@ -459,13 +650,13 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
 #pragma unroll
                 for (int h = 0; h < H; h++) {
                     const int j = jlo + lane + 32 * h;
-                    v[i][h] = (col0 + cc < nev && j < L && row0 + j < n) ? __ldcg(zc + row0 + j) : 0ll;
+                    v[i][h] = (col0 + cc < nev && j < L && row0 + j < nrows) ? __ldcg(zc + row0 + j) : 0ll;
                 }
             }
             if (k > 0) {
-                for (int e = tid; e < kCols5 * (NB - 1); e += kThreads5) {
-                    const int cc = e / (NB - 1), j = e % (NB - 1);
-                    Zs[cc * ZROW + j] = Zs[cc * ZROW + j + b];
+                for (int e = tid; e < kCols5 * CARRY; e += kThreads5) {
+                    const int cc = e / CARRY, j = e % CARRY;
+                    Zs[cc * ZROW + j] = Zs[cc * ZROW + j + ADV];
                 }
                 __syncthreads();  // carried rows read before the new rows overwrite them
             }
@@ -526,11 +717,11 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
                         const uint64_t b0 = vdesc + (uint64_t)((kk * 256) >> 4);
                         const int nt = s == 0 ? kPlanes : kLevels5 - s;          // planes t = 0 .. nt-1
                         if (kk == 0 && s == 1) {
-                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NB * 8, a_t, b0 + (uint64_t)((7 * Gm::VPLANE) >> 4),
-                                            tc5::idesc_f16_f32(128, NB), 0u);
-                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NB, a_t, b0, tc5::idesc_f16_f32(128, NB * 7), 1u);
+                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NBC * 8, a_t, b0 + (uint64_t)((7 * Gm::VPLANE) >> 4),
+                                            tc5::idesc_f16_f32(128, NBC), 0u);
+                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NBC, a_t, b0, tc5::idesc_f16_f32(128, NBC * 7), 1u);
                         } else {
-                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NB * s, a_t, b0, tc5::idesc_f16_f32(128, NB * nt),
+                            tc5::mma_tmem_a(tmem + Gm::T_WACC + NBC * s, a_t, b0, tc5::idesc_f16_f32(128, NBC * nt),
                                             (kk > 0 || s > 0) ? 1u : 0u);
                         }
                     }
@@ -558,15 +749,15 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         // W into digit planes (TMEM: K step q/16, columns s*8 + (q%16)/2)
         tc5_wait(bar_u, (uint32_t)(k & 1), state, sh);   // this tile's U part (row exponents)
         {
-            constexpr int QW = NB / 4;
+            constexpr int QW = NBC / 4;
             const int q0 = wq * QW;
             uint32_t a[kLevels5][QW];
 #pragma unroll
             for (int l = 0; l < kLevels5; l++) {
                 if constexpr (QW == 8) {
-                    tc5::ld_x8(tmem + lane_off + Gm::T_WACC + NB * l + q0, a[l]);
+                    tc5::ld_x8(tmem + lane_off + Gm::T_WACC + NBC * l + q0, a[l]);
                 } else {
-                    tc5::ld_x4(tmem + lane_off + Gm::T_WACC + NB * l + q0, a[l]);
+                    tc5::ld_x4(tmem + lane_off + Gm::T_WACC + NBC * l + q0, a[l]);
                 }
             }
             tc5::wait_ld();
@@ -705,7 +896,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
         {
             constexpr int CW = kCols5 / (kThreads5 / 32);
             constexpr int H = (L + 31) / 32;
-            const int jhi = (k == K - 1) ? L : b;
+            const int jhi = (k == K - 1) ? L : ADV;
             long long v[CW][H];
 #pragma unroll
             for (int i = 0; i < CW; i++)
@@ -723,7 +914,7 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
 #pragma unroll
                 for (int h = 0; h < H; h++) {
                     const int j = lane + 32 * h;
-                    if (j < jhi && row0 + j < n) {
+                    if (j < jhi && row0 + j < nrows) {
                         bad |= tc_out_of_range(v[i][h]);
                         zg[row0 + j] = v[i][h];
                     }
@@ -757,10 +948,10 @@ pipeline_tc5(int n, int nev, long long *__restrict__ Zi, long long ldz, const un
     }
 }
 
-template <int B>
+template <int B, int RF>
 size_t tc5_bytes(int n, int nev)
 {
-    using Gm = Geo<B>;
+    using Gm = Geo<B, RF>;
     const long long G = group_count(n, Gm::NB);
     const long long C = (nev + kCols5 - 1) / kCols5;
     long long tiles = 0;
@@ -773,16 +964,17 @@ size_t tc5_bytes(int n, int nev)
     return o;
 }
 
-template <int B>
+// Z, ldz: the data (complex entries interleaved for RF = 2, ldz in entries)
+template <int B, int RF>
 cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
                     int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
                     int hold_group, cudaStream_t st)
 {
-    using Gm = Geo<B>;
+    using Gm = Geo<B, RF>;
     const int G = group_count(n, Gm::NB);
     const int C = (nev + kCols5 - 1) / kCols5;
     if (G <= 0 || nev <= 0) return cudaSuccess;
-    if (ws_bytes < tc5_bytes<B>(n, nev)) return cudaErrorInvalidValue;
+    if (ws_bytes < tc5_bytes<B, RF>(n, nev)) return cudaErrorInvalidValue;
     char *base = (char *)ws;
     TcState *state = (TcState *)base;
     int *progress = (int *)(base + 256);
@@ -796,25 +988,38 @@ cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, do
     cudaError_t e = cudaMemsetAsync(ws, 0, 256, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(progress, 0xff, (size_t)G * C * 4, st)) != cudaSuccess) return e;
-    const dim3 conv_grid((n + 255) / 256 < 64 ? (n + 255) / 256 : 64, nev < 65535 ? nev : 65535);
-    tc_col_scale<<<(nev + 7) / 8, 256, 0, st>>>(n, nev, Z, ldz, E, state);
-    tc_convert<<<conv_grid, 256, 0, st>>>(n, nev, Z, ldz, E, 1);
+    // the per-column fixed point works on the real form: 2n rows of a complex column
+    const int nr = RF * n;
+    const long long ldr = RF * ldz;
+    const dim3 conv_grid((nr + 255) / 256 < 64 ? (nr + 255) / 256 : 64, nev < 65535 ? nev : 65535);
+    tc_col_scale<<<(nev + 7) / 8, 256, 0, st>>>(nr, nev, Z, ldr, E, state);
+    tc_convert<<<conv_grid, 256, 0, st>>>(nr, nev, Z, ldr, E, 1);
     tc_tile_offsets<<<1, 1, 0, st>>>(n, B, Gm::NB, G, toff);
-    constexpr size_t prep_smem = prep_smem_bytes<B>();
-    if ((e = cudaFuncSetAttribute(tc5_tile_prep<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem)) !=
-        cudaSuccess)
-        return e;
-    tc5_tile_prep<B><<<dim3(group_tiles(n, B, Gm::NB, 0), G), 256, prep_smem, st>>>(n, hh_v, hh_tau, toff, rec);
+    const dim3 prep_grid(group_tiles(n, B, Gm::NB, 0), G);
+    if constexpr (RF == 1) {
+        constexpr size_t prep_smem = prep_smem_bytes<B>();
+        if ((e = cudaFuncSetAttribute(tc5_tile_prep<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prep_smem)) !=
+            cudaSuccess)
+            return e;
+        tc5_tile_prep<B><<<prep_grid, 256, prep_smem, st>>>(n, hh_v, hh_tau, toff, rec);
+    } else {
+        constexpr size_t prep_smem = prep_smem_bytes_z<B>();
+        if ((e = cudaFuncSetAttribute(tc5_tile_prep_z<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)prep_smem)) != cudaSuccess)
+            return e;
+        tc5_tile_prep_z<B><<<prep_grid, 256, prep_smem, st>>>(n, (const double2 *)hh_v, (const double2 *)hh_tau, toff,
+                                                              rec);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(pipeline_tc5<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM)) !=
+    if ((e = cudaFuncSetAttribute(pipeline_tc5<B, RF>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM)) !=
         cudaSuccess)
         return e;
     const int want = column_batch > 0 ? column_batch : kColumnBatch5;
     const int CB = C < want ? C : want;
-    pipeline_tc5<B><<<(unsigned)G * (unsigned)C, kThreads5, Gm::SMEM, st>>>(
-        n, nev, (long long *)Z, ldz, rec, toff, G, C, CB, state, progress, spin_polls, timeout_ns, hold_group);
+    pipeline_tc5<B, RF><<<(unsigned)G * (unsigned)C, kThreads5, Gm::SMEM, st>>>(
+        n, nev, (long long *)Z, ldr, rec, toff, G, C, CB, state, progress, spin_polls, timeout_ns, hold_group);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    tc_convert<<<conv_grid, 256, 0, st>>>(n, nev, Z, ldz, E, 0);
+    tc_convert<<<conv_grid, 256, 0, st>>>(nr, nev, Z, ldr, E, 0);
     return cudaGetLastError();
 }
 
@@ -822,14 +1027,23 @@ cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, do
 
 bool pipeline_tc5_supported(int b) { return b == 16 || b == 32 || b == 64; }
 
-int pipeline_tc5_sweeps_per_tile(int b) { return b == 64 ? Geo<64>::NB : 16; }
+int pipeline_tc5_sweeps_per_tile(int b, int is_complex)
+{
+    if (is_complex) return Geo<64, 2>::NB;
+    return b == 64 ? Geo<64, 1>::NB : Geo<16, 1>::NB;
+}
 
-size_t pipeline_tc5_workspace_bytes(int n, int b, int nev)
+size_t pipeline_tc5_workspace_bytes(int n, int b, int nev, int is_complex)
 {
     if (n < 2 || nev < 1) return 256;
-    if (b == 16) return tc5_bytes<16>(n, nev);
-    if (b == 32) return tc5_bytes<32>(n, nev);
-    return tc5_bytes<64>(n, nev);
+    if (is_complex) {
+        if (b == 16) return tc5_bytes<16, 2>(n, nev);
+        if (b == 32) return tc5_bytes<32, 2>(n, nev);
+        return tc5_bytes<64, 2>(n, nev);
+    }
+    if (b == 16) return tc5_bytes<16, 1>(n, nev);
+    if (b == 32) return tc5_bytes<32, 1>(n, nev);
+    return tc5_bytes<64, 1>(n, nev);
 }
 
 cudaError_t pipeline_tc5_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
@@ -837,14 +1051,30 @@ cudaError_t pipeline_tc5_d(int n, int b, int nev, const double *hh_v, const doub
                            int hold_group, cudaStream_t st)
 {
     if (b == 16)
-        return run_tc5<16>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
-                           hold_group, st);
+        return run_tc5<16, 1>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
+                              hold_group, st);
     if (b == 32)
-        return run_tc5<32>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
-                           hold_group, st);
+        return run_tc5<32, 1>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
+                              hold_group, st);
     if (b == 64)
-        return run_tc5<64>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
-                           hold_group, st);
+        return run_tc5<64, 1>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
+                              hold_group, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t pipeline_tc5_z(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z, long long ldz,
+                           int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
+                           int hold_group, cudaStream_t st)
+{
+    if (b == 16)
+        return run_tc5<16, 2>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
+                              hold_group, st);
+    if (b == 32)
+        return run_tc5<32, 2>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
+                              hold_group, st);
+    if (b == 64)
+        return run_tc5<64, 2>(n, nev, hh_v, hh_tau, Z, ldz, column_batch, ws, ws_bytes, spin_polls, timeout_ns,
+                              hold_group, st);
     return cudaErrorInvalidValue;
 }
 

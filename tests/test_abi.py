@@ -84,9 +84,10 @@ def test_invalid_arguments_rejected_on_host(lib):
 
 
 def test_variant_resolution_is_host_only(lib):
-    """AUTO resolves to the tcgen05 pipeline for real nbw in {16, 32, 64} and
-    n >= 512, the DFMA pipeline for the other real pipeline band widths,
-    the wavefront otherwise; tensor-core requests fall back to the pipeline."""
+    """AUTO resolves to the tcgen05 pipeline for real or complex nbw in
+    {16, 32, 64} and n >= 512, the DFMA pipeline for the other real
+    pipeline band widths, the wavefront otherwise; tensor-core requests fall
+    back to the pipeline (real) or the wavefront (complex)."""
     v = gb.gb_trans_ev_variant
     assert v(16384, 64, 4096) == gb.GB_VARIANT_PIPELINE_TC5
     assert v(1024, 32, 1024) == gb.GB_VARIANT_PIPELINE_TC5
@@ -94,10 +95,14 @@ def test_variant_resolution_is_host_only(lib):
     assert v(500, 64, 10) == gb.GB_VARIANT_PIPELINE
     assert v(4096, 8, 100) == gb.GB_VARIANT_PIPELINE
     assert v(4096, 13, 100) == gb.GB_VARIANT_WAVEFRONT
-    assert v(4096, 64, 100, 1) == gb.GB_VARIANT_WAVEFRONT          # complex
+    assert v(4096, 64, 100, 1) == gb.GB_VARIANT_PIPELINE_TC5         # complex
+    assert v(500, 64, 100, 1) == gb.GB_VARIANT_WAVEFRONT
+    assert v(4096, 13, 100, 1) == gb.GB_VARIANT_WAVEFRONT
     assert v(4096, 64, 100, 0, {"variant": 3}) == gb.GB_VARIANT_PIPELINE_TC
+    assert v(4096, 64, 100, 1, {"variant": 3}) == gb.GB_VARIANT_WAVEFRONT
     assert v(4096, 8, 100, 0, {"variant": 4}) == gb.GB_VARIANT_PIPELINE
-    assert v(4096, 64, 100, 1, {"variant": 4}) == gb.GB_VARIANT_WAVEFRONT
+    assert v(4096, 8, 100, 1, {"variant": 4}) == gb.GB_VARIANT_WAVEFRONT
+    assert v(300, 32, 100, 1, {"variant": 4}) == gb.GB_VARIANT_PIPELINE_TC5
     assert v(4096, 64, 100, 0, {"variant": 5}) == -1
     assert gb.gb_trans_ev_launch_count(4096, 64, 100, 0, {"variant": 4}) == 6
     # the tcgen05 workspace: head, flags, scales, offsets and one 98816-byte
@@ -107,6 +112,12 @@ def test_variant_resolution_is_host_only(lib):
     tiles = sum((n - (1 + 32 * g) + b - 1) // b for g in range(G))
     wsb = gb.gb_trans_ev_workspace_bytes(n, b, nev)
     assert tiles * 98816 <= wsb <= tiles * 98816 + (1 << 20)
+    # complex: tiles of 8 sweeps, the real form's record (16 reflector
+    # columns, window 142 rows padded to 144): 36864 + 37504 bytes
+    Gz = (n - 1 + 7) // 8
+    tz = sum((n - (1 + 8 * g) + b - 1) // b for g in range(Gz))
+    wz = gb.gb_trans_ev_workspace_bytes(n, b, nev, 1)
+    assert tz * (36864 + 37504) <= wz <= tz * (36864 + 37504) + (1 << 20)
 
 
 def test_launch_count_is_host_only(lib):
