@@ -243,8 +243,8 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
  * column-major); 8 ldz >= n; 9 workspace (256-byte aligned); 10 ws_bytes >=
  * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0 or an OR
  * of GB_SOLVE_RECORD_STAGES, GB_SOLVE_DFMA_PRODUCTS and
- * GB_SOLVE_FP64_EMULATED_GEMM (accepted, no effect here: it selects cuBLAS's
- * fixed-point FP64 emulation for the complex solve's cuBLAS products).  By
+ * GB_SOLVE_FP64_EMULATED_GEMM (accepted and ignored: no product of either
+ * solver goes through a vendor BLAS).  By
  * default the large products (the full->band SYMM and SYR2K, the band->full
  * GEMMs, the Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by
  * exact digit slicing (gb_dgemm_sliced below); GB_SOLVE_DFMA_PRODUCTS runs
@@ -262,8 +262,12 @@ int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream)
 /* Complex Hermitian two-stage solve: A (complex128, interleaved, lda) =
  * Z diag(ev) Z^H with real ev (nev, ascending) and complex Z (n x nev, ldz);
  * same arguments, workspace rule (gb_solve_workspace_bytes_z) and flags as
- * gb_solve_d (GB_SOLVE_RECORD_STAGES is ignored).  Device-side status of
- * the bulge chase's waits through gb_solve_query_z. */
+ * gb_solve_d (GB_SOLVE_RECORD_STAGES is ignored).  The large complex
+ * products run sliced on the bf16 tensor cores (GB_SOLVE_DFMA_PRODUCTS:
+ * on the FP64 FMA pipe), the b x b panel products in this library's complex
+ * DFMA kernel, and the back-transformation on the tcgen05 tensor cores
+ * (nbw in {16, 32, 64}, n >= 512).  Device-side status of the waits of the
+ * bulge chase and of the back-transformation through gb_solve_query_z. */
 size_t gb_solve_workspace_bytes_z(int n, int nev, int nbw);
 int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
                void *workspace, size_t ws_bytes, void *stream, int flags);
@@ -274,15 +278,14 @@ int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *strea
  * band->full) of the last gb_solve_d on this stream that had
  * GB_SOLVE_RECORD_STAGES set; ms has 7 entries.  Synchronises the stream. */
 int gb_solve_stage_ms(void *stream, float *ms);
-/* The solvers cache per (device, stream) a cuBLAS handle (complex solve),
- * a look-ahead helper stream with its events (n >= 4096) and the stage
- * events; they are created on first use and otherwise kept until the
- * process exits.  gb_solve_release frees those of `stream` on the current
+/* The solvers cache per (device, stream) a look-ahead helper stream with
+ * its events (n >= 4096) and the stage events; they are created on first
+ * use and otherwise kept until the process exits.  gb_solve_release frees those of `stream` on the current
  * device, or of every stream on every device if all_streams is nonzero.
  * Call it only when no solve is in flight on the streams concerned (it
  * waits for the helper streams).  A later solve on such a stream creates
- * them again.  Returns GB_OK, or GB_ERR_CUDA if a CUDA or cuBLAS call
- * failed (the cache entries are dropped either way). */
+ * them again.  Returns GB_OK, or GB_ERR_CUDA if a CUDA call failed (the
+ * cache entries are dropped either way). */
 int gb_solve_release(void *stream, int all_streams);
 /* Convenience form with host-side defaults: nbw = min(64, n-1), legacy
  * default stream, and a workspace it allocates with cudaMalloc and frees

@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(NVCC))), "lib64")
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + [
-        "-lcublas", "-Xlinker", "-rpath=" + cudalib]
+        "-Xlinker", "-rpath=" + cudalib]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -34,4 +34,13 @@ cudaError_t dfma_syr2k_lower(int n, int k, double alpha, const double *A, long l
 cudaError_t dfma_syrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
                               long long ldc, cudaStream_t st);
 
+// Complex128 (interleaved re, im): C (m x n) = alpha op(A) op(B) + beta C,
+// op(A) = 'N', 'C' (conjugate transpose) or 'H' (A Hermitian, m x m, lower
+// triangle stored), op(B) = 'N' or 'C'; lower_only: only the lower triangle
+// of C is written, its diagonal made real.  `work` (doubles) holds split-K
+// partial products as for dfma_gemm (2 doubles per entry).
+cudaError_t dfma_zgemm(char opa, char opb, int m, int n, int k, double2 alpha, const double *A, long long lda,
+                       const double *B, long long ldb, double2 beta, double *C, long long ldc, int lower_only,
+                       double *work, size_t work_elems, cudaStream_t st);
+
 }  // namespace gb

@@ -17,7 +17,6 @@
 // Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by exact digit
 // slicing (dgemm_sliced.cuh), the small ones in the DFMA kernels
 // (dgemm_dfma.cuh); the complex solve's products in cuBLAS.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -59,29 +58,9 @@ cudaError_t promote_real(long long rows, long long cols, const double *X, long l
 
 namespace {
 
-// One cuBLAS handle per (device, stream): solves that overlap on different
-// streams then never share a handle's internal workspace.  Handles live until
-// the process exits.
-std::mutex g_blas_mutex;
-std::map<std::pair<int, cudaStream_t>, cublasHandle_t> g_blas;
-
-cublasHandle_t blas_handle(cudaStream_t st)
-{
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lock(g_blas_mutex);
-    auto key = std::make_pair(dev, st);
-    auto it = g_blas.find(key);
-    if (it != g_blas.end()) return it->second;
-    cublasHandle_t h = nullptr;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) {
-        cublasDestroy(h);
-        return nullptr;
-    }
-    g_blas[key] = h;
-    return h;
-}
+// Per-(device, stream) resources of the solvers are created on first use and
+// kept until gb_solve_release or process exit; one mutex guards the caches.
+std::mutex g_cache_mutex;
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -100,7 +79,7 @@ const Lookahead *lookahead(cudaStream_t st)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
     auto key = std::make_pair(dev, st);
     auto it = g_lookahead.find(key);
     if (it != g_lookahead.end()) return &it->second;
@@ -126,7 +105,7 @@ cudaEvent_t *stage_events(cudaStream_t st)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
     auto key = std::make_pair(dev, st);
     auto it = g_stage_events.find(key);
     if (it != g_stage_events.end()) return it->second;
@@ -283,10 +262,6 @@ SolveWsZ carve_z(int n, int nev, int b, char *base)
 #define GB_CU(x)                                     \
     do {                                             \
         if ((x) != cudaSuccess) return GB_ERR_CUDA;  \
-    } while (0)
-#define GB_BL(x)                                               \
-    do {                                                       \
-        if ((x) != CUBLAS_STATUS_SUCCESS) return GB_ERR_CUDA;  \
     } while (0)
 
 }  // namespace
@@ -485,17 +460,21 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     SolveWsZ w = carve_z(n, nev, b, (char *)workspace);
     if (ws_bytes < w.total) return -10;
     if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS)) return -12;
-    // large products sliced on the tensor cores unless the caller asks for the FP64 path (cuBLAS here)
+    // large products sliced on the tensor cores unless the caller asks for
+    // the FP64 path; every other product (the b x b panel products, the
+    // small-k updates, and the large ones on the FP64 path) in this
+    // library's complex DFMA kernel
     const bool zslice_ok = w.sl && !(flags & GB_SOLVE_DFMA_PRODUCTS);
     auto use_zsliced = [&](double m_, double n_, double k_) { return zslice_ok && zsliced_pays(m_, n_, k_); };
     cudaStream_t st = (cudaStream_t)stream;
-    cublasHandle_t h = blas_handle(st);
-    if (!h) return GB_ERR_CUDA;
-    GB_BL(cublasSetMathMode(h, (flags & GB_SOLVE_FP64_EMULATED_GEMM) ? CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH
-                                                                       : CUBLAS_DEFAULT_MATH));
-    const cuDoubleComplex one{1.0, 0.0}, zero{0.0, 0.0}, mone{-1.0, 0.0}, mhalf{-0.5, 0.0};
+    const double2 one{1.0, 0.0}, zero{0.0, 0.0}, mone{-1.0, 0.0}, mhalf{-0.5, 0.0};
     const long long ldw = n;
-    typedef cuDoubleComplex C;
+    typedef double2 C;
+    auto zg = [&](char oa, char ob, int m_, int n_, int k_, double2 al, const C *A_, long long la, const C *B_,
+                  long long lb, double2 be, C *C_, long long lc, int lower) {
+        return gb::dfma_zgemm(oa, ob, m_, n_, k_, al, (const double *)A_, la, (const double *)B_, lb, be,
+                              (double *)C_, lc, lower, w.gw, w.gw_elems, st);
+    };
     C *Aw = (C *)w.Aw, *Y = (C *)w.Y, *YT = (C *)w.YT, *X = (C *)w.X, *Pm = (C *)w.Pm, *M = (C *)w.M,
       *G = (C *)w.G, *S = (C *)w.S, *S2 = (C *)w.S2, *Zc = (C *)Z;
 
@@ -510,23 +489,25 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         C *T = (C *)(w.Tall + (long long)P * b * b * 2);
         GB_CU(gb::zpanel_qr(m, b, (double *)panel, ldw, tau, w.part, st));
         GB_CU(gb::zpanel_y(m, b, (const double *)panel, ldw, (double *)Y, m, st));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, m, &one, Y, m, Y, m, &zero, G, b));
+        GB_CU(zg('C', 'N', b, b, m, one, Y, m, Y, m, zero, G, b, 0));
         GB_CU(gb::zpanel_t(b, (const double *)G, b, tau, (double *)T, b, st));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &one, Y, m, T, b, &zero, YT, m));
+        GB_CU(zg('N', 'N', m, b, b, one, Y, m, T, b, zero, YT, m, 0));
         if (use_zsliced(m, b, m))
             GB_CU(gb::sliced_zhemm_left(m, b, 1.0, (const double *)A2, ldw, (const double *)YT, m, 0.0, (double *)X, m,
                                         w.sl, st));
         else
-            GB_BL(cublasZhemm(h, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, m, b, &one, A2, ldw, YT, m, &zero, X, m));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, m, &one, Y, m, X, m, &zero, Pm, b));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, b, b, &one, T, b, Pm, b, &zero, M, b));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, b, b, &mhalf, Y, m, M, b, &one, X, m));
-        const double rone = 1.0;  // ZHER2K: C = alpha A B^H + conj(alpha) B A^H + beta C, beta real
-        if (use_zsliced(m, m, b))
+            GB_CU(zg('H', 'N', m, b, m, one, A2, ldw, YT, m, zero, X, m, 0));
+        GB_CU(zg('C', 'N', b, b, m, one, Y, m, X, m, zero, Pm, b, 0));
+        GB_CU(zg('C', 'N', b, b, b, one, T, b, Pm, b, zero, M, b, 0));
+        GB_CU(zg('N', 'N', m, b, b, mhalf, Y, m, M, b, one, X, m, 0));
+        // lower triangle of A2 -= X Y^H + Y X^H (Hermitian rank-2b update)
+        if (use_zsliced(m, m, b)) {
             GB_CU(gb::sliced_zher2k_lower(m, b, -1.0, (const double *)X, m, (const double *)Y, m, 1.0, (double *)A2,
                                           ldw, w.sl, st));
-        else
-            GB_BL(cublasZher2k(h, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, m, b, &mone, X, m, Y, m, &rone, A2, ldw));
+        } else {
+            GB_CU(zg('N', 'C', m, m, b, mone, X, m, Y, m, one, A2, ldw, 1));
+            GB_CU(zg('N', 'C', m, m, b, mone, Y, m, X, m, one, A2, ldw, 1));
+        }
     }
     GB_CU(gb::zband_from_full(n, b, (const double *)Aw, ldw, w.AB, b + 1, st));
 
@@ -561,13 +542,13 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
             GB_CU(gb::sliced_zgemm('C', b, nev, m, 1.0, (const double *)Y, m, (const double *)Zr, ldz, 0.0,
                                    (double *)S, b, w.sl, st));
         else
-            GB_BL(cublasZgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, b, nev, m, &one, Y, m, Zr, ldz, &zero, S, b));
-        GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, b, nev, b, &one, T, b, S, b, &zero, S2, b));
+            GB_CU(zg('C', 'N', b, nev, m, one, Y, m, Zr, ldz, zero, S, b, 0));
+        GB_CU(zg('N', 'N', b, nev, b, one, T, b, S, b, zero, S2, b, 0));
         if (use_zsliced(m, nev, b))
             GB_CU(gb::sliced_zgemm('N', m, nev, b, -1.0, (const double *)Y, m, (const double *)S2, b, 1.0,
                                    (double *)Zr, ldz, w.sl, st));
         else
-            GB_BL(cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, nev, b, &mone, Y, m, S2, b, &one, Zr, ldz));
+            GB_CU(zg('N', 'N', m, nev, b, mone, Y, m, S2, b, one, Zr, ldz, 0));
     }
     GB_CU(cudaGetLastError());
     return GB_OK;
@@ -587,7 +568,7 @@ int gb_solve_release(void *stream, int all_streams)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
     const cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lock(g_blas_mutex);
+    std::lock_guard<std::mutex> lock(g_cache_mutex);
     auto match = [&](const std::pair<int, cudaStream_t> &k) {
         return all_streams || (k.first == dev && k.second == st);
     };
@@ -595,15 +576,6 @@ int gb_solve_release(void *stream, int all_streams)
     auto on_device = [&](int d) {  // resources are destroyed with their own device current
         if (cudaSetDevice(d) != cudaSuccess) rc = GB_ERR_CUDA;
     };
-    for (auto it = g_blas.begin(); it != g_blas.end();) {
-        if (!match(it->first)) {
-            ++it;
-            continue;
-        }
-        on_device(it->first.first);
-        if (cublasDestroy(it->second) != CUBLAS_STATUS_SUCCESS) rc = GB_ERR_CUDA;
-        it = g_blas.erase(it);
-    }
     for (auto it = g_lookahead.begin(); it != g_lookahead.end();) {
         if (!match(it->first)) {
             ++it;

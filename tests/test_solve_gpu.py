@@ -131,3 +131,28 @@ def test_solve_argument_errors(gb):
     assert f(10, 5, 10, 256, 10, 256, 256, 10, 256, 1 << 30, check=False) == -3
     assert f(10, 5, 3, 256, 9, 256, 256, 10, 256, 1 << 30, check=False) == -5
     assert f(10, 5, 3, 256, 10, 256, 256, 10, 256, 16, check=False) == -10
+
+
+def test_solve_release_frees_and_recreates_stream_resources(gb):
+    """gb_solve_release drops the per-stream resources a solve cached (the
+    look-ahead helper stream of n >= 4096, the stage events); a later solve
+    on the same stream creates them again and is still correct."""
+    n, nev = 4096, 256
+    lam = inputs.clustered_spectrum(n, seed=41)
+    A = inputs.symmetric_with_spectrum(lam, seed=42)
+    st = torch.cuda.Stream()
+    dev = torch.device("cuda")
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev)
+    wsb = gb.gb_solve_workspace_bytes(n, nev, 64)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    for rep in range(2):
+        ev = torch.zeros(nev, dtype=torch.float64, device=dev)
+        Z = torch.zeros((nev, n), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        gb.gb_solve_d(n, nev, 64, A_d, n, ev, Z, n, ws, wsb, st, gb.GB_SOLVE_RECORD_STAGES)
+        assert gb.gb_solve_query(ws, n, nev, 64, st) == 0
+        assert all(t >= 0 for t in gb.gb_solve_stage_ms(st).values())
+        w = ev.cpu().numpy()
+        assert np.abs(w - lam[:nev]).max() / np.abs(lam).max() <= 1e-11
+        assert gb.gb_solve_release(st, 0) == gb.GB_OK
+    assert gb.gb_solve_release(None, 1) == gb.GB_OK       # every stream, every device

@@ -66,12 +66,13 @@ def test_solve_hermitian_clustered(gb):
     check(A, w, Z, nev, lam)
 
 
-@pytest.mark.parametrize("flags", [0, 4], ids=["sliced_products", "cublas_products"])
+@pytest.mark.parametrize("flags", [0, 4], ids=["sliced_products", "dfma_products"])
 def test_solve_hermitian_large_products_both_paths(gb, flags):
     """n = 1200: the complex solve's large products (ZHEMM, ZHER2K, the
     band->full products, the real Newton-Schulz step) take the sliced
-    tensor-core path by default and cuBLAS / DFMA with
-    GB_SOLVE_DFMA_PRODUCTS; both meet the bounds."""
+    tensor-core path by default and this library's complex DFMA kernel with
+    GB_SOLVE_DFMA_PRODUCTS (as do the b x b panel products on either path);
+    both meet the bounds."""
     n, nev = 1200, 300
     lam = inputs.clustered_spectrum(n, seed=31)
     A = inputs.symmetric_with_spectrum(lam, seed=32, cplx=True)
