@@ -123,7 +123,9 @@ struct Geo {
     static constexpr int S_U = VBYTES;
     static constexpr int S_Z = REC;
     static constexpr int S_BAR = S_Z + kCols5 * ZROW * 8;    // 3 mbarriers + TMEM base
-    static constexpr int SMEM = S_BAR + 64;
+    // at least 116 KB, so that shared memory alone keeps the kernel at one
+    // CTA per SM: every CTA allocates all 512 TMEM columns
+    static constexpr int SMEM = (S_BAR + 64) > 116 * 1024 ? (S_BAR + 64) : 116 * 1024;
     static_assert(ZR >= 1 && T_WACC + WLEV <= kTmemCols, "Z digits and W levels fit in TMEM");
     static_assert(T_DZ + kLevels5 * NCH <= kTmemCols, "W digits and dZ levels fit in TMEM");
     // level bounds per K with the top digits bounded by 32 (Z, W) and 64
@@ -198,8 +200,28 @@ __device__ __forceinline__ long long fold9_bits(const uint32_t (&b)[kLevels5], i
     return (long long)((unsigned long long)shift_ll(hi, 26 + e) + (unsigned long long)shift_ll(lo, e - 14));
 }
 
-// round(x 2^(62 - e)) for |x| < 2^e: the row's fixed point (|result| <= 2^62)
-__device__ __forceinline__ long long fixed_row(double x, int e) { return __double2ll_rn(scale_by_pow2(x, 62 - e)); }
+// round(x 2^(62 - e)) for |x| < 2^e, to nearest with ties to even: the row's
+// fixed point (|result| <= 2^62), from the bit pattern with integer
+// operations only (x = M 2^p, M the 53-bit significand; subnormals too)
+__device__ __forceinline__ long long fixed_row(double x, int e)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    const unsigned long long M = (u & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
+    const int sh = (ex ? ex : 1) - 1075 + 62 - e;     // x 2^(62-e) = M 2^sh, sh <= 10
+    unsigned long long r;
+    if (sh >= 0) {
+        r = M << sh;
+    } else if (sh > -64) {
+        const int k = -sh;
+        r = M >> k;
+        const unsigned long long rem = M & ((1ull << k) - 1), half = 1ull << (k - 1);
+        if (rem > half || (rem == half && (r & 1))) r++;
+    } else {
+        r = 0;
+    }
+    return (u >> 63) ? -(long long)r : (long long)r;
+}
 
 // ---- per-tile records ------------------------------------------------------
 
@@ -283,18 +305,20 @@ __global__ void __launch_bounds__(256) tc5_tile_prep(int n, const double *__rest
         }
         __syncthreads();
     }
+    // U = V T; V(j, p) vanishes outside p <= j < p + b
     for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
         const int j = e / NB, q = e % NB;
         double a = 0.0;
-        for (int p = 0; p <= q; p++) a = fma(V[j * NB1 + p], T[p * NB1 + q], a);
+        for (int p = max(0, j - b + 1); p <= min(q, j); p++) a = fma(V[j * NB1 + p], T[p * NB1 + q], a);
         U[j * NB1 + q] = a;
     }
     // unit columns of V (U rescaled to keep U V^T): |v_q^T z| <= ||z||, so W
     // stays inside the column's fixed-point range whatever tau is
     if (threadIdx.x < NB) {
+        const int q = threadIdx.x;
         double a = 0.0;
-        for (int j = 0; j < LP; j++) a = fma(V[j * NB1 + threadIdx.x], V[j * NB1 + threadIdx.x], a);
-        nv[threadIdx.x] = sqrt(a);
+        for (int j = q; j < min(q + b, LP); j++) a = fma(V[j * NB1 + q], V[j * NB1 + q], a);
+        nv[q] = sqrt(a);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
@@ -441,16 +465,17 @@ __global__ void __launch_bounds__(256) tc5_tile_prep_z(int n, const double2 *__r
     for (int e = threadIdx.x; e < LC * NB; e += blockDim.x) {
         const int j = e / NB, q = e % NB;
         double2 a = zero;
-        for (int p = 0; p <= q; p++) a = cfma(V[j * NB1 + p], T[p * NB1 + q], a);
+        for (int p = max(0, j - b + 1); p <= min(q, j); p++) a = cfma(V[j * NB1 + p], T[p * NB1 + q], a);
         U[j * NB1 + q] = a;
     }
     if (threadIdx.x < NB) {
+        const int q = threadIdx.x;
         double a = 0.0;
-        for (int j = 0; j < LC; j++) {
-            const double2 v = V[j * NB1 + threadIdx.x];
+        for (int j = q; j < min(q + b, LC); j++) {
+            const double2 v = V[j * NB1 + q];
             a = fma(v.x, v.x, fma(v.y, v.y, a));
         }
-        nv[threadIdx.x] = sqrt(a);
+        nv[q] = sqrt(a);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < LC * NB; e += blockDim.x) {
