@@ -104,6 +104,14 @@ typedef struct gb_trans_ev_opts {
                             (0 = default: no limit).  Small leads keep the rows
                             passed from group to group in L2 but hold groups
                             back. */
+    void *kernel_begin_event; /* optional cudaEvent_t (NULL = none), recorded on the
+                            call's stream right before the call's dominant kernel
+                            is launched: the pipeline kernel, or the first of the
+                            wavefront's launches.  Lets a caller time that kernel
+                            alone with cudaEventElapsedTime.  An invalid event
+                            makes the call return GB_ERR_CUDA. */
+    void *kernel_end_event; /* optional cudaEvent_t recorded right after that
+                            kernel (the wavefront's last launch) */
 } gb_trans_ev_opts;
 
 /* Number of reflectors of the layout above (-1 if n < 1 or nbw < 1). */

@@ -58,7 +58,8 @@ class gb_trans_ev_opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("sweeps_per_tile", ctypes.c_int),
                 ("cols_per_block", ctypes.c_int), ("spin_limit", ctypes.c_int),
                 ("test_hold_group", ctypes.c_int), ("column_batch", ctypes.c_int),
-                ("lead_tiles", ctypes.c_int)]
+                ("lead_tiles", ctypes.c_int), ("kernel_begin_event", ctypes.c_void_p),
+                ("kernel_end_event", ctypes.c_void_p)]
 
 
 class GbError(RuntimeError):

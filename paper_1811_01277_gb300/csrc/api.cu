@@ -100,6 +100,24 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+namespace gb {
+thread_local KernelMarks g_kernel_marks;
+}
+
+namespace {
+
+// Sets the caller's kernel events (if any) for one call on this thread.
+struct MarksGuard {
+    explicit MarksGuard(const gb_trans_ev_opts *o)
+    {
+        gb::g_kernel_marks.begin = o ? (cudaEvent_t)o->kernel_begin_event : nullptr;
+        gb::g_kernel_marks.end = o ? (cudaEvent_t)o->kernel_end_event : nullptr;
+    }
+    ~MarksGuard() { gb::g_kernel_marks = gb::KernelMarks(); }
+};
+
+}  // namespace
+
 extern "C" {
 
 long long gb_hh_count(int n, int nbw)
@@ -140,6 +158,7 @@ int gb_trans_ev_tridi_to_band_d(int n, int nbw, int nev, const double *hh_v, con
     if (need > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0)) return -8;
     if (ws_bytes < need) return -9;
     if (n == 1 || nev == 0) return GB_OK;
+    MarksGuard marks(opts);
     cudaError_t e;
     if (o.variant == GB_VARIANT_PIPELINE_TC5)
         e = gb::pipeline_tc5_d(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.column_batch, workspace, need, o.spin, kTimeoutNs,
@@ -169,6 +188,7 @@ int gb_trans_ev_tridi_to_band_z(int n, int nbw, int nev, const double *hh_v, con
     if (need > 0 && (!workspace || ((uintptr_t)workspace % 256) != 0)) return -8;
     if (ws_bytes < need) return -9;
     if (n == 1 || nev == 0) return GB_OK;
+    MarksGuard marks(opts);
     cudaError_t e;
     if (o.variant == GB_VARIANT_PIPELINE_TC5)
         e = gb::pipeline_tc5_z(n, nbw, nev, hh_v, hh_tau, Z, ldz, o.column_batch, workspace, need, o.spin, kTimeoutNs,

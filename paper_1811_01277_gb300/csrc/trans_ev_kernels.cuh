@@ -7,6 +7,23 @@
 
 namespace gb {
 
+// Events a caller asked for (gb_trans_ev_opts.kernel_begin_event/_end_event),
+// recorded on the call's stream right before and after the launch(es) of the
+// call's dominant kernel.  The entry points set them for the duration of one
+// call on the issuing thread; null = not asked for.
+struct KernelMarks {
+    cudaEvent_t begin = nullptr, end = nullptr;
+};
+extern thread_local KernelMarks g_kernel_marks;
+inline cudaError_t mark_kernel_begin(cudaStream_t st)
+{
+    return g_kernel_marks.begin ? cudaEventRecord(g_kernel_marks.begin, st) : cudaSuccess;
+}
+inline cudaError_t mark_kernel_end(cudaStream_t st)
+{
+    return g_kernel_marks.end ? cudaEventRecord(g_kernel_marks.end, st) : cudaSuccess;
+}
+
 cudaError_t wavefront_d(int n, int b, int nev, const double *hh_v, const double *hh_tau, double *Z,
                         long long ldz, int nb, int threads, cudaStream_t st);
 long long wavefront_launch_count(int n, int b, int nb);

@@ -204,9 +204,12 @@ static cudaError_t run_pipeline_d(int n, int nev, const double *hh_v, const doub
     const int lead = lead_tiles > 0 ? lead_tiles : kLeadTiles;
     const int want = column_batch > 0 ? column_batch : kColumnBatch;
     const int CB = C < want ? C : want;
+    if ((e = mark_kernel_begin(st)) != cudaSuccess) return e;
     pipeline_d<B, NB, THREADS><<<(unsigned)G * (unsigned)C, THREADS, 0, st>>>(
         n, nev, hh_v, hh_tau, Z, ldz, G, C, CB, lead, state, progress, spin_polls, timeout_ns, hold_group);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark_kernel_end(st)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 size_t pipeline_workspace_bytes(int n, int nev, int nb, int threads)

@@ -143,6 +143,7 @@ static cudaError_t run_smem(int n, int b, int nev, const T *hh_v, const T *hh_ta
     for (int j = 0; j < G; j++) T_ = max(T_, j + group_tiles(n, b, NB, G - 1 - j));
     const unsigned cols = (unsigned)((nev + THREADS - 1) / THREADS);
     int jmin = 0;
+    if (cudaError_t em = mark_kernel_begin(st)) return em;
     for (int t = 0; t < T_; t++) {
         while (jmin < G && jmin + group_tiles(n, b, NB, G - 1 - jmin) <= t) jmin++;
         int jmax = min(t, G - 1);
@@ -152,7 +153,7 @@ static cudaError_t run_smem(int n, int b, int nev, const T *hh_v, const T *hh_ta
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return mark_kernel_end(st);
 }
 
 template <typename T>

@@ -572,9 +572,11 @@ cudaError_t run_tc(int n, int nev, const double *hh_v, const double *hh_tau, dou
         return e;
     const int want = column_batch > 0 ? column_batch : kColumnBatchTc;
     const int CB = C < want ? C : want;
+    if ((e = mark_kernel_begin(st)) != cudaSuccess) return e;
     pipeline_tc<B><<<(unsigned)G * (unsigned)C, kThreads, W::SMEM, st>>>(
         n, nev, (long long *)Z, ldz, E, rec, toff, G, C, CB, state, progress, spin_polls, timeout_ns, hold_group);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark_kernel_end(st)) != cudaSuccess) return e;
     tc_convert<<<conv_grid, 256, 0, st>>>(n, nev, Z, ldz, E, 0);
     return cudaGetLastError();
 }

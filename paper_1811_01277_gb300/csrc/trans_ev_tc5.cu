@@ -1041,9 +1041,11 @@ cudaError_t run_tc5(int n, int nev, const double *hh_v, const double *hh_tau, do
         return e;
     const int want = column_batch > 0 ? column_batch : kColumnBatch5;
     const int CB = C < want ? C : want;
+    if ((e = mark_kernel_begin(st)) != cudaSuccess) return e;
     pipeline_tc5<B, RF><<<(unsigned)G * (unsigned)C, kThreads5, Gm::SMEM, st>>>(
         n, nev, (long long *)Z, ldr, rec, toff, G, C, CB, state, progress, spin_polls, timeout_ns, hold_group);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = mark_kernel_end(st)) != cudaSuccess) return e;
     tc_convert<<<conv_grid, 256, 0, st>>>(nr, nev, Z, ldr, E, 0);
     return cudaGetLastError();
 }

@@ -89,6 +89,7 @@ static cudaError_t run_wavefront_d(int n, int b, int nev, const double *hh_v, co
     for (int j = 0; j < G; j++) T = max(T, j + group_tiles(n, b, NB, G - 1 - j));
     const unsigned cols = (unsigned)((nev + THREADS - 1) / THREADS);
     int jmin = 0;
+    if (cudaError_t em = mark_kernel_begin(st)) return em;
     for (int t = 0; t < T; t++) {
         while (jmin < G && jmin + group_tiles(n, b, NB, G - 1 - jmin) <= t) jmin++;
         int jmax = min(t, G - 1);
@@ -99,7 +100,7 @@ static cudaError_t run_wavefront_d(int n, int b, int nev, const double *hh_v, co
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return mark_kernel_end(st);
 }
 
 template <int NB>

@@ -303,3 +303,40 @@ def test_tc_wait_gives_up_and_context_survives(gb, opts):
     rc, q, out = run(gb, n, b, hv, ht, Z, opts)
     assert rc == 0 and q == 0
     assert np.linalg.norm(out - oracle.trans_ev(n, b, hv, ht, Z)) / np.linalg.norm(Z) <= PARITY
+
+
+@pytest.mark.parametrize("opts", [TC5, TC, {"variant": 2}, {"variant": 1}], ids=["tcgen05", "mma_sync", "pipeline", "wavefront"])
+def test_kernel_events_bracket_the_dominant_kernel(gb, opts):
+    """gb_trans_ev_opts.kernel_begin_event / kernel_end_event: the library
+    records the caller's events around the dominant kernel's launch(es) on the
+    call's stream; the span is positive and inside the whole call's span, and
+    the result is the same as without events."""
+    n, b, nev = 1024, 64, 256
+    hv, ht = inputs.synthetic_reflectors(n, b, seed=3)
+    Z = inputs.z_gaussian(n, nev, seed=4)
+    dev = torch.device("cuda")
+    st = torch.cuda.current_stream()
+    outs = []
+    for with_events in (False, True):
+        Zt = torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev)
+        hv_d = torch.from_numpy(hv).to(dev)
+        ht_d = torch.from_numpy(ht).to(dev)
+        wsb = gb.gb_trans_ev_workspace_bytes(n, b, nev, 0, opts)
+        ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for e in ev:
+            e.record(st)          # the events exist once recorded
+        o = dict(opts)
+        if with_events:
+            o.update(kernel_begin_event=ev[1].cuda_event, kernel_end_event=ev[2].cuda_event)
+        ev[0].record(st)
+        gb.gb_trans_ev_tridi_to_band_d(n, b, nev, hv_d, ht_d, Zt, n, ws, wsb, st, o)
+        ev[3].record(st)
+        torch.cuda.synchronize()
+        assert gb.gb_trans_ev_query(ws if wsb else None, wsb, st) == 0
+        if with_events:
+            k = ev[1].elapsed_time(ev[2])
+            assert 0.0 < k <= ev[0].elapsed_time(ev[3])
+            assert ev[0].elapsed_time(ev[1]) >= 0.0 and ev[2].elapsed_time(ev[3]) >= 0.0
+        outs.append(Zt.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
