@@ -437,18 +437,19 @@ def run_ours(args, wl):
                  "per": "step (the whole call: scales, tile preparation, pipeline, conversions)"}
     if variant_name == "pipeline_tc5":
         # tcgen05 MMAs on FP16 digit planes (same dense rate as bf16): executed
-        # tensor flops against the measured bf16 peak (cuBLAS, tcgen05 path);
-        # the bench loops the call for seconds, so the sustained figure is the
-        # denominator, the burst one beside it
+        # tensor flops against the measured bf16 peak (cuBLAS, tcgen05 path).
+        # The kernel is timed alone (the step is this one call, and it runs at
+        # the maximum clock), so the burst figure is the denominator; the
+        # sustained one (cuBLAS under the power cap) beside it
         pk = measured_peaks()
         Ft = tc5_executed_flops(n, nbw, nev)
         tc_ach = Ft / (kernel_ms / 1e3) / 1e12
-        peak = pk["bf16_tflops_sustained"] or pk["bf16_tflops"]
+        peak = pk["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": tc_ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": tc_ach / peak, "traffic": traffic,
-                "peak_source": f"MEASURED_PEAKS.json bf16_tflops_sustained ({pk['source']}; cuBLAS bf16 on the "
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops, burst ({pk['source']}; cuBLAS bf16 on the "
                                f"tcgen05 path, FP16 runs at the same dense rate)",
-                "frac_of_burst_peak": tc_ach / pk["bf16_tflops"],
+                "frac_of_sustained_peak": tc_ach / (pk["bf16_tflops_sustained"] or pk["bf16_tflops"]),
                 "kernel": kernel, "per": "launch", "kernel_ms_per_launch": kernel_ms,
                 "executed_fp16_tflop_per_launch": Ft / 1e12, "fp64_equivalent": step_fp64}
     elif variant_name == "pipeline_tc":
@@ -971,11 +972,13 @@ def run_stage_trans_ev_z(args):
         pk = measured_peaks()
         Ft = tc5_executed_flops_z(n, nbw, nev)
         ach = Ft / (kernel_ms / 1e3) / 1e12
-        peak = pk["bf16_tflops_sustained"] or pk["bf16_tflops"]
+        peak = pk["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "kernel": "pipeline_tc5 (complex, real 2x2-block form)", "per": "launch",
                 "kernel_ms_per_launch": kernel_ms, "executed_fp16_tflop_per_launch": Ft / 1e12,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained", "fp64_equivalent_per_step": fp64}
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst: the kernel is timed alone)",
+                "frac_of_sustained_peak": ach / (pk["bf16_tflops_sustained"] or pk["bf16_tflops"]),
+                "fp64_equivalent_per_step": fp64}
     else:
         roof = dict(bound="alu", kernel_ms_per_launch=kernel_ms, **fp64)
     print(json.dumps({

@@ -4,9 +4,10 @@ It serves callers that cannot allocate device memory -- code running inside
 a memory pool or arena that owns the whole device, allocation-free service
 loops, hosts that forbid cudaMalloc after start-up.  Its scratch lives in a
 fixed device array inside the library, so these tests check that two calls
-in a row (which share and reuse that array) give the same result as the
-regular entry point with a caller-allocated workspace, and that a problem too
-large for the fixed array is refused before anything runs.
+in a row (which share and reuse that array) match the oracle at the parity
+bar (1e-12 per column) and give the same result as the regular entry point
+with a caller-allocated workspace, and that a problem too large for the fixed
+array is refused before anything runs.
 
 This file is named to be collected last; it passes alone in a fresh process
 as well as after the other tests.
@@ -14,6 +15,7 @@ as well as after the other tests.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1811_01277_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -33,10 +35,14 @@ def gb():
     return m
 
 
+def _host_problem(n, b, nev, seed):
+    hv, ht = inputs.synthetic_reflectors(n, b, seed=seed)
+    return hv, ht, inputs.z_gaussian(n, nev, seed=seed + 1)
+
+
 def _device_problem(n, b, nev, seed):
     dev = torch.device("cuda")
-    hv, ht = inputs.synthetic_reflectors(n, b, seed=seed)
-    Z = inputs.z_gaussian(n, nev, seed=seed + 1)
+    hv, ht, Z = _host_problem(n, b, nev, seed)
     return (torch.from_numpy(hv).to(dev), torch.from_numpy(ht).to(dev),
             torch.from_numpy(np.ascontiguousarray(Z.T)).to(dev))
 
@@ -68,6 +74,11 @@ def test_noalloc_matches_regular_entry_point_twice(gb):
         assert int(status.item()) == 0
         err = torch.linalg.norm(out - ref).item() / torch.linalg.norm(Zt).item()
         assert err <= 1e-12
+        # against the oracle, every column
+        hv_h, ht_h, Z_h = _host_problem(n, b, nev, seed)
+        want = oracle.trans_ev(n, b, hv_h, ht_h, Z_h)
+        got = out.cpu().numpy().T
+        assert np.max(np.linalg.norm(got - want, axis=0) / np.linalg.norm(Z_h, axis=0)) <= 1e-12
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch(gb):
