@@ -505,8 +505,9 @@ def run_ours(args, wl):
             bt = measure_batched(512, 128, 2048, 16, steps=1, warmup=1)
             line["batched"] = {k_: bt[k_] for k_ in ("solves_per_s", "p50_ms", "p99_ms", "seconds_per_batch",
                                                      "streams", "plain_solve_one_at_a_time",
-                                                     "accuracy_worst_over_50nu", "data", "clocks", "metric")}
-            line["batched"].update(steps=1, warmup=1)
+                                                     "accuracy_worst_over_50nu", "data", "clocks", "metric",
+                                                     "graph", "graph_tuned_nbw")}
+            line["batched"].update(steps=1, warmup=1, form="streams (gb_solve_batched_d); the graph forms beside it")
         print(json.dumps(line))
     return 0
 
@@ -890,6 +891,76 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
         o = (Zi.T @ Zi - torch.eye(n, dtype=torch.float64, device=dev)).abs().max()
         worst = max(worst, float(r) / (50 * n * 2.0 ** -53), float(o) / (50 * n * 2.0 ** -53))
     rate = steps * len(sizes) / el
+
+    # the same batch as one CUDA graph (captured once, replayed), first with
+    # the default band widths, then with the band widths a size-class tuner
+    # picked from one timed solve per (class, nbw) trial
+    def graph_form(nbw):
+        gwsb = gb.gb_solve_batched_workspace_bytes_nbw(sizes, sizes, nbw, len(streams))
+        gws = ws if gwsb <= wsb else torch.empty(gwsb, dtype=torch.uint8, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        graph = gb.gb_solve_batched_graph_create(sizes, sizes, nbw, A, sizes, ev, Z, sizes, gws, gwsb,
+                                                 len(streams), es, ee)
+        create_s = time.perf_counter() - t0
+        try:
+            gst = torch.cuda.Stream(device=dev)
+            for _ in range(warmup):
+                gb.gb_solve_batched_graph_launch(graph, gst)
+            torch.cuda.synchronize(dev)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            smp = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+            g0.record(gst)
+            for _ in range(steps):
+                gb.gb_solve_batched_graph_launch(graph, gst)
+            g1.record(gst)
+            torch.cuda.synchronize(dev)
+            gclk = smp.stop()
+            gel = g0.elapsed_time(g1) / 1e3
+            gper = np.array([a.elapsed_time(b) for a, b in zip(es, ee)])
+            nodes = gb.gb_solve_batched_graph_nodes(graph)
+        finally:
+            gb.gb_solve_batched_graph_destroy(graph)
+        return {"value": steps * len(sizes) / gel, "unit": "solves/s", "seconds_per_batch": gel / steps,
+                "p50_ms": float(np.percentile(gper, 50)), "p99_ms": float(np.percentile(gper, 99)),
+                "graph_nodes": int(nodes), "branches": len(streams), "capture_and_instantiate_s": create_s,
+                "clocks": gclk}
+
+    graph_default = graph_form(None)
+    # a trial is a mini-batch: one problem of the class's order per stream,
+    # all solved at once with the trial's band width (the batch's throughput,
+    # not a lone solve's latency, is what the choice has to serve)
+    tuner = gb.gb_solve_tuner_create(lo, hi, 4)
+    trials = []
+    while True:
+        tr = gb.gb_solve_tuner_step(tuner)
+        if tr is None:
+            break
+        tn, tb = tr
+        k = len(streams)
+        At = []
+        for _ in range(k):
+            R = torch.randn(tn, tn, generator=gen, device=dev, dtype=torch.float64)
+            At.append(0.5 * (R + R.T))
+        evt = [torch.zeros(tn, dtype=torch.float64, device=dev) for _ in range(k)]
+        Zt_ = [torch.zeros((tn, tn), dtype=torch.float64, device=dev) for _ in range(k)]
+        tsz, tbw = [tn] * k, [tb] * k
+        twsb = gb.gb_solve_batched_workspace_bytes_nbw(tsz, tsz, tbw, k)
+        tws = torch.empty(twsb, dtype=torch.uint8, device=dev)
+        gb.gb_solve_batched_nbw_d(tsz, tsz, tbw, At, tsz, evt, Zt_, tsz, tws, twsb, streams)   # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        gb.gb_solve_batched_nbw_d(tsz, tsz, tbw, At, tsz, evt, Zt_, tsz, tws, twsb, streams)
+        torch.cuda.synchronize(dev)
+        sec = time.perf_counter() - t0
+        gb.gb_solve_tuner_report(tuner, sec)
+        trials.append({"n": tn, "nbw": tb, "problems": k, "s": sec})
+        del At, evt, Zt_, tws
+    tuned_nbw = [gb.gb_solve_tuner_nbw(tuner, n_) for n_ in sizes]
+    gb.gb_solve_tuner_destroy(tuner)
+    graph_tuned = graph_form(tuned_nbw)
+    graph_tuned["tuner"] = {"classes": 4, "trials": trials,
+                            "chosen": sorted({(n_, b_) for n_, b_ in zip(sizes, tuned_nbw)})[::max(1, count // 16)]}
     out = {
         "metric": f"batched eigensolves/s, {len(sizes)} problems n~U[{lo},{hi}], all eigenpairs",
         "value": rate, "unit": "solves/s", "solves_per_s": rate, "seconds_per_batch": el / steps,
@@ -899,7 +970,8 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
         "plain_solve_one_at_a_time": {"value": plain_rate, "unit": "solves/s",
                                       "sample": f"every {plain_every}th problem ({len(sample)})",
                                       "speedup_of_batched": rate / plain_rate},
-        "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks}
+        "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks,
+        "graph": graph_default, "graph_tuned_nbw": graph_tuned}
     del A, Z, ev, ws, pws
     torch.cuda.empty_cache()
     return out

@@ -318,6 +318,80 @@ int gb_solve_batched_d(int count, const int *n, const int *nev, const double *co
                        size_t ws_bytes, int nslots, void *const *streams, void *const *ev_start,
                        void *const *ev_end);
 
+/* The same with a band width per problem: nbw[i] in 1..min(64, n[i]-1), or
+ * nbw == NULL for gb_solve_default_nbw(n[i]) (e.g. the choices of a
+ * gb_solve_tuner).  Arguments as above with nbw inserted as the 4th, so the
+ * later ones are numbered one higher (workspace -10, ws_bytes -11, nslots
+ * -12). */
+size_t gb_solve_batched_workspace_bytes_nbw(int count, const int *n, const int *nev, const int *nbw,
+                                            int nslots);
+int gb_solve_batched_nbw_d(int count, const int *n, const int *nev, const int *nbw,
+                           const double *const *A, const int *lda, double *const *ev,
+                           double *const *Z, const int *ldz, void *workspace, size_t ws_bytes,
+                           int nslots, void *const *streams, void *const *ev_start,
+                           void *const *ev_end);
+
+/* The batched form as ONE CUDA graph.  The paper's SCF loop solves the same
+ * set of problems again and again with new matrix entries (Sec. 5.1), so the
+ * batch is issued once and replayed:
+ *  * gb_solve_batched_graph_create records every solve of the batch (band
+ *    width nbw[i], or the default when nbw is NULL) by stream capture into a
+ *    graph of nbranches parallel branches -- problem i on branch
+ *    i % nbranches, in workspace slot i % nbranches, after the branch's
+ *    previous problem -- and instantiates it.  Nothing runs during creation.
+ *    Events ev_start[i] / ev_end[i] (or NULL arrays), created by the caller,
+ *    become event-record nodes around problem i.  Panel factorisations inside
+ *    the graph take their non-cooperative form (a graph's kernel nodes carry
+ *    no co-residency guarantee).  The graph owns its branch streams; the
+ *    caller's buffers must stay allocated while it exists.
+ *  * gb_solve_batched_graph_launch runs the whole batch as one graph launch
+ *    on `stream` (asynchronous; on the device the graph was made on).  Each
+ *    launch reads A[i] and writes ev[i] and Z[i] at the pointers given at
+ *    creation, so the caller refreshes the matrices in place between
+ *    launches.  Launches on one stream run one after another.
+ *  * gb_solve_batched_graph_nodes: the graph's node count (-1 for NULL).
+ *  * gb_solve_batched_graph_destroy: call it when no launch of the graph is
+ *    still running.
+ * Arguments of create: 1 count >= 1; 2-3 n, nev; 4 nbw or NULL; 5-9 A, lda,
+ * ev, Z, ldz; 10 workspace (256-byte aligned); 11 ws_bytes >=
+ * gb_solve_batched_workspace_bytes_nbw(count, n, nev, nbw, nbranches);
+ * 12 nbranches >= 1; 13-14 event arrays or NULL; 15 graph (out).  Returns
+ * GB_OK, -i, or GB_ERR_CUDA if the capture or instantiation failed (nothing
+ * is left behind). */
+typedef struct gb_solve_graph gb_solve_graph;
+int gb_solve_batched_graph_create(int count, const int *n, const int *nev, const int *nbw,
+                                  const double *const *A, const int *lda, double *const *ev,
+                                  double *const *Z, const int *ldz, void *workspace,
+                                  size_t ws_bytes, int nbranches, void *const *ev_start,
+                                  void *const *ev_end, gb_solve_graph **graph);
+int gb_solve_batched_graph_launch(gb_solve_graph *graph, void *stream);
+long long gb_solve_batched_graph_nodes(const gb_solve_graph *graph);
+int gb_solve_batched_graph_destroy(gb_solve_graph *graph);
+
+/* Band-width tuning for the two-stage solve by problem size (the paper's
+ * autotuning, Sec. 4.3 and 5.3, applied to the solver's blocking: the band
+ * width is the panel width of full->band, the bulge chase's band and the
+ * back-transformation's tile height).  Orders in [n_lo, n_hi] fall into
+ * `classes` size classes of equal width in log(n).  For each class the tuner
+ * hands out trials (n, nbw): n the class's geometric middle, nbw each of 16,
+ * 32 and 64 below n.  The caller runs one solve per trial and reports its
+ * seconds.  gb_solve_tuner_nbw(t, n) then gives the fastest measured band
+ * width of n's class, capped below n (gb_solve_default_nbw(n) for a class
+ * with no measurement or an n outside [n_lo, n_hi]).
+ * gb_solve_tuner_step returns 1 with a trial, 0 when all are handed out, -1
+ * while the previous trial is unreported.  save/load write and read the
+ * state as text (a trial handed out but not reported is handed out again).
+ * create returns NULL unless 2 <= n_lo <= n_hi and 1 <= classes <= 64.
+ * Host-side only. */
+typedef struct gb_solve_tuner gb_solve_tuner;
+gb_solve_tuner *gb_solve_tuner_create(int n_lo, int n_hi, int classes);
+void gb_solve_tuner_destroy(gb_solve_tuner *t);
+int gb_solve_tuner_step(gb_solve_tuner *t, int *n, int *nbw);
+int gb_solve_tuner_report(gb_solve_tuner *t, double seconds);
+int gb_solve_tuner_nbw(const gb_solve_tuner *t, int n);
+int gb_solve_tuner_save(const gb_solve_tuner *t, const char *path);
+gb_solve_tuner *gb_solve_tuner_load(const char *path);
+
 /* Autotuning of the back-transformation (modelled on the paper's autotuning,
  * Sec. 4.3 and 5.3): a tuning object walks a fixed list of settings; the
  * caller runs one back-transformation (or one solve) with each setting it

@@ -22,6 +22,10 @@ from ._lib import (  # noqa: F401
     gb_dsymm_sliced_workspace_bytes, gb_dsyr2k_sliced, gb_dsyr2k_sliced_workspace_bytes, gb_dsyrk_sliced,
     gb_dsyrk_sliced_workspace_bytes, gb_zgemm_sliced, gb_zgemm_sliced_workspace_bytes, gb_zhemm_sliced,
     gb_zhemm_sliced_workspace_bytes, gb_zher2k_sliced, gb_zher2k_sliced_workspace_bytes,
+    gb_solve_batched_workspace_bytes_nbw, gb_solve_batched_nbw_d, gb_solve_batched_graph_create,
+    gb_solve_batched_graph_launch, gb_solve_batched_graph_nodes, gb_solve_batched_graph_destroy,
+    gb_solve_tuner_create, gb_solve_tuner_destroy, gb_solve_tuner_step, gb_solve_tuner_report, gb_solve_tuner_nbw,
+    gb_solve_tuner_save, gb_solve_tuner_load,
 )
 
 

@@ -35,7 +35,10 @@ EXPORTS = (
     "gb_autotune_create", "gb_autotune_destroy", "gb_autotune_step", "gb_autotune_report",
     "gb_autotune_best", "gb_autotune_progress", "gb_autotune_save", "gb_autotune_load",
     "gb_solve_default_nbw", "gb_solve_batched_workspace_bytes", "gb_solve_batched_d", "gb_solve_stage_ms",
-    "gb_solve_release",
+    "gb_solve_release", "gb_solve_batched_workspace_bytes_nbw", "gb_solve_batched_nbw_d",
+    "gb_solve_batched_graph_create", "gb_solve_batched_graph_launch", "gb_solve_batched_graph_nodes",
+    "gb_solve_batched_graph_destroy", "gb_solve_tuner_create", "gb_solve_tuner_destroy", "gb_solve_tuner_step",
+    "gb_solve_tuner_report", "gb_solve_tuner_nbw", "gb_solve_tuner_save", "gb_solve_tuner_load",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
@@ -130,6 +133,22 @@ def load(path=None):
     L.gb_solve_batched_workspace_bytes.restype = sz
     L.gb_solve_batched_d.argtypes = [i, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
     L.gb_solve_batched_d.restype = i
+    L.gb_solve_batched_workspace_bytes_nbw.argtypes = [i, pi_, pi_, pi_, i]
+    L.gb_solve_batched_workspace_bytes_nbw.restype = sz
+    L.gb_solve_batched_nbw_d.argtypes = [i, pi_, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
+    L.gb_solve_batched_nbw_d.restype = i
+    L.gb_solve_batched_graph_create.argtypes = [i, pi_, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
+    L.gb_solve_batched_graph_create.restype = i
+    L.gb_solve_batched_graph_launch.argtypes = [p, p]; L.gb_solve_batched_graph_launch.restype = i
+    L.gb_solve_batched_graph_nodes.argtypes = [p]; L.gb_solve_batched_graph_nodes.restype = ctypes.c_longlong
+    L.gb_solve_batched_graph_destroy.argtypes = [p]; L.gb_solve_batched_graph_destroy.restype = i
+    L.gb_solve_tuner_create.argtypes = [i, i, i]; L.gb_solve_tuner_create.restype = p
+    L.gb_solve_tuner_destroy.argtypes = [p]; L.gb_solve_tuner_destroy.restype = None
+    L.gb_solve_tuner_step.argtypes = [p, pi_, pi_]; L.gb_solve_tuner_step.restype = i
+    L.gb_solve_tuner_report.argtypes = [p, ctypes.c_double]; L.gb_solve_tuner_report.restype = i
+    L.gb_solve_tuner_nbw.argtypes = [p, i]; L.gb_solve_tuner_nbw.restype = i
+    L.gb_solve_tuner_save.argtypes = [p, ctypes.c_char_p]; L.gb_solve_tuner_save.restype = i
+    L.gb_solve_tuner_load.argtypes = [ctypes.c_char_p]; L.gb_solve_tuner_load.restype = p
     ch, dd = ctypes.c_char, ctypes.c_double
     L.gb_dgemm_workspace_bytes.argtypes = [i, i]; L.gb_dgemm_workspace_bytes.restype = sz
     L.gb_dgemm.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dgemm.restype = i
@@ -401,26 +420,109 @@ def gb_solve_batched_workspace_bytes(n, nev, nslots):
     return load().gb_solve_batched_workspace_bytes(len(n), _iarr(n), _iarr(nev), nslots)
 
 
+def _handle(x):
+    """Raw handle of a torch.cuda.Stream / torch.cuda.Event (or an int)."""
+    if hasattr(x, "cuda_stream"):
+        return x.cuda_stream
+    if hasattr(x, "cuda_event"):
+        if not x.cuda_event:      # torch creates the CUDA event on its first record
+            x.record()
+        return x.cuda_event
+    return int(x)
+
+
+def _harr(xs):
+    return (ctypes.c_void_p * len(xs))(*[_handle(x) for x in xs]) if xs else None
+
+
 def gb_solve_batched_d(n, nev, A, lda, ev, Z, ldz, workspace, ws_bytes, streams, ev_start=None, ev_end=None,
                        check=True):
     """Lists of per-problem sizes and device buffers; streams / events are
     torch.cuda.Stream / torch.cuda.Event objects or raw handles."""
-    def handle(x):
-        if hasattr(x, "cuda_stream"):
-            return x.cuda_stream
-        if hasattr(x, "cuda_event"):
-            if not x.cuda_event:      # torch creates the CUDA event on its first record
-                x.record()
-            return x.cuda_event
-        return int(x)
-    st = (ctypes.c_void_p * len(streams))(*[handle(s) for s in streams])
-    es = (ctypes.c_void_p * len(ev_start))(*[handle(e) for e in ev_start]) if ev_start else None
-    ee = (ctypes.c_void_p * len(ev_end))(*[handle(e) for e in ev_end]) if ev_end else None
     rc = load().gb_solve_batched_d(len(n), _iarr(n), _iarr(nev), _parr(A), _iarr(lda), _parr(ev), _parr(Z),
-                                   _iarr(ldz), _dp(workspace), ws_bytes, len(streams), st, es, ee)
+                                   _iarr(ldz), _dp(workspace), ws_bytes, len(streams), _harr(streams),
+                                   _harr(ev_start), _harr(ev_end))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_solve_batched_d")
     return rc
+
+
+def gb_solve_batched_workspace_bytes_nbw(n, nev, nbw, nslots):
+    return load().gb_solve_batched_workspace_bytes_nbw(len(n), _iarr(n), _iarr(nev),
+                                                       _iarr(nbw) if nbw is not None else None, nslots)
+
+
+def gb_solve_batched_nbw_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, streams, ev_start=None,
+                           ev_end=None, check=True):
+    rc = load().gb_solve_batched_nbw_d(len(n), _iarr(n), _iarr(nev), _iarr(nbw) if nbw is not None else None,
+                                       _parr(A), _iarr(lda), _parr(ev), _parr(Z), _iarr(ldz), _dp(workspace),
+                                       ws_bytes, len(streams), _harr(streams), _harr(ev_start), _harr(ev_end))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_batched_nbw_d")
+    return rc
+
+
+def gb_solve_batched_graph_create(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, nbranches,
+                                  ev_start=None, ev_end=None):
+    """Returns the graph handle (an int); raises GbError on failure."""
+    g = ctypes.c_void_p()
+    rc = load().gb_solve_batched_graph_create(len(n), _iarr(n), _iarr(nev), _iarr(nbw) if nbw is not None else None,
+                                              _parr(A), _iarr(lda), _parr(ev), _parr(Z), _iarr(ldz),
+                                              _dp(workspace), ws_bytes, nbranches, _harr(ev_start), _harr(ev_end),
+                                              ctypes.byref(g))
+    if rc != GB_OK:
+        raise GbError(rc, "gb_solve_batched_graph_create")
+    return g.value
+
+
+def gb_solve_batched_graph_launch(graph, stream=None, check=True):
+    rc = load().gb_solve_batched_graph_launch(graph, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_batched_graph_launch")
+    return rc
+
+
+def gb_solve_batched_graph_nodes(graph):
+    return load().gb_solve_batched_graph_nodes(graph)
+
+
+def gb_solve_batched_graph_destroy(graph):
+    return load().gb_solve_batched_graph_destroy(graph)
+
+
+def gb_solve_tuner_create(n_lo, n_hi, classes):
+    return load().gb_solve_tuner_create(n_lo, n_hi, classes)
+
+
+def gb_solve_tuner_destroy(t):
+    load().gb_solve_tuner_destroy(t)
+
+
+def gb_solve_tuner_step(t):
+    """The next trial (n, nbw), or None when every trial is handed out."""
+    n, b = ctypes.c_int(), ctypes.c_int()
+    rc = load().gb_solve_tuner_step(t, ctypes.byref(n), ctypes.byref(b))
+    if rc == 0:
+        return None
+    if rc != 1:
+        raise GbError(rc, "gb_solve_tuner_step")
+    return n.value, b.value
+
+
+def gb_solve_tuner_report(t, seconds):
+    return load().gb_solve_tuner_report(t, seconds)
+
+
+def gb_solve_tuner_nbw(t, n):
+    return load().gb_solve_tuner_nbw(t, n)
+
+
+def gb_solve_tuner_save(t, path):
+    return load().gb_solve_tuner_save(t, str(path).encode())
+
+
+def gb_solve_tuner_load(path):
+    return load().gb_solve_tuner_load(str(path).encode())
 
 
 def gb_dgemm_workspace_bytes(m, n):

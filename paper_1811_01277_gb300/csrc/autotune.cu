@@ -9,6 +9,7 @@
 //   MEDIUM : the variant and its blocking (sweeps per tile, columns per block;
 //            column batch for the tensor-core pipeline)
 // Host code only; no device memory is touched.
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -173,6 +174,150 @@ gb_autotune *gb_autotune_load(const char *path)
             }
             if (t) t->next = next;
         } else if (t) {
+            delete t;
+            t = NULL;
+        }
+    }
+    fclose(f);
+    return t;
+}
+
+}  // extern "C"
+
+// Band-width tuning of the two-stage solve by size class (declared in
+// elpa_gb300.h): the same walk-and-report protocol, over (n, nbw) trials.
+struct gb_solve_tuner {
+    int n_lo, n_hi, classes;
+    struct Trial {
+        int cls, n, nbw;
+        double secs;  // < 0: not measured yet
+    };
+    std::vector<Trial> trials;
+    int next, pending;
+};
+
+namespace {
+
+// class c covers [n_lo r^c, n_lo r^(c+1)), r = (n_hi / n_lo)^(1 / classes);
+// n_hi itself belongs to the last class
+int tuner_class(const gb_solve_tuner *t, int n)
+{
+    if (n < t->n_lo || n > t->n_hi) return -1;
+    if (t->n_hi == t->n_lo) return 0;
+    const double x = log((double)n / t->n_lo) / log((double)t->n_hi / t->n_lo) * t->classes;
+    int c = (int)floor(x);
+    return c < 0 ? 0 : (c >= t->classes ? t->classes - 1 : c);
+}
+
+void tuner_trials(gb_solve_tuner *t)
+{
+    t->trials.clear();
+    const double r = t->n_hi == t->n_lo ? 1.0 : pow((double)t->n_hi / t->n_lo, 1.0 / t->classes);
+    for (int c = 0; c < t->classes; c++) {
+        int n = (int)lround(t->n_lo * pow(r, c + 0.5));
+        n = n < t->n_lo ? t->n_lo : (n > t->n_hi ? t->n_hi : n);
+        const int cand[3] = {16, 32, 64};
+        bool any = false;
+        for (int b : cand)
+            if (b < n) {
+                t->trials.push_back({c, n, b, -1.0});
+                any = true;
+            }
+        if (!any) t->trials.push_back({c, n, n - 1, -1.0});
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gb_solve_tuner *gb_solve_tuner_create(int n_lo, int n_hi, int classes)
+{
+    if (n_lo < 2 || n_hi < n_lo || classes < 1 || classes > 64) return NULL;
+    gb_solve_tuner *t = new gb_solve_tuner;
+    t->n_lo = n_lo;
+    t->n_hi = n_hi;
+    t->classes = classes;
+    t->next = 0;
+    t->pending = -1;
+    tuner_trials(t);
+    return t;
+}
+
+void gb_solve_tuner_destroy(gb_solve_tuner *t) { delete t; }
+
+int gb_solve_tuner_step(gb_solve_tuner *t, int *n, int *nbw)
+{
+    if (!t) return -1;
+    if (!n || !nbw) return -2;
+    if (t->pending >= 0) return -1;
+    if (t->next >= (int)t->trials.size()) return 0;
+    *n = t->trials[t->next].n;
+    *nbw = t->trials[t->next].nbw;
+    t->pending = t->next++;
+    return 1;
+}
+
+int gb_solve_tuner_report(gb_solve_tuner *t, double seconds)
+{
+    if (!t || t->pending < 0) return -1;
+    if (!(seconds >= 0.0)) return -2;
+    t->trials[t->pending].secs = seconds;
+    t->pending = -1;
+    return 0;
+}
+
+int gb_solve_tuner_nbw(const gb_solve_tuner *t, int n)
+{
+    if (n < 2) return -1;
+    const int c = t ? tuner_class(t, n) : -1;
+    int best = -1;
+    double bs = 0.0;
+    if (c >= 0)
+        for (const auto &tr : t->trials)
+            if (tr.cls == c && tr.secs >= 0.0 && (best < 0 || tr.secs < bs)) {
+                best = tr.nbw;
+                bs = tr.secs;
+            }
+    if (best < 0) return gb_solve_default_nbw(n);
+    return best < n ? best : n - 1;
+}
+
+int gb_solve_tuner_save(const gb_solve_tuner *t, const char *path)
+{
+    if (!t) return -1;
+    if (!path) return -2;
+    FILE *f = fopen(path, "w");
+    if (!f) return GB_ERR_UNSUPPORTED;
+    const int next = t->pending >= 0 ? t->pending : t->next;
+    fprintf(f, "gb_solve_tuner 1\nn_lo %d\nn_hi %d\nclasses %d\nnext %d\ntrials %zu\n", t->n_lo, t->n_hi, t->classes,
+            next, t->trials.size());
+    for (const auto &tr : t->trials) fprintf(f, "t %d %d %d %.17g\n", tr.cls, tr.n, tr.nbw, tr.secs);
+    return fclose(f) == 0 ? GB_OK : GB_ERR_UNSUPPORTED;
+}
+
+gb_solve_tuner *gb_solve_tuner_load(const char *path)
+{
+    if (!path) return NULL;
+    FILE *f = fopen(path, "r");
+    if (!f) return NULL;
+    int ver = 0, lo = 0, hi = 0, classes = 0, next = 0;
+    size_t nt = 0;
+    gb_solve_tuner *t = NULL;
+    if (fscanf(f, "gb_solve_tuner %d n_lo %d n_hi %d classes %d next %d trials %zu", &ver, &lo, &hi, &classes, &next,
+               &nt) == 6 &&
+        ver == 1 && (t = gb_solve_tuner_create(lo, hi, classes)) != NULL) {
+        bool ok = nt == t->trials.size() && next >= 0 && next <= (int)nt;
+        for (size_t i = 0; ok && i < nt; i++) {
+            int c, n, b;
+            double s;
+            ok = fscanf(f, " t %d %d %d %lg", &c, &n, &b, &s) == 4 && c == t->trials[i].cls && n == t->trials[i].n &&
+                 b == t->trials[i].nbw;
+            if (ok) t->trials[i].secs = s;
+        }
+        if (ok) {
+            t->next = next;
+        } else {
             delete t;
             t = NULL;
         }

@@ -295,8 +295,12 @@ cudaError_t panel_qr(int m, int nb, double *P, long long lda, double *tau, doubl
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_qr_fused, kChunk, 0)) != cudaSuccess)
         return e;
     // a quarter of the co-resident capacity at most, so that concurrent
-    // solves on other streams keep room beside it
-    if (coop && (long long)nch * 4 <= (long long)per_sm * sms) {
+    // solves on other streams keep room beside it; never while the stream is
+    // being captured into a graph, whose kernel nodes carry no co-residency
+    // guarantee for the grid-wide barriers
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return e;
+    if (coop && cap == cudaStreamCaptureStatusNone && (long long)nch * 4 <= (long long)per_sm * sms) {
         void *args[] = {&m, &nb, &P, &lda, &tau, &norm_a, &norm_b, &dots, (void *)&nch};
         return cudaLaunchCooperativeKernel((const void *)panel_qr_fused, dim3(nch), dim3(kChunk), args, 0, st);
     }

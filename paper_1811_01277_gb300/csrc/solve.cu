@@ -16,7 +16,7 @@
 // The real solve's large products (SYMM, SYR2K, the band->full GEMMs, the
 // Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by exact digit
 // slicing (dgemm_sliced.cuh), the small ones in the DFMA kernels
-// (dgemm_dfma.cuh); the complex solve's products in cuBLAS.
+// (dgemm_dfma.cuh, and the complex DFMA kernel for the complex solve).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -303,8 +303,6 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     do {                                                                   \
         if (sev && cudaEventRecord(sev[i], st) != cudaSuccess) return GB_ERR_CUDA; \
     } while (0)
-    // the real path's products run in this library's DFMA kernels; the
-    // cuBLAS emulation flag only concerns the complex path
     const long long ldw = n;
 
     // ---- full -> band, with look-ahead: panel p+1 is factored on the helper
@@ -632,29 +630,35 @@ int gb_solve_default_nbw(int n)
     return b < n ? b : n - 1;
 }
 
-size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev, int nslots)
+size_t gb_solve_batched_workspace_bytes_nbw(int count, const int *n, const int *nev, const int *nbw, int nslots)
 {
     if (count < 1 || !n || !nev || nslots < 1) return 0;
     size_t slot = 0;
     for (int i = 0; i < count; i++) {
-        const size_t b = gb_solve_workspace_bytes(n[i], nev[i], gb_solve_default_nbw(n[i]));
+        const size_t b = gb_solve_workspace_bytes(n[i], nev[i], nbw ? nbw[i] : gb_solve_default_nbw(n[i]));
         if (b == 0) return 0;
         if (b > slot) slot = b;
     }
     return a256(slot) * (size_t)nslots;
 }
 
-int gb_solve_batched_d(int count, const int *n, const int *nev, const double *const *A, const int *lda,
-                       double *const *ev, double *const *Z, const int *ldz, void *workspace, size_t ws_bytes,
-                       int nslots, void *const *streams, void *const *ev_start, void *const *ev_end)
+size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev, int nslots)
+{
+    return gb_solve_batched_workspace_bytes_nbw(count, n, nev, nullptr, nslots);
+}
+
+int gb_solve_batched_nbw_d(int count, const int *n, const int *nev, const int *nbw, const double *const *A,
+                           const int *lda, double *const *ev, double *const *Z, const int *ldz, void *workspace,
+                           size_t ws_bytes, int nslots, void *const *streams, void *const *ev_start,
+                           void *const *ev_end)
 {
     if (count < 1) return -1;
     if (!n || !nev || !A || !lda || !ev || !Z || !ldz) return -2;
-    if (nslots < 1 || !streams) return -11;
-    const size_t need = gb_solve_batched_workspace_bytes(count, n, nev, nslots);
+    if (nslots < 1 || !streams) return -12;
+    const size_t need = gb_solve_batched_workspace_bytes_nbw(count, n, nev, nbw, nslots);
     if (need == 0) return -2;
-    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
-    if (ws_bytes < need) return -10;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -10;
+    if (ws_bytes < need) return -11;
     const size_t slot = need / (size_t)nslots;
     // One host thread per slot issues that slot's problems in order: a solve
     // is thousands of launches, and a single issuing thread would block on
@@ -674,7 +678,7 @@ int gb_solve_batched_d(int count, const int *n, const int *nev, const double *co
                 rcs[s] = GB_ERR_CUDA;
                 return;
             }
-            const int b = gb_solve_default_nbw(n[i]);
+            const int b = nbw ? nbw[i] : gb_solve_default_nbw(n[i]);
             const int rc = gb_solve_d(n[i], nev[i], b, A[i], lda[i], ev[i], Z[i], ldz[i], (char *)workspace + s * slot,
                                       slot, (void *)st, 0);
             if (rc != GB_OK) {
@@ -693,6 +697,149 @@ int gb_solve_batched_d(int count, const int *n, const int *nev, const double *co
     for (auto &t : pool) t.join();
     for (int rc : rcs)
         if (rc != GB_OK) return rc;
+    return GB_OK;
+}
+
+int gb_solve_batched_d(int count, const int *n, const int *nev, const double *const *A, const int *lda,
+                       double *const *ev, double *const *Z, const int *ldz, void *workspace, size_t ws_bytes,
+                       int nslots, void *const *streams, void *const *ev_start, void *const *ev_end)
+{
+    const int rc = gb_solve_batched_nbw_d(count, n, nev, nullptr, A, lda, ev, Z, ldz, workspace, ws_bytes, nslots,
+                                          streams, ev_start, ev_end);
+    // the argument numbers of this signature (no nbw array)
+    return rc < -2 ? rc + 1 : rc;
+}
+
+}  // extern "C"
+
+// The batched form as one CUDA graph: every solve of the batch issued once,
+// by stream capture, into nbranches parallel branches.
+struct gb_solve_graph {
+    int device = 0;
+    cudaStream_t origin = nullptr;
+    std::vector<cudaStream_t> branch;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    long long nodes = 0;
+};
+
+namespace {
+
+void destroy_graph_object(gb_solve_graph *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (cudaStream_t s : g->branch) gb_solve_release((void *)s, 0);
+    for (cudaStream_t s : g->branch)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : g->join)
+        if (e) cudaEventDestroy(e);
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->origin) cudaStreamDestroy(g->origin);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gb_solve_batched_graph_create(int count, const int *n, const int *nev, const int *nbw, const double *const *A,
+                                  const int *lda, double *const *ev, double *const *Z, const int *ldz,
+                                  void *workspace, size_t ws_bytes, int nbranches, void *const *ev_start,
+                                  void *const *ev_end, gb_solve_graph **graph)
+{
+    if (!graph) return -15;
+    *graph = nullptr;
+    if (count < 1) return -1;
+    if (!n || !nev || !A || !lda || !ev || !Z || !ldz) return -2;
+    if (nbranches < 1) return -12;
+    const size_t need = gb_solve_batched_workspace_bytes_nbw(count, n, nev, nbw, nbranches);
+    if (need == 0) return -2;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -10;
+    if (ws_bytes < need) return -11;
+    const size_t slot = need / (size_t)nbranches;
+    const int nb = nbranches < count ? nbranches : count;
+    gb_solve_graph *g = new gb_solve_graph;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        delete g;
+        return GB_ERR_CUDA;
+    }
+    int rc = GB_OK;
+    g->branch.assign(nb, nullptr);
+    g->join.assign(nb, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&g->origin, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int s = 0; ok && s < nb; s++)
+        ok = cudaStreamCreateWithFlags(&g->branch[s], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&g->join[s], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        destroy_graph_object(g);
+        return GB_ERR_CUDA;
+    }
+    // relaxed mode: the solves make non-stream calls (function attributes,
+    // occupancy queries) that the stricter capture modes would refuse
+    if (cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        destroy_graph_object(g);
+        return GB_ERR_CUDA;
+    }
+    ok = cudaEventRecord(g->fork, g->origin) == cudaSuccess;
+    for (int s = 0; ok && s < nb; s++) ok = cudaStreamWaitEvent(g->branch[s], g->fork, 0) == cudaSuccess;
+    if (!ok) rc = GB_ERR_CUDA;
+    for (int i = 0; rc == GB_OK && i < count; i++) {
+        const int s = i % nb;
+        const cudaStream_t st = g->branch[s];
+        // external event-record nodes: the caller's events are recorded
+        // when the graph runs (a plain record inside a capture would only
+        // order the graph's own nodes)
+        if (ev_start && cudaEventRecordWithFlags((cudaEvent_t)ev_start[i], st, cudaEventRecordExternal) != cudaSuccess) {
+            rc = GB_ERR_CUDA;
+            break;
+        }
+        const int b = nbw ? nbw[i] : gb_solve_default_nbw(n[i]);
+        rc = gb_solve_d(n[i], nev[i], b, A[i], lda[i], ev[i], Z[i], ldz[i], (char *)workspace + s * slot, slot,
+                        (void *)st, 0);
+        if (rc == GB_OK && ev_end &&
+            cudaEventRecordWithFlags((cudaEvent_t)ev_end[i], st, cudaEventRecordExternal) != cudaSuccess)
+            rc = GB_ERR_CUDA;
+    }
+    for (int s = 0; s < nb; s++) {  // join every branch, also after a failure, so the capture can end
+        if (cudaEventRecord(g->join[s], g->branch[s]) != cudaSuccess ||
+            cudaStreamWaitEvent(g->origin, g->join[s], 0) != cudaSuccess)
+            rc = rc == GB_OK ? GB_ERR_CUDA : rc;
+    }
+    cudaGraph_t cg = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(g->origin, &cg);
+    if (rc == GB_OK && (ee != cudaSuccess || !cg)) rc = GB_ERR_CUDA;
+    size_t nodes = 0;
+    if (rc == GB_OK && cudaGraphGetNodes(cg, nullptr, &nodes) != cudaSuccess) rc = GB_ERR_CUDA;
+    if (rc == GB_OK && cudaGraphInstantiate(&g->exec, cg, 0) != cudaSuccess) rc = GB_ERR_CUDA;
+    if (cg) cudaGraphDestroy(cg);
+    cudaGetLastError();  // a failed capture leaves its error behind; it is reported through rc
+    if (rc != GB_OK) {
+        destroy_graph_object(g);
+        return rc;
+    }
+    g->nodes = (long long)nodes;
+    *graph = g;
+    return GB_OK;
+}
+
+int gb_solve_batched_graph_launch(gb_solve_graph *graph, void *stream)
+{
+    if (!graph || !graph->exec) return -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    if (dev != graph->device) return GB_ERR_UNSUPPORTED;
+    return cudaGraphLaunch(graph->exec, (cudaStream_t)stream) == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+long long gb_solve_batched_graph_nodes(const gb_solve_graph *graph) { return graph ? graph->nodes : -1; }
+
+int gb_solve_batched_graph_destroy(gb_solve_graph *graph)
+{
+    if (!graph) return -1;
+    destroy_graph_object(graph);
     return GB_OK;
 }
 

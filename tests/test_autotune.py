@@ -85,3 +85,47 @@ def test_save_and_resume_mid_walk(tmp_path):
         f.write("garbage\n")
     assert not gb.gb_autotune_load(path)
     assert not gb.gb_autotune_load(str(tmp_path / "missing.txt"))
+
+
+def test_solve_tuner_classes_trials_and_choice(tmp_path):
+    """Band-width tuning of the two-stage solve: geometric size classes, one
+    trial per band width below the class's representative order, the
+    fastest band width per class, the default outside the tuned range or for
+    an unmeasured class, and save/resume with a trial pending."""
+    t = gb.gb_solve_tuner_create(128, 2048, 4)
+    assert t
+    trials = []
+    while True:
+        tr = gb.gb_solve_tuner_step(t)
+        if tr is None:
+            break
+        n, b = tr
+        trials.append(tr)
+        assert b < n and b in (16, 32, 64)
+        # fake cost: 32 wins below 400, 64 above
+        assert gb.gb_solve_tuner_report(t, {16: 3.0, 32: 1.0 if n < 400 else 2.0, 64: 2.0 if n < 400 else 1.0}[b]) == 0
+    reps = sorted({n for n, _ in trials})
+    assert len(reps) == 4 and reps[0] > 128 and reps[-1] < 2048        # geometric middles
+    assert all(sum(1 for n, _ in trials if n == r) == 3 for r in reps)  # 16, 32, 64 below each
+    assert gb.gb_solve_tuner_nbw(t, 130) == 32
+    assert gb.gb_solve_tuner_nbw(t, 2048) == 64
+    assert gb.gb_solve_tuner_nbw(t, 100) == gb.gb_solve_default_nbw(100)      # outside the range
+    assert gb.gb_solve_tuner_nbw(t, 5000) == gb.gb_solve_default_nbw(5000)
+    gb.gb_solve_tuner_destroy(t)
+    # an unmeasured class falls back to the default; tiny orders get n - 1
+    t = gb.gb_solve_tuner_create(2, 16, 1)
+    assert gb.gb_solve_tuner_step(t)[1] < 16
+    assert gb.gb_solve_tuner_nbw(t, 9) == gb.gb_solve_default_nbw(9)
+    # save with the trial pending, load: it is handed out again
+    path = tmp_path / "tuner.txt"
+    assert gb.gb_solve_tuner_save(t, path) == 0
+    gb.gb_solve_tuner_destroy(t)
+    t2 = gb.gb_solve_tuner_load(path)
+    assert t2
+    n, b = gb.gb_solve_tuner_step(t2)
+    assert gb.gb_solve_tuner_report(t2, 0.5) == 0
+    assert gb.gb_solve_tuner_step(t2) is None
+    assert gb.gb_solve_tuner_nbw(t2, 3) == min(b, 2)
+    gb.gb_solve_tuner_destroy(t2)
+    assert not gb.gb_solve_tuner_create(1, 10, 2) and not gb.gb_solve_tuner_create(10, 5, 2)
+    assert not gb.gb_solve_tuner_create(10, 20, 0)

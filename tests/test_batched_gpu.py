@@ -72,3 +72,72 @@ def test_batched_mixed_sizes(gb):
     simple = gaps > 1e-6 * np.linalg.norm(mats[i], 2)
     dots = np.abs(np.sum(Z1n * Zbn, axis=0))
     assert np.abs(dots[simple] - 1.0).max() <= 1e-8
+
+
+def test_batched_graph_replays_and_reads_the_matrices_at_launch(gb):
+    """The batch captured as one CUDA graph (per-problem band widths, three
+    branches): a launch solves every problem (eigenvalues against the oracle,
+    residual, orthogonality), a second launch gives bit-identical results,
+    and after the matrices are shifted in place by c I a third launch returns
+    eigenvalues shifted by c: the graph reads A at launch time.  The stream
+    form with the same band widths agrees within the tolerances."""
+    dev = torch.device("cuda")
+    g = np.random.default_rng(9)
+    sizes = [int(x) for x in g.integers(100, 520, 7)]
+    nevs = [n if i % 3 else n // 3 for i, n in enumerate(sizes)]
+    nbw = [[16, 32, 64][i % 3] for i in range(len(sizes))]
+    mats = [inputs.band_symmetric(n, n, seed=300 + i, dist="normal") for i, n in enumerate(sizes)]
+    A = [torch.from_numpy(np.ascontiguousarray(M.T)).to(dev) for M in mats]
+    ev = [torch.zeros(k, dtype=torch.float64, device=dev) for k in nevs]
+    Z = [torch.zeros((k, n), dtype=torch.float64, device=dev) for n, k in zip(sizes, nevs)]
+    es = [torch.cuda.Event(enable_timing=True) for _ in sizes]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in sizes]
+    wsb = gb.gb_solve_batched_workspace_bytes_nbw(sizes, nevs, nbw, 3)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    graph = gb.gb_solve_batched_graph_create(sizes, nevs, nbw, A, sizes, ev, Z, sizes, ws, wsb, 3, es, ee)
+    try:
+        assert gb.gb_solve_batched_graph_nodes(graph) > len(sizes)
+        st = torch.cuda.current_stream()
+        outs = []
+        for _ in range(2):
+            gb.gb_solve_batched_graph_launch(graph, st)
+            torch.cuda.synchronize()
+            outs.append(([e.cpu().numpy().copy() for e in ev], [z.cpu().numpy().copy() for z in Z]))
+        for i, (n, k, M) in enumerate(zip(sizes, nevs, mats)):
+            w, Zi = outs[0][0][i], outs[0][1][i].T
+            nrm = np.linalg.norm(M, 2)
+            d, e, _, _ = oracle.sytrd(M)
+            lam = np.sort(oracle.tridiag_ql(d, e)[0])
+            assert np.abs(w - lam[:k]).max() / nrm <= 1e-11
+            assert np.linalg.norm(M @ Zi - Zi * w) / np.linalg.norm(M) <= 50 * n * U
+            assert np.abs(Zi.T @ Zi - np.eye(k)).max() <= 50 * n * U
+            assert np.array_equal(outs[0][0][i], outs[1][0][i]) and np.array_equal(outs[0][1][i], outs[1][1][i])
+            assert es[i].elapsed_time(ee[i]) > 0
+        c = 0.75
+        for a in A:
+            a.diagonal().add_(c)
+        gb.gb_solve_batched_graph_launch(graph, st)
+        torch.cuda.synchronize()
+        for i, M in enumerate(mats):
+            w = ev[i].cpu().numpy()
+            assert np.abs(w - (outs[0][0][i] + c)).max() / (np.linalg.norm(M, 2) + c) <= 1e-11
+    finally:
+        assert gb.gb_solve_batched_graph_destroy(graph) == 0
+    # the stream form with the same band widths
+    for a in A:
+        a.diagonal().sub_(c)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    gb.gb_solve_batched_nbw_d(sizes, nevs, nbw, A, sizes, ev, Z, sizes, ws, wsb, streams)
+    torch.cuda.synchronize()
+    for i, M in enumerate(mats):
+        assert np.abs(ev[i].cpu().numpy() - outs[0][0][i]).max() / np.linalg.norm(M, 2) <= 1e-11
+
+
+def test_batched_graph_argument_errors(gb):
+    x = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(gb.GbError) as e:
+        gb.gb_solve_batched_graph_create([100], [10], [16], [x], [100], [x], [x], [100], None, 0, 1)
+    assert e.value.status == -10
+    assert gb.gb_solve_batched_graph_launch(None, None, check=False) == -1
+    assert gb.gb_solve_batched_graph_nodes(None) == -1
