@@ -240,8 +240,10 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
  *   full -> band (Householder panels; trailing updates as symmetric
  *   products on the lower triangle),
  *   band -> tridiagonal (gb_band_to_tridi_d's bulge chase),
- *   eigenpairs of the tridiagonal (multisection, inverse iteration, one
- *   Newton-Schulz orthogonalisation step),
+ *   eigenpairs of the tridiagonal: divide and conquer (gb_tridiag_dc_d)
+ *   when more than half of the eigenvectors are wanted (2 nev > n), else
+ *   multisection, inverse iteration and one Newton-Schulz orthogonalisation
+ *   step,
  *   tridiagonal -> band (gb_trans_ev_tridi_to_band_d, pipeline kernel),
  *   band -> full (block reflectors as matrix products).
  * All FP64 matrix products run in this library's DFMA-tiled kernels.
@@ -250,7 +252,8 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
  * triangles used); 5 lda >= n; 6 ev (nev, ascending); 7 Z (n x nev,
  * column-major); 8 ldz >= n; 9 workspace (256-byte aligned); 10 ws_bytes >=
  * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0 or an OR
- * of GB_SOLVE_RECORD_STAGES, GB_SOLVE_DFMA_PRODUCTS and
+ * of GB_SOLVE_RECORD_STAGES, GB_SOLVE_DFMA_PRODUCTS, GB_SOLVE_TRIDIAG_BISECT
+ * (bisection and inverse iteration even when 2 nev > n) and
  * GB_SOLVE_FP64_EMULATED_GEMM (accepted and ignored: no product of either
  * solver goes through a vendor BLAS).  By
  * default the large products (the full->band SYMM and SYR2K, the band->full
@@ -261,6 +264,7 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
 #define GB_SOLVE_FP64_EMULATED_GEMM 1
 #define GB_SOLVE_RECORD_STAGES 2 /* record CUDA events at the stage boundaries */
 #define GB_SOLVE_DFMA_PRODUCTS 4 /* products on the FP64 FMA pipe, not sliced */
+#define GB_SOLVE_TRIDIAG_BISECT 8 /* tridiagonal step by bisection + inverse iteration */
 size_t gb_solve_workspace_bytes(int n, int nev, int nbw);
 int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
                void *workspace, size_t ws_bytes, void *stream, int flags);
@@ -313,6 +317,23 @@ int elpa_b200_solve(int n, int nev, const double *A, int lda, double *ev, double
  * 12 streams (nslots cudaStream_t); 13-14 event arrays or NULL. */
 int gb_solve_default_nbw(int n);
 size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev, int nslots);
+
+/* All eigenpairs of the real symmetric tridiagonal matrix with diagonal d[0..n)
+ * and off-diagonal e[0..n-1) by divide and conquer (Cuppen's method with
+ * deflation; the secular equation solved per root with the two-pole model of
+ * Bunch, Nielsen and Sorensen; the rank-one vector recomputed from the roots
+ * as Gu and Eisenstat do, so the eigenvectors are orthogonal to working
+ * accuracy; the merged eigenvectors as products, sliced onto the tensor
+ * cores when large).  This is the tridiagonal step of the two-stage solver
+ * (Sec. 2) when all eigenvectors are wanted.
+ * Arguments (device pointers): 1 n >= 1; 2 d (n); 3 e (n-1; may be NULL for
+ * n = 1); 4 lam (n, out, ascending); 5 Q (n x n, column-major, ldq; out:
+ * column j is the eigenvector of lam[j]); 6 ldq >= n; 7 workspace (256-byte
+ * aligned); 8 ws_bytes >= gb_tridiag_dc_workspace_bytes(n) (about 3 n^2
+ * doubles).  Asynchronous on `stream`; d and e are not modified. */
+size_t gb_tridiag_dc_workspace_bytes(int n);
+int gb_tridiag_dc_d(int n, const double *d, const double *e, double *lam, double *Q, int ldq,
+                    void *workspace, size_t ws_bytes, void *stream);
 int gb_solve_batched_d(int count, const int *n, const int *nev, const double *const *A, const int *lda,
                        double *const *ev, double *const *Z, const int *ldz, void *workspace,
                        size_t ws_bytes, int nslots, void *const *streams, void *const *ev_start,

@@ -39,6 +39,7 @@ EXPORTS = (
     "gb_solve_batched_graph_create", "gb_solve_batched_graph_launch", "gb_solve_batched_graph_nodes",
     "gb_solve_batched_graph_destroy", "gb_solve_tuner_create", "gb_solve_tuner_destroy", "gb_solve_tuner_step",
     "gb_solve_tuner_report", "gb_solve_tuner_nbw", "gb_solve_tuner_save", "gb_solve_tuner_load",
+    "gb_tridiag_dc_workspace_bytes", "gb_tridiag_dc_d",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
@@ -49,7 +50,10 @@ EXPORTS = (
 )
 GB_SOLVE_RECORD_STAGES = 2
 GB_SOLVE_DFMA_PRODUCTS = 4
-SOLVE_STAGES = ("full_to_band", "band_to_tridi", "bisection", "inverse_iteration", "orthogonalise",
+GB_SOLVE_TRIDIAG_BISECT = 8
+# stage 2 is the whole tridiagonal step when it runs as divide and conquer
+# (stages 3 and 4 are then empty)
+SOLVE_STAGES = ("full_to_band", "band_to_tridi", "tridiag_bisection_or_dc", "inverse_iteration", "orthogonalise",
                 "trans_ev_tridi_to_band", "band_to_full")
 GB_AUTOTUNE_FAST = 1
 GB_AUTOTUNE_MEDIUM = 2
@@ -149,6 +153,8 @@ def load(path=None):
     L.gb_solve_tuner_nbw.argtypes = [p, i]; L.gb_solve_tuner_nbw.restype = i
     L.gb_solve_tuner_save.argtypes = [p, ctypes.c_char_p]; L.gb_solve_tuner_save.restype = i
     L.gb_solve_tuner_load.argtypes = [ctypes.c_char_p]; L.gb_solve_tuner_load.restype = p
+    L.gb_tridiag_dc_workspace_bytes.argtypes = [i]; L.gb_tridiag_dc_workspace_bytes.restype = sz
+    L.gb_tridiag_dc_d.argtypes = [i, p, p, p, p, i, p, sz, p]; L.gb_tridiag_dc_d.restype = i
     ch, dd = ctypes.c_char, ctypes.c_double
     L.gb_dgemm_workspace_bytes.argtypes = [i, i]; L.gb_dgemm_workspace_bytes.restype = sz
     L.gb_dgemm.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dgemm.restype = i
@@ -523,6 +529,17 @@ def gb_solve_tuner_save(t, path):
 
 def gb_solve_tuner_load(path):
     return load().gb_solve_tuner_load(str(path).encode())
+
+
+def gb_tridiag_dc_workspace_bytes(n):
+    return load().gb_tridiag_dc_workspace_bytes(n)
+
+
+def gb_tridiag_dc_d(n, d, e, lam, Q, ldq, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_tridiag_dc_d(n, _dp(d), _dp(e), _dp(lam), _dp(Q), ldq, _dp(workspace), ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_tridiag_dc_d")
+    return rc
 
 
 def gb_dgemm_workspace_bytes(m, n):

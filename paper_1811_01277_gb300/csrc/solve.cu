@@ -36,6 +36,10 @@
 
 namespace gb {
 
+size_t tridiag_dc_workspace_bytes(int n);
+cudaError_t tridiag_dc_d(int n, int nev, const double *d, const double *e, double *lam, double *Z, long long ldz,
+                         void *ws, cudaStream_t st);
+
 int panel_chunks(int m);
 cudaError_t panel_qr(int m, int nb, double *P, long long lda, double *tau, double *part, cudaStream_t st);
 cudaError_t panel_y_and_t_prep(int m, int nb, const double *P, long long lda, double *Y, long long ldy,
@@ -120,9 +124,14 @@ cudaEvent_t *stage_events(cudaStream_t st)
 struct SolveWs {
     double *Aw, *tauP, *Tall, *Y, *Y2, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2, *gw,
         *gw2;
-    void *chase, *eig, *tev, *sl;
+    void *chase, *eig, *tev, *sl, *dc;
     size_t chase_bytes, tev_bytes, gw_elems, gw2_elems, sl_bytes, total;
 };
+
+// More than half of the eigenvectors: divide and conquer (all of them, by
+// products on the tensor cores) instead of bisection + inverse iteration
+// (O(n nev) per pass, plus the orthogonalisation step).
+bool use_dc(int n, int nev) { return 2LL * nev > n; }
 
 // Products of at least this many flops go to the sliced tensor-core kernels
 // (below it the extra launches of slicing cost more than they save).
@@ -189,6 +198,7 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
     w.sl_bytes = sliced_region_bytes(n, nev, b);
     w.sl = w.sl_bytes ? take(w.sl_bytes) : nullptr;
+    w.dc = use_dc(n, nev) ? take(gb::tridiag_dc_workspace_bytes(n)) : nullptr;
     w.total = off;
     return w;
 }
@@ -196,7 +206,7 @@ SolveWs carve(int n, int nev, int b, char *base)
 // Complex workspace: complex pieces hold 2 doubles per entry.
 struct SolveWsZ {
     double *Aw, *tauP, *Tall, *Y, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Zre, *Gns, *Zns, *S, *S2, *gw;
-    void *chase, *eig, *sl, *tev;
+    void *chase, *eig, *sl, *tev, *dc;
     size_t chase_bytes, gw_elems, sl_bytes, tev_bytes, total;
 };
 
@@ -255,6 +265,7 @@ SolveWsZ carve_z(int n, int nev, int b, char *base)
     w.sl = w.sl_bytes ? take(w.sl_bytes) : nullptr;
     w.tev_bytes = gb_trans_ev_workspace_bytes(n, b, nev, 1, nullptr);
     w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
+    w.dc = use_dc(n, nev) ? take(gb::tridiag_dc_workspace_bytes(n)) : nullptr;
     w.total = off;
     return w;
 }
@@ -289,7 +300,9 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     const int b = nbw;
     SolveWs w = carve(n, nev, b, (char *)workspace);
     if (ws_bytes < w.total) return -10;
-    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS)) return -12;
+    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS |
+                  GB_SOLVE_TRIDIAG_BISECT))
+        return -12;
     // large products on the tensor cores unless the caller asks for DFMA
     const bool slice_ok = w.sl && !(flags & GB_SOLVE_DFMA_PRODUCTS);
     auto use_sliced = [&](double m_, double n_, double k_) { return slice_ok && sliced_pays(m_, n_, k_); };
@@ -390,22 +403,29 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     GB_CU(gb::band_to_tridi_d(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, w.chase_bytes,
                               10LL * 1000 * 1000 * 1000, st));
 
-    // ---- eigenpairs of T, then one Newton-Schulz orthogonalisation step into Z
+    // ---- eigenpairs of T: divide and conquer straight into Z, or bisection,
+    // inverse iteration and one Newton-Schulz orthogonalisation step
     GB_STAGE(2);
-    GB_CU(gb::tridiag_bisect_d(n, nev, w.d, w.e, ev, w.eig, st));
-    GB_STAGE(3);
-    GB_CU(gb::tridiag_invit_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
-    GB_STAGE(4);
-    // G = Z^T Z (lower triangle), M = (3I - G)/2, Z <- Z M
-    if (use_sliced(nev, nev, n))
-        GB_CU(gb::sliced_dsyrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, w.sl, st));
-    else
-        GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, st));
-    GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    if (use_sliced(n, nev, nev))
-        GB_CU(gb::sliced_dsymm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.sl, st));
-    else
-        GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.gw, w.gw_elems, st));
+    if (w.dc && !(flags & GB_SOLVE_TRIDIAG_BISECT)) {
+        GB_CU(gb::tridiag_dc_d(n, nev, w.d, w.e, ev, Z, ldz, w.dc, st));
+        GB_STAGE(3);
+        GB_STAGE(4);
+    } else {
+        GB_CU(gb::tridiag_bisect_d(n, nev, w.d, w.e, ev, w.eig, st));
+        GB_STAGE(3);
+        GB_CU(gb::tridiag_invit_d(n, nev, w.d, w.e, ev, w.Ztri, n, w.eig, st));
+        GB_STAGE(4);
+        // G = Z^T Z (lower triangle), M = (3I - G)/2, Z <- Z M
+        if (use_sliced(nev, nev, n))
+            GB_CU(gb::sliced_dsyrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, w.sl, st));
+        else
+            GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Ztri, n, 0.0, w.Gns, nev, st));
+        GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
+        if (use_sliced(n, nev, nev))
+            GB_CU(gb::sliced_dsymm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.sl, st));
+        else
+            GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Ztri, n, 0.0, Z, ldz, w.gw, w.gw_elems, st));
+    }
 
     // ---- tridiagonal -> band (the hot path)
     GB_STAGE(5);
@@ -457,7 +477,9 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     const int b = nbw;
     SolveWsZ w = carve_z(n, nev, b, (char *)workspace);
     if (ws_bytes < w.total) return -10;
-    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS)) return -12;
+    if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS |
+                  GB_SOLVE_TRIDIAG_BISECT))
+        return -12;
     // large products sliced on the tensor cores unless the caller asks for
     // the FP64 path; every other product (the b x b panel products, the
     // small-k updates, and the large ones on the FP64 path) in this
@@ -512,17 +534,22 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     // ---- band -> tridiagonal (complex reflectors, real T)
     GB_CU(gb::band_to_tridi_z(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, 10LL * 1000 * 1000 * 1000, st));
 
-    // ---- real tridiagonal eigenpairs, Newton-Schulz, promote to complex Z
-    GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Zre, n, w.eig, st));
-    if (zslice_ok && sliced_pays(nev, nev, n))
-        GB_CU(gb::sliced_dsyrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, w.sl, st));
-    else
-        GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, st));
-    GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
-    if (zslice_ok && sliced_pays(n, nev, nev))
-        GB_CU(gb::sliced_dsymm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.sl, st));
-    else
-        GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.gw, w.gw_elems, st));
+    // ---- real tridiagonal eigenpairs (divide and conquer, or bisection,
+    // inverse iteration and Newton-Schulz), promoted to complex Z
+    if (w.dc && !(flags & GB_SOLVE_TRIDIAG_BISECT)) {
+        GB_CU(gb::tridiag_dc_d(n, nev, w.d, w.e, ev, w.Zns, n, w.dc, st));
+    } else {
+        GB_CU(gb::tridiag_eig_d(n, nev, w.d, w.e, ev, w.Zre, n, w.eig, st));
+        if (zslice_ok && sliced_pays(nev, nev, n))
+            GB_CU(gb::sliced_dsyrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, w.sl, st));
+        else
+            GB_CU(gb::dfma_syrk_lower_t(nev, n, 1.0, w.Zre, n, 0.0, w.Gns, nev, st));
+        GB_CU(gb::newton_schulz_matrix(nev, w.Gns, nev, st));
+        if (zslice_ok && sliced_pays(n, nev, nev))
+            GB_CU(gb::sliced_dsymm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.sl, st));
+        else
+            GB_CU(gb::dfma_symm('R', n, nev, 1.0, w.Gns, nev, w.Zre, n, 0.0, w.Zns, n, w.gw, w.gw_elems, st));
+    }
     GB_CU(gb::promote_real(n, nev, w.Zns, n, Z, ldz, st));
 
     // ---- tridiagonal -> band (complex back-transformation)
