@@ -986,6 +986,78 @@ def run_stage_batched(args):
     return 0
 
 
+def run_stage_refine(args):
+    """The mixed-precision configuration's refinement step measured against
+    the direct FP64 solve: all eigenpairs of A = Q L Q^T (L uniform in
+    [-1, 1] with runs of eigenvalues 1e-6 apart) by gb_solve_d (divide and
+    conquer), then the same eigenvectors rounded to FP32 -- the accuracy an
+    FP32 solve would deliver -- refined by gb_refine_syev_d (Ogita-Aishima)
+    step by step, with orthogonality and residual after each step.  An FP32
+    solve plus k steps can only beat the FP64 solve if the FP32 solve takes
+    less than the FP64 solve minus k steps."""
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    from paper_1811_01277_gb300 import inputs
+    gbuild.build()
+    gb.load()
+    n, nbw = args.refine_n, 64
+    dev = torch.device("cuda", 0)
+    lam0 = torch.from_numpy(inputs.gapped_uniform_spectrum(n, seed=n)).to(dev)
+    A = prescribed_symmetric_gpu(lam0, 256, seed=n + 1, dev=dev)
+    st = torch.cuda.current_stream(dev)
+    ev = torch.zeros(n, dtype=torch.float64, device=dev)
+    Z = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    wsb = gb.gb_solve_workspace_bytes(n, n, nbw)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    gb.gb_solve_d(n, n, nbw, A, n, ev, Z, n, ws, wsb, st, 0)      # warm-up
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    gb.gb_solve_d(n, n, nbw, A, n, ev, Z, n, ws, wsb, st, 0)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    solve_s = e0.elapsed_time(e1) / 1e3
+    del ws
+    torch.cuda.empty_cache()
+    eye = torch.eye(n, dtype=torch.float64, device=dev)
+    nrmA = float(torch.linalg.norm(A))
+
+    def accuracy(Xc, lam):       # Xc: column-major storage (rows of the tensor are columns of X)
+        X = Xc.T
+        return {"orth_max": float((X.T @ X - eye).abs().max()),
+                "residual_rel_fro": float(torch.linalg.norm(A @ X - X * lam[None, :]) / nrmA),
+                "max_dlambda_over_norm": float((torch.sort(lam).values - lam0).abs().max() / lam0.abs().max())}
+
+    direct = accuracy(Z, ev)
+    X = Z.float().double()        # FP32-accurate eigenvectors
+    lam = ev.clone()
+    rws_b = gb.gb_refine_syev_workspace_bytes(n)
+    rws = torch.empty(rws_b, dtype=torch.uint8, device=dev)
+    steps = [{"step": 0, "seconds": 0.0, **accuracy(X, lam)}]
+    for k in range(1, args.steps + 1):
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(st)
+        gb.gb_refine_syev_d(n, A, n, lam, X, n, rws, rws_b, st)
+        r1.record(st)
+        torch.cuda.synchronize(dev)
+        steps.append({"step": k, "seconds": r0.elapsed_time(r1) / 1e3, **accuracy(X, lam)})
+    clocks = sampler.stop()
+    step_s = min(x["seconds"] for x in steps[1:]) if len(steps) > 1 else None
+    flops = 7.0 * n ** 3
+    print(json.dumps({
+        "stage": "refine", "metric": f"Ogita-Aishima refinement step vs the direct FP64 solve, n={n}, all eigenpairs",
+        "n": n, "direct_fp64_solve_s": solve_s, "direct_accuracy": direct, "refine_steps": steps,
+        "refine_step_s": step_s,
+        "refine_step_tflops_fp64_equivalent": flops / step_s / 1e12 if step_s else None,
+        "two_steps_s": 2 * step_s if step_s else None,
+        "fp32_solve_budget_for_break_even_s": solve_s - 2 * step_s if step_s else None,
+        "data": "synthetic: A = Q diag(uniform in [-1,1], runs of 8 spaced 1e-6) Q^T; FP32 start = FP64 eigenvectors rounded",
+        "dtype": "f64", "clocks": clocks}))
+    return 0
+
+
 def run_stage_trans_ev_z(args):
     """The complex128 back-transformation alone: synthetic unitary reflectors
     (the bulge chase's layout) applied to Gaussian Z, timed with CUDA events
@@ -1152,8 +1224,10 @@ def main():
                          "instead of one independent problem per rank")
     ap.add_argument("--no-extra", action="store_true",
                     help="default stage: skip the solve and batched measurements that complete the metric")
-    ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm"],
+    ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm",
+                                        "refine"],
                     default="trans_ev")
+    ap.add_argument("--refine-n", type=int, default=8192, help="refine stage: n (all eigenpairs)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-lo", type=int, default=128)
     ap.add_argument("--batch-hi", type=int, default=2048)
@@ -1188,6 +1262,8 @@ def main():
         return run_stage_gemm(args)
     if args.stage == "batched":
         return run_stage_batched(args)
+    if args.stage == "refine":
+        return run_stage_refine(args)
     if args.stage == "trans_ev_z":
         return run_stage_trans_ev_z(args)
     if args.stage == "serve":

@@ -331,6 +331,26 @@ size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev,
  * column j is the eigenvector of lam[j]); 6 ldq >= n; 7 workspace (256-byte
  * aligned); 8 ws_bytes >= gb_tridiag_dc_workspace_bytes(n) (about 3 n^2
  * doubles).  Asynchronous on `stream`; d and e are not modified. */
+/* One step of Ogita and Aishima's iterative refinement of a full symmetric
+ * eigendecomposition (the FP64 refinement that the mixed-precision
+ * configuration pairs with a low-precision solve): with R = I - X^T X,
+ * S = X^T A X, lambda_i = s_ii / (1 - r_ii), delta = 2 (||S - diag(lambda)||
+ * + ||A|| ||R||), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) where
+ * |lambda_i - lambda_j| > delta and r_ij / 2 elsewhere, X <- X + X E.  The
+ * error of X falls quadratically for eigenvalues separated by more than
+ * delta; within a cluster the step refines the cluster's invariant subspace.
+ * The products are sliced on the bf16 tensor cores (FP64-accurate); ||A||_2
+ * is taken as max |lambda_i|, the other norms bounded by Frobenius norms.
+ * Arguments (device pointers): 1 n >= 1; 2 A (n x n symmetric, lower
+ * triangle read, lda); 3 lda >= n; 4 lam (n, out: the Rayleigh quotients
+ * lambda_i of the input X); 5 X (n x n, ldx; in: approximate eigenvectors in
+ * the columns, out: refined); 6 ldx >= n; 7 workspace (256-byte aligned);
+ * 8 ws_bytes >= gb_refine_syev_workspace_bytes(n) (about 4 n^2 doubles plus
+ * the sliced products' planes).  Asynchronous on `stream`. */
+size_t gb_refine_syev_workspace_bytes(int n);
+int gb_refine_syev_d(int n, const double *A, int lda, double *lam, double *X, int ldx, void *workspace,
+                     size_t ws_bytes, void *stream);
+
 size_t gb_tridiag_dc_workspace_bytes(int n);
 int gb_tridiag_dc_d(int n, const double *d, const double *e, double *lam, double *Q, int ldq,
                     void *workspace, size_t ws_bytes, void *stream);

@@ -39,7 +39,7 @@ EXPORTS = (
     "gb_solve_batched_graph_create", "gb_solve_batched_graph_launch", "gb_solve_batched_graph_nodes",
     "gb_solve_batched_graph_destroy", "gb_solve_tuner_create", "gb_solve_tuner_destroy", "gb_solve_tuner_step",
     "gb_solve_tuner_report", "gb_solve_tuner_nbw", "gb_solve_tuner_save", "gb_solve_tuner_load",
-    "gb_tridiag_dc_workspace_bytes", "gb_tridiag_dc_d",
+    "gb_tridiag_dc_workspace_bytes", "gb_tridiag_dc_d", "gb_refine_syev_workspace_bytes", "gb_refine_syev_d",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
@@ -155,6 +155,8 @@ def load(path=None):
     L.gb_solve_tuner_load.argtypes = [ctypes.c_char_p]; L.gb_solve_tuner_load.restype = p
     L.gb_tridiag_dc_workspace_bytes.argtypes = [i]; L.gb_tridiag_dc_workspace_bytes.restype = sz
     L.gb_tridiag_dc_d.argtypes = [i, p, p, p, p, i, p, sz, p]; L.gb_tridiag_dc_d.restype = i
+    L.gb_refine_syev_workspace_bytes.argtypes = [i]; L.gb_refine_syev_workspace_bytes.restype = sz
+    L.gb_refine_syev_d.argtypes = [i, p, i, p, p, i, p, sz, p]; L.gb_refine_syev_d.restype = i
     ch, dd = ctypes.c_char, ctypes.c_double
     L.gb_dgemm_workspace_bytes.argtypes = [i, i]; L.gb_dgemm_workspace_bytes.restype = sz
     L.gb_dgemm.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dgemm.restype = i
@@ -529,6 +531,17 @@ def gb_solve_tuner_save(t, path):
 
 def gb_solve_tuner_load(path):
     return load().gb_solve_tuner_load(str(path).encode())
+
+
+def gb_refine_syev_workspace_bytes(n):
+    return load().gb_refine_syev_workspace_bytes(n)
+
+
+def gb_refine_syev_d(n, A, lda, lam, X, ldx, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_refine_syev_d(n, _dp(A), lda, _dp(lam), _dp(X), ldx, _dp(workspace), ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_refine_syev_d")
+    return rc
 
 
 def gb_tridiag_dc_workspace_bytes(n):
