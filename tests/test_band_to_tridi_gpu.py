@@ -171,8 +171,11 @@ def test_two_stage_tail_complex_on_gpu(gb):
     dev = torch.device("cuda")
     Zt = torch.from_numpy(np.ascontiguousarray(V.T.astype(np.complex128))).to(dev)
     st = torch.cuda.current_stream()
+    wsb = gb.gb_trans_ev_workspace_bytes(n, b, n, 1, None)      # the tensor-core path needs one at n >= 512
+    ws = torch.zeros(max(wsb, 256), dtype=torch.uint8, device=dev)
     gb.gb_trans_ev_tridi_to_band_z(n, b, n, torch.from_numpy(hv).to(dev), torch.from_numpy(ht).to(dev), Zt, n,
-                                   None, 0, st)
+                                   ws, wsb, st)
+    assert gb.gb_trans_ev_query(ws, wsb, st) == 0
     torch.cuda.synchronize()
     Z = Zt.cpu().numpy().T
     assert np.linalg.norm(B @ Z - Z * w) / np.linalg.norm(B) <= 50 * n * U
