@@ -506,7 +506,7 @@ def run_ours(args, wl):
             line["batched"] = {k_: bt[k_] for k_ in ("solves_per_s", "p50_ms", "p99_ms", "seconds_per_batch",
                                                      "streams", "plain_solve_one_at_a_time",
                                                      "accuracy_worst_over_50nu", "data", "clocks", "metric",
-                                                     "graph", "graph_tuned_nbw")}
+                                                     "graph", "graph_tuned_nbw", "staged", "staged_tuned_nbw")}
             line["batched"].update(steps=1, warmup=1, form="streams (gb_solve_batched_d); the graph forms beside it")
         print(json.dumps(line))
     return 0
@@ -926,6 +926,30 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
                 "graph_nodes": int(nodes), "branches": len(streams), "capture_and_instantiate_s": create_s,
                 "clocks": gclk}
 
+    # stage by stage: every front on the streams, all chases in one launch,
+    # every back on the streams (the tuned band widths, once known, below)
+    def staged_form(nbw):
+        swsb = gb.gb_solve_batched_staged_workspace_bytes(sizes, sizes, nbw, len(streams))
+        sws = torch.empty(swsb, dtype=torch.uint8, device=dev)
+        for _ in range(warmup):
+            gb.gb_solve_batched_staged_d(sizes, sizes, nbw, A, sizes, ev, Z, sizes, sws, swsb, streams)
+        torch.cuda.synchronize(dev)
+        smp = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            gb.gb_solve_batched_staged_d(sizes, sizes, nbw, A, sizes, ev, Z, sizes, sws, swsb, streams, es, ee)
+        torch.cuda.synchronize(dev)
+        sel = time.perf_counter() - t0
+        sclk = smp.stop()
+        status = gb.gb_solve_batched_staged_query(sws, sizes, sizes, nbw, streams)
+        sper = np.array([a.elapsed_time(b) for a, b in zip(es, ee)])
+        del sws
+        torch.cuda.empty_cache()
+        return {"value": steps * len(sizes) / sel, "unit": "solves/s", "seconds_per_batch": sel / steps,
+                "p50_ms": float(np.percentile(sper, 50)), "p99_ms": float(np.percentile(sper, 99)),
+                "workspace_gb": swsb / 1e9, "status": status, "clocks": sclk}
+
+    staged_default = staged_form(None)
     graph_default = graph_form(None)
     # a trial is a mini-batch: one problem of the class's order per stream,
     # all solved at once with the trial's band width (the batch's throughput,
@@ -959,6 +983,7 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
     tuned_nbw = [gb.gb_solve_tuner_nbw(tuner, n_) for n_ in sizes]
     gb.gb_solve_tuner_destroy(tuner)
     graph_tuned = graph_form(tuned_nbw)
+    staged_tuned = staged_form(tuned_nbw)
     graph_tuned["tuner"] = {"classes": 4, "trials": trials,
                             "chosen": sorted({(n_, b_) for n_, b_ in zip(sizes, tuned_nbw)})[::max(1, count // 16)]}
     out = {
@@ -971,7 +996,8 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
                                       "sample": f"every {plain_every}th problem ({len(sample)})",
                                       "speedup_of_batched": rate / plain_rate},
         "data": "synthetic N(0,1) symmetrised", "accuracy_worst_over_50nu": worst, "clocks": clocks,
-        "graph": graph_default, "graph_tuned_nbw": graph_tuned}
+        "graph": graph_default, "graph_tuned_nbw": graph_tuned, "staged": staged_default,
+        "staged_tuned_nbw": staged_tuned}
     del A, Z, ev, ws, pws
     torch.cuda.empty_cache()
     return out

@@ -372,6 +372,32 @@ int gb_solve_batched_nbw_d(int count, const int *n, const int *nev, const int *n
                            int nslots, void *const *streams, void *const *ev_start,
                            void *const *ev_end);
 
+/* The batch stage by stage: every problem's first stage (copy, full ->
+ * band) on the streams as in gb_solve_batched_nbw_d, then the bulge chases
+ * of ALL problems in one persistent launch (tickets (problem, sweep) in
+ * sweep-major order, so the chains of all problems advance together and no
+ * wait can deadlock), then every problem's remaining stages on the streams.
+ * The chase is a latency-bound chain per problem; one launch over the whole
+ * batch keeps the SMs busy with many chains at once.  Per-solve latency
+ * grows (every problem waits for the last front), throughput rises.  Each
+ * problem keeps its reflectors, T factors and chase band in the workspace
+ * for the whole call; the scratch of the other stages is per slot.
+ * Arguments as gb_solve_batched_nbw_d (nbw may be NULL), with ws_bytes >=
+ * gb_solve_batched_staged_workspace_bytes(count, n, nev, nbw, nslots).
+ * gb_solve_batched_staged_query synchronises every stream of the batch and
+ * returns the device-side status of the batched chase and of each slot's
+ * last back-transformation (earlier problems' statuses in a slot are
+ * overwritten by its later problems). */
+size_t gb_solve_batched_staged_workspace_bytes(int count, const int *n, const int *nev, const int *nbw,
+                                               int nslots);
+int gb_solve_batched_staged_d(int count, const int *n, const int *nev, const int *nbw,
+                              const double *const *A, const int *lda, double *const *ev,
+                              double *const *Z, const int *ldz, void *workspace, size_t ws_bytes,
+                              int nslots, void *const *streams, void *const *ev_start,
+                              void *const *ev_end);
+int gb_solve_batched_staged_query(const void *workspace, int count, const int *n, const int *nev,
+                                  const int *nbw, int nslots, void *const *streams);
+
 /* The batched form as ONE CUDA graph.  The paper's SCF loop solves the same
  * set of problems again and again with new matrix entries (Sec. 5.1), so the
  * batch is issued once and replayed:

@@ -40,6 +40,7 @@ EXPORTS = (
     "gb_solve_batched_graph_destroy", "gb_solve_tuner_create", "gb_solve_tuner_destroy", "gb_solve_tuner_step",
     "gb_solve_tuner_report", "gb_solve_tuner_nbw", "gb_solve_tuner_save", "gb_solve_tuner_load",
     "gb_tridiag_dc_workspace_bytes", "gb_tridiag_dc_d", "gb_refine_syev_workspace_bytes", "gb_refine_syev_d",
+    "gb_solve_batched_staged_workspace_bytes", "gb_solve_batched_staged_d", "gb_solve_batched_staged_query",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
@@ -141,6 +142,12 @@ def load(path=None):
     L.gb_solve_batched_workspace_bytes_nbw.restype = sz
     L.gb_solve_batched_nbw_d.argtypes = [i, pi_, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
     L.gb_solve_batched_nbw_d.restype = i
+    L.gb_solve_batched_staged_workspace_bytes.argtypes = [i, pi_, pi_, pi_, i]
+    L.gb_solve_batched_staged_workspace_bytes.restype = sz
+    L.gb_solve_batched_staged_d.argtypes = [i, pi_, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
+    L.gb_solve_batched_staged_d.restype = i
+    L.gb_solve_batched_staged_query.argtypes = [p, i, pi_, pi_, pi_, i, pp]
+    L.gb_solve_batched_staged_query.restype = i
     L.gb_solve_batched_graph_create.argtypes = [i, pi_, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
     L.gb_solve_batched_graph_create.restype = i
     L.gb_solve_batched_graph_launch.argtypes = [p, p]; L.gb_solve_batched_graph_launch.restype = i
@@ -468,6 +475,26 @@ def gb_solve_batched_nbw_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes,
     if check and rc != GB_OK:
         raise GbError(rc, "gb_solve_batched_nbw_d")
     return rc
+
+
+def gb_solve_batched_staged_workspace_bytes(n, nev, nbw, nslots):
+    return load().gb_solve_batched_staged_workspace_bytes(len(n), _iarr(n), _iarr(nev),
+                                                          _iarr(nbw) if nbw is not None else None, nslots)
+
+
+def gb_solve_batched_staged_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, streams, ev_start=None,
+                              ev_end=None, check=True):
+    rc = load().gb_solve_batched_staged_d(len(n), _iarr(n), _iarr(nev), _iarr(nbw) if nbw is not None else None,
+                                          _parr(A), _iarr(lda), _parr(ev), _parr(Z), _iarr(ldz), _dp(workspace),
+                                          ws_bytes, len(streams), _harr(streams), _harr(ev_start), _harr(ev_end))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_batched_staged_d")
+    return rc
+
+
+def gb_solve_batched_staged_query(workspace, n, nev, nbw, streams):
+    return load().gb_solve_batched_staged_query(_dp(workspace), len(n), _iarr(n), _iarr(nev),
+                                                _iarr(nbw) if nbw is not None else None, len(streams), _harr(streams))
 
 
 def gb_solve_batched_graph_create(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, nbranches,

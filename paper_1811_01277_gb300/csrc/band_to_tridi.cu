@@ -25,6 +25,8 @@
 #include "layout.cuh"
 #include "trans_ev_kernels.cuh"
 
+#include <vector>
+
 namespace gb {
 
 namespace {
@@ -55,6 +57,16 @@ struct ChaseState {
     int ticket;
     int abort;
     int error;
+};
+
+// One problem of a batched chase: its working band and reflector arrays and
+// its progress flags.
+struct ChaseProblem {
+    int n, b;
+    double *W;
+    long long ldw;
+    double *hh_v, *hh_tau;
+    int *progress;
 };
 
 // Lower band storage of width 2b: A(i,j), i >= j, at W[(i-j) + j*ldw].
@@ -109,129 +121,170 @@ __global__ void __launch_bounds__(256) band_extract(int n, const double *__restr
     }
 }
 
+// Shared scratch of one chase block.
+struct ChaseSmem {
+    double v[64];
+    double q[64];
+    double red[kChaseThreads / 32];
+    double s_tau, s_scal;
+    int s_sweep, s_abort;
+};
+
+// All tasks of sweep s of one problem, in order (the whole block); returns
+// true when the call has to stop (abort raised or a wait timed out).
+__device__ bool chase_sweep_d(int n, int b, const Band &A, double *__restrict__ hh_v, double *__restrict__ hh_tau,
+                              ChaseState *state, int *progress, long long timeout_ns, int s, ChaseSmem &sm)
+{
+    double *v = sm.v, *q = sm.q, *red = sm.red;
+    double &s_tau = sm.s_tau, &s_scal = sm.s_scal;
+    int &s_abort = sm.s_abort;
+    const int tid = threadIdx.x;
+    const int quad = tid >> 2, part = tid & 3;  // 64 quads of 4 lanes; lane 'part' owns rows/cols part+4t
+    const int nk = sweep_count(n, b, s);
+    const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
+    const long long first = sweep_first(n, b, s);
+
+    for (int k = 0; k < nk; k++) {
+        // ---- wait for sweep s-1 to be kLag tasks ahead (bounded)
+        if (tid == 0) {
+            int abort = 0;
+            if (s > 1) {
+                const int need = min(k + kLag, nk_prev);
+                const unsigned long long t0 = now_ns();
+                while (ld_acq(progress + (s - 2)) < need) {
+                    if (*(volatile int *)&state->abort) { abort = 1; break; }
+                    if ((long long)(now_ns() - t0) > timeout_ns) {
+                        atomicExch(&state->error, GB_ERR_TIMEOUT);
+                        atomicExch(&state->abort, 1);
+                        abort = 1;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            } else if (*(volatile int *)&state->abort) {
+                abort = 1;
+            }
+            s_abort = abort;
+        }
+        __syncthreads();
+        if (s_abort) return true;
+
+        const int r = s + k * b;   // 0-based first row of H(s,k)
+        const int len = min(b, n - r);
+        const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
+        const int rb = r + len;
+        const int nleft = r - c - 1, nbelow = min(b, n - rb);
+        const long long idx = first + k;
+
+        // ---- one round of loads: the source column and the three blocks
+        const double xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : 0.0;
+        double L[16], Bl[16], D[16];
+#pragma unroll
+        for (int t = 0; t < 16; t++) {
+            const int i = part + 4 * t;
+            L[t] = (quad < nleft && i < len) ? A.get(r + i, c + 1 + quad) : 0.0;
+            Bl[t] = (quad < nbelow && i < len) ? A.get(rb + quad, r + i) : 0.0;
+            D[t] = (quad < len && i < len) ? A.get(r + quad, r + i) : 0.0;
+        }
+
+        // ---- reflector from column c (LAPACK form, v_0 = 1)
+        const double ss = block_sum(xi * xi, red);
+        if (tid == 0) {
+            const double alpha = A.get(r, c);
+            double tau = 0.0, scal = 0.0, beta = alpha;
+            if (ss != 0.0) {
+                const double nrm = sqrt(alpha * alpha + ss);
+                beta = (alpha >= 0.0) ? -nrm : nrm;
+                tau = (beta - alpha) / beta;
+                scal = 1.0 / (alpha - beta);
+            }
+            s_tau = tau;
+            s_scal = scal;
+            hh_tau[idx] = tau;
+            if (tau != 0.0) *A.at(r, c) = beta;
+        }
+        __syncthreads();
+        const double tau = s_tau;
+        const double vt = (tid == 0) ? 1.0 : ((tid < len && tau != 0.0) ? xi * s_scal : 0.0);
+        if (tid < 64) v[tid] = vt;
+        if (tid < b) hh_v[idx * b + tid] = vt;
+        if (tau != 0.0 && tid >= 1 && tid < len) *A.at(r + tid, c) = 0.0;
+        __syncthreads();
+
+        if (tau != 0.0) {
+            // ---- the three reductions (every lane runs the quad shuffles)
+            double al = 0.0, ab = 0.0, ad = 0.0;
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const double vi = v[part + 4 * t];  // v is zero past len
+                al = fma(vi, L[t], al);
+                ab = fma(Bl[t], vi, ab);
+                ad = fma(D[t], vi, ad);
+            }
+            const double tw = tau * quad_sum(al);   // left: tau v^T A[R, j]
+            const double ty = tau * quad_sum(ab);   // below: tau A[i, R] v
+            const double pi = tau * quad_sum(ad);   // diagonal: p_i = tau (A v)_i
+            // K = tau/2 v^T p, q = p - K v
+            const double K = 0.5 * tau * block_sum((part == 0 && quad < len) ? v[quad] * pi : 0.0, red);
+            if (part == 0 && quad < len) q[quad] = pi - K * v[quad];
+            __syncthreads();
+            const double vq = v[quad], qq = (quad < len) ? q[quad] : 0.0;
+            // ---- updates from registers, one store each
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const int i = part + 4 * t;
+                if (i < len) {
+                    const double vi = v[i];
+                    if (quad < nleft) *A.at(r + i, c + 1 + quad) = fma(-tw, vi, L[t]);
+                    if (quad < nbelow) *A.at(rb + quad, r + i) = fma(-ty, vi, Bl[t]);
+                    if (quad < len && i <= quad) *A.at(r + quad, r + i) = D[t] - vq * q[i] - qq * vi;
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_rel(progress + (s - 1), k + 1);
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(kChaseThreads)
 chase_d(int n, int b, Band A, double *__restrict__ hh_v, double *__restrict__ hh_tau, ChaseState *state,
         int *progress, long long timeout_ns)
 {
-    __shared__ double v[64];
-    __shared__ double q[64];
-    __shared__ double red[kChaseThreads / 32];
-    __shared__ double s_tau, s_scal;
-    __shared__ int s_sweep, s_abort;
-    const int tid = threadIdx.x;
-    const int quad = tid >> 2, part = tid & 3;  // 64 quads of 4 lanes; lane 'part' owns rows/cols part+4t
-
+    __shared__ ChaseSmem sm;
     for (;;) {  // persistent: sweeps by ticket, in increasing s
         __syncthreads();
-        if (tid == 0) s_sweep = 1 + atomicAdd(&state->ticket, 1);
+        if (threadIdx.x == 0) sm.s_sweep = 1 + atomicAdd(&state->ticket, 1);
         __syncthreads();
-        const int s = s_sweep;
+        const int s = sm.s_sweep;
         if (s > n - 1) return;
-        const int nk = sweep_count(n, b, s);
-        const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
-        const long long first = sweep_first(n, b, s);
+        if (chase_sweep_d(n, b, A, hh_v, hh_tau, state, progress, timeout_ns, s, sm)) return;
+    }
+}
 
-        for (int k = 0; k < nk; k++) {
-            // ---- wait for sweep s-1 to be kLag tasks ahead (bounded)
-            if (tid == 0) {
-                int abort = 0;
-                if (s > 1) {
-                    const int need = min(k + kLag, nk_prev);
-                    const unsigned long long t0 = now_ns();
-                    while (ld_acq(progress + (s - 2)) < need) {
-                        if (*(volatile int *)&state->abort) { abort = 1; break; }
-                        if ((long long)(now_ns() - t0) > timeout_ns) {
-                            atomicExch(&state->error, GB_ERR_TIMEOUT);
-                            atomicExch(&state->abort, 1);
-                            abort = 1;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                } else if (*(volatile int *)&state->abort) {
-                    abort = 1;
-                }
-                s_abort = abort;
-            }
-            __syncthreads();
-            if (s_abort) return;
-
-            const int r = s + k * b;   // 0-based first row of H(s,k)
-            const int len = min(b, n - r);
-            const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
-            const int rb = r + len;
-            const int nleft = r - c - 1, nbelow = min(b, n - rb);
-            const long long idx = first + k;
-
-            // ---- one round of loads: the source column and the three blocks
-            const double xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : 0.0;
-            double L[16], Bl[16], D[16];
-#pragma unroll
-            for (int t = 0; t < 16; t++) {
-                const int i = part + 4 * t;
-                L[t] = (quad < nleft && i < len) ? A.get(r + i, c + 1 + quad) : 0.0;
-                Bl[t] = (quad < nbelow && i < len) ? A.get(rb + quad, r + i) : 0.0;
-                D[t] = (quad < len && i < len) ? A.get(r + quad, r + i) : 0.0;
-            }
-
-            // ---- reflector from column c (LAPACK form, v_0 = 1)
-            const double ss = block_sum(xi * xi, red);
-            if (tid == 0) {
-                const double alpha = A.get(r, c);
-                double tau = 0.0, scal = 0.0, beta = alpha;
-                if (ss != 0.0) {
-                    const double nrm = sqrt(alpha * alpha + ss);
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    tau = (beta - alpha) / beta;
-                    scal = 1.0 / (alpha - beta);
-                }
-                s_tau = tau;
-                s_scal = scal;
-                hh_tau[idx] = tau;
-                if (tau != 0.0) *A.at(r, c) = beta;
-            }
-            __syncthreads();
-            const double tau = s_tau;
-            const double vt = (tid == 0) ? 1.0 : ((tid < len && tau != 0.0) ? xi * s_scal : 0.0);
-            if (tid < 64) v[tid] = vt;
-            if (tid < b) hh_v[idx * b + tid] = vt;
-            if (tau != 0.0 && tid >= 1 && tid < len) *A.at(r + tid, c) = 0.0;
-            __syncthreads();
-
-            if (tau != 0.0) {
-                // ---- the three reductions (every lane runs the quad shuffles)
-                double al = 0.0, ab = 0.0, ad = 0.0;
-#pragma unroll
-                for (int t = 0; t < 16; t++) {
-                    const double vi = v[part + 4 * t];  // v is zero past len
-                    al = fma(vi, L[t], al);
-                    ab = fma(Bl[t], vi, ab);
-                    ad = fma(D[t], vi, ad);
-                }
-                const double tw = tau * quad_sum(al);   // left: tau v^T A[R, j]
-                const double ty = tau * quad_sum(ab);   // below: tau A[i, R] v
-                const double pi = tau * quad_sum(ad);   // diagonal: p_i = tau (A v)_i
-                // K = tau/2 v^T p, q = p - K v
-                const double K = 0.5 * tau * block_sum((part == 0 && quad < len) ? v[quad] * pi : 0.0, red);
-                if (part == 0 && quad < len) q[quad] = pi - K * v[quad];
-                __syncthreads();
-                const double vq = v[quad], qq = (quad < len) ? q[quad] : 0.0;
-                // ---- updates from registers, one store each
-#pragma unroll
-                for (int t = 0; t < 16; t++) {
-                    const int i = part + 4 * t;
-                    if (i < len) {
-                        const double vi = v[i];
-                        if (quad < nleft) *A.at(r + i, c + 1 + quad) = fma(-tw, vi, L[t]);
-                        if (quad < nbelow) *A.at(rb + quad, r + i) = fma(-ty, vi, Bl[t]);
-                        if (quad < len && i <= quad) *A.at(r + quad, r + i) = D[t] - vq * q[i] - qq * vi;
-                    }
-                }
-            }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) st_rel(progress + (s - 1), k + 1);
-        }
+// The chases of many independent problems in one persistent launch: ticket
+// t is sweep 1 + t / count of problem t % count (skipped past that problem's
+// last sweep), so every problem's sweeps are taken in increasing order and a
+// task waits only on a sweep with a smaller ticket, which a running block
+// holds: no deadlock at any residency.  One state word (ticket, abort,
+// error) for the launch; progress flags per problem.
+__global__ void __launch_bounds__(kChaseThreads)
+chase_batched_d(int count, int smax, const ChaseProblem *__restrict__ probs, ChaseState *state, long long timeout_ns)
+{
+    __shared__ ChaseSmem sm;
+    const long long total = (long long)count * smax;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sm.s_sweep = atomicAdd(&state->ticket, 1);
+        __syncthreads();
+        const long long t = sm.s_sweep;
+        if (t >= total) return;
+        const ChaseProblem pr = probs[t % count];
+        const int s = 1 + (int)(t / count);
+        if (s > pr.n - 1) continue;
+        if (chase_sweep_d(pr.n, pr.b, Band{pr.W, pr.ldw}, pr.hh_v, pr.hh_tau, state, pr.progress, timeout_ns, s, sm))
+            return;
     }
 }
 
@@ -531,6 +584,25 @@ cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d,
     return cudaGetLastError();
 }
 
+cudaError_t band_to_tridi_prepare_d(int n, int b, const double *AB, int ldab, void *ws, cudaStream_t st)
+{
+    const long long ldw = 2LL * b;
+    char *flags = (char *)ws;
+    double *W = (double *)(flags + flags_bytes(n));
+    cudaError_t err = cudaMemsetAsync(flags, 0, flags_bytes(n), st);
+    if (err != cudaSuccess) return err;
+    band_init<<<1024, 256, 0, st>>>(n, b, AB, ldab, W, ldw);
+    return cudaGetLastError();
+}
+
+cudaError_t band_to_tridi_finish_d(int n, int b, const void *ws, double *d, double *e, cudaStream_t st)
+{
+    const long long ldw = 2LL * b;
+    const double *W = (const double *)((const char *)ws + flags_bytes(n));
+    band_extract<<<64, 256, 0, st>>>(n, W, ldw, d, e);
+    return cudaGetLastError();
+}
+
 cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
                             double *hh_tau, void *ws, size_t ws_bytes, long long timeout_ns, cudaStream_t st)
 {
@@ -538,10 +610,8 @@ cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d,
     const long long ldw = 2LL * b;
     char *flags = (char *)ws;
     double *W = (double *)(flags + flags_bytes(n));
-    cudaError_t err = cudaMemsetAsync(flags, 0, flags_bytes(n), st);
+    cudaError_t err = band_to_tridi_prepare_d(n, b, AB, ldab, ws, st);
     if (err != cudaSuccess) return err;
-    band_init<<<1024, 256, 0, st>>>(n, b, AB, ldab, W, ldw);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (n > 1) {
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
@@ -551,7 +621,52 @@ cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d,
                                                          (int *)(flags + 256), timeout_ns);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    band_extract<<<64, 256, 0, st>>>(n, W, ldw, d, e);
+    return band_to_tridi_finish_d(n, b, ws, d, e, st);
+}
+
+size_t chase_batched_table_bytes(int count) { return 256 + (((size_t)count * sizeof(ChaseProblem) + 255) & ~(size_t)255); }
+
+// The chases of `count` problems in one persistent launch, in two calls on
+// one stream: band_to_tridi_chase_batched_upload_d writes the launch's state
+// word (ticket, abort, error; read it with gb_trans_ev_query) and the problem
+// table into `table` (device, chase_batched_table_bytes(count)), from the
+// host (a copy from pageable memory waits for the stream's earlier work, so
+// issue it before that work); band_to_tridi_chase_batched_d launches once
+// band_to_tridi_prepare_d has run on every problem's workspace ws[i].
+cudaError_t band_to_tridi_chase_batched_upload_d(int count, const int *n, const int *b, void *const *ws,
+                                                 double *const *hh_v, double *const *hh_tau, void *table,
+                                                 cudaStream_t st)
+{
+    if (count < 1) return cudaSuccess;
+    std::vector<ChaseProblem> host((size_t)count);
+    for (int i = 0; i < count; i++) {
+        char *flags = (char *)ws[i];
+        host[i] = ChaseProblem{n[i], b[i], (double *)(flags + flags_bytes(n[i])), 2LL * b[i], hh_v[i], hh_tau[i],
+                               (int *)(flags + 256)};
+    }
+    cudaError_t err = cudaMemsetAsync(table, 0, 256, st);
+    if (err != cudaSuccess) return err;
+    // from pageable memory: staged before the call returns, so `host` may go
+    return cudaMemcpyAsync((char *)table + 256, host.data(), host.size() * sizeof(ChaseProblem),
+                           cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, void *table, long long timeout_ns, cudaStream_t st)
+{
+    int smax = 0;
+    for (int i = 0; i < count; i++) smax = max(smax, n[i] - 1);
+    if (count < 1 || smax < 1) return cudaSuccess;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t err;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chase_batched_d, kChaseThreads, 0)) !=
+        cudaSuccess)
+        return err;
+    const long long tickets = (long long)count * smax;
+    const long long grid = min((long long)sms * max(per_sm, 1), tickets);
+    chase_batched_d<<<(unsigned)grid, kChaseThreads, 0, st>>>(count, smax, (const ChaseProblem *)((char *)table + 256),
+                                                              (ChaseState *)table, timeout_ns);
     return cudaGetLastError();
 }
 

@@ -125,7 +125,7 @@ struct SolveWs {
     double *Aw, *tauP, *Tall, *Y, *Y2, *YT, *X, *Pm, *M, *G, *part, *AB, *d, *e, *hv, *ht, *Ztri, *Gns, *S, *S2, *gw,
         *gw2;
     void *chase, *eig, *tev, *sl, *dc;
-    size_t chase_bytes, tev_bytes, gw_elems, gw2_elems, sl_bytes, total;
+    size_t chase_bytes, tev_bytes, gw_elems, gw2_elems, sl_bytes, total, ptotal;
 };
 
 // More than half of the eigenvectors: divide and conquer (all of them, by
@@ -155,21 +155,31 @@ size_t sliced_region_bytes(int n, int nev, int b)
 // this holds).
 size_t gemm_work_elems(int n, int b) { return std::max((size_t)8 * n * b, (size_t)1 << 22); }
 
-SolveWs carve(int n, int nev, int b, char *base)
+// With split set, the pieces a problem keeps from its first stage to its
+// last (the panels' reflectors and T factors, the bulge chase's band and
+// reflectors) go to pbase, the rest (scratch of one stage at a time) to
+// base; without it everything is in base.
+SolveWs carve(int n, int nev, int b, char *base, char *pbase = nullptr, bool split = false)
 {
     SolveWs w{};
-    size_t off = 0;
+    size_t off = 0, poff = 0;
     auto take = [&](size_t bytes) {
         char *p = base ? base + off : nullptr;
         off += a256(bytes);
         return p;
     };
+    auto ptake = [&](size_t bytes) {
+        if (!split) return take(bytes);
+        char *p = pbase ? pbase + poff : nullptr;
+        poff += a256(bytes);
+        return p;
+    };
     const size_t P = (size_t)(n + b - 1) / b;
     const size_t cnt = (size_t)gb::hh_total(n, b);
     const size_t nch = (size_t)gb::panel_chunks(n);
-    w.Aw = (double *)take((size_t)n * n * 8);
-    w.tauP = (double *)take(P * b * 8);
-    w.Tall = (double *)take(P * b * b * 8);
+    w.Aw = (double *)ptake((size_t)n * n * 8);
+    w.tauP = (double *)ptake(P * b * 8);
+    w.Tall = (double *)ptake(P * b * b * 8);
     w.Y = (double *)take((size_t)n * b * 8);
     w.Y2 = (double *)take((size_t)n * b * 8);
     w.YT = (double *)take((size_t)n * b * 8);
@@ -181,8 +191,8 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.AB = (double *)take((size_t)(b + 1) * n * 8);
     w.d = (double *)take((size_t)n * 8);
     w.e = (double *)take((size_t)n * 8);
-    w.hv = (double *)take((cnt ? cnt : 1) * b * 8);
-    w.ht = (double *)take((cnt ? cnt : 1) * 8);
+    w.hv = (double *)ptake((cnt ? cnt : 1) * b * 8);
+    w.ht = (double *)ptake((cnt ? cnt : 1) * 8);
     w.Ztri = (double *)take((size_t)n * nev * 8);
     w.Gns = (double *)take((size_t)nev * nev * 8);
     w.S = (double *)take((size_t)b * nev * 8);
@@ -192,7 +202,7 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.gw2_elems = (size_t)512 * b * b;  // split-K partials of the panel's Y^T Y on the helper stream
     w.gw2 = (double *)take(w.gw2_elems * 8);
     w.chase_bytes = gb::band_to_tridi_workspace_bytes(n, b);
-    w.chase = take(w.chase_bytes);
+    w.chase = ptake(w.chase_bytes);
     w.eig = take(gb::tridiag_eig_workspace_bytes(n, nev));
     w.tev_bytes = gb_trans_ev_workspace_bytes(n, b, nev, 0, nullptr);
     w.tev = take(w.tev_bytes ? w.tev_bytes : 256);
@@ -200,6 +210,7 @@ SolveWs carve(int n, int nev, int b, char *base)
     w.sl = w.sl_bytes ? take(w.sl_bytes) : nullptr;
     w.dc = use_dc(n, nev) ? take(gb::tridiag_dc_workspace_bytes(n)) : nullptr;
     w.total = off;
+    w.ptotal = poff;
     return w;
 }
 
@@ -285,8 +296,18 @@ size_t gb_solve_workspace_bytes(int n, int nev, int nbw)
     return carve(n, nev, nbw, nullptr).total;
 }
 
-int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
-               size_t ws_bytes, void *stream, int flags)
+}  // extern "C"
+
+namespace {
+
+// Parts of the real solve, so that the batched form can run one stage for
+// every problem at once: the front (copy, full -> band, the band's
+// storage), the chase, and the back (tridiagonal eigenpairs, the
+// back-transformations).
+constexpr int kPartFront = 1, kPartChase = 2, kPartBack = 4;
+
+int solve_d_parts(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
+                  size_t ws_bytes, void *stream, int flags, int parts, const SolveWs *pre = nullptr)
 {
     if (n < 2) return -1;
     if (nev < 1 || nev > n) return -2;
@@ -298,8 +319,8 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     if (ldz < n) return -8;
     if (!workspace || ((uintptr_t)workspace % 256) != 0) return -9;
     const int b = nbw;
-    SolveWs w = carve(n, nev, b, (char *)workspace);
-    if (ws_bytes < w.total) return -10;
+    SolveWs w = pre ? *pre : carve(n, nev, b, (char *)workspace);
+    if (!pre && ws_bytes < w.total) return -10;
     if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS |
                   GB_SOLVE_TRIDIAG_BISECT))
         return -12;
@@ -317,6 +338,8 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         if (sev && cudaEventRecord(sev[i], st) != cudaSuccess) return GB_ERR_CUDA; \
     } while (0)
     const long long ldw = n;
+    const int P = b < n ? (n - 1) / b : 0;  // panels of full -> band
+    if (parts & kPartFront) {
 
     // ---- full -> band, with look-ahead: panel p+1 is factored on the helper
     // stream as soon as its columns have received panel p's update, while
@@ -347,7 +370,7 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
             return e;
         return ahead ? cudaEventRecord(la->factored, fst) : cudaSuccess;
     };
-    int P = 0;
+    int pp = 0;
     if (b < n) {
         if (ahead) {
             GB_CU(cudaEventRecord(la->start, st));
@@ -355,11 +378,11 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         }
         GB_CU(factor(0));
     }
-    for (int j = 0; j + b < n; j += b, P++) {
+    for (int j = 0; j + b < n; j += b, pp++) {
         const int m = n - j - b;
         double *A2 = w.Aw + (long long)(j + b) * ldw + (j + b);
-        const double *T = w.Tall + (long long)P * b * b;
-        const double *Yp = Ybuf[P & 1];
+        const double *T = w.Tall + (long long)pp * b * b;
+        const double *Yp = Ybuf[pp & 1];
         if (ahead) GB_CU(cudaStreamWaitEvent(st, la->factored, 0));
         GB_CU(gb::dfma_gemm('N', 'N', m, b, b, 1.0, Yp, m, T, b, 0.0, w.YT, m, w.gw, w.gw_elems, st));
         // only the lower triangle of A2 is kept: X = A2 (Y T) (symmetric
@@ -382,7 +405,7 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
                 GB_CU(cudaEventRecord(la->ready, st));
                 GB_CU(cudaStreamWaitEvent(la->side, la->ready, 0));
             }
-            GB_CU(factor(P + 1));
+            GB_CU(factor(pp + 1));
             if (use_sliced(m - b, m - b, b))
                 GB_CU(gb::sliced_dsyr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b,
                                               ldw, w.sl, st));
@@ -397,11 +420,15 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         }
     }
     GB_CU(gb::band_from_full(n, b, w.Aw, ldw, w.AB, b + 1, st));
+    }
 
     // ---- band -> tridiagonal
-    GB_STAGE(1);
-    GB_CU(gb::band_to_tridi_d(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, w.chase_bytes,
-                              10LL * 1000 * 1000 * 1000, st));
+    if (parts & kPartChase) {
+        GB_STAGE(1);
+        GB_CU(gb::band_to_tridi_d(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, w.chase_bytes,
+                                  10LL * 1000 * 1000 * 1000, st));
+    }
+    if (!(parts & kPartBack)) return GB_OK;
 
     // ---- eigenpairs of T: divide and conquer straight into Z, or bisection,
     // inverse iteration and one Newton-Schulz orthogonalisation step
@@ -454,6 +481,17 @@ int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, do
 #undef GB_STAGE
     GB_CU(cudaGetLastError());
     return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
+               size_t ws_bytes, void *stream, int flags)
+{
+    return solve_d_parts(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream, flags,
+                         kPartFront | kPartChase | kPartBack);
 }
 
 size_t gb_solve_workspace_bytes_z(int n, int nev, int nbw)
@@ -867,6 +905,160 @@ int gb_solve_batched_graph_destroy(gb_solve_graph *graph)
 {
     if (!graph) return -1;
     destroy_graph_object(graph);
+    return GB_OK;
+}
+
+// ---- the batch stage by stage: every problem's front on the streams, all
+// bulge chases in one persistent launch, every problem's back on the streams
+
+namespace {
+
+struct StagedLayout {
+    size_t table, scratch_slot, total;
+    std::vector<size_t> persist_off;  // per problem, from the workspace base
+};
+
+bool staged_layout(int count, const int *n, const int *nev, const int *nbw, int nslots, StagedLayout *L)
+{
+    if (count < 1 || !n || !nev || nslots < 1) return false;
+    L->table = a256(gb::chase_batched_table_bytes(count));
+    L->persist_off.assign((size_t)count, 0);
+    size_t off = L->table, slot = 0;
+    for (int i = 0; i < count; i++) {
+        const int b = nbw ? nbw[i] : gb_solve_default_nbw(n[i]);
+        if (gb_solve_workspace_bytes(n[i], nev[i], b) == 0) return false;
+        const SolveWs w = carve(n[i], nev[i], b, nullptr, nullptr, true);
+        L->persist_off[i] = off;
+        off += a256(w.ptotal);
+        slot = std::max(slot, a256(w.total));
+    }
+    L->scratch_slot = slot;
+    L->total = off + slot * (size_t)nslots;
+    return true;
+}
+
+}  // namespace
+
+size_t gb_solve_batched_staged_workspace_bytes(int count, const int *n, const int *nev, const int *nbw, int nslots)
+{
+    StagedLayout L;
+    return staged_layout(count, n, nev, nbw, nslots, &L) ? L.total : 0;
+}
+
+int gb_solve_batched_staged_d(int count, const int *n, const int *nev, const int *nbw, const double *const *A,
+                              const int *lda, double *const *ev, double *const *Z, const int *ldz, void *workspace,
+                              size_t ws_bytes, int nslots, void *const *streams, void *const *ev_start,
+                              void *const *ev_end)
+{
+    if (count < 1) return -1;
+    if (!n || !nev || !A || !lda || !ev || !Z || !ldz) return -2;
+    if (nslots < 1 || !streams) return -12;
+    StagedLayout L;
+    if (!staged_layout(count, n, nev, nbw, nslots, &L)) return -2;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -10;
+    if (ws_bytes < L.total) return -11;
+    char *base = (char *)workspace;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GB_ERR_CUDA;
+    const int nthreads = nslots < count ? nslots : count;
+    std::vector<SolveWs> ws((size_t)count);
+    std::vector<int> bw((size_t)count);
+    for (int i = 0; i < count; i++) {
+        bw[i] = nbw ? nbw[i] : gb_solve_default_nbw(n[i]);
+        const int s = i % nslots;
+        char *scr = base + (L.total - L.scratch_slot * (size_t)nslots) + L.scratch_slot * (size_t)s;
+        ws[i] = carve(n[i], nev[i], bw[i], scr, base + L.persist_off[i], true);
+    }
+    {  // the chase's problem table goes up first: its copy from the host waits for the stream
+        std::vector<void *> cws((size_t)count);
+        std::vector<double *> hv((size_t)count), ht((size_t)count);
+        for (int i = 0; i < count; i++) {
+            cws[i] = ws[i].chase;
+            hv[i] = ws[i].hv;
+            ht[i] = ws[i].ht;
+        }
+        if (gb::band_to_tridi_chase_batched_upload_d(count, n, bw.data(), cws.data(), hv.data(), ht.data(), base,
+                                                     (cudaStream_t)streams[0]) != cudaSuccess)
+            return GB_ERR_CUDA;
+    }
+    std::vector<int> rcs(nthreads, GB_OK);
+    auto phase = [&](int s, int which) {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            rcs[s] = GB_ERR_CUDA;
+            return;
+        }
+        cudaStream_t st = (cudaStream_t)streams[s];
+        for (int i = s; i < count && rcs[s] == GB_OK; i += nslots) {
+            const SolveWs &w = ws[i];
+            int rc = GB_OK;
+            if (which == 0) {
+                if (ev_start && cudaEventRecord((cudaEvent_t)ev_start[i], st) != cudaSuccess) rc = GB_ERR_CUDA;
+                if (rc == GB_OK)
+                    rc = solve_d_parts(n[i], nev[i], bw[i], A[i], lda[i], ev[i], Z[i], ldz[i], base, 0, (void *)st, 0,
+                                       kPartFront, &w);
+                if (rc == GB_OK && gb::band_to_tridi_prepare_d(n[i], bw[i], w.AB, bw[i] + 1, w.chase, st) != cudaSuccess)
+                    rc = GB_ERR_CUDA;
+            } else {
+                if (gb::band_to_tridi_finish_d(n[i], bw[i], w.chase, w.d, w.e, st) != cudaSuccess) rc = GB_ERR_CUDA;
+                if (rc == GB_OK)
+                    rc = solve_d_parts(n[i], nev[i], bw[i], A[i], lda[i], ev[i], Z[i], ldz[i], base, 0, (void *)st, 0,
+                                       kPartBack, &w);
+                if (rc == GB_OK && ev_end && cudaEventRecord((cudaEvent_t)ev_end[i], st) != cudaSuccess)
+                    rc = GB_ERR_CUDA;
+            }
+            rcs[s] = rc;
+        }
+    };
+    auto run_phase = [&](int which) {
+        std::vector<std::thread> pool;
+        for (int s = 1; s < nthreads; s++) pool.emplace_back(phase, s, which);
+        phase(0, which);
+        for (auto &t : pool) t.join();
+        for (int rc : rcs)
+            if (rc != GB_OK) return rc;
+        return (int)GB_OK;
+    };
+    int rc = run_phase(0);
+    if (rc != GB_OK) return rc;
+    // every front done -> one chase launch on the first stream -> every back
+    std::vector<cudaEvent_t> evs((size_t)nthreads + 1, nullptr);
+    for (auto &e : evs)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = GB_ERR_CUDA;
+    const cudaStream_t st0 = (cudaStream_t)streams[0];
+    for (int s = 1; rc == GB_OK && s < nthreads; s++)
+        if (cudaEventRecord(evs[s], (cudaStream_t)streams[s]) != cudaSuccess ||
+            cudaStreamWaitEvent(st0, evs[s], 0) != cudaSuccess)
+            rc = GB_ERR_CUDA;
+    if (rc == GB_OK && gb::band_to_tridi_chase_batched_d(count, n, base, 10LL * 1000 * 1000 * 1000, st0) != cudaSuccess)
+        rc = GB_ERR_CUDA;
+    if (rc == GB_OK && cudaEventRecord(evs[0], st0) != cudaSuccess) rc = GB_ERR_CUDA;
+    for (int s = 1; rc == GB_OK && s < nthreads; s++)
+        if (cudaStreamWaitEvent((cudaStream_t)streams[s], evs[0], 0) != cudaSuccess) rc = GB_ERR_CUDA;
+    for (auto &e : evs)
+        if (e) cudaEventDestroy(e);  // released once the work recorded on them completes
+    if (rc != GB_OK) return rc;
+    return run_phase(1);
+}
+
+int gb_solve_batched_staged_query(const void *workspace, int count, const int *n, const int *nev, const int *nbw,
+                                  int nslots, void *const *streams)
+{
+    StagedLayout L;
+    if (!workspace || !streams || !staged_layout(count, n, nev, nbw, nslots, &L)) return -1;
+    for (int s = 0; s < nslots; s++)
+        if (cudaStreamSynchronize((cudaStream_t)streams[s]) != cudaSuccess) return GB_ERR_CUDA;
+    void *stream = streams[0];
+    int rc = gb_trans_ev_query(workspace, 256, stream);  // the batched chase's state word
+    if (rc != GB_OK) return rc;
+    const char *base = (const char *)workspace;
+    for (int i = 0; i < count; i++) {
+        const int b = nbw ? nbw[i] : gb_solve_default_nbw(n[i]);
+        const int s = i % nslots;
+        char *scr = (char *)base + (L.total - L.scratch_slot * (size_t)nslots) + L.scratch_slot * (size_t)s;
+        const SolveWs w = carve(n[i], nev[i], b, scr, (char *)base + L.persist_off[i], true);
+        // each slot's last problem left its back-transformation's status in the slot
+        if (i + nslots >= count && (rc = gb_trans_ev_query(w.tev, w.tev_bytes, stream)) != GB_OK) return rc;
+    }
     return GB_OK;
 }
 

@@ -38,6 +38,15 @@ size_t band_to_tridi_workspace_bytes(int n, int b);
 cudaError_t band_to_tridi_d(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
                             double *hh_tau, void *ws, size_t ws_bytes, long long timeout_ns, cudaStream_t st);
 
+// the chase in three steps, and the chases of many problems in one launch
+cudaError_t band_to_tridi_prepare_d(int n, int b, const double *AB, int ldab, void *ws, cudaStream_t st);
+cudaError_t band_to_tridi_finish_d(int n, int b, const void *ws, double *d, double *e, cudaStream_t st);
+size_t chase_batched_table_bytes(int count);
+cudaError_t band_to_tridi_chase_batched_upload_d(int count, const int *n, const int *b, void *const *ws,
+                                                 double *const *hh_v, double *const *hh_tau, void *table,
+                                                 cudaStream_t st);
+cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, void *table, long long timeout_ns, cudaStream_t st);
+
 size_t band_to_tridi_workspace_bytes_z(int n, int b);
 cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
                             double *hh_tau, void *ws, long long timeout_ns, cudaStream_t st);

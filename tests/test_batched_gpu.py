@@ -141,3 +141,44 @@ def test_batched_graph_argument_errors(gb):
     assert e.value.status == -10
     assert gb.gb_solve_batched_graph_launch(None, None, check=False) == -1
     assert gb.gb_solve_batched_graph_nodes(None) == -1
+
+
+def test_batched_staged_equals_stream_form(gb):
+    """The batch stage by stage (all bulge chases in one launch) gives
+    bit-identical results to the stream form with the same band widths (the
+    same arithmetic per problem), and meets the oracle's eigenvalues and the
+    residual/orthogonality bounds; the chase's status word reads 0."""
+    dev = torch.device("cuda")
+    g = np.random.default_rng(17)
+    sizes = [int(x) for x in g.integers(70, 700, 11)]
+    nevs = [n if i % 2 == 0 else max(1, n // 5) for i, n in enumerate(sizes)]
+    nbw = [[16, 32, 64][i % 3] for i in range(len(sizes))]
+    mats = [inputs.band_symmetric(n, n, seed=500 + i, dist="normal") for i, n in enumerate(sizes)]
+    A = [torch.from_numpy(np.ascontiguousarray(M.T)).to(dev) for M in mats]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = []
+    for staged in (False, True):
+        ev = [torch.zeros(k, dtype=torch.float64, device=dev) for k in nevs]
+        Z = [torch.zeros((k, n), dtype=torch.float64, device=dev) for n, k in zip(sizes, nevs)]
+        if staged:
+            wsb = gb.gb_solve_batched_staged_workspace_bytes(sizes, nevs, nbw, len(streams))
+            ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            gb.gb_solve_batched_staged_d(sizes, nevs, nbw, A, sizes, ev, Z, sizes, ws, wsb, streams)
+            assert gb.gb_solve_batched_staged_query(ws, sizes, nevs, nbw, streams) == 0
+        else:
+            wsb = gb.gb_solve_batched_workspace_bytes_nbw(sizes, nevs, nbw, len(streams))
+            ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            gb.gb_solve_batched_nbw_d(sizes, nevs, nbw, A, sizes, ev, Z, sizes, ws, wsb, streams)
+        torch.cuda.synchronize()
+        outs.append(([e.cpu().numpy() for e in ev], [z.cpu().numpy() for z in Z]))
+    for i, (n, k, M) in enumerate(zip(sizes, nevs, mats)):
+        assert np.array_equal(outs[0][0][i], outs[1][0][i]) and np.array_equal(outs[0][1][i], outs[1][1][i])
+        w, Zi = outs[1][0][i], outs[1][1][i].T
+        nrm = np.linalg.norm(M, 2)
+        d, e, _, _ = oracle.sytrd(M)
+        lam = np.sort(oracle.tridiag_ql(d, e)[0])
+        assert np.abs(w - lam[:k]).max() / nrm <= 1e-11
+        assert np.linalg.norm(M @ Zi - Zi * w) / np.linalg.norm(M) <= 50 * n * U
+        assert np.abs(Zi.T @ Zi - np.eye(k)).max() <= 50 * n * U
