@@ -319,12 +319,14 @@ __global__ void __launch_bounds__(256) tc5_tile_prep(int n, const double *__rest
         double a = 0.0;
         for (int j = q; j < min(q + b, LP); j++) a = fma(V[j * NB1 + q], V[j * NB1 + q], a);
         nv[q] = sqrt(a);
+        Gr[q] = a > 0.0 ? 1.0 / nv[q] : 0.0;  // the Gram matrix is no longer needed
     }
     __syncthreads();
+    // one division per column, not per entry (the FP64 pipe bounds this kernel)
     for (int e = threadIdx.x; e < LP * NB; e += blockDim.x) {
         const int j = e / NB, q = e % NB;
         if (nv[q] > 0.0) {
-            V[j * NB1 + q] = V[j * NB1 + q] / nv[q];
+            V[j * NB1 + q] = V[j * NB1 + q] * Gr[q];
             U[j * NB1 + q] = U[j * NB1 + q] * nv[q];
         }
     }
@@ -476,13 +478,15 @@ __global__ void __launch_bounds__(256) tc5_tile_prep_z(int n, const double2 *__r
             a = fma(v.x, v.x, fma(v.y, v.y, a));
         }
         nv[q] = sqrt(a);
+        ((double *)Gr)[q] = a > 0.0 ? 1.0 / nv[q] : 0.0;  // the Gram matrix is no longer needed
     }
     __syncthreads();
     for (int e = threadIdx.x; e < LC * NB; e += blockDim.x) {
         const int j = e / NB, q = e % NB;
         if (nv[q] > 0.0) {
             const double2 v = V[j * NB1 + q], u = U[j * NB1 + q];
-            V[j * NB1 + q] = make_double2(v.x / nv[q], v.y / nv[q]);
+            const double rn = ((const double *)Gr)[q];
+            V[j * NB1 + q] = make_double2(v.x * rn, v.y * rn);
             U[j * NB1 + q] = make_double2(u.x * nv[q], u.y * nv[q]);
         }
     }
