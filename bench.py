@@ -1203,6 +1203,20 @@ def run_stage_serve(args):
     done = srv.run(reqs)
     clocks = sampler.stop()
     summ = serve.latency_summary(done)
+    # the same requests with the bulge chases batched across requests (one
+    # chase launch in flight at a time, or up to four)
+    stage_batched = {}
+    for lanes in (1, 4):
+        for r in reqs:
+            r.start = r.done = r.status = r.ev = r.Z = None
+        srv_b = serve.EigenServer(slots=args.serve_slots, hbm_budget_bytes=args.serve_budget_gb << 30,
+                                  stage_batching=True, chase_lanes=lanes)
+        done_b = srv_b.run(reqs)
+        summ_b = serve.latency_summary(done_b)
+        stage_batched[f"lanes_{lanes}"] = {
+            "value": summ_b["solves_per_s"], "unit": "solves/s", "p50_ms": summ_b["p50_ms"],
+            "p99_ms": summ_b["p99_ms"], "failed": sum(1 for r in done_b if r.status != 0),
+            "chases_per_launch_mean": float(np.mean(srv_b.chase_sizes)), "chase_launches": len(srv_b.chase_sizes)}
     # the plain solve on the same requests, one after another on one stream
     pst = torch.cuda.Stream(device=dev)
     pmax = max(gb.gb_solve_workspace_bytes_z(r.n, r.nev, gb.gb_solve_default_nbw(r.n)) for r in reqs)
@@ -1224,6 +1238,7 @@ def run_stage_serve(args):
         "hbm_budget_gb": args.serve_budget_gb, "failed": sum(1 for r in done if r.status != 0),
         "plain_solve_one_at_a_time": {"value": plain_rate, "unit": "solves/s", "sample": "the same requests",
                                       "speedup_of_served": summ["solves_per_s"] / plain_rate},
+        "stage_batched_chases": stage_batched,
         "dtype": "complex128", "data": "synthetic Hermitian, A <- A + 1e-3 E per re-submission",
         "clocks": clocks}))
     return 0

@@ -372,6 +372,33 @@ int gb_solve_batched_nbw_d(int count, const int *n, const int *nev, const int *n
                            int nslots, void *const *streams, void *const *ev_start,
                            void *const *ev_end);
 
+/* The two-stage solve (real, is_complex = 0, or complex Hermitian, 1) in
+ * three calls, so that a server can run one stage for several requests at
+ * once -- the bulge chases of all the requests it holds in one launch:
+ *  * gb_solve_stage_front: copy, full -> band and the chase's working band,
+ *    in the request's workspace (gb_solve_workspace_bytes[_z](n, nev, nbw));
+ *  * gb_solve_stage_chase_batched: the bulge chases of `count` requests whose
+ *    fronts have run, in ONE persistent launch on `stream` (tickets
+ *    (request, sweep) in sweep-major order, deadlock-free at any residency);
+ *    `table` is gb_solve_stage_table_bytes(count) device bytes, 256-byte
+ *    aligned, reused only after the launch is done; its first 256 bytes hold
+ *    the launch's status (gb_trans_ev_query(table, 256, stream)).  The table
+ *    goes up by a copy from pageable host memory, which waits for the work
+ *    already on `stream`;
+ *  * gb_solve_stage_back: the tridiagonal eigenpairs and both
+ *    back-transformations into ev and Z (flags as gb_solve_d).
+ * The caller orders the calls of one request (events across streams).  The
+ * three calls give bit-identical results to gb_solve_d / gb_solve_z.
+ * Argument errors return -i as in the single-call forms. */
+size_t gb_solve_stage_table_bytes(int count);
+int gb_solve_stage_front(int is_complex, int n, int nev, int nbw, const double *A, int lda,
+                         void *workspace, size_t ws_bytes, void *stream);
+int gb_solve_stage_chase_batched(int is_complex, int count, const int *n, const int *nev,
+                                 const int *nbw, void *const *workspaces, void *table,
+                                 size_t table_bytes, void *stream);
+int gb_solve_stage_back(int is_complex, int n, int nev, int nbw, double *ev, double *Z, int ldz,
+                        void *workspace, size_t ws_bytes, void *stream, int flags);
+
 /* The batch stage by stage: every problem's first stage (copy, full ->
  * band) on the streams as in gb_solve_batched_nbw_d, then the bulge chases
  * of ALL problems in one persistent launch (tickets (problem, sweep) in

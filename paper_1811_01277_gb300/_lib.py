@@ -41,6 +41,7 @@ EXPORTS = (
     "gb_solve_tuner_report", "gb_solve_tuner_nbw", "gb_solve_tuner_save", "gb_solve_tuner_load",
     "gb_tridiag_dc_workspace_bytes", "gb_tridiag_dc_d", "gb_refine_syev_workspace_bytes", "gb_refine_syev_d",
     "gb_solve_batched_staged_workspace_bytes", "gb_solve_batched_staged_d", "gb_solve_batched_staged_query",
+    "gb_solve_stage_table_bytes", "gb_solve_stage_front", "gb_solve_stage_chase_batched", "gb_solve_stage_back",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
@@ -148,6 +149,11 @@ def load(path=None):
     L.gb_solve_batched_staged_d.restype = i
     L.gb_solve_batched_staged_query.argtypes = [p, i, pi_, pi_, pi_, i, pp]
     L.gb_solve_batched_staged_query.restype = i
+    L.gb_solve_stage_table_bytes.argtypes = [i]; L.gb_solve_stage_table_bytes.restype = sz
+    L.gb_solve_stage_front.argtypes = [i, i, i, i, p, i, p, sz, p]; L.gb_solve_stage_front.restype = i
+    L.gb_solve_stage_chase_batched.argtypes = [i, i, pi_, pi_, pi_, pp, p, sz, p]
+    L.gb_solve_stage_chase_batched.restype = i
+    L.gb_solve_stage_back.argtypes = [i, i, i, i, p, p, i, p, sz, p, i]; L.gb_solve_stage_back.restype = i
     L.gb_solve_batched_graph_create.argtypes = [i, pi_, pi_, pi_, pp, pi_, pp, pp, pi_, p, sz, i, pp, pp, pp]
     L.gb_solve_batched_graph_create.restype = i
     L.gb_solve_batched_graph_launch.argtypes = [p, p]; L.gb_solve_batched_graph_launch.restype = i
@@ -495,6 +501,35 @@ def gb_solve_batched_staged_d(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_byt
 def gb_solve_batched_staged_query(workspace, n, nev, nbw, streams):
     return load().gb_solve_batched_staged_query(_dp(workspace), len(n), _iarr(n), _iarr(nev),
                                                 _iarr(nbw) if nbw is not None else None, len(streams), _harr(streams))
+
+
+def gb_solve_stage_table_bytes(count):
+    return load().gb_solve_stage_table_bytes(count)
+
+
+def gb_solve_stage_front(is_complex, n, nev, nbw, A, lda, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_solve_stage_front(int(is_complex), n, nev, nbw, _dp(A), lda, _dp(workspace), ws_bytes,
+                                     _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_stage_front")
+    return rc
+
+
+def gb_solve_stage_chase_batched(is_complex, n, nev, nbw, workspaces, table, table_bytes, stream=None, check=True):
+    ws = (ctypes.c_void_p * len(workspaces))(*[_dp(w) for w in workspaces])
+    rc = load().gb_solve_stage_chase_batched(int(is_complex), len(n), _iarr(n), _iarr(nev), _iarr(nbw), ws,
+                                             _dp(table), table_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_stage_chase_batched")
+    return rc
+
+
+def gb_solve_stage_back(is_complex, n, nev, nbw, ev, Z, ldz, workspace, ws_bytes, stream=None, flags=0, check=True):
+    rc = load().gb_solve_stage_back(int(is_complex), n, nev, nbw, _dp(ev), _dp(Z), ldz, _dp(workspace), ws_bytes,
+                                    _stream(stream), flags)
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_stage_back")
+    return rc
 
 
 def gb_solve_batched_graph_create(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, nbranches,

@@ -337,178 +337,216 @@ __device__ __forceinline__ Zc quad_sum_z(Zc x)
     return x;
 }
 
+struct ChaseSmemZ {
+    Zc v[64];
+    Zc q[64];
+    double red[kChaseThreads / 32];
+    Zc s_tau, s_scal;
+    int s_sweep, s_abort;
+};
+
+// All tasks of sweep s of one Hermitian problem (the whole block); returns
+// true when the call has to stop.
+__device__ bool chase_sweep_z(int n, int b, const BandZ &A, Zc *__restrict__ hh_v, Zc *__restrict__ hh_tau,
+                              ChaseState *state, int *progress, long long timeout_ns, int s, ChaseSmemZ &sm)
+{
+    Zc *v = sm.v, *q = sm.q;
+    double *red = sm.red;
+    Zc &s_tau = sm.s_tau, &s_scal = sm.s_scal;
+    int &s_abort = sm.s_abort;
+    const int tid = threadIdx.x;
+    const int quad = tid >> 2, part = tid & 3;
+    const int nk = sweep_count(n, b, s);
+    const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
+    const long long first = sweep_first(n, b, s);
+
+    for (int k = 0; k < nk; k++) {
+        if (tid == 0) {
+            int abort = 0;
+            if (s > 1) {
+                const int need = min(k + kLag, nk_prev);
+                const unsigned long long t0 = now_ns();
+                while (ld_acq(progress + (s - 2)) < need) {
+                    if (*(volatile int *)&state->abort) { abort = 1; break; }
+                    if ((long long)(now_ns() - t0) > timeout_ns) {
+                        atomicExch(&state->error, GB_ERR_TIMEOUT);
+                        atomicExch(&state->abort, 1);
+                        abort = 1;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            } else if (*(volatile int *)&state->abort) {
+                abort = 1;
+            }
+            s_abort = abort;
+        }
+        __syncthreads();
+        if (s_abort) return true;
+
+        const int r = s + k * b;
+        const int len = min(b, n - r);
+        const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
+        const int rb = r + len;
+        const int nleft = r - c - 1, nbelow = min(b, n - rb);
+        const long long idx = first + k;
+
+        // ---- reflector (complex, beta real)
+        const Zc xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : Zc{0.0, 0.0};
+        const double ss = block_sum(xi.re * xi.re + xi.im * xi.im, red);
+        if (tid == 0) {
+            const Zc alpha = A.get(r, c);
+            Zc tau{0.0, 0.0}, scal{0.0, 0.0};
+            if (!(ss == 0.0 && alpha.im == 0.0)) {
+                const double nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + ss);
+                const double beta = (alpha.re >= 0.0) ? -nrm : nrm;
+                tau = {(beta - alpha.re) / beta, -alpha.im / beta};
+                const Zc den{alpha.re - beta, alpha.im};           // 1 / (alpha - beta)
+                const double dd = den.re * den.re + den.im * den.im;
+                scal = {den.re / dd, -den.im / dd};
+                A.set_lower(r, c, Zc{beta, 0.0});
+            }
+            s_tau = tau;
+            s_scal = scal;
+            hh_tau[idx] = tau;
+        }
+        __syncthreads();
+        const Zc tau = s_tau;
+        const bool active = !(tau.re == 0.0 && tau.im == 0.0);
+        Zc vt{0.0, 0.0};
+        if (tid == 0) vt = {1.0, 0.0};
+        else if (tid < len && active) vt = zmul(xi, s_scal);
+        if (tid < 64) v[tid] = vt;
+        if (tid < b) hh_v[idx * b + tid] = vt;
+        if (active && tid >= 1 && tid < len) A.set_lower(r + tid, c, Zc{0.0, 0.0});
+        __syncthreads();
+
+        if (active) {
+            const Zc ctau = zconj(tau);
+            // ---- left block: A[R,j] -= conj(tau) v (v^H A[R,j])
+            {
+                const bool act = quad < nleft;
+                const int j = c + 1 + quad;
+                Zc Lr[16];
+                Zc acc{0.0, 0.0};
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int i = part + 4 * t;
+                    Lr[t] = (act && i < len) ? A.get(r + i, j) : Zc{0.0, 0.0};
+                    zdotc(acc, v[i], Lr[t]);
+                }
+                const Zc w = zmul(ctau, quad_sum_z(acc));
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int i = part + 4 * t;
+                    if (act && i < len) {
+                        Zc a = Lr[t];
+                        const Zc vw = zmul(v[i], w);
+                        a.re -= vw.re;
+                        a.im -= vw.im;
+                        A.set_lower(r + i, j, a);
+                    }
+                }
+            }
+            // ---- below block: A[i,R] -= tau (A[i,R] v) v^H
+            {
+                const bool act = quad < nbelow;
+                const int i = rb + quad;
+                Zc Br[16];
+                Zc acc{0.0, 0.0};
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int j = part + 4 * t;
+                    Br[t] = (act && j < len) ? A.get(i, r + j) : Zc{0.0, 0.0};
+                    zfma(acc, Br[t], v[j]);
+                }
+                const Zc y = zmul(tau, quad_sum_z(acc));
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int j = part + 4 * t;
+                    if (act && j < len) {
+                        Zc a = Br[t];
+                        const Zc yv = zmul(y, zconj(v[j]));
+                        a.re -= yv.re;
+                        a.im -= yv.im;
+                        A.set_lower(i, r + j, a);
+                    }
+                }
+            }
+            // ---- diagonal block: p = tau A v, K = conj(tau)/2 v^H p, q = p - K v,
+            //      A -= q v^H + v q^H on the lower triangle
+            Zc Dr[16];
+            Zc pa{0.0, 0.0};
+            const bool actd = quad < len;
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const int j = part + 4 * t;
+                Dr[t] = (actd && j < len) ? A.get(r + quad, r + j) : Zc{0.0, 0.0};
+                zfma(pa, Dr[t], v[j]);
+            }
+            const Zc pi = zmul(tau, quad_sum_z(pa));
+            Zc vp{0.0, 0.0};
+            if (part == 0 && actd) zdotc(vp, v[quad], pi);
+            const double kre = block_sum(vp.re, red), kim = block_sum(vp.im, red);
+            const Zc K = zmul(Zc{0.5 * ctau.re, 0.5 * ctau.im}, Zc{kre, kim});
+            if (part == 0 && actd) {
+                const Zc kv = zmul(K, v[quad]);
+                q[quad] = Zc{pi.re - kv.re, pi.im - kv.im};
+            }
+            __syncthreads();
+            if (actd) {
+                const Zc vq = v[quad], qq = q[quad];
+#pragma unroll
+                for (int t = 0; t < 16; t++) {
+                    const int j = part + 4 * t;
+                    if (j < len && j <= quad) {
+                        const Zc t1 = zmul(qq, zconj(v[j])), t2 = zmul(vq, zconj(q[j]));
+                        A.set_lower(r + quad, r + j, Zc{Dr[t].re - t1.re - t2.re, Dr[t].im - t1.im - t2.im});
+                    }
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_rel(progress + (s - 1), k + 1);
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(kChaseThreads)
 chase_z(int n, int b, BandZ A, Zc *__restrict__ hh_v, Zc *__restrict__ hh_tau, ChaseState *state, int *progress,
         long long timeout_ns)
 {
-    __shared__ Zc v[64];
-    __shared__ Zc q[64];
-    __shared__ double red[kChaseThreads / 32];
-    __shared__ Zc s_tau, s_scal;
-    __shared__ int s_sweep, s_abort;
-    const int tid = threadIdx.x;
-    const int quad = tid >> 2, part = tid & 3;
-
+    __shared__ ChaseSmemZ sm;
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_sweep = 1 + atomicAdd(&state->ticket, 1);
+        if (threadIdx.x == 0) sm.s_sweep = 1 + atomicAdd(&state->ticket, 1);
         __syncthreads();
-        const int s = s_sweep;
+        const int s = sm.s_sweep;
         if (s > n - 1) return;
-        const int nk = sweep_count(n, b, s);
-        const int nk_prev = (s > 1) ? sweep_count(n, b, s - 1) : 0;
-        const long long first = sweep_first(n, b, s);
+        if (chase_sweep_z(n, b, A, hh_v, hh_tau, state, progress, timeout_ns, s, sm)) return;
+    }
+}
 
-        for (int k = 0; k < nk; k++) {
-            if (tid == 0) {
-                int abort = 0;
-                if (s > 1) {
-                    const int need = min(k + kLag, nk_prev);
-                    const unsigned long long t0 = now_ns();
-                    while (ld_acq(progress + (s - 2)) < need) {
-                        if (*(volatile int *)&state->abort) { abort = 1; break; }
-                        if ((long long)(now_ns() - t0) > timeout_ns) {
-                            atomicExch(&state->error, GB_ERR_TIMEOUT);
-                            atomicExch(&state->abort, 1);
-                            abort = 1;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                } else if (*(volatile int *)&state->abort) {
-                    abort = 1;
-                }
-                s_abort = abort;
-            }
-            __syncthreads();
-            if (s_abort) return;
-
-            const int r = s + k * b;
-            const int len = min(b, n - r);
-            const int c = (k == 0) ? s - 1 : s + (k - 1) * b;
-            const int rb = r + len;
-            const int nleft = r - c - 1, nbelow = min(b, n - rb);
-            const long long idx = first + k;
-
-            // ---- reflector (complex, beta real)
-            const Zc xi = (tid >= 1 && tid < len) ? A.get(r + tid, c) : Zc{0.0, 0.0};
-            const double ss = block_sum(xi.re * xi.re + xi.im * xi.im, red);
-            if (tid == 0) {
-                const Zc alpha = A.get(r, c);
-                Zc tau{0.0, 0.0}, scal{0.0, 0.0};
-                if (!(ss == 0.0 && alpha.im == 0.0)) {
-                    const double nrm = sqrt(alpha.re * alpha.re + alpha.im * alpha.im + ss);
-                    const double beta = (alpha.re >= 0.0) ? -nrm : nrm;
-                    tau = {(beta - alpha.re) / beta, -alpha.im / beta};
-                    const Zc den{alpha.re - beta, alpha.im};           // 1 / (alpha - beta)
-                    const double dd = den.re * den.re + den.im * den.im;
-                    scal = {den.re / dd, -den.im / dd};
-                    A.set_lower(r, c, Zc{beta, 0.0});
-                }
-                s_tau = tau;
-                s_scal = scal;
-                hh_tau[idx] = tau;
-            }
-            __syncthreads();
-            const Zc tau = s_tau;
-            const bool active = !(tau.re == 0.0 && tau.im == 0.0);
-            Zc vt{0.0, 0.0};
-            if (tid == 0) vt = {1.0, 0.0};
-            else if (tid < len && active) vt = zmul(xi, s_scal);
-            if (tid < 64) v[tid] = vt;
-            if (tid < b) hh_v[idx * b + tid] = vt;
-            if (active && tid >= 1 && tid < len) A.set_lower(r + tid, c, Zc{0.0, 0.0});
-            __syncthreads();
-
-            if (active) {
-                const Zc ctau = zconj(tau);
-                // ---- left block: A[R,j] -= conj(tau) v (v^H A[R,j])
-                {
-                    const bool act = quad < nleft;
-                    const int j = c + 1 + quad;
-                    Zc Lr[16];
-                    Zc acc{0.0, 0.0};
-#pragma unroll
-                    for (int t = 0; t < 16; t++) {
-                        const int i = part + 4 * t;
-                        Lr[t] = (act && i < len) ? A.get(r + i, j) : Zc{0.0, 0.0};
-                        zdotc(acc, v[i], Lr[t]);
-                    }
-                    const Zc w = zmul(ctau, quad_sum_z(acc));
-#pragma unroll
-                    for (int t = 0; t < 16; t++) {
-                        const int i = part + 4 * t;
-                        if (act && i < len) {
-                            Zc a = Lr[t];
-                            const Zc vw = zmul(v[i], w);
-                            a.re -= vw.re;
-                            a.im -= vw.im;
-                            A.set_lower(r + i, j, a);
-                        }
-                    }
-                }
-                // ---- below block: A[i,R] -= tau (A[i,R] v) v^H
-                {
-                    const bool act = quad < nbelow;
-                    const int i = rb + quad;
-                    Zc Br[16];
-                    Zc acc{0.0, 0.0};
-#pragma unroll
-                    for (int t = 0; t < 16; t++) {
-                        const int j = part + 4 * t;
-                        Br[t] = (act && j < len) ? A.get(i, r + j) : Zc{0.0, 0.0};
-                        zfma(acc, Br[t], v[j]);
-                    }
-                    const Zc y = zmul(tau, quad_sum_z(acc));
-#pragma unroll
-                    for (int t = 0; t < 16; t++) {
-                        const int j = part + 4 * t;
-                        if (act && j < len) {
-                            Zc a = Br[t];
-                            const Zc yv = zmul(y, zconj(v[j]));
-                            a.re -= yv.re;
-                            a.im -= yv.im;
-                            A.set_lower(i, r + j, a);
-                        }
-                    }
-                }
-                // ---- diagonal block: p = tau A v, K = conj(tau)/2 v^H p, q = p - K v,
-                //      A -= q v^H + v q^H on the lower triangle
-                Zc Dr[16];
-                Zc pa{0.0, 0.0};
-                const bool actd = quad < len;
-#pragma unroll
-                for (int t = 0; t < 16; t++) {
-                    const int j = part + 4 * t;
-                    Dr[t] = (actd && j < len) ? A.get(r + quad, r + j) : Zc{0.0, 0.0};
-                    zfma(pa, Dr[t], v[j]);
-                }
-                const Zc pi = zmul(tau, quad_sum_z(pa));
-                Zc vp{0.0, 0.0};
-                if (part == 0 && actd) zdotc(vp, v[quad], pi);
-                const double kre = block_sum(vp.re, red), kim = block_sum(vp.im, red);
-                const Zc K = zmul(Zc{0.5 * ctau.re, 0.5 * ctau.im}, Zc{kre, kim});
-                if (part == 0 && actd) {
-                    const Zc kv = zmul(K, v[quad]);
-                    q[quad] = Zc{pi.re - kv.re, pi.im - kv.im};
-                }
-                __syncthreads();
-                if (actd) {
-                    const Zc vq = v[quad], qq = q[quad];
-#pragma unroll
-                    for (int t = 0; t < 16; t++) {
-                        const int j = part + 4 * t;
-                        if (j < len && j <= quad) {
-                            const Zc t1 = zmul(qq, zconj(v[j])), t2 = zmul(vq, zconj(q[j]));
-                            A.set_lower(r + quad, r + j, Zc{Dr[t].re - t1.re - t2.re, Dr[t].im - t1.im - t2.im});
-                        }
-                    }
-                }
-            }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) st_rel(progress + (s - 1), k + 1);
-        }
+// The Hermitian chases of many problems in one launch (the ticket order of
+// chase_batched_d); the table's W, hh_v, hh_tau point at complex data.
+__global__ void __launch_bounds__(kChaseThreads)
+chase_batched_z(int count, int smax, const ChaseProblem *__restrict__ probs, ChaseState *state, long long timeout_ns)
+{
+    __shared__ ChaseSmemZ sm;
+    const long long total = (long long)count * smax;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sm.s_sweep = atomicAdd(&state->ticket, 1);
+        __syncthreads();
+        const long long t = sm.s_sweep;
+        if (t >= total) return;
+        const ChaseProblem pr = probs[t % count];
+        const int s = 1 + (int)(t / count);
+        if (s > pr.n - 1) continue;
+        if (chase_sweep_z(pr.n, pr.b, BandZ{(Zc *)pr.W, pr.ldw}, (Zc *)pr.hh_v, (Zc *)pr.hh_tau, state, pr.progress,
+                          timeout_ns, s, sm))
+            return;
     }
 }
 
@@ -561,8 +599,7 @@ static int chase_grid(int n, int b, int sms)
     return max(1, min(min(n - 1, sms), active));
 }
 
-cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
-                            double *hh_tau, void *ws, long long timeout_ns, cudaStream_t st)
+cudaError_t band_to_tridi_prepare_z(int n, int b, const double *AB, int ldab, void *ws, cudaStream_t st)
 {
     const long long ldw = 2LL * b;
     char *flags = (char *)ws;
@@ -570,7 +607,25 @@ cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d,
     cudaError_t err = cudaMemsetAsync(flags, 0, flags_bytes(n), st);
     if (err != cudaSuccess) return err;
     band_init_z<<<1024, 256, 0, st>>>(n, b, (const Zc *)AB, ldab, W, ldw);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    return cudaGetLastError();
+}
+
+cudaError_t band_to_tridi_finish_z(int n, int b, const void *ws, double *d, double *e, cudaStream_t st)
+{
+    const long long ldw = 2LL * b;
+    const Zc *W = (const Zc *)((const char *)ws + flags_bytes(n));
+    band_extract_z<<<64, 256, 0, st>>>(n, W, ldw, d, e);
+    return cudaGetLastError();
+}
+
+cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,
+                            double *hh_tau, void *ws, long long timeout_ns, cudaStream_t st)
+{
+    const long long ldw = 2LL * b;
+    char *flags = (char *)ws;
+    Zc *W = (Zc *)(flags + flags_bytes(n));
+    cudaError_t err = band_to_tridi_prepare_z(n, b, AB, ldab, ws, st);
+    if (err != cudaSuccess) return err;
     if (n > 1) {
         int dev = 0, sms = 0;
         if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
@@ -580,8 +635,7 @@ cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d,
                                                          (ChaseState *)flags, (int *)(flags + 256), timeout_ns);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    band_extract_z<<<64, 256, 0, st>>>(n, W, ldw, d, e);
-    return cudaGetLastError();
+    return band_to_tridi_finish_z(n, b, ws, d, e, st);
 }
 
 cudaError_t band_to_tridi_prepare_d(int n, int b, const double *AB, int ldab, void *ws, cudaStream_t st)
@@ -651,7 +705,14 @@ cudaError_t band_to_tridi_chase_batched_upload_d(int count, const int *n, const 
                            cudaMemcpyHostToDevice, st);
 }
 
-cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, void *table, long long timeout_ns, cudaStream_t st)
+cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, const int *b, void *table, long long timeout_ns,
+                                          cudaStream_t st)
+{
+    return band_to_tridi_chase_batched(count, n, b, table, timeout_ns, st, 0);
+}
+
+cudaError_t band_to_tridi_chase_batched(int count, const int *n, const int *b, void *table, long long timeout_ns,
+                                        cudaStream_t st, int is_complex)
 {
     int smax = 0;
     for (int i = 0; i < count; i++) smax = max(smax, n[i] - 1);
@@ -660,13 +721,22 @@ cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, void *table, 
     cudaError_t err;
     if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
     if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chase_batched_d, kChaseThreads, 0)) !=
-        cudaSuccess)
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, is_complex ? (const void *)chase_batched_z
+                                                                                 : (const void *)chase_batched_d,
+                                                             kChaseThreads, 0)) != cudaSuccess)
         return err;
+    // no more blocks than the problems' sweeps that can be in flight at once
+    // (as for one problem): extra blocks would only poll, holding SM slots
+    // that work on other streams could use
+    long long active = 0;
+    for (int i = 0; i < count; i++) active += chase_grid(n[i], b[i], sms);
     const long long tickets = (long long)count * smax;
-    const long long grid = min((long long)sms * max(per_sm, 1), tickets);
-    chase_batched_d<<<(unsigned)grid, kChaseThreads, 0, st>>>(count, smax, (const ChaseProblem *)((char *)table + 256),
-                                                              (ChaseState *)table, timeout_ns);
+    const long long grid = min(min((long long)sms * max(per_sm, 1), tickets), max(active, 1LL));
+    const ChaseProblem *tab = (const ChaseProblem *)((char *)table + 256);
+    if (is_complex)
+        chase_batched_z<<<(unsigned)grid, kChaseThreads, 0, st>>>(count, smax, tab, (ChaseState *)table, timeout_ns);
+    else
+        chase_batched_d<<<(unsigned)grid, kChaseThreads, 0, st>>>(count, smax, tab, (ChaseState *)table, timeout_ns);
     return cudaGetLastError();
 }
 

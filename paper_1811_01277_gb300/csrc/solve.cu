@@ -500,8 +500,12 @@ size_t gb_solve_workspace_bytes_z(int n, int nev, int nbw)
     return carve_z(n, nev, nbw, nullptr).total;
 }
 
-int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
-               size_t ws_bytes, void *stream, int flags)
+}  // extern "C"
+
+namespace {
+
+int solve_z_parts(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
+                  size_t ws_bytes, void *stream, int flags, int parts)
 {
     if (n < 2) return -1;
     if (nev < 1 || nev > n) return -2;
@@ -536,15 +540,17 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     C *Aw = (C *)w.Aw, *Y = (C *)w.Y, *YT = (C *)w.YT, *X = (C *)w.X, *Pm = (C *)w.Pm, *M = (C *)w.M,
       *G = (C *)w.G, *S = (C *)w.S, *S2 = (C *)w.S2, *Zc = (C *)Z;
 
+    const int P = b < n ? (n - 1) / b : 0;  // panels of full -> band
+    if (parts & kPartFront) {
     // ---- full -> band: A2 <- Q^H A2 Q, Q = I - Y T Y^H
     GB_CU(cudaMemcpy2DAsync(Aw, (size_t)n * 16, A, (size_t)lda * 16, (size_t)n * 16, n, cudaMemcpyDeviceToDevice, st));
-    int P = 0;
-    for (int j = 0; j + b < n; j += b, P++) {
+    int pp = 0;
+    for (int j = 0; j + b < n; j += b, pp++) {
         const int m = n - j - b;
         C *panel = Aw + (long long)j * ldw + (j + b);
         C *A2 = Aw + (long long)(j + b) * ldw + (j + b);
-        double *tau = w.tauP + (long long)P * b * 2;
-        C *T = (C *)(w.Tall + (long long)P * b * b * 2);
+        double *tau = w.tauP + (long long)pp * b * 2;
+        C *T = (C *)(w.Tall + (long long)pp * b * b * 2);
         GB_CU(gb::zpanel_qr(m, b, (double *)panel, ldw, tau, w.part, st));
         GB_CU(gb::zpanel_y(m, b, (const double *)panel, ldw, (double *)Y, m, st));
         GB_CU(zg('C', 'N', b, b, m, one, Y, m, Y, m, zero, G, b, 0));
@@ -568,9 +574,12 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
         }
     }
     GB_CU(gb::zband_from_full(n, b, (const double *)Aw, ldw, w.AB, b + 1, st));
+    }
 
     // ---- band -> tridiagonal (complex reflectors, real T)
-    GB_CU(gb::band_to_tridi_z(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, 10LL * 1000 * 1000 * 1000, st));
+    if (parts & kPartChase)
+        GB_CU(gb::band_to_tridi_z(n, b, w.AB, b + 1, w.d, w.e, w.hv, w.ht, w.chase, 10LL * 1000 * 1000 * 1000, st));
+    if (!(parts & kPartBack)) return GB_OK;
 
     // ---- real tridiagonal eigenpairs (divide and conquer, or bisection,
     // inverse iteration and Newton-Schulz), promoted to complex Z
@@ -615,6 +624,94 @@ int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, do
     }
     GB_CU(cudaGetLastError());
     return GB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gb_solve_z(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz, void *workspace,
+               size_t ws_bytes, void *stream, int flags)
+{
+    return solve_z_parts(n, nev, nbw, A, lda, ev, Z, ldz, workspace, ws_bytes, stream, flags,
+                         kPartFront | kPartChase | kPartBack);
+}
+
+// ---- the solve in three calls, so that a server can run one stage for
+// several requests at once (the bulge chases in one launch)
+
+size_t gb_solve_stage_table_bytes(int count) { return count >= 1 ? gb::chase_batched_table_bytes(count) : 0; }
+
+int gb_solve_stage_front(int is_complex, int n, int nev, int nbw, const double *A, int lda, void *workspace,
+                         size_t ws_bytes, void *stream)
+{
+    const cudaStream_t st = (cudaStream_t)stream;
+    // ev and Z are not touched by the front; any aligned non-null pointer passes the checks
+    double *dummy = (double *)workspace;
+    int rc;
+    if (is_complex) {
+        rc = solve_z_parts(n, nev, nbw, A, lda, dummy, dummy, n, workspace, ws_bytes, stream, 0, kPartFront);
+        if (rc != GB_OK) return rc;
+        const SolveWsZ w = carve_z(n, nev, nbw, (char *)workspace);
+        return gb::band_to_tridi_prepare_z(n, nbw, w.AB, nbw + 1, w.chase, st) == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+    }
+    rc = solve_d_parts(n, nev, nbw, A, lda, dummy, dummy, n, workspace, ws_bytes, stream, 0, kPartFront);
+    if (rc != GB_OK) return rc;
+    const SolveWs w = carve(n, nev, nbw, (char *)workspace);
+    return gb::band_to_tridi_prepare_d(n, nbw, w.AB, nbw + 1, w.chase, st) == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+int gb_solve_stage_chase_batched(int is_complex, int count, const int *n, const int *nev, const int *nbw,
+                                 void *const *workspaces, void *table, size_t table_bytes, void *stream)
+{
+    if (count < 1) return -2;
+    if (!n || !nev || !nbw) return -3;
+    if (!workspaces) return -6;
+    if (!table || ((uintptr_t)table % 256) != 0) return -7;
+    if (table_bytes < gb_solve_stage_table_bytes(count)) return -8;
+    std::vector<void *> cws((size_t)count);
+    std::vector<double *> hv((size_t)count), ht((size_t)count);
+    for (int i = 0; i < count; i++) {
+        if (!workspaces[i]) return -6;
+        if (is_complex) {
+            const SolveWsZ w = carve_z(n[i], nev[i], nbw[i], (char *)workspaces[i]);
+            cws[i] = w.chase;
+            hv[i] = w.hv;
+            ht[i] = w.ht;
+        } else {
+            const SolveWs w = carve(n[i], nev[i], nbw[i], (char *)workspaces[i]);
+            cws[i] = w.chase;
+            hv[i] = w.hv;
+            ht[i] = w.ht;
+        }
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (gb::band_to_tridi_chase_batched_upload_d(count, n, nbw, cws.data(), hv.data(), ht.data(), table, st) !=
+        cudaSuccess)
+        return GB_ERR_CUDA;
+    return gb::band_to_tridi_chase_batched(count, n, nbw, table, 10LL * 1000 * 1000 * 1000, st, is_complex) == cudaSuccess
+               ? GB_OK
+               : GB_ERR_CUDA;
+}
+
+int gb_solve_stage_back(int is_complex, int n, int nev, int nbw, double *ev, double *Z, int ldz, void *workspace,
+                        size_t ws_bytes, void *stream, int flags)
+{
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (n < 2 || nbw < 1 || nbw > 64 || nbw >= n || nev < 1 || nev > n) return -2;
+    if (!workspace || ((uintptr_t)workspace % 256) != 0) return -7;
+    if (is_complex) {
+        const SolveWsZ w = carve_z(n, nev, nbw, (char *)workspace);
+        if (ws_bytes < w.total) return -8;
+        if (gb::band_to_tridi_finish_z(n, nbw, w.chase, w.d, w.e, st) != cudaSuccess) return GB_ERR_CUDA;
+        return solve_z_parts(n, nev, nbw, (const double *)workspace, n, ev, Z, ldz, workspace, ws_bytes, stream,
+                             flags, kPartBack);
+    }
+    const SolveWs w = carve(n, nev, nbw, (char *)workspace);
+    if (ws_bytes < w.total) return -8;
+    if (gb::band_to_tridi_finish_d(n, nbw, w.chase, w.d, w.e, st) != cudaSuccess) return GB_ERR_CUDA;
+    return solve_d_parts(n, nev, nbw, (const double *)workspace, n, ev, Z, ldz, workspace, ws_bytes, stream, flags,
+                         kPartBack);
 }
 
 int gb_solve_query_z(const void *workspace, int n, int nev, int nbw, void *stream)
@@ -1029,7 +1126,7 @@ int gb_solve_batched_staged_d(int count, const int *n, const int *nev, const int
         if (cudaEventRecord(evs[s], (cudaStream_t)streams[s]) != cudaSuccess ||
             cudaStreamWaitEvent(st0, evs[s], 0) != cudaSuccess)
             rc = GB_ERR_CUDA;
-    if (rc == GB_OK && gb::band_to_tridi_chase_batched_d(count, n, base, 10LL * 1000 * 1000 * 1000, st0) != cudaSuccess)
+    if (rc == GB_OK && gb::band_to_tridi_chase_batched_d(count, n, bw.data(), base, 10LL * 1000 * 1000 * 1000, st0) != cudaSuccess)
         rc = GB_ERR_CUDA;
     if (rc == GB_OK && cudaEventRecord(evs[0], st0) != cudaSuccess) rc = GB_ERR_CUDA;
     for (int s = 1; rc == GB_OK && s < nthreads; s++)

@@ -45,7 +45,12 @@ size_t chase_batched_table_bytes(int count);
 cudaError_t band_to_tridi_chase_batched_upload_d(int count, const int *n, const int *b, void *const *ws,
                                                  double *const *hh_v, double *const *hh_tau, void *table,
                                                  cudaStream_t st);
-cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, void *table, long long timeout_ns, cudaStream_t st);
+cudaError_t band_to_tridi_chase_batched_d(int count, const int *n, const int *b, void *table, long long timeout_ns,
+                                          cudaStream_t st);
+cudaError_t band_to_tridi_chase_batched(int count, const int *n, const int *b, void *table, long long timeout_ns,
+                                        cudaStream_t st, int is_complex);
+cudaError_t band_to_tridi_prepare_z(int n, int b, const double *AB, int ldab, void *ws, cudaStream_t st);
+cudaError_t band_to_tridi_finish_z(int n, int b, const void *ws, double *d, double *e, cudaStream_t st);
 
 size_t band_to_tridi_workspace_bytes_z(int n, int b);
 cudaError_t band_to_tridi_z(int n, int b, const double *AB, int ldab, double *d, double *e, double *hh_v,

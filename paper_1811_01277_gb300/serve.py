@@ -9,6 +9,15 @@ memory (workspace and outputs) fits in the HBM budget; admitted requests run
 concurrently on their streams, so new work overlaps work already on the GPU.
 Completion is detected with CUDA events; latency = completion - arrival.
 
+With stage_batching the server also batches one stage across requests: each
+admitted request runs its first stage (full -> band) on its slot, and the
+bulge chases of every request whose first stage has finished run together
+in one persistent launch on one of a few chase lanes (streams); each request
+then runs its remaining stages on its slot again.  The results are
+bit-identical to the one-call solve.  Merging pays little when the requests'
+chases already overlap on their own streams; it pays when more problems are
+ready at once than there are streams.
+
 All numerical work happens in the library's C entry points
 (gb_solve_d / gb_solve_z); this module only schedules.
 """
@@ -36,6 +45,8 @@ class Request:
     _ws: torch.Tensor = None
     _ready: torch.cuda.Event = None   # recorded on the submitting stream: A is written
     _end: torch.cuda.Event = None
+    _front: torch.cuda.Event = None
+    _phase: str = None          # stage batching: "front", "chase_wait", "chase", "back"
     _slot: int = None
     _bytes: int = 0
 
@@ -58,9 +69,19 @@ def request_bytes(n, nev, cplx, nbw):
 
 
 class EigenServer:
-    def __init__(self, slots=4, hbm_budget_bytes=64 << 30, device=0):
+    def __init__(self, slots=4, hbm_budget_bytes=64 << 30, device=0, stage_batching=False, chase_lanes=4):
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.stage_batching = stage_batching
+        if stage_batching:
+            # chase lanes: up to chase_lanes merged chase launches in flight,
+            # each on its own stream with its own problem table, so a long
+            # chase does not hold back the requests that become ready after it
+            self.table_bytes = gb.gb_solve_stage_table_bytes(slots)
+            self.lanes = [{"stream": torch.cuda.Stream(device=self.device),
+                           "table": torch.zeros(self.table_bytes, dtype=torch.uint8, device=self.device),
+                           "batch": [], "end": None} for _ in range(max(1, chase_lanes))]
+            self.chase_sizes = []       # requests per chase launch
         self.free = collections.deque(range(slots))
         self.budget = hbm_budget_bytes
         self.in_use = 0
@@ -104,17 +125,72 @@ class EigenServer:
             st.wait_event(req._ready)
             req.A.record_stream(st)
             req.start = self.now()
-            req.status = f(req.n, req.nev, req.nbw, req.A, req.n, req.ev, req.Z, req.n, req._ws, wsb, st, 0,
-                           check=False)
-            req._end = torch.cuda.Event()
-            req._end.record(st)
+            if self.stage_batching:
+                req.status = gb.gb_solve_stage_front(req.complex, req.n, req.nev, req.nbw, req.A, req.n, req._ws, wsb,
+                                                     st, check=False)
+                req._front = torch.cuda.Event()
+                req._front.record(st)
+                req._phase = "front"
+            else:
+                req.status = f(req.n, req.nev, req.nbw, req.A, req.n, req.ev, req.Z, req.n, req._ws, wsb, st, 0,
+                               check=False)
+                req._end = torch.cuda.Event()
+                req._end.record(st)
             req._slot, req._bytes = slot, need
             self.in_use += need
             self.active.append(req)
 
+    def _advance(self):
+        """Stage batching: start the backs of every finished chase launch,
+        then merge the chases of all requests whose front is done (one kind
+        of data per launch) into one launch on a free chase lane."""
+        for lane in self.lanes:
+            if lane["end"] is not None and lane["end"].query():
+                status = gb.gb_trans_ev_query(lane["table"], 256, lane["stream"])
+                for req in lane["batch"]:
+                    st = self.streams[req._slot]
+                    st.wait_event(lane["end"])
+                    wsb = (gb.gb_solve_workspace_bytes_z if req.complex else gb.gb_solve_workspace_bytes)(
+                        req.n, req.nev, req.nbw)
+                    rc = gb.gb_solve_stage_back(req.complex, req.n, req.nev, req.nbw, req.ev, req.Z, req.n, req._ws,
+                                                wsb, st, check=False)
+                    if req.status == gb.GB_OK:
+                        req.status = status if status != gb.GB_OK else rc
+                    req._end = torch.cuda.Event()
+                    req._end.record(st)
+                    req._phase = "back"
+                lane["batch"], lane["end"] = [], None
+        for req in self.active:
+            if req._phase == "front" and req._front.query():
+                req._phase = "chase_wait"
+        for lane in self.lanes:
+            if lane["end"] is not None:
+                continue
+            ready = [r for r in self.active if r._phase == "chase_wait"]
+            if not ready:
+                break
+            kind = ready[0].complex
+            batch = [r for r in ready if r.complex == kind]
+            for r in batch:                 # done already; the wait orders their writes before the chase
+                lane["stream"].wait_event(r._front)
+            rc = gb.gb_solve_stage_chase_batched(kind, [r.n for r in batch], [r.nev for r in batch],
+                                                 [r.nbw for r in batch], [r._ws for r in batch], lane["table"],
+                                                 self.table_bytes, lane["stream"], check=False)
+            for r in batch:
+                r._phase = "chase"
+                if r.status == gb.GB_OK:
+                    r.status = rc
+            lane["end"] = torch.cuda.Event()
+            lane["end"].record(lane["stream"])
+            lane["batch"] = batch
+            self.chase_sizes.append(len(batch))
+
     def _reap(self):
         still = []
         for req in self.active:
+            if req._phase in ("front", "chase_wait", "chase"):
+                still.append(req)
+                continue
             if req._end.query():
                 req.done = self.now()
                 q = (gb.gb_solve_query_z if req.complex else gb.gb_solve_query)(
@@ -130,6 +206,8 @@ class EigenServer:
         self.active = still
 
     def poll(self):
+        if self.stage_batching:
+            self._advance()
         self._reap()
         self._admit()
 

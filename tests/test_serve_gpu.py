@@ -128,3 +128,61 @@ def test_matrix_built_on_the_device_right_before_submit(serve):
         lamj = np.sort(lam + 1e-3 * r.rid * mu)
         M = (A0 + (1e-3 * r.rid) * E).cpu().numpy().T
         check(M, r.ev.cpu().numpy(), r.Z.cpu().numpy().T, lamj)
+
+
+def test_stage_batching_equals_one_call_solves(serve):
+    """With stage batching the bulge chases of the requests whose first
+    stage has finished run in one launch; every result is bit-identical to
+    the one-call solve of the same request, and matches its spectrum."""
+    import paper_1811_01277_gb300 as m
+    reqs, (mats, spectra) = make_requests(serve)
+    srv = serve.EigenServer(slots=6, stage_batching=True)
+    done = srv.run(reqs)
+    assert len(done) == len(reqs) and all(r.status == 0 for r in done)
+    assert max(srv.chase_sizes) >= 2 and sum(srv.chase_sizes) == len(reqs)   # chases were merged
+    dev = torch.device("cuda")
+    for r in done:
+        n, nev = r.n, r.nev
+        wsb = m.gb_solve_workspace_bytes_z(n, nev, r.nbw)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        ev = torch.empty(nev, dtype=torch.float64, device=dev)
+        Z = torch.empty((nev, n), dtype=torch.complex128, device=dev)
+        st = torch.cuda.current_stream()
+        m.gb_solve_z(n, nev, r.nbw, r.A, n, ev, Z, n, ws, wsb, st, 0)
+        assert m.gb_solve_query_z(ws, n, nev, r.nbw, st) == 0
+        assert torch.equal(ev, r.ev) and torch.equal(Z, r.Z)
+        check(mats[r.rid], r.ev.cpu().numpy(), r.Z.cpu().numpy().T, spectra[r.rid])
+
+
+def test_stage_api_real_equals_one_call(serve):
+    """gb_solve_stage_front / _chase_batched / _back on three real problems
+    (their chases in one launch) give the same bits as gb_solve_d."""
+    import paper_1811_01277_gb300 as m
+    dev = torch.device("cuda")
+    st = torch.cuda.current_stream()
+    probs = []
+    for k, (n, nev, nbw) in enumerate([(300, 300, 32), (520, 100, 64), (200, 60, 16)]):
+        M = inputs.band_symmetric(n, n, seed=70 + k, dist="normal")
+        A = torch.from_numpy(np.ascontiguousarray(M.T)).to(dev)
+        wsb = m.gb_solve_workspace_bytes(n, nev, nbw)
+        probs.append((n, nev, nbw, A, wsb, torch.empty(wsb, dtype=torch.uint8, device=dev)))
+    for n, nev, nbw, A, wsb, ws in probs:
+        m.gb_solve_stage_front(0, n, nev, nbw, A, n, ws, wsb, st)
+    tb = m.gb_solve_stage_table_bytes(len(probs))
+    table = torch.empty(tb, dtype=torch.uint8, device=dev)
+    m.gb_solve_stage_chase_batched(0, [p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
+                                   [p[5] for p in probs], table, tb, st)
+    outs = []
+    for n, nev, nbw, A, wsb, ws in probs:
+        ev = torch.empty(nev, dtype=torch.float64, device=dev)
+        Z = torch.empty((nev, n), dtype=torch.float64, device=dev)
+        m.gb_solve_stage_back(0, n, nev, nbw, ev, Z, n, ws, wsb, st)
+        outs.append((ev, Z))
+    assert m.gb_trans_ev_query(table, 256, st) == 0
+    for (n, nev, nbw, A, wsb, ws), (ev, Z) in zip(probs, outs):
+        ws1 = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        ev1 = torch.empty(nev, dtype=torch.float64, device=dev)
+        Z1 = torch.empty((nev, n), dtype=torch.float64, device=dev)
+        m.gb_solve_d(n, nev, nbw, A, n, ev1, Z1, n, ws1, wsb, st, 0)
+        torch.cuda.synchronize()
+        assert torch.equal(ev, ev1) and torch.equal(Z, Z1)
