@@ -949,8 +949,15 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
                 "p50_ms": float(np.percentile(sper, 50)), "p99_ms": float(np.percentile(sper, 99)),
                 "workspace_gb": swsb / 1e9, "status": status, "clocks": sclk}
 
-    staged_default = staged_form(None)
-    graph_default = graph_form(None)
+    def guarded(f, *a):
+        # the extra forms must not take the stream form's line down with them
+        try:
+            return f(*a)
+        except Exception as exc:          # noqa: BLE001 -- reported in the line
+            return {"error": f"{type(exc).__name__}: {exc}"}
+
+    staged_default = guarded(staged_form, None)
+    graph_default = guarded(graph_form, None)
     # a trial is a mini-batch: one problem of the class's order per stream,
     # all solved at once with the trial's band width (the batch's throughput,
     # not a lone solve's latency, is what the choice has to serve)
@@ -982,8 +989,9 @@ def measure_batched(count, lo, hi, nstreams, steps=1, warmup=1, plain_every=8):
         del At, evt, Zt_, tws
     tuned_nbw = [gb.gb_solve_tuner_nbw(tuner, n_) for n_ in sizes]
     gb.gb_solve_tuner_destroy(tuner)
-    graph_tuned = graph_form(tuned_nbw)
-    staged_tuned = staged_form(tuned_nbw)
+    graph_tuned = guarded(graph_form, tuned_nbw)
+    staged_tuned = guarded(staged_form, tuned_nbw)
+    graph_tuned.setdefault("tuner", {})
     graph_tuned["tuner"] = {"classes": 4, "trials": trials,
                             "chosen": sorted({(n_, b_) for n_, b_ in zip(sizes, tuned_nbw)})[::max(1, count // 16)]}
     out = {
