@@ -145,3 +145,51 @@ def test_device_arguments_refuse_host_memory(lib):
         gb.gb_solve_batched_d([4], [4], [h], [4], [h], [h], [4], None, 0, [0], check=False)
     # argument checks on raw addresses still reach the library
     assert gb.gb_trans_ev_tridi_to_band_d(10, 3, 2, 256, 256, 256, 9, check=False) == -7
+
+
+def test_newer_entry_points_check_arguments_host_only(lib):
+    """The divide-and-conquer, refinement, stage, staged-batch and graph entry
+    points reject bad arguments with -i before touching a GPU, and their
+    workspace queries are host arithmetic."""
+    dc = gb.gb_tridiag_dc_d
+    assert dc(0, 256, 256, 256, 256, 1, 256, 1 << 30, None, check=False) == -1
+    assert dc(4, None, 256, 256, 256, 4, 256, 1 << 30, None, check=False) == -2
+    assert dc(4, 256, None, 256, 256, 4, 256, 1 << 30, None, check=False) == -3
+    assert dc(4, 256, 256, None, 256, 4, 256, 1 << 30, None, check=False) == -4
+    assert dc(4, 256, 256, 256, None, 4, 256, 1 << 30, None, check=False) == -5
+    assert dc(4, 256, 256, 256, 256, 3, 256, 1 << 30, None, check=False) == -6
+    assert dc(4, 256, 256, 256, 256, 4, None, 1 << 30, None, check=False) == -7
+    assert dc(4, 256, 256, 256, 256, 4, 256, 8, None, check=False) == -8
+    assert gb.gb_tridiag_dc_workspace_bytes(0) == 0
+    assert gb.gb_tridiag_dc_workspace_bytes(1000) >= 3 * 1000 * 1000 * 8
+    rf = gb.gb_refine_syev_d
+    assert rf(0, 256, 1, 256, 256, 1, 256, 1 << 30, None, check=False) == -1
+    assert rf(4, None, 4, 256, 256, 4, 256, 1 << 30, None, check=False) == -2
+    assert rf(4, 256, 3, 256, 256, 4, 256, 1 << 30, None, check=False) == -3
+    assert rf(4, 256, 4, None, 256, 4, 256, 1 << 30, None, check=False) == -4
+    assert rf(4, 256, 4, 256, None, 4, 256, 1 << 30, None, check=False) == -5
+    assert rf(4, 256, 4, 256, 256, 3, 256, 1 << 30, None, check=False) == -6
+    assert rf(4, 256, 4, 256, 256, 4, None, 1 << 30, None, check=False) == -7
+    assert rf(4, 256, 4, 256, 256, 4, 256, 8, None, check=False) == -8
+    assert gb.gb_refine_syev_workspace_bytes(100) >= 4 * 100 * 100 * 8
+    # the solve in three calls
+    assert gb.gb_solve_stage_front(0, 1, 1, 1, 256, 1, 256, 1 << 30, None, check=False) == -1
+    assert gb.gb_solve_stage_front(1, 100, 10, 100, 256, 100, 256, 1 << 30, None, check=False) == -3
+    assert gb.gb_solve_stage_back(0, 1, 1, 1, 256, 256, 1, 256, 1 << 30, None, check=False) == -2
+    assert gb.gb_solve_stage_back(0, 100, 10, 16, 256, 256, 100, None, 1 << 30, None, check=False) == -7
+    assert gb.gb_solve_stage_table_bytes(0) == 0 and gb.gb_solve_stage_table_bytes(3) > 256
+    ch = gb.gb_solve_stage_chase_batched
+    assert ch(0, [100], [10], [16], [256], None, 1 << 20, None, check=False) == -7
+    assert ch(0, [100], [10], [16], [256], 256, 16, None, check=False) == -8
+    # staged batch and graph: workspace checks come first
+    sizes, nevs, bws = [100, 200], [100, 50], [16, 32]
+    wsb = gb.gb_solve_batched_staged_workspace_bytes(sizes, nevs, bws, 2)
+    assert wsb > gb.gb_solve_batched_staged_workspace_bytes(sizes, nevs, bws, 1) > 0
+    assert gb.gb_solve_batched_staged_workspace_bytes(sizes, nevs, [16, 300], 1) == 0   # nbw >= n
+    args = (sizes, nevs, bws, [256, 256], sizes, [256, 256], [256, 256], sizes)
+    assert gb.gb_solve_batched_staged_d(*args, None, wsb, [0, 0], check=False) == -10
+    assert gb.gb_solve_batched_staged_d(*args, 256, wsb - 1, [0, 0], check=False) == -11
+    with pytest.raises(gb.GbError) as e:
+        gb.gb_solve_batched_graph_create(*args, None, 1 << 30, 2)
+    assert e.value.status == -10
+    assert gb.gb_solve_batched_graph_nodes(None) == -1
