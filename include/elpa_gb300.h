@@ -94,7 +94,7 @@ typedef struct gb_trans_ev_opts {
                             next group's wait must give up; 0 = off */
     int column_batch;    /* PIPELINE, PIPELINE_TC and PIPELINE_TC5: column blocks
                             per ticket batch, 1..1024 (0 = default: 16, 8 for
-                            PIPELINE_TC (64-column blocks), 4 for PIPELINE_TC5
+                            PIPELINE_TC (64-column blocks), 8 for PIPELINE_TC5
                             (128-column blocks)).  Items of one batch run
                             group after group; smaller batches keep fewer
                             eigenvector rows live in L2, larger ones read the

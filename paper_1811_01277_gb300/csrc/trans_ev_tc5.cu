@@ -73,7 +73,7 @@ constexpr int kCols5 = 128;       // eigenvector columns per work item (the MMA'
 constexpr int kThreads5 = 512;    // 16 warps: four per TMEM lane quarter (and per SM sub-partition)
 constexpr int kPlanes = 8;        // balanced base-256 digits of a 64-bit value
 constexpr int kLevels5 = 9;       // digit-pair levels 0..8
-constexpr int kColumnBatch5 = 4;  // 128-column blocks per ticket batch
+constexpr int kColumnBatch5 = 8;  // 128-column blocks per ticket batch (2 and 4 re-read the records more, 16 gains nothing)
 constexpr int kTmemCols = 512;
 constexpr unsigned long long kDigitBias = 0x8080808080808080ull;
 constexpr long long kMbarTimeoutNs = 2000000000ll;  // an MMA batch or a record copy takes microseconds
