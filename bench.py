@@ -1119,11 +1119,12 @@ def run_stage_trans_ev_z(args):
     for a, b in kev:          # the events exist once recorded
         a.record(st)
         b.record(st)
-    kopts = [{"kernel_begin_event": a.cuda_event, "kernel_end_event": b.cuda_event} for a, b in kev]
+    zopts = {"column_batch": args.column_batch} if args.column_batch else {}
+    kopts = [dict(zopts, kernel_begin_event=a.cuda_event, kernel_end_event=b.cuda_event) for a, b in kev]
 
     def step(i=None):
         gb.gb_trans_ev_tridi_to_band_z(n, nbw, nev, hv_d, ht_d, Zt, n, ws if wsb else None, wsb, st,
-                                       None if i is None else kopts[i])
+                                       (zopts or None) if i is None else kopts[i])
 
     for _ in range(args.warmup):
         step()
