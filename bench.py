@@ -1079,7 +1079,7 @@ def run_stage_refine(args):
         steps.append({"step": k, "seconds": r0.elapsed_time(r1) / 1e3, **accuracy(X, lam)})
     clocks = sampler.stop()
     step_s = min(x["seconds"] for x in steps[1:]) if len(steps) > 1 else None
-    flops = 7.0 * n ** 3
+    flops = 6.0 * n ** 3
     print(json.dumps({
         "stage": "refine", "metric": f"Ogita-Aishima refinement step vs the direct FP64 solve, n={n}, all eigenpairs",
         "n": n, "direct_fp64_solve_s": solve_s, "direct_accuracy": direct, "refine_steps": steps,
@@ -1089,6 +1089,86 @@ def run_stage_refine(args):
         "fp32_solve_budget_for_break_even_s": solve_s - 2 * step_s if step_s else None,
         "data": "synthetic: A = Q diag(uniform in [-1,1], runs of 8 spaced 1e-6) Q^T; FP32 start = FP64 eigenvectors rounded",
         "dtype": "f64", "clocks": clocks}))
+    return 0
+
+
+def run_stage_mixed(args):
+    """The mixed-precision configuration: gb_solve_mixed_d (all eigenpairs
+    with FP32 products in full -> band and band -> full, then FP64
+    Ogita-Aishima steps with Rayleigh-Ritz on clusters, the lowest nev
+    returned) timed beside the FP64 solve gb_solve_d on the same matrix,
+    A = Q diag(uniform [-1, 1], 10% in runs of 8 spaced 1e-6) Q^T; the
+    eigenvalue error against the prescribed spectrum, the residual and the
+    orthogonality of both, and of the mixed solve with no refinement step
+    (the low-precision half alone).  One solve per form, CUDA events."""
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    from paper_1811_01277_gb300 import inputs
+    gbuild.build()
+    gb.load()
+    n, nbw, K = args.mixed_n, 64, args.mixed_steps
+    nev = args.mixed_nev or n // 2
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    lam0 = torch.from_numpy(inputs.gapped_uniform_spectrum(n, seed=n)).to(dev)
+    A = prescribed_symmetric_gpu(lam0, 256, seed=n + 1, dev=dev)
+    u = 2.0 ** -53
+    nrmA = float(torch.linalg.norm(A))
+
+    def accuracy(ev, Z):
+        Zc = Z.T
+        dlam = float((ev - lam0[:nev]).abs().max() / lam0.abs().max())
+        R = A @ Zc - Zc * ev[None, :]
+        res = float(torch.linalg.norm(R) / nrmA)
+        del R
+        orth = float((Zc.T @ Zc - torch.eye(nev, dtype=torch.float64, device=dev)).abs().max())
+        return {"max_dlambda_over_norm": dlam, "residual_rel_fro": res, "orth_max": orth,
+                "within": bool(dlam <= 1e-11 and res <= 50 * n * u and orth <= 50 * n * u)}
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / 1e3
+
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    ev = torch.zeros(nev, dtype=torch.float64, device=dev)
+    Z = torch.zeros((nev, n), dtype=torch.float64, device=dev)
+    out = {"stage": "mixed", "n": n, "nev": nev, "nbw": nbw, "refine_steps": K}
+    wsb = gb.gb_solve_workspace_bytes(n, nev, nbw)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    if args.warmup:
+        gb.gb_solve_d(n, nev, nbw, A, n, ev, Z, n, ws, wsb, st, 0)
+    t = timed(lambda: gb.gb_solve_d(n, nev, nbw, A, n, ev, Z, n, ws, wsb, st, 0))
+    out["fp64_solve"] = {"seconds": t, "status": gb.gb_solve_query(ws, n, nev, nbw, st), **accuracy(ev, Z)}
+    del ws
+    torch.cuda.empty_cache()
+    wsb = gb.gb_solve_mixed_workspace_bytes(n, nev, nbw)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    runs = []
+    for steps in ([0, K] if K else [0]):
+        ev.zero_()
+        Z.zero_()
+        t = timed(lambda: gb.gb_solve_mixed_d(n, nev, nbw, A, n, ev, Z, n, steps, ws, wsb, st))
+        runs.append({"refine_steps": steps, "seconds": t, "status": gb.gb_solve_mixed_query(ws, n, nev, nbw, st),
+                     **accuracy(ev, Z)})
+    out["mixed_solve"] = runs
+    if K:
+        out["refine_step_s"] = (runs[1]["seconds"] - runs[0]["seconds"]) / K
+        out["mixed_over_fp64_time"] = runs[1]["seconds"] / out["fp64_solve"]["seconds"]
+    out.update({
+        "metric": f"mixed-precision solve s vs FP64 solve s, n={n}, nev={nev}",
+        "workspace_gb": {"fp64": gb.gb_solve_workspace_bytes(n, nev, nbw) / 1e9, "mixed": wsb / 1e9},
+        "data": "synthetic: A = Q diag(uniform [-1,1], 10% in runs of 8 spaced 1e-6) Q^T, Q a product of 256 "
+                "seeded Householders",
+        "dtype": "f64 (FP32 products in the mixed solve's reduction and back-transformation)",
+        "clocks": sampler.stop()})
+    print(json.dumps(out))
+    del ws, A, Z, ev
+    torch.cuda.empty_cache()
     return 0
 
 
@@ -1275,9 +1355,12 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="default stage: skip the solve and batched measurements that complete the metric")
     ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm",
-                                        "refine"],
+                                        "refine", "mixed"],
                     default="trans_ev")
     ap.add_argument("--refine-n", type=int, default=8192, help="refine stage: n (all eigenpairs)")
+    ap.add_argument("--mixed-n", type=int, default=8192, help="mixed stage: n")
+    ap.add_argument("--mixed-nev", type=int, default=0, help="mixed stage: nev (0: n/2)")
+    ap.add_argument("--mixed-steps", type=int, default=3, help="mixed stage: refinement steps")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-lo", type=int, default=128)
     ap.add_argument("--batch-hi", type=int, default=2048)
@@ -1314,6 +1397,8 @@ def main():
         return run_stage_batched(args)
     if args.stage == "refine":
         return run_stage_refine(args)
+    if args.stage == "mixed":
+        return run_stage_mixed(args)
     if args.stage == "trans_ev_z":
         return run_stage_trans_ev_z(args)
     if args.stage == "serve":

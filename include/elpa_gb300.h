@@ -246,16 +246,19 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
  *   step,
  *   tridiagonal -> band (gb_trans_ev_tridi_to_band_d, pipeline kernel),
  *   band -> full (block reflectors as matrix products).
- * All FP64 matrix products run in this library's DFMA-tiled kernels.
+ * Every matrix product runs in this library's own kernels (no vendor BLAS).
  * Arguments (device pointers): 1 n >= 2; 2 nev in 1..n; 3 nbw in 1..min(64,
  * n-1), the intermediate band width; 4 A (column-major, lda; read only, both
  * triangles used); 5 lda >= n; 6 ev (nev, ascending); 7 Z (n x nev,
  * column-major); 8 ldz >= n; 9 workspace (256-byte aligned); 10 ws_bytes >=
  * gb_solve_workspace_bytes(n, nev, nbw); 11 stream; 12 flags: 0 or an OR
  * of GB_SOLVE_RECORD_STAGES, GB_SOLVE_DFMA_PRODUCTS, GB_SOLVE_TRIDIAG_BISECT
- * (bisection and inverse iteration even when 2 nev > n) and
- * GB_SOLVE_FP64_EMULATED_GEMM (accepted and ignored: no product of either
- * solver goes through a vendor BLAS).  By
+ * (bisection and inverse iteration even when 2 nev > n),
+ * GB_SOLVE_FP32_PRODUCTS (the sliced products of full->band and band->full
+ * become FP32 products: operands rounded to FP32 and split exactly into
+ * three bf16 parts, six bf16 tensor-core products per step accumulated in
+ * FP32; the low-precision half of gb_solve_mixed_d) and GB_SOLVE_FP64_EMULATED_GEMM (accepted and ignored:
+ * no product of either solver goes through a vendor BLAS).  By
  * default the large products (the full->band SYMM and SYR2K, the band->full
  * GEMMs, the Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by
  * exact digit slicing (gb_dgemm_sliced below); GB_SOLVE_DFMA_PRODUCTS runs
@@ -265,6 +268,7 @@ int gb_band_to_tridi_z(int n, int nbw, const double *AB, int ldab, double *d, do
 #define GB_SOLVE_RECORD_STAGES 2 /* record CUDA events at the stage boundaries */
 #define GB_SOLVE_DFMA_PRODUCTS 4 /* products on the FP64 FMA pipe, not sliced */
 #define GB_SOLVE_TRIDIAG_BISECT 8 /* tridiagonal step by bisection + inverse iteration */
+#define GB_SOLVE_FP32_PRODUCTS 16 /* FP32 products in full->band and band->full */
 size_t gb_solve_workspace_bytes(int n, int nev, int nbw);
 int gb_solve_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
                void *workspace, size_t ws_bytes, void *stream, int flags);
@@ -339,17 +343,41 @@ size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev,
  * |lambda_i - lambda_j| > delta and r_ij / 2 elsewhere, X <- X + X E.  The
  * error of X falls quadratically for eigenvalues separated by more than
  * delta; within a cluster the step refines the cluster's invariant subspace.
- * The products are sliced on the bf16 tensor cores (FP64-accurate); ||A||_2
- * is taken as max |lambda_i|, the other norms bounded by Frobenius norms.
+ * The products are sliced on the bf16 tensor cores (FP64-accurate; 6 n^3
+ * flops a step: X^T X and X^T (A X) on their lower triangles); ||A||_2 is
+ * taken as max |lambda_i|, the other norms bounded by Frobenius norms.
  * Arguments (device pointers): 1 n >= 1; 2 A (n x n symmetric, lower
  * triangle read, lda); 3 lda >= n; 4 lam (n, out: the Rayleigh quotients
  * lambda_i of the input X); 5 X (n x n, ldx; in: approximate eigenvectors in
  * the columns, out: refined); 6 ldx >= n; 7 workspace (256-byte aligned);
- * 8 ws_bytes >= gb_refine_syev_workspace_bytes(n) (about 4 n^2 doubles plus
- * the sliced products' planes).  Asynchronous on `stream`. */
+ * 8 ws_bytes >= gb_refine_syev_workspace_bytes(n) (3 n^2 doubles plus two
+ * n x n operands' digit planes, 16 n^2 bytes each).  Asynchronous on `stream`. */
 size_t gb_refine_syev_workspace_bytes(int n);
 int gb_refine_syev_d(int n, const double *A, int lda, double *lam, double *X, int ldx, void *workspace,
                      size_t ws_bytes, void *stream);
+
+/* Mixed-precision two-stage solve (the FP32 tensor-core reduction and
+ * back-transformation with FP64 Ogita-Aishima refinement): all n eigenpairs
+ * by gb_solve_d with GB_SOLVE_FP32_PRODUCTS (the tridiagonal step, the bulge
+ * chase and trans_ev_tridi_to_band stay FP64), then refine_steps steps of
+ * gb_refine_syev_d in FP64 on the whole decomposition, then the lowest nev
+ * pairs copied out.  ev are the Rayleigh quotients of the eigenvectors
+ * before the last step (ascending up to rounding within clusters; the low-
+ * precision solve's eigenvalues if refine_steps = 0).  The refinement
+ * converges where the low-precision eigenvectors' errors are small against
+ * the eigenvalue gaps; inside clusters narrower than its threshold it
+ * refines the cluster's subspace only.
+ * Arguments 1-8 as for gb_solve_d; 9 refine_steps in 0..GB_SOLVE_MIXED_MAX_STEPS;
+ * 10 workspace (256-byte aligned); 11 ws_bytes >=
+ * gb_solve_mixed_workspace_bytes(n, nev, nbw) (n x n eigenvectors plus the
+ * larger of the all-pairs solve's and the refinement's workspaces).
+ * Asynchronous on `stream`; device-side status through gb_solve_mixed_query
+ * (synchronises the stream). */
+#define GB_SOLVE_MIXED_MAX_STEPS 8
+size_t gb_solve_mixed_workspace_bytes(int n, int nev, int nbw);
+int gb_solve_mixed_d(int n, int nev, int nbw, const double *A, int lda, double *ev, double *Z, int ldz,
+                     int refine_steps, void *workspace, size_t ws_bytes, void *stream);
+int gb_solve_mixed_query(const void *workspace, int n, int nev, int nbw, void *stream);
 
 size_t gb_tridiag_dc_workspace_bytes(int n);
 int gb_tridiag_dc_d(int n, const double *d, const double *e, double *lam, double *Q, int ldq,

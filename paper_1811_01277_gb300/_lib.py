@@ -40,6 +40,7 @@ EXPORTS = (
     "gb_solve_batched_graph_destroy", "gb_solve_tuner_create", "gb_solve_tuner_destroy", "gb_solve_tuner_step",
     "gb_solve_tuner_report", "gb_solve_tuner_nbw", "gb_solve_tuner_save", "gb_solve_tuner_load",
     "gb_tridiag_dc_workspace_bytes", "gb_tridiag_dc_d", "gb_refine_syev_workspace_bytes", "gb_refine_syev_d",
+    "gb_solve_mixed_workspace_bytes", "gb_solve_mixed_d", "gb_solve_mixed_query",
     "gb_solve_batched_staged_workspace_bytes", "gb_solve_batched_staged_d", "gb_solve_batched_staged_query",
     "gb_solve_stage_table_bytes", "gb_solve_stage_front", "gb_solve_stage_chase_batched", "gb_solve_stage_back",
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
@@ -53,6 +54,8 @@ EXPORTS = (
 GB_SOLVE_RECORD_STAGES = 2
 GB_SOLVE_DFMA_PRODUCTS = 4
 GB_SOLVE_TRIDIAG_BISECT = 8
+GB_SOLVE_FP32_PRODUCTS = 16
+GB_SOLVE_MIXED_MAX_STEPS = 8
 # stage 2 is the whole tridiagonal step when it runs as divide and conquer
 # (stages 3 and 4 are then empty)
 SOLVE_STAGES = ("full_to_band", "band_to_tridi", "tridiag_bisection_or_dc", "inverse_iteration", "orthogonalise",
@@ -170,6 +173,9 @@ def load(path=None):
     L.gb_tridiag_dc_d.argtypes = [i, p, p, p, p, i, p, sz, p]; L.gb_tridiag_dc_d.restype = i
     L.gb_refine_syev_workspace_bytes.argtypes = [i]; L.gb_refine_syev_workspace_bytes.restype = sz
     L.gb_refine_syev_d.argtypes = [i, p, i, p, p, i, p, sz, p]; L.gb_refine_syev_d.restype = i
+    L.gb_solve_mixed_workspace_bytes.argtypes = [i, i, i]; L.gb_solve_mixed_workspace_bytes.restype = sz
+    L.gb_solve_mixed_d.argtypes = [i, i, i, p, i, p, p, i, i, p, sz, p]; L.gb_solve_mixed_d.restype = i
+    L.gb_solve_mixed_query.argtypes = [p, i, i, i, p]; L.gb_solve_mixed_query.restype = i
     ch, dd = ctypes.c_char, ctypes.c_double
     L.gb_dgemm_workspace_bytes.argtypes = [i, i]; L.gb_dgemm_workspace_bytes.restype = sz
     L.gb_dgemm.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dgemm.restype = i
@@ -604,6 +610,22 @@ def gb_refine_syev_d(n, A, lda, lam, X, ldx, workspace, ws_bytes, stream=None, c
     if check and rc != GB_OK:
         raise GbError(rc, "gb_refine_syev_d")
     return rc
+
+
+def gb_solve_mixed_workspace_bytes(n, nev, nbw):
+    return load().gb_solve_mixed_workspace_bytes(n, nev, nbw)
+
+
+def gb_solve_mixed_d(n, nev, nbw, A, lda, ev, Z, ldz, refine_steps, workspace, ws_bytes, stream=None, check=True):
+    rc = load().gb_solve_mixed_d(n, nev, nbw, _dp(A), lda, _dp(ev), _dp(Z), ldz, refine_steps, _dp(workspace),
+                                 ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_solve_mixed_d")
+    return rc
+
+
+def gb_solve_mixed_query(workspace, n, nev, nbw, stream=None):
+    return load().gb_solve_mixed_query(_dp(workspace), n, nev, nbw, _stream(stream))
 
 
 def gb_tridiag_dc_workspace_bytes(n):

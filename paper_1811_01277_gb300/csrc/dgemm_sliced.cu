@@ -9,12 +9,13 @@
 //
 // Product: one 256-thread block per 64 x 32 tile of C, warps 4 (rows) x 2
 // (columns), each warp 16 x 16 = two m16n8 accumulator tiles per level.
-// K advances 32 at a time through a two-stage cp.async pipeline holding all
-// digit planes of the A and B tiles (rows padded to 80 bytes so that the
-// ldmatrix row addresses of a phase fall in distinct banks).  Per k16 step
-// the warp loads the eight A-plane fragments once and, per B plane j, issues
-// mma.sync m16n8k16 bf16 for every A plane i with i + j < kSlices into the
-// accumulator of level i + j.
+// K advances 32 at a time through a two-stage cp.async pipeline holding the
+// D digit planes of the A and B tiles that the product forms (rows padded to
+// 80 bytes so that the ldmatrix row addresses of a phase fall in distinct
+// banks).  Per k16 step the warp loads the D A-plane fragments once and, per
+// B plane j, issues mma.sync m16n8k16 bf16 for every A plane i whose level
+// i + j is formed, into the accumulator of that level.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,11 +32,14 @@ constexpr int kBM = 64, kBN = 32, kBK = 32;
 constexpr int kRowPad = 40;  // bf16 per staged row (32 used)
 constexpr int kThreads = 256;
 constexpr int kStages = 2;
-constexpr size_t kStageElems = (size_t)kSlices * (kBM + kBN) * kRowPad;  // bf16 per stage
-constexpr size_t kProductSmem = kStages * kStageElems * sizeof(uint16_t);
+// bf16 per pipeline stage and dynamic shared memory of a D-digit product
+template <int D>
+__host__ __device__ constexpr size_t stage_elems() { return (size_t)D * (kBM + kBN) * kRowPad; }
+template <int D>
+__host__ __device__ constexpr size_t product_smem() { return kStages * stage_elems<D>() * sizeof(uint16_t); }
 
 static_assert(kSlices * kDigitBits <= 56, "digits come from the 56-bit fixed-point magnitude");
-static_assert(kSlices == 8 && kLevels == 9, "the level folding below assumes eight digits, levels 0..8");
+static_assert(kSlices == 8 && kLevels == 9, "the level folding below assumes at most eight digits, levels 0..8");
 static_assert(kSlices * 127 * 127 * kFlushK < (1 << 24), "every level must stay below 2^24 units per flush");
 constexpr int kMaxSplitK = 65536;  // keeps lo below 2^61: 512 flushes of at most 2^52
 
@@ -46,6 +50,8 @@ struct SliceLayout {
     size_t planes, e, rmax, total;
 };
 
+// (the layout always has room for kSlices planes, so one buffer serves every
+// digit count)
 SliceLayout slice_layout(int R, int K)
 {
     const size_t Rp = (size_t)round_up(R > 0 ? R : 1, kBM), Kp = (size_t)round_up(K > 0 ? K : 1, kBK);
@@ -130,9 +136,11 @@ __global__ void __launch_bounds__(256) slice_rowmax(int view, const double *__re
 }
 
 
+// Writes the eight digit planes, or the three planes of the FP32 split.
 __global__ void __launch_bounds__(256) slice_digits(int view, const double *__restrict__ src, long long ld, int R,
                                                      int K, int Rp, int Kp, const unsigned long long *__restrict__ rmax,
-                                                     uint16_t *__restrict__ planes, int *__restrict__ e_out)
+                                                     uint16_t *__restrict__ planes, int *__restrict__ e_out,
+                                                     int digits)
 {
     __shared__ double t[32][33];
     const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
@@ -142,31 +150,47 @@ __global__ void __launch_bounds__(256) slice_digits(int view, const double *__re
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int r = r0 + i, k = k0 + threadIdx.x;
         if (r >= Rp || k >= Kp) continue;
+        const double x = t[i][threadIdx.x];
+        if (digits == kSplitPlanes) {  // FP32 value split into three bf16 parts (exact)
+            if (blockIdx.x == 0 && threadIdx.x == 0) e_out[r] = 0;
+            const float f = __double2float_rn(x);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(f);
+            const float r1 = f - __bfloat162float(h0);
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+            const size_t at = (size_t)r * Kp + k;
+            planes[at] = __bfloat16_as_ushort(h0);
+            planes[plane + at] = __bfloat16_as_ushort(h1);
+            planes[2 * plane + at] = __bfloat16_as_ushort(h2);
+            continue;
+        }
         const int er = r < R ? exponent_above(rmax[r]) : 0;
         if (blockIdx.x == 0 && threadIdx.x == 0) e_out[r] = er;
-        const double x = t[i][threadIdx.x];
         const unsigned long long Y = fixed56(x, er);
         const bool neg = x < 0.0;
 #pragma unroll
         for (int s = 0; s < kSlices; s++) {
+            if (s >= digits) break;
             const uint16_t h = bf16_digit((int)((Y >> (kDigitBits * (kSlices - 1 - s))) & 127u), s, neg);
             planes[s * plane + (size_t)r * Kp + k] = h;
         }
     }
 }
 
-// Stage loader: all digit planes of the A rows [m0, m0+kBM) and B rows
-// [n0, n0+kBN) for k in [kt, kt+32).
+// Stage loader: the leading D digit planes of the A rows [m0, m0+kBM) and B
+// rows [n0, n0+kBN) for k in [kt, kt+32).
+template <int D>
 __device__ __forceinline__ void load_stage(uint16_t *stage, const uint16_t *__restrict__ Ap, size_t a_plane,
                                            int a_kp, const uint16_t *__restrict__ Bp, size_t b_plane, int b_kp,
                                            int m0, int n0, int kt)
 {
-    // kSlices planes x rows x 4 chunks of 16 bytes (32 bf16 of k)
-    constexpr int kChunksA = kSlices * kBM * 4, kChunksB = kSlices * kBN * 4;
-    static_assert((kChunksA + kChunksB) % kThreads == 0, "whole chunks per thread");
+    // D planes x rows x 4 chunks of 16 bytes (32 bf16 of k)
+    constexpr int kChunksA = D * kBM * 4, kChunksB = D * kBN * 4;
+    constexpr int kTotal = kChunksA + kChunksB;
 #pragma unroll
-    for (int it = 0; it < (kChunksA + kChunksB) / kThreads; it++) {
+    for (int it = 0; it < (kTotal + kThreads - 1) / kThreads; it++) {
         const int c = threadIdx.x + it * kThreads;
+        if (kTotal % kThreads != 0 && c >= kTotal) break;
         const bool isA = c < kChunksA;
         const int rem = isA ? c : c - kChunksA;
         const int rows = isA ? kBM : kBN;
@@ -174,24 +198,33 @@ __device__ __forceinline__ void load_stage(uint16_t *stage, const uint16_t *__re
         const uint16_t *g = isA ? Ap + s * a_plane + (size_t)(m0 + row) * a_kp + kt + part * 8
                                 : Bp + s * b_plane + (size_t)(n0 + row) * b_kp + kt + part * 8;
         uint16_t *d = isA ? stage + ((size_t)s * kBM + row) * kRowPad + part * 8
-                          : stage + (size_t)kSlices * kBM * kRowPad + ((size_t)s * kBN + row) * kRowPad + part * 8;
+                          : stage + (size_t)D * kBM * kRowPad + ((size_t)s * kBN + row) * kRowPad + part * 8;
         cp_async16(d, g);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// Levels a product forms: i + j <= 8 for the eight digits; the FP32 split
+// (D = kSplitPlanes) sums its pairs i + j <= 2 in one FP32 accumulator.
+template <int D>
+__host__ __device__ constexpr int product_levels() { return D == kSlices ? kLevels : 1; }
+
 // One kBM x kBN tile of C (or of split z's partial product).  Warps 4 x 2,
-// each 16 x 16 (two m16n8 tiles); level l = i + j <= kLevels - 1 of the
-// digit pairs has its own FP32 accumulator, exact over kFlushK values of k,
-// folded into two 64-bit integers: hi = sum_{l<4} L_l 2^(7(3-l)),
+// each 16 x 16 (two m16n8 tiles); level l = i + j < product_levels<D>() of
+// the digit pairs has its own FP32 accumulator, exact over kFlushK values of
+// k, folded into two 64-bit integers: hi = sum_{l<4} L_l 2^(7(3-l)),
 // lo = sum_{l>=4} L_l 2^(7(8-l)), with L_l the level's sum in units of
 // 2^(-7l).
-__global__ void __launch_bounds__(kThreads, 1)
+template <int D>
+__global__ void __launch_bounds__(kThreads, D == kSlices ? 1 : 2)
 sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int a_rp, int a_kp,
                const uint16_t *__restrict__ Bp, const int *__restrict__ eb, int b_rp, int b_kp, int m, int n,
                int ksplit, int K, double alpha, double beta, double *__restrict__ C, long long ldc, int fill,
                double *__restrict__ part)
 {
+    constexpr int kLev = product_levels<D>();
+    constexpr bool kSplit = D == kSplitPlanes;
+    constexpr size_t kStageElems = stage_elems<D>();
     extern __shared__ __align__(16) uint16_t smem[];
     const int tm = blockIdx.y, tn = blockIdx.x;
     const int m0 = tm * kBM, n0 = tn * kBN;
@@ -202,10 +235,11 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp & 3, wn = warp >> 2;
 
-    float acc[kLevels][2][4];
+    float acc[kLev][2][4];
     long long hi[2][4], lo[2][4];
+    double dacc[2][4];  // FP32 split: the FP32 sums folded every kFlushK
 #pragma unroll
-    for (int l = 0; l < kLevels; l++)
+    for (int l = 0; l < kLev; l++)
 #pragma unroll
         for (int t = 0; t < 2; t++)
 #pragma unroll
@@ -213,42 +247,45 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
 #pragma unroll
     for (int t = 0; t < 2; t++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) hi[t][q] = lo[t][q] = 0;
+        for (int q = 0; q < 4; q++) {
+            hi[t][q] = lo[t][q] = 0;
+            dacc[t][q] = 0.0;
+        }
 
     // ldmatrix lane offsets within a stage's operand block
     const int a_row = wm * 16 + (lane & 7) + ((lane >> 3) & 1) * 8, a_k = (lane >> 4) * 8;
     const int b_row = wn * 16 + (lane & 7) + (lane >> 4) * 8, b_k = ((lane >> 3) & 1) * 8;
 
     int stage = 0;
-    if (kbeg < kend) load_stage(smem, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0, kbeg);
+    if (kbeg < kend) load_stage<D>(smem, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0, kbeg);
     int steps = 0;
     for (int kt = kbeg; kt < kend; kt += kBK, steps++) {
         const bool more = kt + kBK < kend;
         if (more)
-            load_stage(smem + (size_t)(stage ^ 1) * kStageElems, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0,
-                       kt + kBK);
+            load_stage<D>(smem + (size_t)(stage ^ 1) * kStageElems, Ap, a_plane, a_kp, Bp, b_plane, b_kp, m0, n0,
+                          kt + kBK);
         if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         const uint16_t *As = smem + (size_t)stage * kStageElems;
-        const uint16_t *Bs = As + (size_t)kSlices * kBM * kRowPad;
+        const uint16_t *Bs = As + (size_t)D * kBM * kRowPad;
 #pragma unroll
         for (int ks = 0; ks < kBK / 16; ks++) {
-            unsigned af[kSlices][4];
+            unsigned af[D][4];
 #pragma unroll
-            for (int s = 0; s < kSlices; s++)
+            for (int s = 0; s < D; s++)
                 ldsm_x4(af[s][0], af[s][1], af[s][2], af[s][3],
                         As + ((size_t)s * kBM + a_row) * kRowPad + ks * 16 + a_k);
 #pragma unroll
-            for (int j = 0; j < kSlices; j++) {
+            for (int j = 0; j < D; j++) {
                 unsigned bf[2][2];
                 ldsm_x4(bf[0][0], bf[0][1], bf[1][0], bf[1][1],
                         Bs + ((size_t)j * kBN + b_row) * kRowPad + ks * 16 + b_k);
 #pragma unroll
-                for (int i = 0; i < kSlices; i++)
-                    if (i + j < kLevels)
+                for (int i = 0; i < D; i++)
+                    if (kSplit ? i + j <= 2 : i + j < kLev)
 #pragma unroll
-                        for (int t = 0; t < 2; t++) mma_bf16(acc[i + j][t], af[i], bf[t][0], bf[t][1]);
+                        for (int t = 0; t < 2; t++) mma_bf16(acc[kSplit ? 0 : i + j][t], af[i], bf[t][0], bf[t][1]);
             }
         }
         __syncthreads();  // this stage's buffer is refilled two steps later
@@ -256,11 +293,16 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
         // fold the levels into the integer accumulators every kFlushK
         if ((steps + 1) % (kFlushK / kBK) == 0 || !more) {
 #pragma unroll
-            for (int l = 0; l < kLevels; l++)
+            for (int l = 0; l < kLev; l++)
 #pragma unroll
                 for (int t = 0; t < 2; t++)
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
+                        if (kSplit) {
+                            dacc[t][q] += (double)acc[l][t][q];
+                            acc[l][t][q] = 0.f;
+                            continue;
+                        }
                         // level l holds an integer multiple of 2^(-7l) below 2^24 units
                         const float unit = __int_as_float((127 + kDigitBits * l) << 23);  // 2^(7l)
                         const long long iv = __float2int_rn(acc[l][t][q] * unit);
@@ -281,8 +323,13 @@ sliced_product(const uint16_t *__restrict__ Ap, const int *__restrict__ ea, int 
             const int c = n0 + wn * 16 + t * 8 + tig * 2 + (q & 1);
             if (r >= m || c >= n || (fill == kFillLower && r < c) || (fill == kFillZLower && (r >> 1) < c))
                 continue;
-            double v = (double)hi[t][q] * 0x1p-21 + (double)lo[t][q] * 0x1p-56;
-            v = scale_by_pow2(v, ea[r] + eb[c] - 2 * kDigitBits);
+            double v;
+            if (kSplit) {
+                v = dacc[t][q];
+            } else {
+                v = (double)hi[t][q] * 0x1p-21 + (double)lo[t][q] * 0x1p-56;
+                v = scale_by_pow2(v, ea[r] + eb[c] - 2 * kDigitBits);
+            }
             if (fill == kFillZLower && (r >> 1) == c && (r & 1)) {  // Hermitian diagonal: real
                 if (part) part[(size_t)blockIdx.z * m * n + (size_t)c * m + r] = 0.0;
                 else C[r + (long long)c * ldc] = 0.0;
@@ -320,8 +367,9 @@ __global__ void __launch_bounds__(256) sliced_reduce(int m, int n, int splits, c
 size_t sliced_bytes(int R, int K) { return slice_layout(R, K).total; }
 
 cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long long ld, void *buf, SlicedOp *out,
-                         cudaStream_t st)
+                         cudaStream_t st, int digits)
 {
+    if (digits != kSplitPlanes && digits != kSlices) return cudaErrorInvalidValue;
     const SliceLayout L = slice_layout(R, K);
     const int Rp = round_up(R > 0 ? R : 1, kBM), Kp = round_up(K > 0 ? K : 1, kBK);
     char *base = (char *)buf;
@@ -334,29 +382,45 @@ cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long l
     out->K = K;
     out->Rp = Rp;
     out->Kp = Kp;
+    out->digits = digits;
     cudaError_t err = cudaMemsetAsync(rmax, 0, (size_t)Rp * sizeof(unsigned long long), st);
     if (err != cudaSuccess) return err;
     const dim3 block(32, 8);
-    if (R > 0 && K > 0) {
+    if (R > 0 && K > 0 && digits != kSplitPlanes) {  // the split needs no row maxima
         const dim3 grid((K + 31) / 32, (R + 31) / 32);
         slice_rowmax<<<grid, block, 0, st>>>((int)view, src, ld, R, K, rmax);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     // digits over the padded extent (zeros outside R x K)
     const dim3 grid2(Kp / 32, Rp / 32);
-    slice_digits<<<grid2, block, 0, st>>>((int)view, src, ld, R, K, Rp, Kp, rmax, planes, e);
+    slice_digits<<<grid2, block, 0, st>>>((int)view, src, ld, R, K, Rp, Kp, rmax, planes, e, digits);
     return cudaGetLastError();
 }
+
+namespace {
+
+template <int D>
+cudaError_t launch_product(dim3 grid, cudaStream_t st, const SlicedOp &A, const SlicedOp &B, int m, int n, int ksplit,
+                           int Kp, double alpha, double beta, double *C, long long ldc, int fill, double *part)
+{
+    // opt in to the large dynamic shared memory (cheap; per device, so every call)
+    cudaError_t e = cudaFuncSetAttribute(sliced_product<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)product_smem<D>());
+    if (e != cudaSuccess) return e;
+    sliced_product<D><<<grid, kThreads, product_smem<D>(), st>>>(A.planes, A.e, A.Rp, A.Kp, B.planes, B.e, B.Rp,
+                                                                B.Kp, m, n, ksplit, Kp, alpha, beta, C, ldc, fill,
+                                                                part);
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, double alpha, double beta, double *C,
                         long long ldc, int fill, double *work, size_t work_elems, cudaStream_t st)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (A.K != B.K || A.Kp != B.Kp || m > A.R || n > B.R) return cudaErrorInvalidValue;
-    // opt in to the large dynamic shared memory (cheap; per device, so every call)
-    cudaError_t ea = cudaFuncSetAttribute(sliced_product, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kProductSmem);
-    if (ea != cudaSuccess) return ea;
+    const int D = std::min(A.digits, B.digits);
     const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
     long long tiles = (long long)tiles_m * tiles_n;
     if (fill != kFillAll) {  // tiles not wholly above the diagonal
@@ -388,10 +452,12 @@ cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, doub
         splits = (Kp + ksplit - 1) / ksplit;
     }
     const dim3 grid(tiles_n, tiles_m, splits);
-    sliced_product<<<grid, kThreads, kProductSmem, st>>>(A.planes, A.e, A.Rp, A.Kp, B.planes, B.e, B.Rp, B.Kp, m, n,
-                                                         ksplit, Kp, alpha, beta, C, ldc, fill,
-                                                         splits > 1 ? work : nullptr);
-    cudaError_t e = cudaGetLastError();
+    double *part = splits > 1 ? work : nullptr;
+    cudaError_t e;
+    if ((A.digits == kSplitPlanes) != (B.digits == kSplitPlanes)) return cudaErrorInvalidValue;
+    if (D == kSplitPlanes) e = launch_product<kSplitPlanes>(grid, st, A, B, m, n, ksplit, Kp, alpha, beta, C, ldc, fill, part);
+    else if (D == kSlices) e = launch_product<kSlices>(grid, st, A, B, m, n, ksplit, Kp, alpha, beta, C, ldc, fill, part);
+    else return cudaErrorInvalidValue;
     if (e != cudaSuccess || splits == 1) return e;
     const long long total = (long long)m * n;
     sliced_reduce<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(m, n, splits, work, alpha, beta, C, ldc, fill);
@@ -447,35 +513,37 @@ size_t sliced_syrk_ws_bytes(int n, int k) { return sliced_ws(n, 0, k, 0, 0, null
 
 cudaError_t sliced_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double *A, long long lda,
                          const double *B, long long ldb, double beta, double *C, long long ldc, void *ws,
-                         cudaStream_t st)
+                         cudaStream_t st, int digits)
 {
     SlicedWs w = sliced_ws(m, n, k, 0, 0, ws);
     SlicedOp a, b;
-    cudaError_t e = slice_matrix(transa == 'N' ? kViewRow : kViewCol, m, k, A, lda, w.a, &a, st);
+    cudaError_t e = slice_matrix(transa == 'N' ? kViewRow : kViewCol, m, k, A, lda, w.a, &a, st, digits);
     if (e != cudaSuccess) return e;
-    if ((e = slice_matrix(transb == 'N' ? kViewCol : kViewRow, n, k, B, ldb, w.b, &b, st)) != cudaSuccess) return e;
+    if ((e = slice_matrix(transb == 'N' ? kViewCol : kViewRow, n, k, B, ldb, w.b, &b, st, digits)) != cudaSuccess)
+        return e;
     return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, kFillAll, w.part, kPartialElems, st);
 }
 
 cudaError_t sliced_dsymm(char side, int m, int n, double alpha, const double *S, long long lds, const double *B,
-                         long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st)
+                         long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st, int digits)
 {
     const int K = side == 'L' ? m : n;
     SlicedWs w = sliced_ws(m, n, K, 0, 0, ws);
     SlicedOp a, b;
     cudaError_t e;
     if (side == 'L') {  // C = S B: rows of S, columns of B
-        if ((e = slice_matrix(kViewSym, m, m, S, lds, w.a, &a, st)) != cudaSuccess) return e;
-        if ((e = slice_matrix(kViewCol, n, m, B, ldb, w.b, &b, st)) != cudaSuccess) return e;
+        if ((e = slice_matrix(kViewSym, m, m, S, lds, w.a, &a, st, digits)) != cudaSuccess) return e;
+        if ((e = slice_matrix(kViewCol, n, m, B, ldb, w.b, &b, st, digits)) != cudaSuccess) return e;
     } else {            // C = B S: rows of B, columns (= rows) of S
-        if ((e = slice_matrix(kViewRow, m, n, B, ldb, w.a, &a, st)) != cudaSuccess) return e;
-        if ((e = slice_matrix(kViewSym, n, n, S, lds, w.b, &b, st)) != cudaSuccess) return e;
+        if ((e = slice_matrix(kViewRow, m, n, B, ldb, w.a, &a, st, digits)) != cudaSuccess) return e;
+        if ((e = slice_matrix(kViewSym, n, n, S, lds, w.b, &b, st, digits)) != cudaSuccess) return e;
     }
     return sliced_gemm(a, b, m, n, alpha, beta, C, ldc, kFillAll, w.part, kPartialElems, st);
 }
 
 cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, long long lda, const double *B,
-                                long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st)
+                                long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st,
+                                int digits)
 {
     // A B^T + B A^T = [A B] [B A]^T
     SlicedWs w = sliced_ws(n, n, 2 * k, n, 2 * k, ws);
@@ -492,18 +560,18 @@ cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, lon
             return e;
     }
     SlicedOp a, b;
-    if ((e = slice_matrix(kViewRow, n, 2 * k, AB, n, w.a, &a, st)) != cudaSuccess) return e;
-    if ((e = slice_matrix(kViewRow, n, 2 * k, BA, n, w.b, &b, st)) != cudaSuccess) return e;
+    if ((e = slice_matrix(kViewRow, n, 2 * k, AB, n, w.a, &a, st, digits)) != cudaSuccess) return e;
+    if ((e = slice_matrix(kViewRow, n, 2 * k, BA, n, w.b, &b, st, digits)) != cudaSuccess) return e;
     return sliced_gemm(a, b, n, n, alpha, beta, C, ldc, kFillLower, w.part, kPartialElems, st);
 }
 
 cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
-                                 long long ldc, void *ws, cudaStream_t st)
+                                 long long ldc, void *ws, cudaStream_t st, int digits)
 {
     // A^T A: both operands are the columns of A
     SlicedWs w = sliced_ws(n, 0, k, 0, 0, ws);
     SlicedOp a;
-    cudaError_t e = slice_matrix(kViewCol, n, k, A, lda, w.a, &a, st);
+    cudaError_t e = slice_matrix(kViewCol, n, k, A, lda, w.a, &a, st, digits);
     if (e != cudaSuccess) return e;
     return sliced_gemm(a, a, n, n, alpha, beta, C, ldc, kFillLower, w.part, kPartialElems, st);
 }

@@ -23,6 +23,15 @@
 // |C - AB| <~ 2^-53 k max_j|a_ij| max_i|b_ij| per entry.  Inputs must be
 // finite; subnormal inputs are read as zero.
 //
+// FP32 products (digits = kSplitPlanes): every entry is rounded to FP32 and
+// split exactly into three bf16 parts h0 + h1 + h2 with their own
+// exponents (no row scaling); the pairs i + j <= 2 (six products per k16
+// step) accumulate in one FP32 tensor-core accumulator, folded into FP64
+// every kFlushK.  The error is that of an FP32 product: about 2^-24 of
+// sum_k |a_ik b_kj| from the rounding to FP32 and the dropped pairs, plus
+// the FP32 accumulation over kFlushK terms.  This is the low-precision half
+// of the mixed-precision solve.
+//
 // A sliced operand is an R x K "slice-row" matrix; its rows are the rows of
 // op(A) (for the left operand) or the columns of op(B) (for the right).
 #pragma once
@@ -36,6 +45,7 @@ constexpr int kSlices = 8;
 constexpr int kLevels = 9;  // digit pairs i + j <= 8 are formed
 constexpr int kDigitBits = 7;
 constexpr int kFlushK = 128;
+constexpr int kSplitPlanes = 3;  // `digits` value of the FP32 split
 
 // How a slice-row matrix reads a column-major FP64 source `src` (leading
 // dimension ld): element (r, k) is
@@ -63,9 +73,10 @@ enum SliceView {
 };
 
 struct SlicedOp {
-    const uint16_t *planes;  // kSlices planes of Rp x Kp bf16, row-major (k fastest)
+    const uint16_t *planes;  // digits planes of Rp x Kp bf16, row-major (k fastest)
     const int *e;            // Rp row exponents: the row's entries are below 2^e
     int R, K, Rp, Kp;        // Rp: R rounded up to 64; Kp: K rounded up to 32
+    int digits;              // kSlices digit planes, or kSplitPlanes (the FP32 split)
 };
 
 // Bytes a sliced R x K operand occupies (planes, exponents and a reduction
@@ -73,9 +84,11 @@ struct SlicedOp {
 size_t sliced_bytes(int R, int K);
 
 // Slices an R x K view of src into buf (sliced_bytes(R, K) bytes, 256-byte
-// aligned); fills *out.  Two launches and a memset on st.
+// aligned); fills *out.  Two launches and a memset on st.  `digits`:
+// kSlices (the FP64-accurate digits) or kSplitPlanes (the FP32 split; both
+// operands of a product must then be split).
 cudaError_t slice_matrix(SliceView view, int R, int K, const double *src, long long ld, void *buf, SlicedOp *out,
-                         cudaStream_t st);
+                         cudaStream_t st, int digits = kSlices);
 
 // Which part of C a product writes.
 enum SlicedFill {
@@ -87,26 +100,29 @@ enum SlicedFill {
 
 // C (m x n, column-major) = alpha A B^T + beta C where A, B are sliced
 // (A.R >= m, B.R >= n, A.K == B.K): row r of A times row c of B; `fill`
-// selects the entries written.  `work` (doubles) holds split-K partials; the
+// selects the entries written.  Both operands split: the FP32 product.  `work` (doubles) holds split-K partials; the
 // reduction splits while splits * m * n <= work_elems.
 cudaError_t sliced_gemm(const SlicedOp &A, const SlicedOp &B, int m, int n, double alpha, double beta, double *C,
                         long long ldc, int fill, double *work, size_t work_elems, cudaStream_t st);
 
 // Whole products (slice both operands into ws, multiply), with the DFMA
 // forms' conventions (dgemm_dfma.cuh); ws must hold the matching *_ws_bytes.
+// `digits` as for slice_matrix (kSlices: FP64 accuracy).
 size_t sliced_gemm_ws_bytes(int m, int n, int k);
 size_t sliced_symm_ws_bytes(char side, int m, int n);
 size_t sliced_syr2k_ws_bytes(int n, int k);
 size_t sliced_syrk_ws_bytes(int n, int k);
 cudaError_t sliced_dgemm(char transa, char transb, int m, int n, int k, double alpha, const double *A, long long lda,
                          const double *B, long long ldb, double beta, double *C, long long ldc, void *ws,
-                         cudaStream_t st);
+                         cudaStream_t st, int digits = kSlices);
 cudaError_t sliced_dsymm(char side, int m, int n, double alpha, const double *S, long long lds, const double *B,
-                         long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
+                         long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st,
+                         int digits = kSlices);
 cudaError_t sliced_dsyr2k_lower(int n, int k, double alpha, const double *A, long long lda, const double *B,
-                                long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st);
+                                long long ldb, double beta, double *C, long long ldc, void *ws, cudaStream_t st,
+                                int digits = kSlices);
 cudaError_t sliced_dsyrk_lower_t(int n, int k, double alpha, const double *A, long long lda, double beta, double *C,
-                                 long long ldc, void *ws, cudaStream_t st);
+                                 long long ldc, void *ws, cudaStream_t st, int digits = kSlices);
 
 // Complex (interleaved) products with real alpha, beta; lda etc. in complex
 // elements.  C (m x n) = alpha op(A) B + beta C, op = 'N' or 'C'.

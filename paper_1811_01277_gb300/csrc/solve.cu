@@ -17,6 +17,9 @@
 // Newton-Schulz SYRK and SYMM) run on the bf16 tensor cores by exact digit
 // slicing (dgemm_sliced.cuh), the small ones in the DFMA kernels
 // (dgemm_dfma.cuh, and the complex DFMA kernel for the complex solve).
+// With GB_SOLVE_FP32_PRODUCTS the sliced products of full -> band and
+// band -> full are FP32 products (operands rounded to FP32, split into three
+// bf16 parts, six tensor-core products per step, FP32 accumulation).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -322,11 +325,14 @@ int solve_d_parts(int n, int nev, int nbw, const double *A, int lda, double *ev,
     SolveWs w = pre ? *pre : carve(n, nev, b, (char *)workspace);
     if (!pre && ws_bytes < w.total) return -10;
     if (flags & ~(GB_SOLVE_FP64_EMULATED_GEMM | GB_SOLVE_RECORD_STAGES | GB_SOLVE_DFMA_PRODUCTS |
-                  GB_SOLVE_TRIDIAG_BISECT))
+                  GB_SOLVE_TRIDIAG_BISECT | GB_SOLVE_FP32_PRODUCTS))
         return -12;
     // large products on the tensor cores unless the caller asks for DFMA
     const bool slice_ok = w.sl && !(flags & GB_SOLVE_DFMA_PRODUCTS);
     auto use_sliced = [&](double m_, double n_, double k_) { return slice_ok && sliced_pays(m_, n_, k_); };
+    // the sliced products of full -> band and band -> full: FP32 products
+    // (the FP32 split) for the low-precision half of the mixed-precision solve
+    const int pd = (flags & GB_SOLVE_FP32_PRODUCTS) ? gb::kSplitPlanes : gb::kSlices;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t *sev = nullptr;
     if (flags & GB_SOLVE_RECORD_STAGES) {
@@ -388,7 +394,7 @@ int solve_d_parts(int n, int nev, int nbw, const double *A, int lda, double *ev,
         // only the lower triangle of A2 is kept: X = A2 (Y T) (symmetric
         // product), W = X - Y M / 2, then A2 -= W Y^T + Y W^T on the lower triangle
         if (use_sliced(m, b, m))
-            GB_CU(gb::sliced_dsymm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.sl, st));
+            GB_CU(gb::sliced_dsymm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.sl, st, pd));
         else
             GB_CU(gb::dfma_symm('L', m, b, 1.0, A2, ldw, w.YT, m, 0.0, w.X, m, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('T', 'N', b, b, m, 1.0, Yp, m, w.X, m, 0.0, w.Pm, b, w.gw, w.gw_elems, st));
@@ -408,13 +414,13 @@ int solve_d_parts(int n, int nev, int nbw, const double *A, int lda, double *ev,
             GB_CU(factor(pp + 1));
             if (use_sliced(m - b, m - b, b))
                 GB_CU(gb::sliced_dsyr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b,
-                                              ldw, w.sl, st));
+                                              ldw, w.sl, st, pd));
             else
                 GB_CU(gb::dfma_syr2k_lower(m - b, b, -1.0, w.X + b, m, Yp + b, m, 1.0, A2 + (long long)b * ldw + b,
                                            ldw, st));
         } else {
             if (use_sliced(m, m, b))
-                GB_CU(gb::sliced_dsyr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, w.sl, st));
+                GB_CU(gb::sliced_dsyr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, w.sl, st, pd));
             else
                 GB_CU(gb::dfma_syr2k_lower(m, b, -1.0, w.X, m, Yp, m, 1.0, A2, ldw, st));
         }
@@ -468,12 +474,12 @@ int solve_d_parts(int n, int nev, int nbw, const double *A, int lda, double *ev,
         double *Zr = Z + (j + b);
         GB_CU(gb::panel_y_and_t_prep(m, b, panel, ldw, w.Y, m, st));
         if (use_sliced(b, nev, m))
-            GB_CU(gb::sliced_dgemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.sl, st));
+            GB_CU(gb::sliced_dgemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.sl, st, pd));
         else
             GB_CU(gb::dfma_gemm('T', 'N', b, nev, m, 1.0, w.Y, m, Zr, ldz, 0.0, w.S, b, w.gw, w.gw_elems, st));
         GB_CU(gb::dfma_gemm('N', 'N', b, nev, b, 1.0, T, b, w.S, b, 0.0, w.S2, b, w.gw, w.gw_elems, st));
         if (use_sliced(m, nev, b))
-            GB_CU(gb::sliced_dgemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.sl, st));
+            GB_CU(gb::sliced_dgemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.sl, st, pd));
         else
             GB_CU(gb::dfma_gemm('N', 'N', m, nev, b, -1.0, w.Y, m, w.S2, b, 1.0, Zr, ldz, w.gw, w.gw_elems, st));
     }
@@ -775,6 +781,28 @@ int gb_solve_stage_ms(void *stream, float *ms)
         if (cudaEventElapsedTime(&ms[i], sev[i], sev[i + 1]) != cudaSuccess) return GB_ERR_CUDA;
     return GB_OK;
 }
+
+}  // extern "C"
+
+namespace gb {
+
+cudaError_t solve_status_copy(const void *ws, int n, int nev, int nbw, void *dst, cudaStream_t st)
+{
+    SolveWs w = carve(n, nev, nbw, (char *)ws);
+    const void *src[2] = {w.chase, w.tev};
+    const size_t bytes[2] = {w.chase_bytes, w.tev_bytes};
+    for (int i = 0; i < 2; i++) {
+        char *d = (char *)dst + 256 * i;
+        const cudaError_t e = bytes[i] >= 256 ? cudaMemcpyAsync(d, src[i], 16, cudaMemcpyDeviceToDevice, st)
+                                              : cudaMemsetAsync(d, 0, 16, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace gb
+
+extern "C" {
 
 int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream)
 {

@@ -87,4 +87,10 @@ cudaError_t pipeline_tc5_z(int n, int b, int nev, const double *hh_v, const doub
                            int column_batch, void *ws, size_t ws_bytes, long long spin_polls, long long timeout_ns,
                            int hold_group, cudaStream_t st);
 
+// Copies the device-side status words of the last real solve that used
+// `ws` (its bulge chase's and its back-transformation's) into dst (two
+// 256-byte slots), in stream order, so that the workspace can be reused
+// before gb_solve_query-style reads of dst.
+cudaError_t solve_status_copy(const void *ws, int n, int nev, int nbw, void *dst, cudaStream_t st);
+
 }  // namespace gb

@@ -172,6 +172,20 @@ def test_newer_entry_points_check_arguments_host_only(lib):
     assert rf(4, 256, 4, 256, 256, 4, None, 1 << 30, None, check=False) == -7
     assert rf(4, 256, 4, 256, 256, 4, 256, 8, None, check=False) == -8
     assert gb.gb_refine_syev_workspace_bytes(100) >= 4 * 100 * 100 * 8
+    # the mixed-precision solve
+    mx = gb.gb_solve_mixed_d
+    assert mx(1, 1, 1, 256, 1, 256, 256, 1, 1, 256, 1 << 30, None, check=False) == -1
+    assert mx(10, 11, 3, 256, 10, 256, 256, 10, 1, 256, 1 << 30, None, check=False) == -2
+    assert mx(10, 5, 10, 256, 10, 256, 256, 10, 1, 256, 1 << 30, None, check=False) == -3
+    assert mx(10, 5, 3, 256, 9, 256, 256, 10, 1, 256, 1 << 30, None, check=False) == -5
+    assert mx(10, 5, 3, 256, 10, 256, 256, 9, 1, 256, 1 << 30, None, check=False) == -8
+    assert mx(10, 5, 3, 256, 10, 256, 256, 10, -1, 256, 1 << 30, None, check=False) == -9
+    assert mx(10, 5, 3, 256, 10, 256, 256, 10, 9, 256, 1 << 30, None, check=False) == -9
+    assert mx(10, 5, 3, 256, 10, 256, 256, 10, 1, None, 1 << 30, None, check=False) == -10
+    assert mx(10, 5, 3, 256, 10, 256, 256, 10, 1, 256, 8, None, check=False) == -11
+    assert gb.gb_solve_mixed_workspace_bytes(10, 11, 3) == 0
+    assert gb.gb_solve_mixed_workspace_bytes(1000, 10, 32) >= (
+        1000 * 1000 * 8 + max(gb.gb_solve_workspace_bytes(1000, 1000, 32), gb.gb_refine_syev_workspace_bytes(1000)))
     # the solve in three calls
     assert gb.gb_solve_stage_front(0, 1, 1, 1, 256, 1, 256, 1 << 30, None, check=False) == -1
     assert gb.gb_solve_stage_front(1, 100, 10, 100, 256, 100, 256, 1 << 30, None, check=False) == -3

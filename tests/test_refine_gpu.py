@@ -107,3 +107,26 @@ def test_refine_argument_errors(gb):
     wsb = gb.gb_refine_syev_workspace_bytes(2)
     ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     assert gb.gb_refine_syev_d(2, x, 2, x, x, 2, ws, wsb - 1, None, check=False) == -8
+
+
+@pytest.mark.parametrize("eta", [1e-7, 1e-5])
+def test_refine_from_perturbed_problem_with_tight_clusters(gb, eta):
+    """Start from the exact eigenvectors of A + eta P (||P||_2 ~ 1), the
+    state a low-precision solve with backward error eta leaves, on a
+    spectrum with runs of 8 eigenvalues 1e-6 apart: the eigenvectors of a
+    run are mixed at O(eta / 1e-6) and need the Rayleigh-Ritz treatment of
+    clusters.  Three steps reach the residual and orthogonality bounds and
+    the prescribed eigenvalues."""
+    n = 640
+    lam0 = inputs.gapped_uniform_spectrum(n, seed=31)
+    A = inputs.symmetric_with_spectrum(lam0, seed=32)
+    g = np.random.default_rng(33)
+    P = g.standard_normal((n, n))
+    P = (P + P.T) / np.sqrt(8 * n)
+    _, X0 = np.linalg.eigh(A + eta * P)
+    o0, r0 = errors(A, X0, np.linalg.eigvalsh(A + eta * P))
+    assert r0 > 1e-9
+    (l1, X1), (l2, X2), (l3, X3) = refine(gb, A, X0, 3)
+    o, r = errors(A, X3, np.diag(X3.T @ A @ X3))
+    assert o <= 50 * n * U and r <= 50 * n * U
+    assert np.abs(np.sort(l3) - lam0).max() / np.abs(lam0).max() <= 1e-13
