@@ -275,11 +275,10 @@ __device__ void ritz_jacobi(int k, double *B, double *Q, double *rot)
 // Per cluster (blocks stride over the cluster list): M = G_JJ^(-1/2) from
 // the Jacobi decomposition of G_JJ, H = M S_JJ M, Y = eigenvectors of H in
 // ascending order of the Ritz values; Vst rows of the cluster = columns of
-// M Y, lamr = the Ritz values.
+// M Y.
 __global__ void __launch_bounds__(128) ref_ritz(int n, const double *__restrict__ S, const double *__restrict__ G,
                                                 const int *__restrict__ clist, const int *__restrict__ ccount,
-                                                const int *__restrict__ clen, double *__restrict__ Vst,
-                                                double *__restrict__ lamr)
+                                                const int *__restrict__ clen, double *__restrict__ Vst)
 {
     constexpr int L = kClusterMax;
     extern __shared__ double sm[];
@@ -347,55 +346,80 @@ __global__ void __launch_bounds__(128) ref_ritz(int n, const double *__restrict_
             for (int c = 0; c < k; c++) acc += T[a + c * L] * Q[c + pc * L];
             Vst[(size_t)(b0 + jj) * L + a] = acc;
         }
-        for (int jj = threadIdx.x; jj < k; jj += blockDim.x) lamr[b0 + jj] = Gc[perm[jj] + perm[jj] * L];
     }
 }
 
-// lamr[j] = lam[j] for the columns outside clusters
-__global__ void ref_lamr_single(int n, const int *__restrict__ clen, const double *__restrict__ lam,
-                                double *__restrict__ lamr)
+// Copies the lower triangle of the n x n matrix M onto its upper triangle
+// (32 x 32 tiles through shared memory, both sides coalesced).
+__global__ void __launch_bounds__(256) ref_symmetrize(int n, double *__restrict__ M)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n && clen[j] == 1) lamr[j] = lam[j];
+    __shared__ double t[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;  // lower tile (bi, bj), bi >= bj
+    if (bi < bj) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int q = ty; q < 32; q += 8) {
+        const int r = bi * 32 + tx, c = bj * 32 + q;
+        if (r < n && c < n) t[q][tx] = M[r + (size_t)c * n];
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {  // M[c, r] = M[r, c] for r > c
+        const int c = bj * 32 + tx, r = bi * 32 + q;
+        if (r < n && c < n && r > c) M[c + (size_t)r * n] = t[tx][q];
+    }
 }
 
-// E in the rotated basis: s' = v_i^T S v_j and g' = v_i^T G v_j over the two
-// columns' clusters (v = 1 outside clusters), r' = delta_ij - g'; inside one
+// M[J, c] <- V_J^T M[J, c] for every cluster J and column c, in place: a
+// warp per (cluster, column), the column's k entries contiguous.
+__global__ void __launch_bounds__(256) ref_rotate_rows(int n, double *__restrict__ M, const int *__restrict__ clist,
+                                                       const int *__restrict__ ccount, const int *__restrict__ clen,
+                                                       const double *__restrict__ Vst)
+{
+    constexpr int L = kClusterMax;
+    extern __shared__ double sm[];
+    double *vs = sm, *buf = sm + L * L;  // buf: L doubles per warp
+    const int count = *ccount;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *old = buf + warp * L;
+    for (int ci = blockIdx.y; ci < count; ci += gridDim.y) {
+        const int b0 = clist[ci], k = clen[b0];
+        __syncthreads();
+        for (int t = threadIdx.x; t < k * L; t += blockDim.x) vs[t] = Vst[(size_t)b0 * L + t];
+        __syncthreads();
+        for (int c = blockIdx.x * 8 + warp; c < n; c += gridDim.x * 8) {
+            double *col = M + (size_t)c * n + b0;
+            for (int a = lane; a < k; a += 32) old[a] = col[a];
+            __syncwarp();
+            for (int jj = lane; jj < k; jj += 32) {
+                double acc = 0.0;
+                for (int a = 0; a < k; a++) acc += vs[jj * L + a] * old[a];
+                col[jj] = acc;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// lamr[j] = s'_jj / g'_jj in the rotated basis
+__global__ void ref_lamr(int n, const double *__restrict__ S, const double *__restrict__ G, double *__restrict__ lamr)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) lamr[j] = S[j + (size_t)j * n] / G[j + (size_t)j * n];
+}
+
+// E from the rotated S' = V^T S V and G' = V^T G V (full matrices; the
+// lower triangle is read for both halves), r' = delta_ij - g'; inside one
 // cluster, on the diagonal and for pairs within delta E = r' / 2, else
-// E = (s' + lambda_j r') / (lambda_j - lambda_i).  S and G are symmetric,
-// their lower triangles are read.
+// E = (s' + lambda_j r') / (lambda_j - lambda_i).
 __global__ void ref_correction(int n, const double *__restrict__ S, const double *__restrict__ G,
                                const double *__restrict__ lamr, const double *__restrict__ norms,
-                               const int *__restrict__ cbeg, const int *__restrict__ clen,
-                               const double *__restrict__ Vst, double *__restrict__ E)
+                               const int *__restrict__ cbeg, const int *__restrict__ clen, double *__restrict__ E)
 {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const int j = (int)(idx / n), i = (int)(idx - (long long)j * n);
-    const int ki = clen[i], kj = clen[j];
-    double s, g;
-    if (ki == 1 && kj == 1) {
-        s = sym_at(S, n, i, j);
-        g = sym_at(G, n, i, j);
-    } else {
-        const int bi = ki > 1 ? cbeg[i] : i, bj = kj > 1 ? cbeg[j] : j;
-        const double *vi = Vst + (size_t)i * kClusterMax, *vj = Vst + (size_t)j * kClusterMax;
-        s = 0.0;
-        g = 0.0;
-        for (int a = 0; a < ki; a++) {
-            const double ca = ki > 1 ? vi[a] : 1.0;
-            double ss = 0.0, gg = 0.0;
-            for (int b = 0; b < kj; b++) {
-                const double cb = kj > 1 ? vj[b] : 1.0;
-                ss += cb * sym_at(S, n, bi + a, bj + b);
-                gg += cb * sym_at(G, n, bi + a, bj + b);
-            }
-            s += ca * ss;
-            g += ca * gg;
-        }
-    }
-    const double r = (i == j ? 1.0 : 0.0) - g;
-    const bool same = ki > 1 && cbeg[i] == cbeg[j];
+    const double s = sym_at(S, n, i, j);
+    const double r = (i == j ? 1.0 : 0.0) - sym_at(G, n, i, j);
+    const bool same = clen[i] > 1 && cbeg[i] == cbeg[j];
     const double li = lamr[i], lj = lamr[j];
     double e;
     if (i != j && !same && fabs(li - lj) > ref_delta(norms)) e = (s + lj * r) / (lj - li);
@@ -403,8 +427,8 @@ __global__ void ref_correction(int n, const double *__restrict__ S, const double
     E[i + (size_t)j * n] = e;
 }
 
-// X_J <- X_J V_J for every cluster, in place (each thread a row; blocks
-// along y stride over the cluster list)
+// X_J <- X_J V_J for every cluster (columns J of X), in place (each thread
+// a row; blocks along y stride over the cluster list)
 __global__ void __launch_bounds__(128) ref_rotate_x(int n, double *__restrict__ X, long long ldx,
                                                     const int *__restrict__ clist, const int *__restrict__ ccount,
                                                     const int *__restrict__ clen, const double *__restrict__ Vst)
@@ -493,18 +517,31 @@ int gb_refine_syev_d(int n, const double *A, int lda, double *lam, double *X, in
     const size_t ritz_smem = (size_t)4 * L * L * 8 + 4 * 8 + L * 4;
     GB_RF(cudaFuncSetAttribute(gb::ref_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ritz_smem));
     gb::ref_ritz<<<std::max(1, std::min(n / 2, 152 * 4)), 128, ritz_smem, st>>>(n, w.S, w.G, w.clist, w.ccount,
-                                                                                w.clen, w.Vst, w.lamr);
+                                                                                w.clen, w.Vst);
     GB_RF(cudaGetLastError());
-    gb::ref_lamr_single<<<g1, 256, 0, st>>>(n, w.clen, w.lam, w.lamr);
+    // S' = V^T S V and G' = V^T G V in place: full matrices, then the
+    // columns and the rows of every cluster rotated
+    const unsigned tiles = (unsigned)((n + 31) / 32);
+    const size_t rot_smem = (size_t)L * L * 8;
+    const size_t rows_smem = (size_t)L * L * 8 + (size_t)8 * L * 8;
+    GB_RF(cudaFuncSetAttribute(gb::ref_rotate_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem));
+    GB_RF(cudaFuncSetAttribute(gb::ref_rotate_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem));
+    const dim3 gcols((unsigned)((n + 127) / 128), 32), grows((unsigned)std::min((n + 7) / 8, 152 * 2), 32);
+    for (double *M : {w.S, w.G}) {
+        gb::ref_symmetrize<<<dim3(tiles, tiles), 256, 0, st>>>(n, M);
+        GB_RF(cudaGetLastError());
+        gb::ref_rotate_x<<<gcols, 128, rot_smem, st>>>(n, M, n, w.clist, w.ccount, w.clen, w.Vst);
+        GB_RF(cudaGetLastError());
+        gb::ref_rotate_rows<<<grows, 256, rows_smem, st>>>(n, M, w.clist, w.ccount, w.clen, w.Vst);
+        GB_RF(cudaGetLastError());
+    }
+    gb::ref_lamr<<<g1, 256, 0, st>>>(n, w.S, w.G, w.lamr);
     GB_RF(cudaGetLastError());
     double *E = w.W;  // W is no longer needed
     gb::ref_correction<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, w.S, w.G, w.lamr, w.norms, w.cbeg,
-                                                                        w.clen, w.Vst, E);
+                                                                        w.clen, E);
     GB_RF(cudaGetLastError());
-    const size_t rot_smem = (size_t)L * L * 8;
-    GB_RF(cudaFuncSetAttribute(gb::ref_rotate_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rot_smem));
-    gb::ref_rotate_x<<<dim3((unsigned)((n + 127) / 128), 32), 128, rot_smem, st>>>(n, X, ldx, w.clist, w.ccount,
-                                                                                 w.clen, w.Vst);
+    gb::ref_rotate_x<<<gcols, 128, rot_smem, st>>>(n, X, ldx, w.clist, w.ccount, w.clen, w.Vst);
     GB_RF(cudaGetLastError());
     GB_RF(gb::slice_matrix(gb::kViewRow, n, n, X, ldx, w.slX, &xr, st));                          // rows of X V
     GB_RF(gb::slice_matrix(gb::kViewCol, n, n, E, n, w.slY, &ec, st));
