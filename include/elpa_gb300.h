@@ -590,6 +590,18 @@ size_t gb_dgemm_sliced_workspace_bytes(int m, int n, int k);
 int gb_dgemm_sliced(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
                     const double *B, int ldb, double beta, double *C, int ldc, void *workspace,
                     size_t ws_bytes, void *stream);
+/* The FP32 product of the mixed-precision solve, with gb_dgemm_sliced's
+ * arguments, statuses and workspace (gb_dgemm_sliced_workspace_bytes): each
+ * entry of op(A) and op(B) is rounded to FP32 and split exactly into three
+ * bf16 parts with their own exponents; the six part products of weight at
+ * least 2^-16 per k16 step run on mma.sync bf16 into one FP32 accumulator,
+ * folded into FP64 every 128 values of k.  Error: about (3 + 128) 2^-24
+ * |alpha| sum_k |op(A)_ik| |op(B)_kj| per entry at most (the FP32 rounding
+ * of the inputs, the dropped parts, the FP32 sums over 128 terms); typical
+ * errors are near 2^-24 of that sum. */
+int gb_dgemm_fp32split(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+                       const double *B, int ldb, double beta, double *C, int ldc, void *workspace,
+                       size_t ws_bytes, void *stream);
 size_t gb_dsymm_sliced_workspace_bytes(char side, int m, int n);
 int gb_dsymm_sliced(char side, int m, int n, double alpha, const double *S, int lds, const double *B, int ldb,
                     double beta, double *C, int ldc, void *workspace, size_t ws_bytes, void *stream);

@@ -29,7 +29,7 @@ from ._lib import (  # noqa: F401
     gb_refine_syev_workspace_bytes, gb_refine_syev_d, gb_solve_batched_staged_workspace_bytes,
     gb_solve_batched_staged_d, gb_solve_batched_staged_query, gb_solve_stage_table_bytes, gb_solve_stage_front,
     gb_solve_stage_chase_batched, gb_solve_stage_back, GB_SOLVE_FP32_PRODUCTS, GB_SOLVE_MIXED_MAX_STEPS,
-    gb_solve_mixed_workspace_bytes, gb_solve_mixed_d, gb_solve_mixed_query,
+    gb_solve_mixed_workspace_bytes, gb_solve_mixed_d, gb_solve_mixed_query, gb_dgemm_fp32split,
 )
 
 

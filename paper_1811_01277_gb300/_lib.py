@@ -46,7 +46,8 @@ EXPORTS = (
     "gb_band_to_tridi_workspace_bytes_z", "gb_band_to_tridi_z",
     "gb_solve_workspace_bytes_z", "gb_solve_z", "gb_solve_query_z",
     "gb_dgemm_workspace_bytes", "gb_dgemm", "gb_dsymm", "gb_dsyr2k", "gb_dsyrk",
-    "gb_dgemm_sliced_workspace_bytes", "gb_dgemm_sliced", "gb_dsymm_sliced_workspace_bytes", "gb_dsymm_sliced",
+    "gb_dgemm_sliced_workspace_bytes", "gb_dgemm_sliced", "gb_dgemm_fp32split", "gb_dsymm_sliced_workspace_bytes",
+    "gb_dsymm_sliced",
     "gb_dsyr2k_sliced_workspace_bytes", "gb_dsyr2k_sliced", "gb_dsyrk_sliced_workspace_bytes", "gb_dsyrk_sliced",
     "gb_zgemm_sliced_workspace_bytes", "gb_zgemm_sliced", "gb_zhemm_sliced_workspace_bytes", "gb_zhemm_sliced",
     "gb_zher2k_sliced_workspace_bytes", "gb_zher2k_sliced",
@@ -185,6 +186,8 @@ def load(path=None):
     L.gb_dgemm_sliced_workspace_bytes.argtypes = [i, i, i]; L.gb_dgemm_sliced_workspace_bytes.restype = sz
     L.gb_dgemm_sliced.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]
     L.gb_dgemm_sliced.restype = i
+    L.gb_dgemm_fp32split.argtypes = [ch, ch, i, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]
+    L.gb_dgemm_fp32split.restype = i
     L.gb_dsymm_sliced_workspace_bytes.argtypes = [ch, i, i]; L.gb_dsymm_sliced_workspace_bytes.restype = sz
     L.gb_dsymm_sliced.argtypes = [ch, i, i, dd, p, i, p, i, dd, p, i, p, sz, p]; L.gb_dsymm_sliced.restype = i
     L.gb_dsyr2k_sliced_workspace_bytes.argtypes = [i, i]; L.gb_dsyr2k_sliced_workspace_bytes.restype = sz
@@ -689,6 +692,15 @@ def gb_dgemm_sliced(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc
                                 _dp(workspace), ws_bytes, _stream(stream))
     if check and rc != GB_OK:
         raise GbError(rc, "gb_dgemm_sliced")
+    return rc
+
+
+def gb_dgemm_fp32split(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes,
+                       stream=None, check=True):
+    rc = load().gb_dgemm_fp32split(_c(transa), _c(transb), m, n, k, alpha, _dp(A), lda, _dp(B), ldb, beta, _dp(C),
+                                   ldc, _dp(workspace), ws_bytes, _stream(stream))
+    if check and rc != GB_OK:
+        raise GbError(rc, "gb_dgemm_fp32split")
     return rc
 
 

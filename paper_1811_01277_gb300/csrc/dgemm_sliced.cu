@@ -647,9 +647,9 @@ size_t gb_dgemm_sliced_workspace_bytes(int m, int n, int k)
     return gb::sliced_gemm_ws_bytes(m, n, k);
 }
 
-int gb_dgemm_sliced(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
-                    const double *B, int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes,
-                    void *stream)
+static int dgemm_sliced_digits(char transa, char transb, int m, int n, int k, double alpha, const double *A,
+                               int lda, const double *B, int ldb, double beta, double *C, int ldc, void *workspace,
+                               size_t ws_bytes, void *stream, int digits)
 {
     const bool ta = transa == 'T' || transa == 't', tb = transb == 'T' || transb == 't';
     if (!ta && transa != 'N' && transa != 'n') return -1;
@@ -667,8 +667,24 @@ int gb_dgemm_sliced(char transa, char transb, int m, int n, int k, double alpha,
     if (sl_bad_ws(workspace)) return -14;
     if (ws_bytes < gb::sliced_gemm_ws_bytes(m, n, k)) return -15;
     cudaError_t e = gb::sliced_dgemm(ta ? 'T' : 'N', tb ? 'T' : 'N', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
-                                     workspace, (cudaStream_t)stream);
+                                     workspace, (cudaStream_t)stream, digits);
     return e == cudaSuccess ? GB_OK : GB_ERR_CUDA;
+}
+
+int gb_dgemm_sliced(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes,
+                    void *stream)
+{
+    return dgemm_sliced_digits(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes,
+                               stream, gb::kSlices);
+}
+
+int gb_dgemm_fp32split(char transa, char transb, int m, int n, int k, double alpha, const double *A, int lda,
+                       const double *B, int ldb, double beta, double *C, int ldc, void *workspace, size_t ws_bytes,
+                       void *stream)
+{
+    return dgemm_sliced_digits(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace, ws_bytes,
+                               stream, gb::kSplitPlanes);
 }
 
 size_t gb_dsymm_sliced_workspace_bytes(char side, int m, int n)

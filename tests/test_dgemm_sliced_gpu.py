@@ -292,3 +292,49 @@ def test_zher2k_sliced_lower_triangle(gb, n, k):
     assert np.all((zerr(got, ref) <= zbound(XY, YX.conj().T, -1.0, 1.0, C0))[low])
     assert np.all(got.imag[np.diag_indices(n)] == 0.0)
     assert np.all(got[~low] == sentinel)
+
+
+def fp32_bound(opA, opB, alpha, beta, C0):
+    """|C - exact| for gb_dgemm_fp32split: (3 + 128) 2^-24 |alpha| sum_k
+    |a_ik| |b_kj| (inputs rounded to FP32, dropped parts, FP32 sums over 128
+    terms) plus the FP64 roundings of the result and of the beta C term."""
+    prod = np.abs(alpha) * (np.abs(opA) @ np.abs(opB))
+    return (3 + 128) * 2.0 ** -24 * prod + 4 * U * (prod + abs(beta) * np.abs(C0)) + 1e-300
+
+
+@pytest.mark.parametrize("m,n,k", [(37, 29, 13), (65, 63, 200), (513, 64, 1000), (64, 64, 5000), (130, 129, 0)])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+def test_dgemm_fp32split(gb, m, n, k, ta, tb):
+    """The FP32 product: within the FP32 bound of every entry, with entries
+    of very different magnitude in one row (per-entry exponents: a
+    Householder-like column with a unit leading entry and 1e-3 others, rows
+    scaled by 2^+-40), and clearly less accurate than the FP64 product (so
+    the FP32 path is the one that ran)."""
+    g = np.random.default_rng(m + 7 * n + 11 * k)
+    A = g.uniform(-1, 1, (k, m) if ta == "T" else (m, k))
+    B = g.uniform(-1, 1, (n, k) if tb == "T" else (k, n))
+    if k:
+        opB_view = B.T if tb == "T" else B
+        opB_view[1:, 0] *= 1e-3                       # column 0 of op(B): 1, then small entries
+        opA_view = A.T if ta == "T" else A
+        opA_view[: m // 3] *= 2.0 ** 40
+        opA_view[m // 3: 2 * m // 3] *= 2.0 ** -40
+    C0 = g.uniform(-1, 1, (m, n))
+    alpha, beta = 0.75, -1.25
+    Ad, lda = dev_cm(A, A.shape[0] + 3)
+    Bd, ldb = dev_cm(B, B.shape[0] + 1)
+    Cd, ldc = dev_cm(C0, m + 2)
+    w, wsb = ws(gb.gb_dgemm_sliced_workspace_bytes(m, n, k))
+    gb.gb_dgemm_fp32split(ta, tb, m, n, k, alpha, Ad, lda, Bd, ldb, beta, Cd, ldc, w, wsb,
+                          torch.cuda.current_stream())
+    opA = A.T if ta == "T" else A
+    opB = B.T if tb == "T" else B
+    ref = ref_hp(opA, opB, alpha, beta, C0)
+    got = host_cm(Cd, m, n)
+    e = err(got, ref)
+    assert np.all(e <= fp32_bound(opA, opB, alpha, beta, C0))
+    if k >= 100:
+        rel = e / (np.abs(alpha) * (np.abs(opA) @ np.abs(opB)))
+        assert np.median(rel) > 1e-12                  # FP32, not FP64
+        assert np.median(rel) < 2.0 ** -20
+    assert np.all(np.isnan(Cd.cpu().numpy()[:n, m:ldc]))
