@@ -342,16 +342,22 @@ size_t gb_solve_batched_workspace_bytes(int count, const int *n, const int *nev,
  * + ||A|| ||R||), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) where
  * |lambda_i - lambda_j| > delta and r_ij / 2 elsewhere, X <- X + X E.  The
  * error of X falls quadratically for eigenvalues separated by more than
- * delta; within a cluster the step refines the cluster's invariant subspace.
- * The products are sliced on the bf16 tensor cores (FP64-accurate; 6 n^3
- * flops a step: X^T X and X^T (A X) on their lower triangles); ||A||_2 is
- * taken as max |lambda_i|, the other norms bounded by Frobenius norms.
+ * delta.  Clusters (runs of neighbouring columns whose gap is within delta
+ * or whose first-order correction exceeds 1e-3; at most 64 columns) first
+ * get a Rayleigh-Ritz rotation X_J <- X_J G_JJ^(-1/2) Y_J (Y_J the
+ * eigenvectors of G_JJ^(-1/2) S_JJ G_JJ^(-1/2)), and E is taken in the
+ * rotated basis (r / 2 inside a cluster).  The products are sliced on the
+ * bf16 tensor cores (FP64-accurate; 6 n^3 flops a step: X^T X and
+ * X^T (A X) on their lower triangles); ||A||_2 is taken as max |lambda_i|,
+ * the other norms bounded by Frobenius norms.
  * Arguments (device pointers): 1 n >= 1; 2 A (n x n symmetric, lower
- * triangle read, lda); 3 lda >= n; 4 lam (n, out: the Rayleigh quotients
- * lambda_i of the input X); 5 X (n x n, ldx; in: approximate eigenvectors in
- * the columns, out: refined); 6 ldx >= n; 7 workspace (256-byte aligned);
- * 8 ws_bytes >= gb_refine_syev_workspace_bytes(n) (3 n^2 doubles plus two
- * n x n operands' digit planes, 16 n^2 bytes each).  Asynchronous on `stream`. */
+ * triangle read, lda); 3 lda >= n; 4 lam (n, out: the Rayleigh quotients of
+ * the input X after the clusters' rotation, i.e. Ritz values inside
+ * clusters); 5 X (n x n, ldx; in: approximate eigenvectors in the columns,
+ * ordered by eigenvalue, out: refined); 6 ldx >= n; 7 workspace (256-byte
+ * aligned); 8 ws_bytes >= gb_refine_syev_workspace_bytes(n) (3 n^2 doubles
+ * plus two n x n operands' digit planes, 16 n^2 bytes each, plus 512 n
+ * bytes of cluster rotations).  Asynchronous on `stream`. */
 size_t gb_refine_syev_workspace_bytes(int n);
 int gb_refine_syev_d(int n, const double *A, int lda, double *lam, double *X, int ldx, void *workspace,
                      size_t ws_bytes, void *stream);
