@@ -278,7 +278,8 @@ int gb_solve_query(const void *workspace, int n, int nev, int nbw, void *stream)
 /* Complex Hermitian two-stage solve: A (complex128, interleaved, lda) =
  * Z diag(ev) Z^H with real ev (nev, ascending) and complex Z (n x nev, ldz);
  * same arguments, workspace rule (gb_solve_workspace_bytes_z) and flags as
- * gb_solve_d (GB_SOLVE_RECORD_STAGES is ignored).  The large complex
+ * gb_solve_d (GB_SOLVE_RECORD_STAGES is ignored; GB_SOLVE_FP32_PRODUCTS is
+ * refused with -12: the mixed-precision solve is real only).  The large complex
  * products run sliced on the bf16 tensor cores (GB_SOLVE_DFMA_PRODUCTS:
  * on the FP64 FMA pipe), the b x b panel products in this library's complex
  * DFMA kernel, and the back-transformation on the tcgen05 tensor cores
