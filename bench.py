@@ -1092,6 +1092,60 @@ def run_stage_refine(args):
     return 0
 
 
+def run_stage_gemm_fp32(args):
+    """The FP32 split product (gb_dgemm_fp32split, the mixed solve's
+    reduction and back-transformation products) beside the FP64-accurate
+    sliced product (gb_dgemm_sliced) at the band->full shapes of an
+    n = 16384 solve and at a square size: TFLOP/s on 2 m n k flops (CUDA
+    events, best of --steps after --warmup) and each result's largest error
+    against torch's float64 product relative to sum_k |a| |b|."""
+    import torch
+    import paper_1811_01277_gb300 as gb
+    from paper_1811_01277_gb300 import build as gbuild
+    gbuild.build()
+    gb.load()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev).manual_seed(78)
+    q = args.gemm_n
+    shapes = [("T", "N", 64, 4096, 16384, "band->full Y^T Z"), ("N", "N", 16384, 4096, 64, "band->full Z -= Y S"),
+              ("N", "N", q, q, q, "square")]
+    rows = []
+    for ta, tb, m, n, k, what in shapes:
+        A = torch.rand(m if ta == "T" else k, k if ta == "T" else m, generator=g, device=dev,
+                       dtype=torch.float64) - 0.5                                  # column-major op(A) storage
+        B = torch.rand(n, k, generator=g, device=dev, dtype=torch.float64) - 0.5  # k x n column-major
+        lda = k if ta == "T" else m
+        wsb = gb.gb_dgemm_sliced_workspace_bytes(m, n, k)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        opA = A if ta == "T" else A.T              # m x k op(A)
+        ref = opA @ B.T
+        absref = opA.abs() @ B.T.abs()
+        row = {"shape": f"{ta}{tb} {m} x {n}, k = {k} ({what})"}
+        for name, fn in (("fp32split", gb.gb_dgemm_fp32split), ("fp64_sliced", gb.gb_dgemm_sliced)):
+            C = torch.zeros(n, m, device=dev, dtype=torch.float64)              # m x n column-major
+            call = lambda: fn(ta, tb, m, n, k, 1.0, A, lda, B, k, 0.0, C, m, ws, wsb, st)
+            for _ in range(max(args.warmup, 1)):
+                call()
+            best = None
+            for _ in range(max(args.steps, 1)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                call()
+                e1.record(st)
+                torch.cuda.synchronize(dev)
+                t = e0.elapsed_time(e1) / 1e3
+                best = t if best is None else min(best, t)
+            row[name] = {"ms": best * 1e3, "tflops": 2.0 * m * n * k / best / 1e12,
+                         "max_err_over_abs_sum": float(((C.T - ref).abs() / absref.clamp_min(1e-300)).max())}
+        rows.append(row)
+        del A, B, C, ws, ref, absref
+        torch.cuda.empty_cache()
+    print(json.dumps({"stage": "gemm_fp32", "metric": "FP32 split vs FP64-accurate sliced products, TFLOP/s",
+                      "cases": rows, "dtype": "f64 in/out", "data": "synthetic: uniform [-0.5, 0.5]"}))
+    return 0
+
+
 def run_stage_mixed(args):
     """The mixed-precision configuration: gb_solve_mixed_d (all eigenpairs
     with FP32 products in full -> band and band -> full, then FP64
@@ -1355,10 +1409,11 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="default stage: skip the solve and batched measurements that complete the metric")
     ap.add_argument("--stage", choices=["trans_ev", "trans_ev_z", "band_to_tridi", "solve", "batched", "serve", "gemm",
-                                        "refine", "mixed"],
+                                        "refine", "mixed", "gemm_fp32"],
                     default="trans_ev")
     ap.add_argument("--refine-n", type=int, default=8192, help="refine stage: n (all eigenpairs)")
     ap.add_argument("--mixed-n", type=int, default=8192, help="mixed stage: n")
+    ap.add_argument("--gemm-n", type=int, default=8192, help="gemm_fp32 stage: the square size")
     ap.add_argument("--mixed-nev", type=int, default=0, help="mixed stage: nev (0: n/2)")
     ap.add_argument("--mixed-steps", type=int, default=3, help="mixed stage: refinement steps")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -1399,6 +1454,8 @@ def main():
         return run_stage_refine(args)
     if args.stage == "mixed":
         return run_stage_mixed(args)
+    if args.stage == "gemm_fp32":
+        return run_stage_gemm_fp32(args)
     if args.stage == "trans_ev_z":
         return run_stage_trans_ev_z(args)
     if args.stage == "serve":
