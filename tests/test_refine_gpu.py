@@ -130,3 +130,23 @@ def test_refine_from_perturbed_problem_with_tight_clusters(gb, eta):
     o, r = errors(A, X3, np.diag(X3.T @ A @ X3))
     assert o <= 50 * n * U and r <= 50 * n * U
     assert np.abs(np.sort(l3) - lam0).max() / np.abs(lam0).max() <= 1e-13
+
+
+def test_refine_step_matches_the_oracle_step(gb):
+    """One step of gb_refine_syev_d against the oracle's step
+    (oracle/refine.py) from the same basis, on a spectrum with gaps near 2/n
+    where no pair is clustered: X' element by element and lambda.  The two
+    differ only by the rounding of the residual products (u sqrt(n) / gap
+    in E), five orders below the correction itself."""
+    from oracle.refine import ogita_aishima_step
+    n = 512
+    g = np.random.default_rng(51)
+    lam0 = -1.0 + 2.0 * (np.arange(n) + 0.5 + 0.2 * g.uniform(-1, 1, n)) / n
+    A = inputs.symmetric_with_spectrum(lam0, seed=52)
+    _, V = np.linalg.eigh(A)
+    X0 = V + 1e-6 * g.standard_normal((n, n)) / np.sqrt(n)
+    X_or, l_or = ogita_aishima_step(A, X0)
+    (l_gpu, X_gpu), = refine(gb, A, X0, 1)
+    assert np.abs(X_or - X0).max() > 1e-8                  # the correction is real
+    assert np.abs(X_gpu - X_or).max() <= 1e-11
+    assert np.abs(l_gpu - l_or).max() <= 1e-14
